@@ -1,0 +1,185 @@
+"""Pins of the oracle's whole scheme (Secs. 2-3 of the paper).
+
+  * Free stream: a constant state stays constant through WENO, predictor, fluxes and update,
+    on a uniform grid and on an AMR grid with local time stepping.
+  * Conservation (Eq. eq:finite_vol with the memory variables of Eq. eqn.memory.sum): on a
+    periodic domain the totals sum(vol * u) over active cells are conserved to round-off
+    across refinement levels with local time stepping.
+  * Local time stepping (Eq. eqn.update.criterion): a level-0 grid that is refined
+    everywhere (l_max = 1) advanced by dt_0 equals a uniform r-times finer grid advanced
+    r times by dt_0 / r.
+  * Projection and averaging (Sec. 3.1.3, Eq. eqn.average): the average of the r^d child
+    projections of a mother polynomial is the mother's average.
+  * Design order of accuracy on the isentropic vortex of Sec. 4.1 with its exact solution
+    (advection by (1,1)): observed L2 order of rho close to M+1.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from tests.polyref import gl01
+
+VORTEX = [5.0, 5.0, 5.0, 1.0, 1.0, 1.0, 1.0]
+
+
+def vortex_prim(x, y, t, gamma=1.4, eps=5.0):
+    # exact solution: the initial vortex advected with velocity (1, 1), period 10
+    xc = (x - t - 5.0 + 5.0) % 10.0 - 5.0
+    yc = (y - t - 5.0 + 5.0) % 10.0 - 5.0
+    r2 = xc * xc + yc * yc
+    dT = -eps * eps * (gamma - 1) / (8 * gamma * math.pi ** 2) * np.exp(1 - r2)
+    rho = (1 + dT) ** (1 / (gamma - 1))
+    return rho
+
+
+def exact_rho_averages(n, L, t, nq=8):
+    x, w = gl01(nq)
+    h = L / n
+    out = np.zeros((n, n))
+    for j in range(n):
+        for i in range(n):
+            X = (i + x[:, None]) * h
+            Y = (j + x[None, :]) * h
+            out[j, i] = np.sum(w[:, None] * w[None, :] * vortex_prim(X, Y, t))
+    return out
+
+
+def test_free_stream_uniform_and_amr():
+    q = [1.1, 0.4, -0.3, 0.9]
+    for lmax in (0, 1):
+        cfg = oracle.make_cfg(dim=2, M=3, n=(9, 9, 1), lo=(0, 0, 0), hi=(1, 1, 1), lmax=lmax, r=3,
+                              auto_regrid=0)
+        o = oracle.Oracle(cfg)
+        o.set_initial(oracle.IC_CONST, q, nrefine=0)
+        if lmax:
+            _, u = o.cells()
+            flags = np.zeros(len(u), dtype=np.int8)
+            flags[[10, 11, 40]] = 1
+            o.regrid_with_flags(flags, init_mode=1)
+        meta0, u0 = o.cells()
+        for _ in range(2):
+            o.advance_dt(0.5 * o.compute_dt())
+        meta1, u1 = o.cells()
+        assert np.array_equal(meta0, meta1)
+        act = meta1[:, 1] <= 0
+        cons = np.array([1.1, 1.1 * 0.4, 1.1 * -0.3, 0.9 / 0.4 + 0.5 * 1.1 * (0.16 + 0.09)])
+        assert np.allclose(u1[act], cons, rtol=1e-13, atol=1e-13)
+
+
+@pytest.mark.parametrize("M,lmax", [(2, 1), (3, 2)])
+def test_conservation_amr_lts_periodic(M, lmax):
+    cfg = oracle.make_cfg(dim=2, M=M, n=(6, 6, 1), lo=(0, 0, 0), hi=(10, 10, 1), lmax=lmax, r=3,
+                          chi_ref=0.05, chi_rec=0.01, auto_regrid=1)
+    o = oracle.Oracle(cfg)
+    o.set_initial(oracle.IC_VORTEX, VORTEX)
+    n, per, act = o.counts()
+    assert all(a > 0 for a in act), "every level must hold active cells for this test"
+    tot0 = o.totals()
+    for _ in range(2):
+        rc, _ = o.step()
+        assert rc == 0
+    tot1 = o.totals()
+    assert np.allclose(tot1, tot0, rtol=1e-13, atol=1e-13 * np.abs(tot0).max())
+
+
+@pytest.mark.parametrize("M", [2, 3])
+def test_fully_refined_equals_uniform_fine(M):
+    n, r = 6, 3
+    params = [1.0, 0.5, -0.2, 1.0, 2, 0, 1, 1, 0, 0.1, 0.3, 3, 2, 1, 0, 0.05, 1.1]
+    a = oracle.Oracle(oracle.make_cfg(dim=2, M=M, n=(n, n, 1), lmax=1, r=r, auto_regrid=0))
+    a.set_initial(oracle.IC_FOURIER, params, nrefine=0)
+    _, u = a.cells()
+    a.regrid_with_flags(np.ones(len(u), dtype=np.int8), init_mode=1)
+    b = oracle.Oracle(oracle.make_cfg(dim=2, M=M, n=(n * r, n * r, 1), lmax=0))
+    b.set_initial(oracle.IC_FOURIER, params, nrefine=0)
+    meta, ua = a.cells()
+    fine = meta[:, 0] == 1
+    assert np.all(meta[fine, 1] == 0) and np.all(meta[~fine, 1] == -1)
+    _, ub = b.cells()
+    assert np.allclose(ua[fine], ub, rtol=0, atol=1e-15)
+    dt0 = 0.5 * a.compute_dt()
+    a.advance_dt(dt0)
+    for _ in range(r):
+        b.advance_dt(dt0 / r)
+    meta, ua = a.cells()
+    _, ub = b.cells()
+    assert np.allclose(ua[fine], ub, rtol=1e-14, atol=1e-14)
+
+
+@pytest.mark.parametrize("d", [2, 3])
+def test_projection_then_average_is_identity(d):
+    M, r = 3 if d == 2 else 2, 3
+    o = oracle.Oracle(oracle.make_cfg(dim=d, M=M, n=(4, 4, 4), r=r))
+    rng = np.random.default_rng(12)
+    wh = rng.normal(size=o.V * o.nsp)
+    qh = rng.normal(size=o.V * o.nst)
+    mother_avg_sp = np.zeros(o.V)
+    x, w = gl01(M + 1)
+    # mother's own averages by Gauss quadrature of the nodal polynomial = weighted nodal sum
+    W = np.ones(1)
+    for _a in range(d):
+        W = np.kron(w, W)
+    mother_avg_sp = wh.reshape(o.V, o.nsp) @ W
+    kids = []
+    kids_st = []
+    tau = 0.37
+    for c in np.ndindex(*([r] * d)):
+        ch = list(c[::-1])
+        kids.append(o.project_sp(wh, ch))
+        kids_st.append(o.project_st(qh, ch, tau))
+    assert np.allclose(np.mean(kids, axis=0), mother_avg_sp, rtol=1e-13, atol=1e-13)
+    # space-time: the mother's average at tau, from its own nodal dofs
+    x, _ = gl01(M + 1)
+    from tests.polyref import lagrange_values
+    bt = lagrange_values(x, [tau])[0]
+    q = qh.reshape(o.V, M + 1, o.nsp)        # [v][s][spatial]
+    avg_tau = np.einsum("vsp,s,p->v", q, bt, W)
+    assert np.allclose(np.mean(kids_st, axis=0), avg_tau, rtol=1e-13, atol=1e-13)
+
+
+def _vortex_l2(M, n, t_end):
+    cfg = oracle.make_cfg(dim=2, M=M, n=(n, n, 1), lo=(0, 0, 0), hi=(10, 10, 1))
+    o = oracle.Oracle(cfg, threads=4)
+    o.set_initial(oracle.IC_VORTEX, VORTEX)
+    while o.t < t_end:
+        rc, _ = o.step(t_end)
+        assert rc == 0
+    meta, u = o.cells()
+    rho = u[:, 0].reshape(n, n)
+    ex = exact_rho_averages(n, 10.0, t_end)
+    return math.sqrt(np.sum((rho - ex) ** 2) * (10.0 / n) ** 2)
+
+
+@pytest.mark.parametrize("M,grids,lo_order", [(2, (48, 96), 2.6), (3, (20, 40), 3.2)])
+def test_vortex_design_order(M, grids, lo_order):
+    e = [_vortex_l2(M, n, 1.0) for n in grids]
+    order = math.log(e[0] / e[1]) / math.log(grids[1] / grids[0])
+    assert order > lo_order, (e, order)
+
+
+def _linadv_err(M, n, t_end):
+    cfg = oracle.make_cfg(dim=2, pde=oracle.PDE_LINADV, M=M, n=(n, n, 1), lo=(0, 0, 0), hi=(1, 1, 1),
+                          adv=(1.0, 1.0, 0.0))
+    o = oracle.Oracle(cfg, threads=4)
+    o.set_initial(oracle.IC_FOURIER, [0.0, 1, 0, 1, 1, 0, 1.0, 0.0])
+    while o.t < t_end:
+        o.step(t_end)
+    _, u = o.cells()
+    x, w = gl01(8)
+    h = 1.0 / n
+    ex = np.zeros((n, n))
+    for j in range(n):
+        for i in range(n):
+            X = (i + x[:, None]) * h - t_end
+            Y = (j + x[None, :]) * h - t_end
+            ex[j, i] = np.sum(w[:, None] * w[None, :] * np.sin(2 * np.pi * (X + Y)))
+    return math.sqrt(np.mean((u[:, 0].reshape(n, n) - ex) ** 2))
+
+
+@pytest.mark.parametrize("M,lo_order", [(2, 2.85), (3, 3.8)])
+def test_linear_advection_design_order(M, lo_order):
+    e = [_linadv_err(M, n, 0.5) for n in (10, 20, 40)]
+    orders = [math.log(e[i] / e[i + 1], 2) for i in range(2)]
+    assert min(orders) > lo_order, (e, orders)
