@@ -632,14 +632,19 @@ static void ic_average(const osolver *S, int lv, const int *ijk, double *out) {
 
 /* One-dimensional WENO: v[0..2M] are the values at offsets -M..M (cell averages, or
  * degrees of freedom of a previous sweep); out[0..M] the nodal coefficients of the
- * reconstruction polynomial (Eqs. eqn.rec.x, eqn.weno, eqn.omegas, eqn.sigmas). */
+ * reconstruction polynomial (Eqs. eqn.rec.x, eqn.weno, eqn.omegas, eqn.sigmas).
+ * Reading: the stencil polynomials and the oscillation indicators are evaluated on the
+ * differences v - v[M] from the cell's own value.  This is exact (every stencil reproduces
+ * constants, and Sigma annihilates them because it only involves derivatives), and it keeps
+ * the rounding of a large constant part out of sigma, which the exponent r = 8 would
+ * otherwise amplify into the weights. */
 static void weno1d(const tables *T, const double *v, double *out) {
   int N = T->N, M = T->M;
-  double ws[4][MAXN], om[4], sum = 0.0;
+  double ws[4][MAXN], om[4], sum = 0.0, c = v[M];
   for (int s = 0; s < T->Ns; s++) {
     for (int p = 0; p < N; p++) {
       double a = 0.0;
-      for (int e = 0; e < N; e++) a += T->Ainv[s][p][e] * v[M - T->SL[s] + e];
+      for (int e = 0; e < N; e++) a += T->Ainv[s][p][e] * (v[M - T->SL[s] + e] - c);
       ws[s][p] = a;
     }
     double sig = 0.0;
@@ -655,6 +660,7 @@ static void weno1d(const tables *T, const double *v, double *out) {
     double w = om[s] / sum;
     for (int p = 0; p < N; p++) out[p] += w * ws[s][p];
   }
+  for (int p = 0; p < N; p++) out[p] += c;
 }
 
 /* value at level lv of the cell at integer coordinates c[] (through the BCs) */
