@@ -386,7 +386,13 @@ static double max_speed(const phys *P, const double *q, int n) {
   if (P->pde == PDE_LINADV) return fabs(P->adv[n]);
   double rho = q[0], p = pressure(P, q);
   double vn = q[1 + n] / rho;
-  if (P->pde == PDE_EULER) return fabs(vn) + sqrt(P->gamma * p / rho);
+  if (P->pde == PDE_EULER) {
+    /* eigenvalues v_n, v_n +- c with c^2 = gamma p / rho; a state extrapolated to a face can
+     * have c^2 < 0, where v_n +- c are complex and the largest modulus is sqrt(v_n^2 - c^2)
+     * (reading of Eq. eqn.rusanov: the spectral radius, taken literally) */
+    double c2 = P->gamma * p / rho;
+    return c2 >= 0.0 ? fabs(vn) + sqrt(c2) : sqrt(vn * vn - c2);
+  }
   double a2 = P->gamma * p / rho;
   double B2 = q[5] * q[5] + q[6] * q[6] + q[7] * q[7];
   double b2 = B2 / rho, bn2 = q[5 + n] * q[5 + n] / rho;
@@ -1478,6 +1484,7 @@ int orc_advance_dt(void *h, double dt0) {
 /* one level-0 step with CFL dt clipped at t_end, followed by a regrid if auto_regrid */
 int orc_step(void *h, double t_end, double *dt_out) {
   osolver *S = h;
+  if (!(t_end > S->t)) { seterr("t_end is not after t"); return -1; }
   double dt = compute_dt(S);
   int clipped = 0;
   if (S->t + dt >= t_end) { dt = t_end - S->t; clipped = 1; }
