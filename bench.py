@@ -1,0 +1,313 @@
+#!/usr/bin/env python
+"""Benchmark: ADER-WENO cell-updates/s on the 2D AMR explosion workload.
+
+Workload (one "step" = one complete solve): 2D Euler, gamma 1.4, FP64, ADER-WENO M=3 (fourth
+order), base grid 100x100 on [-1,1]^2, refinement factor 3, l_max = 2, local time stepping,
+Loehner density indicator, cylindrical explosion (rho=1, p=1 inside r=0.5; rho=0.125, p=0.1
+outside), transmissive boundaries, Rusanov flux, CFL 0.6, from t=0 to t=0.25.  Each solve
+re-initialises the mesh on the device (aw_reset + initial condition + l_max refinement passes)
+and advances to t_end with a regrid after every level-0 step.
+
+value   = cell updates (active cell advanced by its level's dt) per second, device-resident
+e2e     = the same through the C ABI with host buffers: level-0 averages uploaded from pinned
+          host memory, data-driven refinement, solve, all cell averages read back
+roofline= the dominant kernel's algorithmic FP64 FLOP rate against the FP64 peak
+cpu_baseline = the FP64 CPU oracle on the host cores, on the first level-0 step of the same solve
+
+Multi-GPU: one independent replica per rank (the path has no exchange step), weak scaling.
+"""
+import argparse
+import ctypes as C
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ADER-WENO cell-updates/s vs roofline; batched solves/s + p99 latency vs plain"
+UNIT = "cell-updates/s"
+WORKLOAD = ("2D Euler FP64, ADER-WENO M=3, base 100x100 on [-1,1]^2, r=3, l_max=2, local time stepping, "
+            "cylindrical explosion (R=0.5; rho,p = 1,1 inside; 0.125,0.1 outside), transmissive, "
+            "Rusanov, CFL 0.6, t_end=0.25")
+CFG = dict(dim=2, M=3, n=(100, 100, 1), lo=(-1.0, -1.0, 0.0), hi=(1.0, 1.0, 1.0), r=3, lmax=2, gamma=1.4,
+           chi_ref=0.2, chi_rec=0.1, cfl=0.6)
+T_END = 0.25
+SM_COUNT = 152
+FP64_FMA_PER_CLK_PER_SM = 2      # sm_103a: measured 0.598 T DFMA/s at ~1.97 GHz on 152 SMs
+SM_MAX_MHZ = 2070.0
+FP64_PEAK_TFLOPS = 2 * FP64_FMA_PER_CLK_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12   # 1.2586
+
+
+def predictor_flops_per_cell(D, M, V, P, flux_flops):
+    """Algorithmic FP64 FLOPs of the space-time predictor per cell update in its factorised form
+    (FMA = 2): flux evaluations at the nodes, spatial derivative contractions, time contraction;
+    the first Picard iteration starts from a state constant in time."""
+    N = M + 1
+    nsp, nst = N ** D, N ** (D + 1)
+    first = nsp * flux_flops + nsp * V * D * N * 2 + nst * V * 2
+    later = nst * flux_flops + nst * V * D * N * 2 + nst * V * N * 2
+    return first + (P - 1) * later
+
+
+# FP64 operations of the Euler fluxes in all D directions at one state (1/rho, velocities,
+# kinetic energy, pressure, E+p, then D*(D+2) components)
+EULER_FLUX_FLOPS = {2: 18, 3: 25}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p:
+            self.p.terminate()
+            self.p.wait()
+
+    def summary(self):
+        self.f.seek(0)
+        rows = [ln.strip().split(", ") for ln in self.f.read().splitlines() if ln.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def combine_replicas(updates, ms, world_size, max_reduce):
+    """Whole-job throughput of independent replicas: every rank did `updates` cell updates in
+    `ms`; the job time is the slowest rank's."""
+    job_ms = max_reduce(ms)
+    return world_size * updates / (job_ms * 1e-3), job_ms
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_reference(args):
+    """The FP64 CPU oracle as it stands, timed on the host cores; each step = the first level-0
+    step of the workload (setup untimed)."""
+    import oracle
+    import aw_inputs
+    threads = os.cpu_count() or 1
+    times, updates = [], []
+    for i in range(args.warmup + args.steps):
+        o = oracle.Oracle(oracle.make_cfg(dim=2, M=3, n=(100, 100, 1), lo=CFG["lo"], hi=CFG["hi"],
+                                          bc=oracle.BC_TRANSMISSIVE, r=3, lmax=2, cfl=0.6, auto_regrid=1),
+                          threads=threads)
+        o.set_initial(oracle.IC_EXPLOSION, aw_inputs.EXPLOSION)
+        u0 = o.updates()[0]
+        t0 = time.perf_counter()
+        o.step(T_END)
+        el = time.perf_counter() - t0
+        if i >= args.warmup:
+            times.append(el)
+            updates.append(o.updates()[0] - u0)
+        del o
+    value = sum(updates) / sum(times)
+    sample = "first level-0 step (all 3 levels, LTS, regrid) of the workload, per step"
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "n/a (CPU)", "parallelism": "none"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def cpu_baseline_sample():
+    import oracle
+    import aw_inputs
+    threads = os.cpu_count() or 1
+    o = oracle.Oracle(oracle.make_cfg(dim=2, M=3, n=(100, 100, 1), lo=CFG["lo"], hi=CFG["hi"],
+                                      bc=oracle.BC_TRANSMISSIVE, r=3, lmax=2, cfl=0.6, auto_regrid=1),
+                      threads=threads)
+    o.set_initial(oracle.IC_EXPLOSION, aw_inputs.EXPLOSION)
+    u0 = o.updates()[0]
+    t0 = time.perf_counter()
+    o.step(T_END)
+    el = time.perf_counter() - t0
+    n = o.updates()[0] - u0
+    return {"value": n / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"first level-0 step of the workload ({n} cell updates, {el:.1f} s)"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        print(json.dumps(run_reference(args)))
+        return 0
+
+    import numpy as np
+    import torch
+    import aw_inputs
+    import paper_1212_3585_gb300 as pg
+    torch.cuda.set_device(local)
+    pgroup = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        pgroup = dist
+
+    def barrier():
+        if pgroup:
+            pgroup.barrier()
+
+    stream = torch.cuda.current_stream()
+    cfg = pg.make_config(bc=pg.AW_BC_TRANSMISSIVE, auto_regrid=1, **CFG)
+    s = pg.Solver(cfg, stream.cuda_stream)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > 129 MB of L2
+
+    def solve():
+        s.reset()
+        s.set_initial(pg.AW_IC_EXPLOSION, aw_inputs.EXPLOSION, -1)
+        st = s.advance_to(T_END)
+        return st.cell_updates, st.level0_steps
+
+    for _ in range(args.warmup):
+        solve()
+        flush.fill_(1)
+    torch.cuda.synchronize()
+    s.set_profiling(True)
+    s.kernel_times()
+    launches0 = s.kernel_launches()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    upd, l0 = 0, 0
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            evs[i][0].record(stream)
+            u, n0 = solve()
+            evs[i][1].record(stream)
+            upd += u
+            l0 += n0
+            flush.fill_(1)
+        torch.cuda.synchronize()
+    barrier()
+    ms = sum(a.elapsed_time(b) for a, b in evs)
+    launches = s.kernel_launches() - launches0
+    kms, kn = s.kernel_times()
+    s.set_profiling(False)
+    def max_reduce(x):
+        if not pgroup:
+            return x
+        t = torch.tensor([x], device="cuda", dtype=torch.float64)
+        pgroup.all_reduce(t, op=pgroup.ReduceOp.MAX)
+        return float(t.item())
+
+    value, ms = combine_replicas(upd, ms, ws, max_reduce)
+
+    # dominant kernel and its algorithmic FP64 rate
+    names = ["weno", "predictor", "face_flux", "update", "projection"]
+    dom = int(np.argmax(kms))
+    upd_per_step = upd / args.steps
+    V = 4
+    pf = predictor_flops_per_cell(2, 3, V, 4, EULER_FLUX_FLOPS[2])
+    roofline = None
+    if names[dom] == "predictor" and kn[dom] > 0:
+        ach = pf * upd / (kms[dom] * 1e-3) / 1e12
+        roofline = {"bound": "alu", "kernel": "k_predict<2,3,Euler>", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                    "flops_per_cell_update": pf, "launches": int(kn[dom]),
+                    "avg_launch_ms": float(kms[dom] / kn[dom]),
+                    "peak_note": "FP64 FMA pipe: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (derived; 1.195 measured)"}
+    else:
+        roofline = {"bound": "alu", "kernel": names[dom], "achieved": None, "peak": FP64_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": None, "traffic": None}
+    kernel_share = {n: float(kms[i] / max(kms.sum(), 1e-9)) for i, n in enumerate(names)}
+
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cell_updates_per_solve": upd_per_step, "level0_steps_per_solve": l0 / args.steps,
+                   "l2": "flushed between timed solves (256 MB write)", "parallelism": f"replicas x{ws}"},
+        "roofline": roofline, "kernel_time_share": kernel_share, "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+    }
+
+    if not args.no_e2e:
+        # end to end through the C ABI with host buffers
+        s.reset()
+        s.set_initial(pg.AW_IC_EXPLOSION, aw_inputs.EXPLOSION, 0)
+        _, u0 = s.cells()
+        h_u0 = torch.from_numpy(u0).pin_memory()
+        n_out = 0
+        t_e2e, upd_e2e = 0.0, 0
+        ncell_out = 0
+        for i in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.reset()
+            s.set_cell_averages(h_u0.numpy())
+            for _ in range(cfg.lmax):
+                s.regrid(0)
+            st = s.advance_to(T_END)
+            meta, u = s.cells()
+            el = time.perf_counter() - t0
+            if i >= args.warmup:
+                t_e2e += el
+                upd_e2e += st.cell_updates
+                ncell_out = len(u)
+        e2e_val = ws * upd_e2e / t_e2e
+        out["e2e"] = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(u0.nbytes),
+                      "d2h_bytes_per_step": int(ncell_out * (V * 8 + 20)),
+                      "note": "level-0 averages uploaded from pinned host memory, data-driven refinement "
+                              "(projection mode), solve, every cell read back"}
+    if rank == 0:
+        if not args.no_cpu_baseline and ws == 1:
+            out["cpu_baseline"] = cpu_baseline_sample()
+        print(json.dumps(out))
+    s.close()
+    if pgroup:
+        pgroup.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

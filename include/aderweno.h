@@ -1,0 +1,207 @@
+/*
+ * aderweno.h -- C ABI of the GB300 (sm_103a) ADER-WENO finite volume solver on space-time
+ * adaptive Cartesian meshes (Dumbser, Zanotti, Hidalgo, Balsara, arXiv:1212.3585).
+ *
+ * The library advances the cell averages of a hyperbolic conservation law
+ * (Sec. 2.1, Eq. eq:governingPDE, source zero) on a cell-by-cell AMR mesh (Sec. 3.1) with
+ * time-accurate local time stepping (Sec. 3.1.2), one level-0 step at a time.  Every step
+ * of the method runs in CUDA kernels on the caller's stream:
+ *   - dimension-by-dimension WENO reconstruction (Sec. 2.2),
+ *   - element-local space-time DG predictor by Picard iteration (Sec. 2.3, Eq. eqn.stdg.final),
+ *   - Rusanov fluxes integrated over space-time faces (Eqs. flux:F..flux:H, eqn.rusanov),
+ *   - the one-step finite volume update (Eq. eq:finite_vol) with memory variables at
+ *     coarse/fine faces (Eq. eqn.memory.sum),
+ *   - projection (Sec. 3.1.3) and averaging (Eq. eqn.average) of virtual cells,
+ *   - the refinement indicator (Eq. eqn.indicator) and the regrid under rules 1-7 of Sec. 3.1.
+ *
+ * Conventions
+ *   - Every call returns an int status: AW_OK (0) or a negative AW_E* code; aw_last_error()
+ *     returns a message for the last failing call on this thread.
+ *   - The library owns every device buffer.  The caller owns every host pointer it passes;
+ *     host buffers are only read/written during the call.
+ *   - A call given a capacity smaller than needed returns AW_EINVAL and writes the needed
+ *     size through its size pointer.
+ *   - `stream` is a cudaStream_t passed as an integer (0 = the legacy default stream).  All
+ *     device work of a solver is ordered on that stream; calls that return host data
+ *     synchronise it.
+ *   - Canonical cell order: level ascending, then k, j, i ascending (z slowest).
+ *   - Cell status (Sec. 3.1 rule 2): 0 active, 1 virtual child, -1 virtual mother.
+ *   - Conserved variables: Euler (rho, rho u, rho v[, rho w], E) with 2+d components;
+ *     MHD-GLM (rho, rho u, rho v, rho w, E, Bx, By, Bz, psi) in rationalised units;
+ *     linear advection (u).
+ */
+#ifndef ADERWENO_H
+#define ADERWENO_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AW_OK 0
+#define AW_EINVAL (-1)       /* bad argument, size mismatch or capacity too small */
+#define AW_ENOMEM (-2)       /* device allocation failed */
+#define AW_ECUDA (-3)        /* a CUDA call failed (message has the CUDA error string) */
+#define AW_ENONPHYSICAL (-4) /* rho <= 0, p <= 0 or NaN appeared in an updated cell average */
+#define AW_ETIMEOUT (-5)     /* a bounded device-side wait gave up */
+#define AW_ESTATE (-6)       /* call not valid in the solver's current state */
+
+#define AW_PDE_EULER 0
+#define AW_PDE_MHD_GLM 1
+#define AW_PDE_LINADV 2
+
+#define AW_BC_PERIODIC 0
+#define AW_BC_TRANSMISSIVE 1
+
+#define AW_FLUX_RUSANOV 0
+
+/* initial conditions of Sec. 4; parameter layouts:
+ *  AW_IC_CONST:     primitive state (Euler: rho, v_1..v_d, p; MHD: rho, vx, vy, vz, p, Bx, By,
+ *                   Bz, psi; linear advection: u)
+ *  AW_IC_VORTEX:    eps, xc, yc, rho0, u0, v0, p0 (isentropic vortex of Sec. 4.1)
+ *  AW_IC_EXPLOSION: R, rho_in, p_in, rho_out, p_out (explosion problems of Sec. 4.1)
+ *  AW_IC_OT:        none (Orszag-Tang data of Sec. 4.2, rationalised units)
+ *  AW_IC_RP4:       x0, y0, then (rho, u, v, p) of quadrants 1..4 (x>x0,y>y0; x<x0,y>y0;
+ *                   x<x0,y<y0; x>x0,y<y0), the 2D Riemann problems of Sec. 4.1
+ *  AW_IC_FOURIER:   base primitive state (V values), nmodes, then per mode
+ *                   (var, kx, ky, kz, amp, phase) adding amp*sin(2 pi k.(x-lo)/(hi-lo) + phase)
+ * Cell averages are taken with the (M+1)^d-point tensor Gauss rule. */
+#define AW_IC_CONST 0
+#define AW_IC_VORTEX 1
+#define AW_IC_EXPLOSION 2
+#define AW_IC_OT 3
+#define AW_IC_RP4 4
+#define AW_IC_FOURIER 5
+
+/* aw_read_internal selectors */
+#define AW_INTERNAL_WENO 0      /* WENO dofs of active cells of a level: V*N^d each, [v][p + N q + N^2 r] */
+#define AW_INTERNAL_PREDICTOR 1 /* predictor dofs of active cells: V*N^(d+1) each, [v][spatial + N^d s] */
+#define AW_INTERNAL_CHI 2       /* indicator of every existing cell of a level (0 where not computed) */
+#define AW_INTERNAL_FLUX 3      /* face fluxes of active cells from the last update: 2d*V each, [axis][side][v] */
+
+typedef struct aw_config {
+  int32_t dim;          /* 2 or 3 */
+  int32_t pde;          /* AW_PDE_* */
+  int32_t M;            /* polynomial degree of the reconstruction, 2 or 3 (order M+1) */
+  int32_t nx, ny, nz;   /* level-0 cells per direction (nz ignored when dim == 2) */
+  double gamma;         /* ratio of specific heats */
+  double c_h;           /* GLM cleaning speed (MHD) */
+  double lo[3], hi[3];  /* domain box */
+  int32_t bc[6];        /* AW_BC_* for faces x-, x+, y-, y+, z-, z+; periodic must pair up */
+  int32_t refine_factor;/* r of Eq. refine-factor; r >= max(2, M) when lmax > 0 */
+  int32_t lmax;         /* finest level, 0..4 */
+  double chi_ref;       /* refine when chi > chi_ref (Sec. 3.1.1) */
+  double chi_rec;       /* recoarsen when chi < chi_rec */
+  double eps_ind;       /* filter epsilon of Eq. eqn.indicator */
+  double cfl;           /* CFL number */
+  int32_t picard_iters; /* Picard iterations of the predictor, 0 -> M+1 */
+  int32_t flux;         /* AW_FLUX_RUSANOV */
+  int32_t auto_regrid;  /* 1: regrid after every level-0 step (aw_step / aw_advance_to) */
+  int32_t reserved;
+  double adv[3];        /* advection velocity of AW_PDE_LINADV */
+} aw_config;
+
+typedef struct aw_stats {
+  int64_t level0_steps;          /* level-0 steps taken by this call */
+  int64_t cell_updates;          /* active-cell updates (one cell advanced by its level's dt) */
+  int64_t updates_per_level[8];
+  double last_dt0;               /* last level-0 time step */
+  double t;                      /* solver time after the call */
+} aw_stats;
+
+typedef struct aw_cell {
+  int32_t level, status, i, j, k;
+} aw_cell;
+
+typedef struct aw_solver aw_solver;
+
+/* Create a solver on the current CUDA device.  Allocates the dense per-level grids (Sec. 3.1:
+ * level l has n*r^l cells per direction) and installs a uniform level-0 mesh of active cells
+ * with zero averages.  Errors: AW_EINVAL (bad config), AW_ENOMEM, AW_ECUDA. */
+int aw_create(const aw_config* cfg, uintptr_t stream, aw_solver** out);
+
+/* Release every device buffer of the solver.  Safe on NULL. */
+void aw_destroy(aw_solver* s);
+
+/* Message of the last failing call on this thread (never NULL). */
+const char* aw_last_error(void);
+
+/* Set the averages of every existing cell from an analytic initial condition (see AW_IC_*),
+ * then apply `nrefine` passes of indicator + regrid in initial-condition mode, in which new
+ * cells take the initial condition's averages (Sec. 3.1: the refinement criterion is applied
+ * to the initial condition up to l_max).  nrefine < 0 means lmax passes.  Resets t to 0. */
+int aw_set_initial(aw_solver* s, int32_t ic_kind, const double* params, int32_t nparams, int32_t nrefine);
+
+/* Set the averages of every existing cell (canonical order, V doubles per cell, host memory).
+ * Virtual mothers are then re-averaged from their children (Eq. eqn.average).
+ * n must equal the current cell count (AW_EINVAL otherwise). */
+int aw_set_cell_averages(aw_solver* s, const double* u_host, int64_t n);
+
+/* One level-0 step: dt_0 from the CFL condition (clipped at t_end), the recursive local time
+ * stepping of all levels (Eq. eqn.update.criterion), then, if auto_regrid, one regrid.
+ * Returns AW_ENONPHYSICAL if a non-physical state appeared. */
+int aw_step(aw_solver* s, double t_end, aw_stats* stats);
+
+/* One level-0 step of a given size dt0 (no CFL, no clipping, no regrid); for tests. */
+int aw_step_dt(aw_solver* s, double dt0, aw_stats* stats);
+
+/* Level-0 steps (with regrids if auto_regrid) until t reaches t_end. */
+int aw_advance_to(aw_solver* s, double t_end, aw_stats* stats);
+
+/* Stable level-0 time step of the current state (CFL condition over all active cells). */
+int aw_compute_dt(aw_solver* s, double* dt0);
+
+/* Regrid from the refinement indicator (Eq. eqn.indicator, Phi = rho) under rules 1-7 of
+ * Sec. 3.1.  init_mode = 1 takes new cells from the initial condition, 0 projects the
+ * mothers' WENO polynomials. */
+int aw_regrid(aw_solver* s, int32_t init_mode);
+
+/* Regrid with caller-supplied flags, one per existing cell in canonical order:
+ * +1 refine (honoured on active cells below lmax), -1 recoarsen (honoured on virtual mothers
+ * whose children are all active leaves), 0 keep.  The tree that results is a function of the
+ * flags alone; this is the hook for bit-exact tree parity. */
+int aw_regrid_with_flags(aw_solver* s, const int8_t* flags, int64_t n, int32_t init_mode);
+
+/* Flags the indicator gives for the current state (canonical order), without regridding. */
+int aw_compute_flags(aw_solver* s, int32_t init_mode, int8_t* flags, int64_t cap, int64_t* n);
+
+/* Cell counts: all existing cells, active cells, and per level (arrays of 8, may be NULL). */
+int aw_get_counts(aw_solver* s, int64_t* n_cells, int64_t* n_active, int64_t* cells_per_level,
+                  int64_t* active_per_level);
+
+/* Canonical export of every existing cell: meta (may be NULL) and V averages per cell. */
+int aw_read_cells(aw_solver* s, aw_cell* meta, double* u, int64_t cap, int64_t* n);
+
+/* Internal per-level arrays for kernel-level parity (AW_INTERNAL_*), in the level's
+ * canonical order.  *n receives the number of doubles. */
+int aw_read_internal(aw_solver* s, int32_t what, int32_t level, double* buf, int64_t cap, int64_t* n);
+
+/* Solver time, and total sum(volume * u) over active cells (V doubles). */
+int aw_get_time(aw_solver* s, double* t);
+int aw_totals(aw_solver* s, double* tot);
+
+/* Number of conserved variables of the configured PDE. */
+int aw_num_vars(const aw_solver* s);
+
+/* Reset the mesh to the uniform level-0 grid of active cells with zero averages, t = 0
+ * (re-uses the solver's device memory for a new problem). */
+int aw_reset(aw_solver* s);
+
+/* Per-kernel timing: when on, every launch of the hot kernels is bracketed by CUDA events on the
+ * solver's stream.  aw_kernel_times() synchronises, returns the accumulated device time (ms) and
+ * launch count per kind since the previous call, and restarts the accumulation.
+ * Kinds: 0 WENO, 1 predictor, 2 face flux, 3 update, 4 projection of virtual cells (arrays of 8). */
+int aw_set_profiling(aw_solver* s, int32_t on);
+int aw_kernel_times(aw_solver* s, double* ms, int64_t* launches);
+
+/* Wait for all work of the solver on its stream. */
+int aw_sync(aw_solver* s);
+
+/* Kernel launches issued by this solver since creation (device work the library ran). */
+int64_t aw_kernel_launches(const aw_solver* s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,158 @@
+"""GB300-native ADER-WENO finite volume solver on space-time adaptive meshes.
+
+The solver (WENO reconstruction, space-time DG predictor, Rusanov fluxes, one-step update,
+local time stepping, AMR bookkeeping) lives in the CUDA library ``lib/libaderweno.so`` behind
+the C ABI of ``include/aderweno.h``; this package only binds it.  ``Solver`` mirrors the C
+calls one to one.
+"""
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import (AW_BC_PERIODIC, AW_BC_TRANSMISSIVE, AW_FLUX_RUSANOV, AW_IC_CONST, AW_IC_EXPLOSION,  # noqa: F401
+                   AW_IC_FOURIER, AW_IC_OT, AW_IC_RP4, AW_IC_VORTEX, AW_INTERNAL_CHI, AW_INTERNAL_FLUX,
+                   AW_INTERNAL_PREDICTOR, AW_INTERNAL_WENO, AW_PDE_EULER, AW_PDE_LINADV, AW_PDE_MHD_GLM,
+                   AwCell, AwConfig, AwError, AwStats)
+
+
+def make_config(dim=2, pde=AW_PDE_EULER, M=2, n=(16, 16, 1), gamma=1.4, c_h=2.0, lo=(0.0, 0.0, 0.0),
+                hi=(1.0, 1.0, 1.0), bc=AW_BC_PERIODIC, r=3, lmax=0, chi_ref=0.2, chi_rec=0.1, eps_ind=0.01,
+                cfl=0.9, picard=0, auto_regrid=1, adv=(1.0, 1.0, 1.0)) -> AwConfig:
+    c = AwConfig()
+    c.dim, c.pde, c.M = dim, pde, M
+    c.nx, c.ny, c.nz = n[0], n[1], (n[2] if dim == 3 else 1)
+    c.gamma, c.c_h = gamma, c_h
+    for a in range(3):
+        c.lo[a], c.hi[a], c.adv[a] = lo[a], hi[a], adv[a]
+    bcs = bc if isinstance(bc, (list, tuple)) else [bc] * 6
+    for i in range(6):
+        c.bc[i] = bcs[i]
+    c.refine_factor, c.lmax = r, lmax
+    c.chi_ref, c.chi_rec, c.eps_ind, c.cfl = chi_ref, chi_rec, eps_ind, cfl
+    c.picard_iters, c.flux, c.auto_regrid = picard, AW_FLUX_RUSANOV, auto_regrid
+    return c
+
+
+def _dp(a):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+class Solver:
+    """One solver on the current CUDA device, ordered on `stream` (an integer cudaStream_t)."""
+
+    def __init__(self, cfg: AwConfig, stream: int = 0):
+        self.L = _lib.load()
+        self.cfg = cfg
+        h = C.c_void_p()
+        _lib.check(self.L.aw_create(C.byref(cfg), stream, C.byref(h)))
+        self.h = h
+        self.V = self.L.aw_num_vars(h)
+        self.d = cfg.dim
+        self.N = cfg.M + 1
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.aw_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def set_initial(self, ic, params, nrefine=-1):
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        _lib.check(self.L.aw_set_initial(self.h, ic, _dp(p), len(p), nrefine))
+
+    def set_cell_averages(self, u):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+        _lib.check(self.L.aw_set_cell_averages(self.h, _dp(u), u.shape[0]))
+
+    def step(self, t_end=1e300):
+        st = AwStats()
+        _lib.check(self.L.aw_step(self.h, t_end, C.byref(st)))
+        return st
+
+    def step_dt(self, dt0):
+        st = AwStats()
+        _lib.check(self.L.aw_step_dt(self.h, dt0, C.byref(st)))
+        return st
+
+    def advance_to(self, t_end):
+        st = AwStats()
+        _lib.check(self.L.aw_advance_to(self.h, t_end, C.byref(st)))
+        return st
+
+    def compute_dt(self):
+        d = C.c_double()
+        _lib.check(self.L.aw_compute_dt(self.h, C.byref(d)))
+        return d.value
+
+    def regrid(self, init_mode=0):
+        _lib.check(self.L.aw_regrid(self.h, init_mode))
+
+    def regrid_with_flags(self, flags, init_mode=0):
+        f = np.ascontiguousarray(flags, dtype=np.int8)
+        _lib.check(self.L.aw_regrid_with_flags(self.h, f.ctypes.data_as(C.POINTER(C.c_int8)), len(f), init_mode))
+
+    def compute_flags(self, init_mode=0):
+        n, _ = self.counts()[:2]
+        f = np.zeros(max(n, 1), dtype=np.int8)
+        got = C.c_int64()
+        _lib.check(self.L.aw_compute_flags(self.h, init_mode, f.ctypes.data_as(C.POINTER(C.c_int8)), len(f),
+                                           C.byref(got)))
+        return f[: got.value]
+
+    def counts(self):
+        nc, na = C.c_int64(), C.c_int64()
+        cpl, apl = (C.c_int64 * 8)(), (C.c_int64 * 8)()
+        _lib.check(self.L.aw_get_counts(self.h, C.byref(nc), C.byref(na), cpl, apl))
+        lm = self.cfg.lmax + 1
+        return nc.value, na.value, list(cpl)[:lm], list(apl)[:lm]
+
+    def cells(self):
+        n = self.counts()[0]
+        meta = (AwCell * max(n, 1))()
+        u = np.zeros((max(n, 1), self.V))
+        got = C.c_int64()
+        _lib.check(self.L.aw_read_cells(self.h, meta, _dp(u), n, C.byref(got)))
+        m = np.frombuffer(meta, dtype=np.int32).reshape(-1, 5)[:n].copy()
+        return m, u[:n]
+
+    def internal(self, what, level=0):
+        got = C.c_int64()
+        rc = self.L.aw_read_internal(self.h, what, level, None, 0, C.byref(got))
+        if rc not in (0, _lib.AW_EINVAL):
+            _lib.check(rc)
+        buf = np.zeros(max(got.value, 1))
+        _lib.check(self.L.aw_read_internal(self.h, what, level, _dp(buf), len(buf), C.byref(got)))
+        return buf[: got.value]
+
+    @property
+    def t(self):
+        d = C.c_double()
+        _lib.check(self.L.aw_get_time(self.h, C.byref(d)))
+        return d.value
+
+    def totals(self):
+        out = np.zeros(self.V)
+        _lib.check(self.L.aw_totals(self.h, _dp(out)))
+        return out
+
+    def reset(self):
+        _lib.check(self.L.aw_reset(self.h))
+
+    def set_profiling(self, on=True):
+        _lib.check(self.L.aw_set_profiling(self.h, 1 if on else 0))
+
+    def kernel_times(self):
+        """(ms, launches) per kind: WENO, predictor, face flux, update, projection"""
+        ms = np.zeros(8)
+        n = np.zeros(8, dtype=np.int64)
+        _lib.check(self.L.aw_kernel_times(self.h, _dp(ms), n.ctypes.data_as(C.POINTER(C.c_int64))))
+        return ms[:5], n[:5]
+
+    def sync(self):
+        _lib.check(self.L.aw_sync(self.h))
+
+    def kernel_launches(self):
+        return self.L.aw_kernel_launches(self.h)

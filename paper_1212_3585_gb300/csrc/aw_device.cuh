@@ -1,0 +1,242 @@
+// aw_device.cuh -- device-side definitions shared by the kernels of the ADER-WENO solver:
+// reference-element tables, PDE systems, per-level views and kernel arguments.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace aw {
+
+constexpr int MAXN = 4;   // N = M + 1 <= 4 (M in {2, 3})
+constexpr int MAXR = 4;   // refinement factor r <= 4
+constexpr int MAXL = 5;   // levels 0..4
+constexpr int MAXV = 9;
+constexpr int8_t ST_NONE = -2;
+
+enum { PDE_EULER = 0, PDE_MHD = 1, PDE_LINADV = 2 };
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1 };
+
+__host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+__host__ __device__ constexpr int nvars(int D, int PDE) {
+  return PDE == PDE_LINADV ? 1 : (PDE == PDE_EULER ? D + 2 : 9);
+}
+
+// Reference-element tables (Sec. 2.2-2.3 and 3.1.3), computed on the host and passed by value
+// in the kernel parameter space (read through the constant cache).
+struct Tables {
+  int N, M, Ns, r;
+  double x[MAXN], w[MAXN];        // Gauss-Legendre nodes/weights on [0,1]
+  double psi0[MAXN], psi1[MAXN];  // psi_l(0), psi_l(1)
+  double Dm[MAXN][MAXN];          // Dm[i][l] = psi_l'(x_i): nodal derivative matrix
+  int SL[4];                      // left extent of WENO stencil s
+  double lam[4];                  // linear weight lambda_s
+  double Ainv[4][MAXN][MAXN];     // Ainv[s][p][e]: stencil reconstruction matrix
+  double Sig[MAXN][MAXN];         // oscillation indicator matrix
+  double G[MAXN][MAXN];           // K_t^{-1} diag(w): time block of the predictor
+  double gsum[MAXN];              // row sums of G
+  double Wc[MAXR][MAXN];          // Wc[c][l] = r * int_{c/r}^{(c+1)/r} psi_l (child averages)
+  double Pf[MAXR][MAXN][MAXN];    // Pf[c][i][l] = psi_l((c + x_i)/r) (fine points in coarse frame)
+  double Pt[MAXR][MAXN];          // Pt[k][l] = psi_l(k/r)
+};
+
+struct Phys {
+  double gamma, c_h;
+  double adv[3];
+};
+
+struct Bc6 {
+  int v[6];  // boundary condition of faces x-, x+, y-, y+, z-, z+
+};
+
+// One level of the mesh: dense status/average/active-id grids over the whole level box.
+struct LevelView {
+  int L[3];
+  long long n;         // L[0]*L[1]*L[2]
+  const int8_t* st;    // status per dense cell (ST_NONE, -1, 0, 1)
+  double* u;           // averages, structure of arrays: u[v * n + c]
+  const int32_t* aid;  // active id per dense cell or -1
+  double dx[3];
+};
+
+__host__ __device__ inline long long didx(const LevelView& L, int i, int j, int k) {
+  return ((long long)k * L.L[1] + j) * L.L[0] + i;
+}
+
+// Map coordinate c of axis a through the boundary conditions.  Returns true inside (possibly
+// wrapped), false outside a transmissive boundary, where *out is clamped (ghost layers copy the
+// adjacent interior cell of the same level).
+__device__ __forceinline__ bool bcmap(const int* L, const int* bc, int a, int c, int* out) {
+  int n = L[a];
+  if (c >= 0 && c < n) { *out = c; return true; }
+  if (bc[2 * a + (c < 0 ? 0 : 1)] == BC_PERIODIC) {
+    int m = c % n;
+    *out = m < 0 ? m + n : m;
+    return true;
+  }
+  *out = c < 0 ? 0 : n - 1;
+  return false;
+}
+
+// ------------------------------------------------------------------------------------------
+// PDE systems.  Euler (Eq. eq:Euler-system), ideal MHD with hyperbolic GLM cleaning (Sec. 4.2,
+// rationalised units) and linear advection.  All in FP64.
+// ------------------------------------------------------------------------------------------
+template <int PDE, int D>
+struct Pde;
+
+template <int D>
+struct Pde<PDE_EULER, D> {
+  static constexpr int V = D + 2;
+  // fluxes in every direction at one state, sharing the primitive variables
+  __device__ __forceinline__ static void fluxes(const double* q, double (*F)[V], const Phys& P) {
+    double ir = 1.0 / q[0];
+    double v[D];
+#pragma unroll
+    for (int a = 0; a < D; a++) v[a] = q[1 + a] * ir;
+    double ke = q[1] * v[0];
+#pragma unroll
+    for (int a = 1; a < D; a++) ke = fma(q[1 + a], v[a], ke);
+    const double gm1 = P.gamma - 1.0;
+    double p = gm1 * (q[D + 1] - 0.5 * ke);
+    double Ep = q[D + 1] + p;
+#pragma unroll
+    for (int n = 0; n < D; n++) {
+      F[n][0] = q[1 + n];
+#pragma unroll
+      for (int a = 0; a < D; a++) F[n][1 + a] = q[1 + a] * v[n] + (a == n ? p : 0.0);
+      F[n][D + 1] = v[n] * Ep;
+    }
+  }
+  __device__ __forceinline__ static void flux(const double* q, int n, double* f, const Phys& P) {
+    double ir = 1.0 / q[0];
+    double ke = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; a++) ke += q[1 + a] * q[1 + a];
+    double p = (P.gamma - 1.0) * (q[D + 1] - 0.5 * ke * ir);
+    double vn = q[1 + n] * ir;
+    f[0] = q[1 + n];
+#pragma unroll
+    for (int a = 0; a < D; a++) f[1 + a] = q[1 + a] * vn + (a == n ? p : 0.0);
+    f[D + 1] = vn * (q[D + 1] + p);
+  }
+  __device__ __forceinline__ static double pressure(const double* q, const Phys& P) {
+    double ke = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; a++) ke += q[1 + a] * q[1 + a];
+    return (P.gamma - 1.0) * (q[D + 1] - 0.5 * ke / q[0]);
+  }
+  // spectral radius of the flux Jacobian: eigenvalues v_n, v_n +- c with c^2 = gamma p / rho;
+  // for a face state with c^2 < 0 the pair v_n +- c is complex with modulus sqrt(v_n^2 - c^2)
+  __device__ __forceinline__ static double speed(const double* q, int n, const Phys& P) {
+    double p = pressure(q, P);
+    double vn = q[1 + n] / q[0], c2 = P.gamma * p / q[0];
+    return c2 >= 0.0 ? fabs(vn) + sqrt(c2) : sqrt(vn * vn - c2);
+  }
+  __device__ __forceinline__ static bool physical(const double* q, const Phys& P) {
+#pragma unroll
+    for (int v = 0; v < V; v++)
+      if (!(q[v] == q[v])) return false;
+    return q[0] > 0.0 && pressure(q, P) > 0.0;
+  }
+};
+
+template <int D>
+struct Pde<PDE_MHD, D> {
+  static constexpr int V = 9;
+  __device__ __forceinline__ static void flux(const double* q, int n, double* f, const Phys& P) {
+    double ir = 1.0 / q[0];
+    double v0 = q[1] * ir, v1 = q[2] * ir, v2 = q[3] * ir;
+    double vv[3] = {v0, v1, v2};
+    double B2 = q[5] * q[5] + q[6] * q[6] + q[7] * q[7];
+    double mv = q[1] * v0 + q[2] * v1 + q[3] * v2;
+    double p = (P.gamma - 1.0) * (q[4] - 0.5 * mv - 0.5 * B2);
+    double vB = v0 * q[5] + v1 * q[6] + v2 * q[7];
+    double pt = p + 0.5 * B2;
+    double vn = vv[n], Bn = q[5 + n];
+    f[0] = q[1 + n];
+#pragma unroll
+    for (int a = 0; a < 3; a++) f[1 + a] = q[1 + a] * vn + (a == n ? pt : 0.0) - q[5 + a] * Bn;
+    f[4] = vn * (q[4] + pt) - Bn * vB;
+#pragma unroll
+    for (int a = 0; a < 3; a++) f[5 + a] = (a == n) ? q[8] : (vn * q[5 + a] - Bn * vv[a]);
+    f[8] = P.c_h * P.c_h * Bn;
+  }
+  __device__ __forceinline__ static void fluxes(const double* q, double (*F)[V], const Phys& P) {
+#pragma unroll
+    for (int n = 0; n < D; n++) flux(q, n, F[n], P);
+  }
+  __device__ __forceinline__ static double pressure(const double* q, const Phys& P) {
+    double m2 = q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    double B2 = q[5] * q[5] + q[6] * q[6] + q[7] * q[7];
+    return (P.gamma - 1.0) * (q[4] - 0.5 * m2 / q[0] - 0.5 * B2);
+  }
+  __device__ __forceinline__ static double speed(const double* q, int n, const Phys& P) {
+    double p = pressure(q, P);
+    double a2 = P.gamma * p / q[0];
+    double B2 = q[5] * q[5] + q[6] * q[6] + q[7] * q[7];
+    double b2 = B2 / q[0], bn2 = q[5 + n] * q[5 + n] / q[0];
+    double s = a2 + b2;
+    double cf = sqrt(0.5 * (s + sqrt(s * s - 4.0 * a2 * bn2)));
+    double c = fabs(q[1 + n] / q[0]) + cf;
+    return c > P.c_h ? c : P.c_h;
+  }
+  __device__ __forceinline__ static bool physical(const double* q, const Phys& P) {
+#pragma unroll
+    for (int v = 0; v < V; v++)
+      if (!(q[v] == q[v])) return false;
+    return q[0] > 0.0 && pressure(q, P) > 0.0;
+  }
+};
+
+template <int D>
+struct Pde<PDE_LINADV, D> {
+  static constexpr int V = 1;
+  __device__ __forceinline__ static void flux(const double* q, int n, double* f, const Phys& P) {
+    f[0] = P.adv[n] * q[0];
+  }
+  __device__ __forceinline__ static void fluxes(const double* q, double (*F)[V], const Phys& P) {
+#pragma unroll
+    for (int n = 0; n < D; n++) F[n][0] = P.adv[n] * q[0];
+  }
+  __device__ __forceinline__ static double speed(const double*, int n, const Phys& P) { return fabs(P.adv[n]); }
+  __device__ __forceinline__ static bool physical(const double* q, const Phys&) { return q[0] == q[0]; }
+};
+
+// Rusanov flux, Eq. eqn.rusanov: s_max is the larger of the two states' largest |eigenvalue|.
+template <int PDE, int D>
+__device__ __forceinline__ void rusanov(const double* qm, const double* qp, int n, double* out, const Phys& P) {
+  using Q = Pde<PDE, D>;
+  constexpr int V = Q::V;
+  double fm[V], fp[V];
+  Q::flux(qm, n, fm, P);
+  Q::flux(qp, n, fp, P);
+  double sm = Q::speed(qm, n, P), sp = Q::speed(qp, n, P);
+  double s = sm > sp ? sm : sp;
+#pragma unroll
+  for (int v = 0; v < V; v++) out[v] = 0.5 * (fm[v] + fp[v]) - 0.5 * s * (qp[v] - qm[v]);
+}
+
+// Arguments of the per-level hot kernels.
+struct HotArgs {
+  Tables T;
+  Phys P;
+  int bc[6];
+  int level, sub, picard;
+  LevelView lv;         // this level
+  LevelView lvm;        // mother level (level-1), valid when level >= 1
+  LevelView lvc;        // child level (level+1), valid when level < lmax
+  const int32_t* alist; // active cells of this level (dense indices), canonical order
+  int na;
+  const int32_t* tiles; // tile origins (tile linear index on the level's tile grid)
+  int ntiles;
+  int tdim[3];          // tiles per direction
+  double* wh;           // WENO dofs per active cell [aid][V][N^d]
+  double* qh;           // predictor dofs per active cell [aid][V][N^(d+1)]
+  const double* qhm;    // predictor dofs of the mother level
+  double* fl;           // face fluxes per active cell [aid][2d][V]
+  double* mem;          // memory variables per active cell of this level [aid][2d][V]
+  double* memc;         // memory variables of the child level
+  const double* dtl;    // device array: dt of each level
+  int* err;             // device error word
+};
+
+}  // namespace aw

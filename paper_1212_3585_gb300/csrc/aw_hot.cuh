@@ -1,0 +1,618 @@
+// aw_hot.cuh -- the per-level hot kernels of the ADER-WENO update, templated on the space
+// dimension D, the polynomial degree M and the PDE system.  Instantiated per configuration in
+// aw_inst_*.cu.  Everything here is FP64: the scheme is bound by the FP64 pipe on sm_103a, so
+// the kernels are laid out to keep every lane of every issued FP64 instruction busy (compacted
+// work lists, one thread per cell x spatial node) rather than for memory traffic.
+#pragma once
+#include "aw_device.cuh"
+#include "aw_ops.h"
+
+namespace aw {
+
+template <int M>
+struct Sten {
+  static constexpr int NS = (M % 2 == 0) ? 3 : 4;
+  __host__ __device__ static constexpr int SL(int s) {
+    return (M % 2 == 0) ? (s == 0 ? M / 2 : (s == 1 ? M : 0))
+                        : (s == 0 ? M / 2 + 1 : (s == 1 ? M / 2 : (s == 2 ? M : 0)));
+  }
+};
+
+// One-dimensional WENO reconstruction (Sec. 2.2, Eqs. eqn.rec.x, eqn.weno, eqn.omegas,
+// eqn.sigmas): values at offsets -M..M (stride apart) -> N nodal coefficients.  The stencil
+// polynomials and oscillation indicators are formed from the differences to the cell's own value
+// (exact: stencils reproduce constants and Sigma annihilates them), so that the rounding of a
+// large constant part does not reach sigma, whose 8th power sets the weights.
+template <int M>
+__device__ __forceinline__ void weno1d(const Tables& T, const double* v, int stride, double* out) {
+  constexpr int N = M + 1, W = 2 * M + 1, NS = Sten<M>::NS;
+  double val[W];
+  const double c = v[M * stride];
+#pragma unroll
+  for (int e = 0; e < W; e++) val[e] = v[e * stride] - c;
+  double acc[N], sum = 0.0;
+#pragma unroll
+  for (int p = 0; p < N; p++) acc[p] = 0.0;
+#pragma unroll
+  for (int s = 0; s < NS; s++) {
+    const int o = M - Sten<M>::SL(s);
+    double ws[N];
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      double t = T.Ainv[s][p][0] * val[o];
+#pragma unroll
+      for (int e = 1; e < N; e++) t = fma(T.Ainv[s][p][e], val[o + e], t);
+      ws[p] = t;
+    }
+    double sig = 0.0;
+#pragma unroll
+    for (int p = 0; p < N; p++) {
+      double t = T.Sig[p][0] * ws[0];
+#pragma unroll
+      for (int m = 1; m < N; m++) t = fma(T.Sig[p][m], ws[m], t);
+      sig = fma(t, ws[p], sig);
+    }
+    double x = sig + 1e-14, x2 = x * x, x4 = x2 * x2, x8 = x4 * x4;
+    double om = T.lam[s] / x8;
+    sum += om;
+#pragma unroll
+    for (int p = 0; p < N; p++) acc[p] = fma(om, ws[p], acc[p]);
+  }
+  double is = 1.0 / sum;
+#pragma unroll
+  for (int p = 0; p < N; p++) out[p] = fma(acc[p], is, c);
+}
+
+// Warp 0 compacts the candidates 0..ncand-1 for which pred(c) holds into list[], count into *cnt.
+template <class Pred>
+__device__ __forceinline__ void warp0_compact(int ncand, Pred pred, int16_t* list, int* cnt) {
+  if (threadIdx.x >= 32) return;
+  int lane = threadIdx.x, base = 0;
+  for (int c0 = 0; c0 < ncand; c0 += 32) {
+    int c = c0 + lane;
+    bool f = c < ncand && pred(c);
+    unsigned b = __ballot_sync(0xffffffffu, f);
+    if (f) list[base + __popc(b & ((1u << lane) - 1u))] = (int16_t)c;
+    base += __popc(b);
+  }
+  if (lane == 0) *cnt = base;
+}
+
+// ------------------------------------------------------------------------------------------
+// WENO kernel: one CTA per tile of TS^D cells of one level.  The (TS+2M)^D box of averages is
+// staged in shared memory through the boundary map; x sweeps run on every box line that feeds
+// an active cell of the tile, then y (and z) sweeps on the active cells only (compacted work
+// lists, Eqs. eqn.weno, eqn.weno.y, eqn.weno.z).  Output: WENO dofs per active cell.
+// ------------------------------------------------------------------------------------------
+template <int D, int M, int PDE, int TS>
+struct WenoCfg {
+  static constexpr int N = M + 1, V = nvars(D, PDE), B = TS + 2 * M;
+  static constexpr int NB = ipow(B, D);
+  static constexpr int NXS = (D == 2) ? V * B * TS * N : V * B * B * TS * N;
+  static constexpr int NYS = (D == 2) ? 0 : V * B * TS * TS * N * N;
+  static constexpr int SMEM = (V * NB + NXS + NYS) * 8;
+  static constexpr int NC = ipow(TS, D);
+  static constexpr int NXC = (D == 2) ? B * TS : B * B * TS;
+  static constexpr int NYC = (D == 2) ? 0 : B * TS * TS;
+};
+
+template <int D, int M, int PDE, int TS>
+__global__ void __launch_bounds__(256) k_weno(HotArgs a) {
+  using C = WenoCfg<D, M, PDE, TS>;
+  constexpr int N = C::N, V = C::V, B = C::B, NB = C::NB, NSP = ipow(N, D);
+  extern __shared__ double smem[];
+  double* box = smem;
+  double* xs = box + V * NB;
+  double* ys = xs + C::NXS;
+  __shared__ int taid[C::NC];
+  __shared__ int16_t lx[C::NXC];
+  __shared__ int16_t ly[(C::NYC > 0) ? C::NYC : 1];
+  __shared__ int16_t lc[C::NC];
+  __shared__ int nx_, ny_, nc_;
+  __shared__ uint8_t needxy[(C::NYC > 0) ? C::NYC : 1];
+
+  const LevelView& L = a.lv;
+  const int tile = a.tiles[blockIdx.x];
+  int org[3] = {0, 0, 0};
+  {
+    int t = tile;
+    for (int d = 0; d < D; d++) { org[d] = (t % a.tdim[d]) * TS; t /= a.tdim[d]; }
+  }
+  // stage the box
+  for (int idx = threadIdx.x; idx < NB; idx += blockDim.x) {
+    int t = idx, c[3] = {0, 0, 0};
+    for (int d = 0; d < D; d++) {
+      int b = t % B;
+      t /= B;
+      bcmap(L.L, a.bc, d, org[d] - M + b, &c[d]);
+    }
+    long long di = didx(L, c[0], c[1], c[2]);
+#pragma unroll
+    for (int v = 0; v < V; v++) box[v * NB + idx] = L.u[v * L.n + di];
+  }
+  for (int idx = threadIdx.x; idx < C::NC; idx += blockDim.x) {
+    int t = idx, c[3] = {0, 0, 0};
+    bool in = true;
+    for (int d = 0; d < D; d++) {
+      c[d] = org[d] + t % TS;
+      t /= TS;
+      in &= c[d] < L.L[d];
+    }
+    taid[idx] = in ? L.aid[didx(L, c[0], c[1], c[2])] : -1;
+  }
+  __syncthreads();
+
+  if (D == 2) {
+    // x sweeps needed at box row y, tile column cx: an active cell (cx, ty) with |y - ty - M| <= M
+    warp0_compact(C::NXC, [&](int c) {
+      int y = c / TS, cx = c % TS;
+      for (int ty = 0; ty < TS; ty++)
+        if (taid[ty * TS + cx] >= 0 && abs(y - ty - M) <= M) return true;
+      return false;
+    }, lx, &nx_);
+    warp0_compact(C::NC, [&](int c) { return taid[c] >= 0; }, lc, &nc_);
+    __syncthreads();
+    const int nx = nx_ * V;
+    for (int it = threadIdx.x; it < nx; it += blockDim.x) {
+      int pos = lx[it / V], v = it % V;
+      int y = pos / TS, cx = pos % TS;
+      double o[N];
+      weno1d<M>(a.T, box + v * NB + y * B + cx, 1, o);
+#pragma unroll
+      for (int p = 0; p < N; p++) xs[((v * B + y) * TS + cx) * N + p] = o[p];
+    }
+    __syncthreads();
+    const int nyi = nc_ * N * V;
+    for (int it = threadIdx.x; it < nyi; it += blockDim.x) {
+      int k = it / (N * V), rem = it % (N * V), p = rem / V, v = rem % V;
+      int c = lc[k], cx = c % TS, cy = c / TS;
+      double o[N];
+      weno1d<M>(a.T, xs + ((v * B + cy) * TS + cx) * N + p, TS * N, o);
+      double* dst = a.wh + ((long long)taid[c] * V + v) * NSP;
+#pragma unroll
+      for (int q = 0; q < N; q++) dst[p + N * q] = o[q];
+    }
+  } else {
+    // z sweeps at active cells; y sweeps where an active cell within M in z needs them; x sweeps
+    // where a needed y sweep within M in y needs them.
+    for (int c = threadIdx.x; c < C::NYC; c += blockDim.x) {
+      int z = c / (TS * TS), cy = (c / TS) % TS, cx = c % TS;
+      bool f = false;
+      for (int tz = 0; tz < TS; tz++)
+        f |= taid[(tz * TS + cy) * TS + cx] >= 0 && abs(z - tz - M) <= M;
+      needxy[c] = f;
+    }
+    __syncthreads();
+    warp0_compact(C::NXC, [&](int c) {
+      int z = c / (B * TS), y = (c / TS) % B, cx = c % TS;
+      for (int cy = 0; cy < TS; cy++)
+        if (needxy[(z * TS + cy) * TS + cx] && abs(y - cy - M) <= M) return true;
+      return false;
+    }, lx, &nx_);
+    warp0_compact(C::NYC, [&](int c) { return needxy[c] != 0; }, ly, &ny_);
+    warp0_compact(C::NC, [&](int c) { return taid[c] >= 0; }, lc, &nc_);
+    __syncthreads();
+    const int nx = nx_ * V;
+    for (int it = threadIdx.x; it < nx; it += blockDim.x) {
+      int pos = lx[it / V], v = it % V;
+      int z = pos / (B * TS), y = (pos / TS) % B, cx = pos % TS;
+      double o[N];
+      weno1d<M>(a.T, box + v * NB + (z * B + y) * B + cx, 1, o);
+#pragma unroll
+      for (int p = 0; p < N; p++) xs[(((v * B + z) * B + y) * TS + cx) * N + p] = o[p];
+    }
+    __syncthreads();
+    const int nyi = ny_ * N * V;
+    for (int it = threadIdx.x; it < nyi; it += blockDim.x) {
+      int k = it / (N * V), rem = it % (N * V), p = rem / V, v = rem % V;
+      int pos = ly[k];
+      int z = pos / (TS * TS), cy = (pos / TS) % TS, cx = pos % TS;
+      double o[N];
+      weno1d<M>(a.T, xs + (((v * B + z) * B + cy) * TS + cx) * N + p, TS * N, o);
+#pragma unroll
+      for (int q = 0; q < N; q++) ys[((((v * B + z) * TS + cy) * TS + cx) * N + p) * N + q] = o[q];
+    }
+    __syncthreads();
+    const int nzi = nc_ * N * N * V;
+    for (int it = threadIdx.x; it < nzi; it += blockDim.x) {
+      int k = it / (N * N * V), rem = it % (N * N * V), pq = rem / V, v = rem % V;
+      int p = pq % N, q = pq / N;
+      int c = lc[k], cx = c % TS, cy = (c / TS) % TS, cz = c / (TS * TS);
+      double o[N];
+      weno1d<M>(a.T, ys + ((((v * B + cz) * TS + cy) * TS + cx) * N + p) * N + q, TS * TS * N * N, o);
+      double* dst = a.wh + ((long long)taid[c] * V + v) * NSP;
+#pragma unroll
+      for (int r = 0; r < N; r++) dst[p + N * q + N * N * r] = o[r];
+    }
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Predictor kernel (Sec. 2.3, Eq. eqn.stdg.final).  One thread per (active cell, spatial node);
+// the thread holds the time column of q_h at its node for all variables.  With the nodal
+// tensor basis the Picard step reads
+//     q(node, s) = w(node) - sum_s' G[s][s'] R(node, s'),
+//     R(node, s') = sum_d (dt/dx_d) sum_k Dm[i_d][k] f_d(q(node with i_d = k, s')),
+// where G = K_t^{-1} diag(w) is the inverted time block of K1 and K_t^{-1} psi(0) = 1.  The
+// spatial derivative contractions read the neighbouring nodes' fluxes from shared memory.
+// The first iteration starts from q = w, constant in time, so it needs one flux evaluation per
+// node and R is constant in time.
+// ------------------------------------------------------------------------------------------
+template <int D, int M, int PDE>
+struct PredCfg {
+  static constexpr int N = M + 1, NSP = ipow(N, D), NST = NSP * N, V = nvars(D, PDE);
+  static constexpr int CPB = (NSP == 9) ? 32 : (NSP == 16 ? 16 : (NSP == 27 ? 16 : 4));
+  static constexpr int THREADS = CPB * NSP;
+  static constexpr int SMEM = CPB * D * V * NSP * 8;
+};
+
+template <int D, int M, int PDE>
+__global__ void __launch_bounds__(PredCfg<D, M, PDE>::THREADS) k_predict(HotArgs a) {
+  using C = PredCfg<D, M, PDE>;
+  using Q = Pde<PDE, D>;
+  constexpr int N = C::N, NSP = C::NSP, NST = C::NST, V = C::V;
+  extern __shared__ double sh[];  // [CPB][D][V][NSP]
+  const int lc = threadIdx.x / NSP, node = threadIdx.x % NSP;
+  const int cell = blockIdx.x * C::CPB + lc;
+  const bool ok = cell < a.na;
+  int ix[D];
+  {
+    int t = node;
+#pragma unroll
+    for (int d = 0; d < D; d++) { ix[d] = t % N; t /= N; }
+  }
+  const double dt = a.dtl[a.level];
+  double Dr[D][N];
+#pragma unroll
+  for (int d = 0; d < D; d++) {
+    double lam = dt / a.lv.dx[d];
+#pragma unroll
+    for (int k = 0; k < N; k++) Dr[d][k] = lam * a.T.Dm[ix[d]][k];
+  }
+  double w[V];
+  const double* wsrc = a.wh + (long long)(ok ? cell : 0) * V * NSP;
+#pragma unroll
+  for (int v = 0; v < V; v++) w[v] = wsrc[v * NSP + node];
+  double* shc = sh + lc * D * V * NSP;
+  double q[V][N], R[V][N];
+  // first Picard iteration from q = w
+  {
+    double F[D][V];
+    Q::fluxes(w, F, a.P);
+#pragma unroll
+    for (int d = 0; d < D; d++)
+#pragma unroll
+      for (int v = 0; v < V; v++) shc[(d * V + v) * NSP + node] = F[d][v];
+    __syncthreads();
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+      double r = 0.0;
+#pragma unroll
+      for (int d = 0; d < D; d++) {
+        const int st = (d == 0 ? 1 : (d == 1 ? N : N * N));
+        const int base = node - ix[d] * st;
+#pragma unroll
+        for (int k = 0; k < N; k++) r = fma(Dr[d][k], shc[(d * V + v) * NSP + base + k * st], r);
+      }
+#pragma unroll
+      for (int s = 0; s < N; s++) q[v][s] = fma(-a.T.gsum[s], r, w[v]);
+    }
+    __syncthreads();
+  }
+  for (int it = 1; it < a.picard; it++) {
+#pragma unroll
+    for (int s = 0; s < N; s++) {
+      double qs[V], F[D][V];
+#pragma unroll
+      for (int v = 0; v < V; v++) qs[v] = q[v][s];
+      Q::fluxes(qs, F, a.P);
+#pragma unroll
+      for (int d = 0; d < D; d++)
+#pragma unroll
+        for (int v = 0; v < V; v++) shc[(d * V + v) * NSP + node] = F[d][v];
+      __syncthreads();
+#pragma unroll
+      for (int v = 0; v < V; v++) {
+        double r = 0.0;
+#pragma unroll
+        for (int d = 0; d < D; d++) {
+          const int st = (d == 0 ? 1 : (d == 1 ? N : N * N));
+          const int base = node - ix[d] * st;
+#pragma unroll
+          for (int k = 0; k < N; k++) r = fma(Dr[d][k], shc[(d * V + v) * NSP + base + k * st], r);
+        }
+        R[v][s] = r;
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int v = 0; v < V; v++)
+#pragma unroll
+      for (int s = 0; s < N; s++) {
+        double t = w[v];
+#pragma unroll
+        for (int s2 = 0; s2 < N; s2++) t = fma(-a.T.G[s][s2], R[v][s2], t);
+        q[v][s] = t;
+      }
+  }
+  if (ok) {
+    double* dst = a.qh + (long long)cell * V * NST;
+#pragma unroll
+    for (int v = 0; v < V; v++)
+#pragma unroll
+      for (int s = 0; s < N; s++) dst[v * NST + node + NSP * s] = q[v][s];
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Face flux kernel (Eqs. flux:F..flux:H, eqn.rusanov, eqn.memory.sum).  One thread per
+// (active cell, axis, face quadrature point); the N^(d-1) x N space-time Gauss points of a face
+// coincide with the nodal points, so a trace is one N-term contraction along the normal.  Each
+// active cell computes its low face on every axis, and its high face where the neighbour is not
+// an active cell of the same level (boundary, coarse or fine neighbour).  Faces toward a
+// virtual child are fine sides of a coarse/fine face: the coarse predictor is evaluated at this
+// cell's points and sub-step, and the face integral is added to this cell's memory variable.
+// Faces toward a virtual mother are coarse sides: the flux is the sum of the fine cells' memory
+// variables over the r sub-steps, normalised by dt * area of this level.
+// ------------------------------------------------------------------------------------------
+template <int D, int M, int PDE>
+struct FluxCfg {
+  static constexpr int N = M + 1, NPT = ipow(N, D), TPC = D * NPT, V = nvars(D, PDE);
+  static constexpr int CPB = (256 / TPC) > 0 ? (256 / TPC) : 1;
+  static constexpr int THREADS = CPB * TPC;
+  static constexpr int SMEM = THREADS * V * 8;
+};
+
+enum { FK_SAME = 0, FK_FINE = 1, FK_COARSE = 2, FK_BOUNDARY = 3, FK_SKIP = 4 };
+
+template <int D, int M, int PDE>
+__global__ void __launch_bounds__(FluxCfg<D, M, PDE>::THREADS) k_flux(HotArgs a) {
+  using C = FluxCfg<D, M, PDE>;
+  constexpr int N = C::N, NPT = C::NPT, TPC = C::TPC, V = C::V;
+  constexpr int NSP = ipow(N, D), NST = NSP * N;
+  extern __shared__ double sh[];
+  const int lc = threadIdx.x / TPC, rem = threadIdx.x % TPC, d = rem / NPT, g = rem % NPT;
+  const int cell = blockIdx.x * C::CPB + lc;
+  const bool ok = cell < a.na;
+  const LevelView& L = a.lv;
+  const int r = a.T.r;
+  // transverse node indices (axes b != d in increasing order) and time node
+  int jt[3] = {0, 0, 0}, s;
+  {
+    int t = g;
+    for (int b = 0; b < D; b++) {
+      if (b == d) continue;
+      jt[b] = t % N;
+      t /= N;
+    }
+    s = t;
+  }
+  double wgt = a.T.w[s];
+  for (int b = 0; b < D; b++)
+    if (b != d) wgt *= a.T.w[jt[b]];
+  int ijk[3] = {0, 0, 0};
+  if (ok) {
+    long long di = a.alist[cell];
+    ijk[0] = (int)(di % L.L[0]);
+    ijk[1] = (int)((di / L.L[0]) % L.L[1]);
+    ijk[2] = (int)(di / ((long long)L.L[0] * L.L[1]));
+  }
+  const double dt = a.dtl[a.level];
+  double area = 1.0;
+  for (int b = 0; b < D; b++)
+    if (b != d) area *= L.dx[b];
+  const double* qA = a.qh + (long long)(ok ? cell : 0) * V * NST;
+  // node index with i_d = k, transverse jt, time s
+  int nbase = NSP * s;
+  {
+    int st = 1;
+    for (int b = 0; b < D; b++) {
+      if (b != d) nbase += jt[b] * st;
+      st *= N;
+    }
+  }
+  const int dstr = (d == 0 ? 1 : (d == 1 ? N : N * N));
+
+  for (int side = 0; side < 2; side++) {
+    int kind = FK_SKIP;
+    int nb[3] = {ijk[0], ijk[1], ijk[2]};
+    long long nbd = 0;
+    if (ok) {
+      bool inside = bcmap(L.L, a.bc, d, ijk[d] + (side ? 1 : -1), &nb[d]);
+      if (!inside) kind = FK_BOUNDARY;
+      else {
+        nbd = didx(L, nb[0], nb[1], nb[2]);
+        int8_t sn = L.st[nbd];
+        kind = sn == 0 ? (side ? FK_SKIP : FK_SAME) : (sn == 1 ? FK_FINE : FK_COARSE);
+      }
+    }
+    double contrib[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) contrib[v] = 0.0;
+    if (kind == FK_SAME || kind == FK_FINE || kind == FK_BOUNDARY) {
+      const double* pa = side ? a.T.psi1 : a.T.psi0;
+      double qa[V], qb[V], f[V];
+#pragma unroll
+      for (int v = 0; v < V; v++) {
+        double t = 0.0;
+#pragma unroll
+        for (int k = 0; k < N; k++) t = fma(pa[k], qA[v * NST + nbase + k * dstr], t);
+        qa[v] = t;
+      }
+      if (kind == FK_BOUNDARY) {
+        Pde<PDE, D>::flux(qa, d, f, a.P);
+      } else {
+        if (kind == FK_SAME) {
+          const double* qB = a.qh + (long long)L.aid[nbd] * V * NST;
+          const double* pb = side ? a.T.psi0 : a.T.psi1;
+#pragma unroll
+          for (int v = 0; v < V; v++) {
+            double t = 0.0;
+#pragma unroll
+            for (int k = 0; k < N; k++) t = fma(pb[k], qB[v * NST + nbase + k * dstr], t);
+            qb[v] = t;
+          }
+        } else {
+          // coarse mother of the virtual neighbour, evaluated at this cell's face point
+          const LevelView& Lm = a.lvm;
+          int cm[3] = {nb[0] / r, nb[1] / r, D == 3 ? nb[2] / r : 0};
+          long long mdi = didx(Lm, cm[0], cm[1], cm[2]);
+          const double* qC = a.qhm + (long long)Lm.aid[mdi] * V * NST;
+          double bas[3][N], bt[N];
+          for (int b = 0; b < D; b++) {
+#pragma unroll
+            for (int l = 0; l < N; l++)
+              bas[b][l] = (b == d) ? (side ? a.T.psi0[l] : a.T.psi1[l])
+                                   : a.T.Pf[ijk[b] - r * cm[b]][jt[b]][l];
+          }
+#pragma unroll
+          for (int l = 0; l < N; l++) bt[l] = a.T.Pf[a.sub][s][l];
+#pragma unroll
+          for (int v = 0; v < V; v++) qb[v] = 0.0;
+          for (int nn = 0; nn < NST; nn++) {
+            int t = nn;
+            double th = 1.0;
+            for (int b = 0; b < D; b++) { th *= bas[b][t % N]; t /= N; }
+            th *= bt[t];
+#pragma unroll
+            for (int v = 0; v < V; v++) qb[v] = fma(th, qC[v * NST + nn], qb[v]);
+          }
+        }
+        if (side) rusanov<PDE, D>(qa, qb, d, f, a.P);
+        else rusanov<PDE, D>(qb, qa, d, f, a.P);
+      }
+#pragma unroll
+      for (int v = 0; v < V; v++) contrib[v] = wgt * f[v];
+    }
+#pragma unroll
+    for (int v = 0; v < V; v++) sh[threadIdx.x * V + v] = contrib[v];
+    __syncthreads();
+    if (ok && g == 0 && kind != FK_SKIP) {
+      double F[V];
+      if (kind == FK_COARSE) {
+        // fine cells of the refined neighbour that touch this face; their memory slot is the
+        // face facing this cell
+        const LevelView& Lc = a.lvc;
+        double acc[V];
+#pragma unroll
+        for (int v = 0; v < V; v++) acc[v] = 0.0;
+        const int nr2 = (D == 3) ? r : 1;
+        int t0 = -1, t1 = -1;
+        for (int b = 0; b < D; b++)
+          if (b != d) { if (t0 < 0) t0 = b; else t1 = b; }
+        for (int c1 = 0; c1 < nr2; c1++)
+          for (int c0 = 0; c0 < r; c0++) {
+            int fc[3] = {0, 0, 0};
+            fc[d] = side ? r * nb[d] : r * nb[d] + r - 1;
+            fc[t0] = r * ijk[t0] + c0;
+            if (D == 3) fc[t1] = r * ijk[t1] + c1;
+            int fa = Lc.aid[didx(Lc, fc[0], fc[1], fc[2])];
+            if (fa < 0) { atomicOr(a.err, 2); continue; }
+            double* m = a.memc + ((long long)fa * 2 * D + 2 * d + (1 - side)) * V;
+#pragma unroll
+            for (int v = 0; v < V; v++) { acc[v] += m[v]; m[v] = 0.0; }
+          }
+#pragma unroll
+        for (int v = 0; v < V; v++) F[v] = acc[v] / (dt * area);
+      } else {
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+          double t = 0.0;
+          for (int gg = 0; gg < NPT; gg++) t += sh[(threadIdx.x + gg) * V + v];
+          F[v] = t;
+        }
+      }
+      double* dst = a.fl + ((long long)cell * 2 * D + 2 * d + side) * V;
+#pragma unroll
+      for (int v = 0; v < V; v++) dst[v] = F[v];
+      if (kind == FK_FINE) {
+        double* m = a.mem + ((long long)cell * 2 * D + 2 * d + side) * V;
+#pragma unroll
+        for (int v = 0; v < V; v++) m[v] += F[v] * dt * area;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Update kernel, Eq. eq:finite_vol (source zero): one thread per active cell.  The high face of
+// axis d is the low face of the +d neighbour when that neighbour is active on this level.
+// ------------------------------------------------------------------------------------------
+template <int D, int M, int PDE>
+__global__ void k_update(HotArgs a) {
+  constexpr int V = nvars(D, PDE);
+  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  if (cell >= a.na) return;
+  const LevelView& L = a.lv;
+  long long di = a.alist[cell];
+  int ijk[3] = {(int)(di % L.L[0]), (int)((di / L.L[0]) % L.L[1]), (int)(di / ((long long)L.L[0] * L.L[1]))};
+  const double dt = a.dtl[a.level];
+  double u[V];
+#pragma unroll
+  for (int v = 0; v < V; v++) u[v] = L.u[v * L.n + di];
+  for (int d = 0; d < D; d++) {
+    const double* flo = a.fl + ((long long)cell * 2 * D + 2 * d) * V;
+    const double* fhi = a.fl + ((long long)cell * 2 * D + 2 * d + 1) * V;
+    int nb[3] = {ijk[0], ijk[1], ijk[2]};
+    if (bcmap(L.L, a.bc, d, ijk[d] + 1, &nb[d])) {
+      long long nd = didx(L, nb[0], nb[1], nb[2]);
+      if (L.st[nd] == 0) fhi = a.fl + ((long long)L.aid[nd] * 2 * D + 2 * d) * V;
+    }
+    const double c = dt / L.dx[d];
+#pragma unroll
+    for (int v = 0; v < V; v++) u[v] -= c * (fhi[v] - flo[v]);
+  }
+#pragma unroll
+  for (int v = 0; v < V; v++) L.u[v * L.n + di] = u[v];
+  if (!Pde<PDE, D>::physical(u, a.P)) atomicOr(a.err, 1);
+}
+
+// ------------------------------------------------------------------------------------------
+// Projection of virtual children (Sec. 3.1.3): child-box average of the mother's space-time
+// polynomial at mother time tau = sub / r; one thread per (virtual cell, variable).
+// With spatial dofs only (predictor == false) the mother's WENO polynomial is projected.
+// ------------------------------------------------------------------------------------------
+template <int D, int M, int PDE>
+__global__ void k_project(HotArgs a, const int32_t* vlist, int nv, const double* src, int spacetime,
+                          double* out_u, int write_dense) {
+  constexpr int N = M + 1, V = nvars(D, PDE), NSP = ipow(N, D), NST = NSP * N;
+  const int it = blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= nv * V) return;
+  const int k = it / V, v = it % V;
+  const LevelView& L = a.lv;
+  const LevelView& Lm = a.lvm;
+  const int r = a.T.r;
+  long long di = vlist[k];
+  int ijk[3] = {(int)(di % L.L[0]), (int)((di / L.L[0]) % L.L[1]), (int)(di / ((long long)L.L[0] * L.L[1]))};
+  int cm[3] = {ijk[0] / r, ijk[1] / r, D == 3 ? ijk[2] / r : 0};
+  int ch[3] = {ijk[0] - r * cm[0], ijk[1] - r * cm[1], D == 3 ? ijk[2] - r * cm[2] : 0};
+  int ma = Lm.aid[didx(Lm, cm[0], cm[1], cm[2])];
+  if (ma < 0) { atomicOr(a.err, 4); return; }
+  double acc = 0.0;
+  if (spacetime) {
+    const double* q = src + ((long long)ma * V + v) * NST;
+    for (int nn = 0; nn < NST; nn++) {
+      int t = nn;
+      double th = 1.0;
+      for (int b = 0; b < D; b++) { th *= a.T.Wc[ch[b]][t % N]; t /= N; }
+      th *= a.T.Pt[a.sub][t];
+      acc = fma(th, q[nn], acc);
+    }
+  } else {
+    const double* q = src + ((long long)ma * V + v) * NSP;
+    for (int nn = 0; nn < NSP; nn++) {
+      int t = nn;
+      double th = 1.0;
+      for (int b = 0; b < D; b++) { th *= a.T.Wc[ch[b]][t % N]; t /= N; }
+      acc = fma(th, q[nn], acc);
+    }
+  }
+  if (write_dense) L.u[v * L.n + di] = acc;
+  else out_u[(long long)k * V + v] = acc;
+}
+
+template <int D, int M, int PDE>
+HotOps make_ops();
+
+}  // namespace aw

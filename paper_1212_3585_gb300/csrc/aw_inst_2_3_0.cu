@@ -1,0 +1,3 @@
+// Hot kernels instantiated for D=2, M=3, PDE=0 (0 Euler, 1 MHD-GLM, 2 linear advection).
+#include "aw_inst.cuh"
+AW_INSTANTIATE(2, 3, 0)

@@ -1,0 +1,24 @@
+// aw_ops.h -- launch table of the templated hot kernels for one (D, M, PDE) configuration.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+
+namespace aw {
+struct HotArgs;
+
+struct HotOps {
+  int D, M, PDE, V, wenoTS;
+  // each launcher returns the number of kernels it launched (0 when there was no work)
+  int (*weno)(const HotArgs&, cudaStream_t);
+  int (*predict)(const HotArgs&, cudaStream_t);
+  int (*flux)(const HotArgs&, cudaStream_t);
+  int (*update)(const HotArgs&, cudaStream_t);
+  // project virtual cells (vlist, nv) from mother dofs `src` (space-time if spacetime != 0,
+  // else spatial WENO dofs), into the dense averages (dense != 0) or into out[k*V + v]
+  int (*project)(const HotArgs&, const int32_t* vlist, int nv, const double* src, int spacetime,
+                 double* out, int dense, cudaStream_t);
+};
+
+// returns false when the configuration is not compiled in
+bool get_ops(int D, int M, int PDE, HotOps* out);
+}  // namespace aw

@@ -1,0 +1,1420 @@
+// aw_solver.cu -- solver state, local time stepping scheduler, AMR bookkeeping kernels and the
+// C ABI of include/aderweno.h.
+//
+// Data layout (GB300-first; one GPU holds the whole mesh): every level l is a dense grid of
+// n*r^l cells per direction (Sec. 3.1: Delta x_l = r Delta x_{l+1}) with a status byte per cell
+// (ST_NONE where no cell exists), the cell averages as a structure of arrays, and an active-id
+// map.  Compact per-level lists (active, virtual child, virtual mother, existing cells, tiles)
+// are rebuilt after every regrid by an order-preserving stream compaction, so every list is in
+// canonical order (k, j, i) and every result is deterministic.  The per-active FP64 arrays
+// (WENO dofs, predictor dofs, face fluxes, memory variables) are indexed by the active id.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "aderweno.h"
+#include "aw_device.cuh"
+#include "aw_ops.h"
+
+namespace aw {
+bool build_tables(int M, int r, Tables* T);
+}
+using namespace aw;
+
+static thread_local std::string g_err = "";
+
+#define AW_FAIL(code, ...)                        \
+  do {                                            \
+    char b_[600];                                 \
+    snprintf(b_, sizeof b_, __VA_ARGS__);         \
+    g_err = b_;                                   \
+    return code;                                  \
+  } while (0)
+#define CK(x)                                                                                          \
+  do {                                                                                                 \
+    cudaError_t e_ = (x);                                                                              \
+    if (e_ != cudaSuccess) AW_FAIL(AW_ECUDA, "%s: %s (%s:%d)", #x, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+#define TRY(x)                \
+  do {                        \
+    int rc_ = (x);            \
+    if (rc_ != AW_OK) return rc_; \
+  } while (0)
+
+static const int CHUNK = 4096;
+
+struct Level {
+  int L[3] = {1, 1, 1};
+  long long n = 0;
+  double dx[3] = {1, 1, 1};
+  int8_t *st = nullptr, *R = nullptr, *nst = nullptr, *flag = nullptr;
+  double *u = nullptr, *chi = nullptr;
+  int32_t *aid = nullptr, *alist = nullptr, *vlist = nullptr, *mlist = nullptr, *clist = nullptr;
+  int na = 0, nv = 0, nm = 0, nc = 0;
+  int tdim[3] = {1, 1, 1};
+  long long ntd = 0;
+  int8_t* tflag = nullptr;
+  int32_t* tiles = nullptr;
+  int ntiles = 0;
+  double *wh = nullptr, *qh = nullptr, *fl = nullptr, *mem = nullptr;
+  long long cap = 0;
+};
+
+struct aw_solver {
+  aw_config cfg;
+  int D, V, N, M, r, lmax, NSP, NST, P;
+  cudaStream_t stream;
+  Tables T;
+  Phys phys;
+  HotOps ops;
+  Level lev[MAXL];
+  double t = 0.0;
+  int ic = -1;
+  std::vector<double> icp;
+  double* d_dtl = nullptr;
+  unsigned long long* d_dtmin = nullptr;
+  int* d_err = nullptr;
+  int* d_cnt = nullptr;
+  int* h_cnt = nullptr;
+  double* h_dtl = nullptr;
+  int* d_bcnt = nullptr;
+  long long bcnt_cap = 0;
+  double* d_buf = nullptr;
+  long long buf_cap = 0;
+  int64_t launches = 0;
+  // optional per-kernel timing with CUDA events on the solver's stream
+  int prof = 0;
+  std::vector<cudaEvent_t> ev_free;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
+  double kind_ms[8] = {0};
+  int64_t kind_n[8] = {0};
+};
+
+enum { KIND_WENO = 0, KIND_PREDICT = 1, KIND_FLUX = 2, KIND_UPDATE = 3, KIND_PROJECT = 4 };
+
+static cudaEvent_t take_event(aw_solver* s) {
+  if (!s->ev_free.empty()) {
+    cudaEvent_t e = s->ev_free.back();
+    s->ev_free.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// run one hot launcher, bracketed by events when profiling
+template <class F>
+static int timed(aw_solver* s, int kind, F&& launch) {
+  if (!s->prof) return launch();
+  cudaEvent_t a = take_event(s), b = take_event(s);
+  cudaEventRecord(a, s->stream);
+  int n = launch();
+  cudaEventRecord(b, s->stream);
+  if (n > 0) s->ev_used.push_back({kind, {a, b}});
+  else { s->ev_free.push_back(a); s->ev_free.push_back(b); }
+  s->kind_n[kind] += n;
+  return n;
+}
+
+static void harvest_events(aw_solver* s) {
+  for (auto& e : s->ev_used) {
+    float ms = 0.f;
+    cudaEventSynchronize(e.second.second);
+    cudaEventElapsedTime(&ms, e.second.first, e.second.second);
+    s->kind_ms[e.first] += ms;
+    s->ev_free.push_back(e.second.first);
+    s->ev_free.push_back(e.second.second);
+  }
+  s->ev_used.clear();
+}
+
+// ------------------------------------------------------------------------------------------
+// runtime-generic device helpers for the bookkeeping kernels
+// ------------------------------------------------------------------------------------------
+struct RtPhys {
+  int pde, D, V;
+  Phys P;
+};
+
+__device__ double rt_pressure(const RtPhys& R, const double* q) {
+  double g = R.P.gamma;
+  if (R.pde == PDE_EULER) {
+    double m2 = 0.0;
+    for (int a = 0; a < R.D; a++) m2 += q[1 + a] * q[1 + a];
+    return (g - 1.0) * (q[R.D + 1] - 0.5 * m2 / q[0]);
+  }
+  if (R.pde == PDE_MHD) {
+    double m2 = q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+    double B2 = q[5] * q[5] + q[6] * q[6] + q[7] * q[7];
+    return (g - 1.0) * (q[4] - 0.5 * m2 / q[0] - 0.5 * B2);
+  }
+  return 1.0;
+}
+
+__device__ double rt_speed(const RtPhys& R, const double* q, int n) {
+  if (R.pde == PDE_LINADV) return fabs(R.P.adv[n]);
+  double p = rt_pressure(R, q);
+  double vn = fabs(q[1 + n] / q[0]);
+  if (R.pde == PDE_EULER) {
+    double c2 = R.P.gamma * p / q[0];
+    return c2 >= 0.0 ? vn + sqrt(c2) : sqrt(vn * vn - c2);
+  }
+  double a2 = R.P.gamma * p / q[0];
+  double B2 = q[5] * q[5] + q[6] * q[6] + q[7] * q[7];
+  double b2 = B2 / q[0], bn2 = q[5 + n] * q[5 + n] / q[0];
+  double s = a2 + b2;
+  double c = vn + sqrt(0.5 * (s + sqrt(s * s - 4.0 * a2 * bn2)));
+  return c > R.P.c_h ? c : R.P.c_h;
+}
+
+__device__ __forceinline__ void cell_coords(const LevelView& L, long long di, int* ijk) {
+  ijk[0] = (int)(di % L.L[0]);
+  ijk[1] = (int)((di / L.L[0]) % L.L[1]);
+  ijk[2] = (int)(di / ((long long)L.L[0] * L.L[1]));
+}
+
+// ---- initial conditions (Sec. 4) ----
+struct IcArgs {
+  int kind, np;
+  double p[128];
+  RtPhys R;
+  double lo[3], hi[3];
+  double x[MAXN], w[MAXN];
+  int N;
+};
+
+__device__ void ic_point(const IcArgs& I, const double* x, double* q) {
+  const int D = I.R.D, V = I.R.V;
+  double w[MAXV];
+  for (int v = 0; v < MAXV; v++) w[v] = 0.0;
+  const double* p = I.p;
+  const double g = I.R.P.gamma;
+  const int ip = (I.R.pde == PDE_EULER) ? D + 1 : 4;  // index of the pressure in the primitive state
+  switch (I.kind) {
+    case AW_IC_CONST:
+      for (int v = 0; v < V; v++) w[v] = p[v];
+      break;
+    case AW_IC_VORTEX: {
+      double dx = x[0] - p[1], dy = x[1] - p[2], r2 = dx * dx + dy * dy;
+      double dT = -p[0] * p[0] * (g - 1.0) / (8.0 * g * M_PI * M_PI) * exp(1.0 - r2);
+      double e = p[0] / (2.0 * M_PI) * exp(0.5 * (1.0 - r2));
+      w[0] = p[3] * pow(1.0 + dT, 1.0 / (g - 1.0));
+      w[1] = p[4] - dy * e;
+      w[2] = p[5] + dx * e;
+      w[ip] = p[6] * pow(1.0 + dT, g / (g - 1.0));
+      break;
+    }
+    case AW_IC_EXPLOSION: {
+      double r2 = 0.0;
+      for (int a = 0; a < D; a++) r2 += x[a] * x[a];
+      bool in = sqrt(r2) <= p[0];
+      w[0] = in ? p[1] : p[3];
+      w[ip] = in ? p[2] : p[4];
+      break;
+    }
+    case AW_IC_OT:
+      w[0] = g * g; w[1] = -sin(x[1]); w[2] = sin(x[0]); w[3] = 0.0; w[4] = g;
+      w[5] = -sin(x[1]); w[6] = sin(2.0 * x[0]); w[7] = 0.0; w[8] = 0.0;
+      break;
+    case AW_IC_RP4: {
+      int qd = (x[0] > p[0]) ? ((x[1] > p[1]) ? 0 : 3) : ((x[1] > p[1]) ? 1 : 2);
+      const double* s = p + 2 + 4 * qd;
+      w[0] = s[0]; w[1] = s[1]; w[2] = s[2]; w[ip] = s[3];
+      break;
+    }
+    case AW_IC_FOURIER: {
+      for (int v = 0; v < V; v++) w[v] = p[v];
+      int nm = (int)p[V];
+      for (int m = 0; m < nm; m++) {
+        const double* md = p + V + 1 + 6 * m;
+        double ph = md[5];
+        for (int a = 0; a < D; a++) ph += 2.0 * M_PI * md[1 + a] * (x[a] - I.lo[a]) / (I.hi[a] - I.lo[a]);
+        w[(int)md[0]] += md[4] * sin(ph);
+      }
+      break;
+    }
+  }
+  // primitive -> conserved
+  if (I.R.pde == PDE_LINADV) { q[0] = w[0]; return; }
+  if (I.R.pde == PDE_EULER) {
+    double ke = 0.0;
+    q[0] = w[0];
+    for (int a = 0; a < D; a++) { q[1 + a] = w[0] * w[1 + a]; ke += w[1 + a] * w[1 + a]; }
+    q[D + 1] = w[D + 1] / (g - 1.0) + 0.5 * w[0] * ke;
+    return;
+  }
+  double v2 = w[1] * w[1] + w[2] * w[2] + w[3] * w[3];
+  double B2 = w[5] * w[5] + w[6] * w[6] + w[7] * w[7];
+  q[0] = w[0]; q[1] = w[0] * w[1]; q[2] = w[0] * w[2]; q[3] = w[0] * w[3];
+  q[4] = w[4] / (g - 1.0) + 0.5 * w[0] * v2 + 0.5 * B2;
+  q[5] = w[5]; q[6] = w[6]; q[7] = w[7]; q[8] = w[8];
+}
+
+// IC cell averages by the (M+1)^d-point Gauss rule.  mode 0: every existing cell; mode 1: cells
+// that exist in `stn` but not in `sto` (new cells of an initial-condition regrid).
+__global__ void k_ic(LevelView L, IcArgs I, const int8_t* sto, const int8_t* stn, int mode) {
+  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.n) return;
+  if (mode == 0 && L.st[c] == ST_NONE) return;
+  if (mode == 1 && !(sto[c] == ST_NONE && stn[c] != ST_NONE)) return;
+  int ijk[3];
+  cell_coords(L, c, ijk);
+  const int D = I.R.D, V = I.R.V, N = I.N;
+  double acc[MAXV];
+  for (int v = 0; v < V; v++) acc[v] = 0.0;
+  int nq = 1;
+  for (int a = 0; a < D; a++) nq *= N;
+  for (int g = 0; g < nq; g++) {
+    int t = g;
+    double x[3] = {0, 0, 0}, wt = 1.0, q[MAXV];
+    for (int a = 0; a < D; a++) {
+      int gi = t % N;
+      t /= N;
+      x[a] = I.lo[a] + (ijk[a] + I.x[gi]) * L.dx[a];
+      wt *= I.w[gi];
+    }
+    ic_point(I, x, q);
+    for (int v = 0; v < V; v++) acc[v] += wt * q[v];
+  }
+  for (int v = 0; v < V; v++) L.u[v * L.n + c] = acc[v];
+}
+
+// ---- CFL time step: min over active cells of r^l * CFL / sum_d(s_d / dx_d) ----
+__global__ void k_dt(LevelView L, const int32_t* alist, int na, RtPhys R, double cfl, double rl,
+                     unsigned long long* out) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  double dt = 1e300;
+  if (k < na) {
+    long long di = alist[k];
+    double q[MAXV];
+    for (int v = 0; v < R.V; v++) q[v] = L.u[v * L.n + di];
+    double den = 0.0;
+    for (int a = 0; a < R.D; a++) den += rt_speed(R, q, a) / L.dx[a];
+    dt = rl * cfl / den;
+    if (!(dt > 0.0)) dt = 0.0;  // NaN or negative: report a zero step
+  }
+  for (int o = 16; o > 0; o >>= 1) dt = fmin(dt, __shfl_xor_sync(0xffffffffu, dt, o));
+  if ((threadIdx.x & 31) == 0 && dt < 1e300) atomicMin(out, (unsigned long long)__double_as_longlong(dt));
+}
+
+// ---- averaging (Eq. eqn.average): virtual mothers of level l from level l+1, children summed in
+// canonical order ----
+__global__ void k_average(LevelView L, LevelView Lc, const int32_t* mlist, int nm, int V, int D, int r) {
+  int it = blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= nm * V) return;
+  int k = it / V, v = it % V;
+  long long di = mlist[k];
+  int ijk[3];
+  cell_coords(L, di, ijk);
+  double s = 0.0;
+  int rz = D == 3 ? r : 1;
+  for (int kk = 0; kk < rz; kk++)
+    for (int jj = 0; jj < r; jj++)
+      for (int ii = 0; ii < r; ii++)
+        s += Lc.u[v * Lc.n + didx(Lc, r * ijk[0] + ii, r * ijk[1] + jj, D == 3 ? r * ijk[2] + kk : 0)];
+  double rd = 1.0;
+  for (int a = 0; a < D; a++) rd *= r;
+  L.u[v * L.n + di] = s / rd;
+}
+
+// ---- refinement indicator (Eq. eqn.indicator), Phi = rho, undivided differences on the 3^d
+// same-level box; see the solver documentation for the discrete form ----
+__device__ __forceinline__ double phi(const LevelView& L, const int* bc, const int* ijk, int D, int a, int sa, int b,
+                                      int sb) {
+  int c[3] = {ijk[0], ijk[1], ijk[2]};
+  c[a] += sa;
+  c[b] += sb;
+  int m[3] = {0, 0, 0};
+  for (int e = 0; e < D; e++) bcmap(L.L, bc, e, c[e], &m[e]);
+  return L.u[didx(L, m[0], m[1], m[2])];
+}
+
+__global__ void k_indicator(LevelView L, Bc6 bc6, int D, double eps, double* chi) {
+  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.n) return;
+  int8_t s = L.st[c];
+  if (s != 0 && s != -1) { chi[c] = 0.0; return; }
+  int ijk[3];
+  cell_coords(L, c, ijk);
+  const int* bc = bc6.v;
+  double P0 = L.u[c], num = 0.0, den = 0.0;
+  for (int k = 0; k < D; k++)
+    for (int l = 0; l < D; l++) {
+      double d2, g, a;
+      if (k == l) {
+        double Pp = phi(L, bc, ijk, D, k, 1, k, 0), Pm = phi(L, bc, ijk, D, k, -1, k, 0);
+        d2 = Pp - 2.0 * P0 + Pm;
+        g = fabs(Pp - P0) + fabs(P0 - Pm);
+        a = fabs(Pp) + 2.0 * fabs(P0) + fabs(Pm);
+      } else {
+        double Ppp = phi(L, bc, ijk, D, k, 1, l, 1), Ppm = phi(L, bc, ijk, D, k, 1, l, -1);
+        double Pmp = phi(L, bc, ijk, D, k, -1, l, 1), Pmm = phi(L, bc, ijk, D, k, -1, l, -1);
+        d2 = (Ppp - Ppm - Pmp + Pmm) / 4.0;
+        g = (fabs(Ppp - Pmp) + fabs(Ppm - Pmm)) / 4.0;
+        a = (fabs(Ppp) + fabs(Ppm) + fabs(Pmp) + fabs(Pmm)) / 4.0;
+      }
+      num += d2 * d2;
+      double e = g + eps * a;
+      den += e * e;
+    }
+  chi[c] = den > 0.0 ? sqrt(num / den) : 0.0;
+}
+
+__global__ void k_flags_from_chi(LevelView L, const double* chi, int is_below_lmax, double chi_ref, double chi_rec,
+                                 int8_t* flag) {
+  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.n) return;
+  int8_t f = 0;
+  if (is_below_lmax) {
+    if (L.st[c] == 0 && chi[c] > chi_ref) f = 1;
+    if (L.st[c] == -1 && chi[c] < chi_rec) f = -1;
+  }
+  flag[c] = f;
+}
+
+// R (cells with children of status <= 0) after the flags: refine active cells flagged +1
+// below lmax; drop virtual mothers flagged -1 whose children are all active, none flagged +1,
+// with no grandchildren of any status (rule 7).
+__global__ void k_rinit(LevelView L, LevelView Lc, LevelView Lg, const int8_t* flag, const int8_t* cflag,
+                        int below_lmax, int has_grand, int D, int r, int8_t* R) {
+  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.n) return;
+  int8_t s = L.st[c];
+  int8_t v = (s == -1);
+  if (below_lmax) {
+    if (flag[c] == 1 && s == 0) v = 1;
+    if (flag[c] == -1 && s == -1) {
+      int ijk[3];
+      cell_coords(L, c, ijk);
+      bool ok = true;
+      int rz = D == 3 ? r : 1;
+      for (int kk = 0; kk < rz && ok; kk++)
+        for (int jj = 0; jj < r && ok; jj++)
+          for (int ii = 0; ii < r && ok; ii++) {
+            int cc[3] = {r * ijk[0] + ii, r * ijk[1] + jj, D == 3 ? r * ijk[2] + kk : 0};
+            long long cd = didx(Lc, cc[0], cc[1], cc[2]);
+            if (Lc.st[cd] != 0 || cflag[cd] == 1) ok = false;
+            else if (has_grand &&
+                     Lg.st[didx(Lg, r * cc[0], r * cc[1], D == 3 ? r * cc[2] : 0)] != ST_NONE)
+              ok = false;
+          }
+      if (ok) v = 0;
+    }
+  } else {
+    v = 0;
+  }
+  R[c] = v;
+}
+
+// closure under rules 4-5: every Voronoi neighbour of a cell in R (level l >= 1) gets its mother
+// into R (level l-1)
+__global__ void k_closure(LevelView L, LevelView Lm, Bc6 bc6, const int8_t* R, int8_t* Rm, int D, int r) {
+  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.n || !R[c]) return;
+  int ijk[3];
+  cell_coords(L, c, ijk);
+  int kz0 = D == 3 ? -1 : 0, kz1 = D == 3 ? 1 : 0;
+  for (int oz = kz0; oz <= kz1; oz++)
+    for (int oy = -1; oy <= 1; oy++)
+      for (int ox = -1; ox <= 1; ox++) {
+        if (!ox && !oy && !oz) continue;
+        int nb[3] = {ijk[0] + ox, ijk[1] + oy, ijk[2] + oz};
+        bool in = true;
+        for (int a = 0; a < D; a++) in &= bcmap(L.L, bc6.v, a, nb[a], &nb[a]);
+        if (!in) continue;
+        Rm[didx(Lm, nb[0] / r, nb[1] / r, D == 3 ? nb[2] / r : 0)] = 1;
+      }
+}
+
+// new statuses: -1 in R; 0 if the mother is in R (or level 0); 1 if the mother is active and
+// has a Voronoi neighbour in R; otherwise no cell
+__global__ void k_newstatus(LevelView L, LevelView Lm, Bc6 bc6, const int8_t* R, const int8_t* Rm,
+                            const int8_t* nstm, int level, int D, int r, int8_t* nst) {
+  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.n) return;
+  if (level == 0) { nst[c] = R[c] ? -1 : 0; return; }
+  int ijk[3];
+  cell_coords(L, c, ijk);
+  int mi[3] = {ijk[0] / r, ijk[1] / r, D == 3 ? ijk[2] / r : 0};
+  long long m = didx(Lm, mi[0], mi[1], mi[2]);
+  int8_t s = ST_NONE;
+  if (Rm[m]) s = R[c] ? -1 : 0;
+  else if (nstm[m] == 0) {
+    bool has = false;
+    int kz0 = D == 3 ? -1 : 0, kz1 = D == 3 ? 1 : 0;
+    for (int oz = kz0; oz <= kz1 && !has; oz++)
+      for (int oy = -1; oy <= 1 && !has; oy++)
+        for (int ox = -1; ox <= 1 && !has; ox++) {
+          if (!ox && !oy && !oz) continue;
+          int nb[3] = {mi[0] + ox, mi[1] + oy, mi[2] + oz};
+          bool in = true;
+          for (int a = 0; a < D; a++) in &= bcmap(Lm.L, bc6.v, a, nb[a], &nb[a]);
+          if (in && Rm[didx(Lm, nb[0], nb[1], nb[2])]) has = true;
+        }
+    if (has) s = 1;
+  }
+  nst[c] = s;
+}
+
+// newly active cells (new, or virtual before the edit) take the child-box average of the
+// mother's WENO polynomial (mother active before the edit; its pre-edit active id is used)
+__global__ void k_newvalues(LevelView L, LevelView Lm, const int8_t* nst, const double* whm, Tables T, int D, int V,
+                            int* err) {
+  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.n) return;
+  int8_t o = L.st[c], n = nst[c];
+  if (!(n == 0 || n == -1) || !(o == ST_NONE || o == 1)) return;
+  int r = T.r, N = T.N;
+  int ijk[3];
+  cell_coords(L, c, ijk);
+  int mi[3] = {ijk[0] / r, ijk[1] / r, D == 3 ? ijk[2] / r : 0};
+  int ch[3] = {ijk[0] - r * mi[0], ijk[1] - r * mi[1], D == 3 ? ijk[2] - r * mi[2] : 0};
+  int ma = Lm.aid[didx(Lm, mi[0], mi[1], mi[2])];
+  if (ma < 0) { atomicOr(err, 8); return; }
+  int nsp = 1;
+  for (int a = 0; a < D; a++) nsp *= N;
+  for (int v = 0; v < V; v++) {
+    const double* q = whm + ((long long)ma * V + v) * nsp;
+    double acc = 0.0;
+    for (int nn = 0; nn < nsp; nn++) {
+      int t = nn;
+      double th = 1.0;
+      for (int b = 0; b < D; b++) { th *= T.Wc[ch[b]][t % N]; t /= N; }
+      acc = fma(th, q[nn], acc);
+    }
+    L.u[v * L.n + c] = acc;
+  }
+}
+
+__global__ void k_commit(LevelView L, const int8_t* nst, int8_t* st, int V) {
+  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.n) return;
+  st[c] = nst[c];
+  if (nst[c] == ST_NONE)
+    for (int v = 0; v < V; v++) L.u[v * L.n + c] = 0.0;
+}
+
+// virtual children hold their mother's average until the next projection
+__global__ void k_virtual_from_mother(LevelView L, LevelView Lm, int D, int V, int r) {
+  long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= L.n || L.st[c] != 1) return;
+  int ijk[3];
+  cell_coords(L, c, ijk);
+  long long m = didx(Lm, ijk[0] / r, ijk[1] / r, D == 3 ? ijk[2] / r : 0);
+  for (int v = 0; v < V; v++) L.u[v * L.n + c] = Lm.u[v * Lm.n + m];
+}
+
+// ---- order-preserving stream compaction of a dense int8 array ----
+// mode 0: a == val; mode 1: a != ST_NONE; mode 2: a != 0
+__device__ __forceinline__ bool cpred(int8_t x, int mode, int val) {
+  return mode == 0 ? x == val : (mode == 1 ? x != ST_NONE : x != 0);
+}
+
+__global__ void k_ccount(const int8_t* a, long long n, int mode, int val, int* bcnt) {
+  long long base = (long long)blockIdx.x * CHUNK;
+  int c = 0;
+  for (int i = threadIdx.x; i < CHUNK; i += blockDim.x) {
+    long long k = base + i;
+    if (k < n && cpred(a[k], mode, val)) c++;
+  }
+  for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+  __shared__ int ws[32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int s = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += ws[w];
+    bcnt[blockIdx.x] = s;
+  }
+}
+
+__global__ void k_cscan(int* b, int nb, int* total) {
+  __shared__ int s[1024];
+  int carry = 0;
+  for (int base = 0; base < nb; base += 1024) {
+    int i = base + threadIdx.x;
+    int v = i < nb ? b[i] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+      int t = threadIdx.x >= off ? s[threadIdx.x - off] : 0;
+      __syncthreads();
+      s[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (i < nb) b[i] = carry + s[threadIdx.x] - v;
+    int tot = s[1023];
+    __syncthreads();
+    carry += tot;
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void k_cscatter(const int8_t* a, long long n, int mode, int val, const int* boff, int32_t* list,
+                           int32_t* idmap) {
+  __shared__ int ws[32];
+  __shared__ int wo[32];
+  long long base = (long long)blockIdx.x * CHUNK;
+  int off = boff[blockIdx.x];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i0 = 0; i0 < CHUNK; i0 += blockDim.x) {
+    long long k = base + i0 + threadIdx.x;
+    bool f = k < n && cpred(a[k], mode, val);
+    unsigned b = __ballot_sync(0xffffffffu, f);
+    if (lane == 0) ws[wid] = __popc(b);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int s = 0;
+      for (int w = 0; w < nw; w++) { wo[w] = s; s += ws[w]; }
+      ws[31] = s;
+    }
+    __syncthreads();
+    int pos = off + wo[wid] + __popc(b & ((1u << lane) - 1u));
+    if (f) {
+      list[pos] = (int32_t)k;
+      if (idmap) idmap[k] = pos;
+    } else if (idmap && k < n) {
+      idmap[k] = -1;
+    }
+    off += ws[31];
+    __syncthreads();
+  }
+}
+
+__global__ void k_tmark(LevelView L, const int32_t* alist, int na, int TS, int t0, int t1, int8_t* tflag) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= na) return;
+  int ijk[3];
+  cell_coords(L, alist[k], ijk);
+  long long t = ((long long)(ijk[2] / TS) * t1 + ijk[1] / TS) * t0 + ijk[0] / TS;
+  tflag[t] = 1;
+}
+
+// canonical gather / scatter of cell averages and metadata
+__global__ void k_gather(LevelView L, const int32_t* clist, int nc, int V, double* out, aw_cell* meta, int level) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nc) return;
+  long long di = clist[k];
+  for (int v = 0; v < V; v++) out[(long long)k * V + v] = L.u[v * L.n + di];
+  if (meta) {
+    int ijk[3];
+    cell_coords(L, di, ijk);
+    meta[k].level = level;
+    meta[k].status = L.st[di];
+    meta[k].i = ijk[0];
+    meta[k].j = ijk[1];
+    meta[k].k = ijk[2];
+  }
+}
+__global__ void k_scatter(LevelView L, const int32_t* clist, int nc, int V, const double* in) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nc) return;
+  long long di = clist[k];
+  for (int v = 0; v < V; v++) L.u[v * L.n + di] = in[(long long)k * V + v];
+}
+__global__ void k_gather_d(const double* src, const int32_t* clist, int nc, double* out) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nc) out[k] = src[clist[k]];
+}
+__global__ void k_gather_i8(const int8_t* src, const int32_t* clist, int nc, int8_t* out) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nc) out[k] = src[clist[k]];
+}
+__global__ void k_scatter_i8(int8_t* dst, const int32_t* clist, int nc, const int8_t* in) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < nc) dst[clist[k]] = in[k];
+}
+// per-block partial sums of the active cells' averages (fixed reduction order)
+__global__ void k_partial(LevelView L, const int32_t* alist, int na, int V, double* part) {
+  __shared__ double sh[256];
+  for (int v = 0; v < V; v++) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    sh[threadIdx.x] = k < na ? L.u[v * L.n + alist[k]] : 0.0;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+      if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) part[(long long)blockIdx.x * V + v] = sh[0];
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// host helpers
+// ------------------------------------------------------------------------------------------
+static inline unsigned nblk(long long n, int b) { return (unsigned)((n + b - 1) / b); }
+
+static LevelView view(const aw_solver* s, int l) {
+  LevelView v;
+  const Level& L = s->lev[l];
+  for (int a = 0; a < 3; a++) { v.L[a] = L.L[a]; v.dx[a] = L.dx[a]; }
+  v.n = L.n;
+  v.st = L.st;
+  v.u = L.u;
+  v.aid = L.aid;
+  return v;
+}
+
+static Bc6 bc6_of(const aw_solver* s) {
+  Bc6 b;
+  for (int i = 0; i < 6; i++) b.v[i] = s->cfg.bc[i];
+  return b;
+}
+
+static RtPhys rtphys(const aw_solver* s) {
+  RtPhys R;
+  R.pde = s->cfg.pde;
+  R.D = s->D;
+  R.V = s->V;
+  R.P = s->phys;
+  return R;
+}
+
+static int ensure_buf(aw_solver* s, long long ndouble) {
+  if (ndouble <= s->buf_cap) return AW_OK;
+  if (s->d_buf) cudaFree(s->d_buf);
+  s->d_buf = nullptr;
+  long long cap = std::max(ndouble, (long long)1024);
+  if (cudaMalloc(&s->d_buf, cap * sizeof(double)) != cudaSuccess) AW_FAIL(AW_ENOMEM, "staging buffer of %lld doubles", cap);
+  s->buf_cap = cap;
+  return AW_OK;
+}
+
+// compact a dense int8 array into list (+ idmap); the count lands in d_cnt[slot]
+static int compact(aw_solver* s, const int8_t* a, long long n, int mode, int val, int32_t* list, int32_t* idmap,
+                   int slot) {
+  long long nb = (n + CHUNK - 1) / CHUNK;
+  if (nb > s->bcnt_cap) {
+    if (s->d_bcnt) cudaFree(s->d_bcnt);
+    s->d_bcnt = nullptr;
+    if (cudaMalloc(&s->d_bcnt, nb * sizeof(int)) != cudaSuccess) AW_FAIL(AW_ENOMEM, "scan scratch");
+    s->bcnt_cap = nb;
+  }
+  k_ccount<<<(unsigned)nb, 256, 0, s->stream>>>(a, n, mode, val, s->d_bcnt);
+  k_cscan<<<1, 1024, 0, s->stream>>>(s->d_bcnt, (int)nb, s->d_cnt + slot);
+  k_cscatter<<<(unsigned)nb, 256, 0, s->stream>>>(a, n, mode, val, s->d_bcnt, list, idmap);
+  s->launches += 3;
+  CK(cudaGetLastError());
+  return AW_OK;
+}
+
+static int ensure_active_cap(aw_solver* s, int l, long long need) {
+  Level& L = s->lev[l];
+  if (need <= L.cap) return AW_OK;
+  long long cap = std::max(need + need / 2, (long long)64);
+  cudaFree(L.wh); cudaFree(L.qh); cudaFree(L.fl); cudaFree(L.mem);
+  L.wh = L.qh = L.fl = L.mem = nullptr;
+  L.cap = 0;
+  size_t V = s->V;
+  if (cudaMalloc(&L.wh, cap * V * s->NSP * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&L.qh, cap * V * s->NST * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&L.fl, cap * 2 * s->D * V * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(&L.mem, cap * 2 * s->D * V * sizeof(double)) != cudaSuccess)
+    AW_FAIL(AW_ENOMEM, "per-active arrays of level %d (%lld cells)", l, cap);
+  L.cap = cap;
+  return AW_OK;
+}
+
+// rebuild every per-level list and read the counts back
+static int rebuild_lists(aw_solver* s) {
+  for (int l = 0; l <= s->lmax; l++) {
+    Level& L = s->lev[l];
+    TRY(compact(s, L.st, L.n, 0, 0, L.alist, L.aid, 5 * l + 0));
+    TRY(compact(s, L.st, L.n, 0, 1, L.vlist, nullptr, 5 * l + 1));
+    TRY(compact(s, L.st, L.n, 0, -1, L.mlist, nullptr, 5 * l + 2));
+    TRY(compact(s, L.st, L.n, 1, 0, L.clist, nullptr, 5 * l + 3));
+  }
+  CK(cudaMemcpyAsync(s->h_cnt, s->d_cnt, sizeof(int) * 5 * MAXL, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  for (int l = 0; l <= s->lmax; l++) {
+    Level& L = s->lev[l];
+    L.na = s->h_cnt[5 * l + 0];
+    L.nv = s->h_cnt[5 * l + 1];
+    L.nm = s->h_cnt[5 * l + 2];
+    L.nc = s->h_cnt[5 * l + 3];
+    CK(cudaMemsetAsync(L.tflag, 0, L.ntd, s->stream));
+    if (L.na > 0) {
+      k_tmark<<<nblk(L.na, 256), 256, 0, s->stream>>>(view(s, l), L.alist, L.na, s->ops.wenoTS, L.tdim[0], L.tdim[1],
+                                                      L.tflag);
+      s->launches++;
+    }
+    TRY(compact(s, L.tflag, L.ntd, 2, 0, L.tiles, nullptr, 5 * l + 4));
+    TRY(ensure_active_cap(s, l, L.na));
+    CK(cudaMemsetAsync(L.mem, 0, (size_t)L.cap * 2 * s->D * s->V * sizeof(double), s->stream));
+  }
+  CK(cudaMemcpyAsync(s->h_cnt, s->d_cnt, sizeof(int) * 5 * MAXL, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  for (int l = 0; l <= s->lmax; l++) s->lev[l].ntiles = s->h_cnt[5 * l + 4];
+  return AW_OK;
+}
+
+static HotArgs make_args(const aw_solver* s, int l, int sub) {
+  HotArgs a;
+  memset(&a, 0, sizeof a);
+  a.T = s->T;
+  a.P = s->phys;
+  for (int i = 0; i < 6; i++) a.bc[i] = s->cfg.bc[i];
+  a.level = l;
+  a.sub = sub;
+  a.picard = s->P;
+  a.lv = view(s, l);
+  if (l >= 1) a.lvm = view(s, l - 1);
+  if (l < s->lmax) a.lvc = view(s, l + 1);
+  const Level& L = s->lev[l];
+  a.alist = L.alist;
+  a.na = L.na;
+  a.tiles = L.tiles;
+  a.ntiles = L.ntiles;
+  for (int i = 0; i < 3; i++) a.tdim[i] = L.tdim[i];
+  a.wh = L.wh;
+  a.qh = L.qh;
+  a.fl = L.fl;
+  a.mem = L.mem;
+  if (l >= 1) a.qhm = s->lev[l - 1].qh;
+  if (l < s->lmax) a.memc = s->lev[l + 1].mem;
+  a.dtl = s->d_dtl;
+  a.err = s->d_err;
+  return a;
+}
+
+static int average_into(aw_solver* s, int l) {
+  Level& L = s->lev[l];
+  if (L.nm == 0) return AW_OK;
+  k_average<<<nblk((long long)L.nm * s->V, 128), 128, 0, s->stream>>>(view(s, l), view(s, l + 1), L.mlist, L.nm, s->V,
+                                                                   s->D, s->r);
+  s->launches++;
+  CK(cudaGetLastError());
+  return AW_OK;
+}
+
+static int average_all(aw_solver* s) {
+  for (int l = s->lmax - 1; l >= 0; l--) TRY(average_into(s, l));
+  return AW_OK;
+}
+
+// one step of level l (Eq. eqn.update.criterion by recursion): reconstruction and prediction of
+// level l, then r sub-steps of level l+1, then the fluxes and update of level l
+static int advance(aw_solver* s, int l, int sub) {
+  HotArgs a = make_args(s, l, sub);
+  const Level& L = s->lev[l];
+  cudaStream_t st = s->stream;
+  if (l >= 1)
+    s->launches += timed(s, KIND_PROJECT, [&] { return s->ops.project(a, L.vlist, L.nv, s->lev[l - 1].qh, 1, nullptr, 1, st); });
+  s->launches += timed(s, KIND_WENO, [&] { return s->ops.weno(a, st); });
+  s->launches += timed(s, KIND_PREDICT, [&] { return s->ops.predict(a, st); });
+  CK(cudaGetLastError());
+  if (l < s->lmax)
+    for (int k = 0; k < s->r; k++) TRY(advance(s, l + 1, k));
+  s->launches += timed(s, KIND_FLUX, [&] { return s->ops.flux(a, st); });
+  s->launches += timed(s, KIND_UPDATE, [&] { return s->ops.update(a, st); });
+  CK(cudaGetLastError());
+  if (l >= 1 && sub == s->r - 1) TRY(average_into(s, l - 1));
+  return AW_OK;
+}
+
+static int compute_dt(aw_solver* s, double* dt) {
+  double big = 1e300;
+  CK(cudaMemcpyAsync(s->d_dtmin, &big, sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  double rl = 1.0;
+  for (int l = 0; l <= s->lmax; l++) {
+    const Level& L = s->lev[l];
+    if (L.na > 0) {
+      k_dt<<<nblk(L.na, 256), 256, 0, s->stream>>>(view(s, l), L.alist, L.na, rtphys(s), s->cfg.cfl, rl, s->d_dtmin);
+      s->launches++;
+    }
+    rl *= s->r;
+  }
+  CK(cudaGetLastError());
+  double h;
+  CK(cudaMemcpyAsync(&h, s->d_dtmin, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  if (!(h > 0.0) || h >= 1e300) AW_FAIL(AW_ENONPHYSICAL, "no positive stable time step (dt = %g)", h);
+  *dt = h;
+  return AW_OK;
+}
+
+static int step_dt(aw_solver* s, double dt0, aw_stats* st) {
+  double dt = dt0;
+  for (int l = 0; l < MAXL; l++) {
+    s->h_dtl[l] = dt;
+    dt /= s->r;
+  }
+  CK(cudaMemcpyAsync(s->d_dtl, s->h_dtl, sizeof(double) * MAXL, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream));
+  TRY(advance(s, 0, 0));
+  int err = 0;
+  CK(cudaMemcpyAsync(s->h_cnt + 5 * MAXL, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  err = s->h_cnt[5 * MAXL];
+  int64_t rl = 1;
+  for (int l = 0; l <= s->lmax; l++) {
+    int64_t u = (int64_t)s->lev[l].na * rl;
+    if (st) { st->cell_updates += u; st->updates_per_level[l] += u; }
+    rl *= s->r;
+  }
+  if (st) { st->level0_steps++; st->last_dt0 = dt0; }
+  if (err & 1) AW_FAIL(AW_ENONPHYSICAL, "non-physical state (rho <= 0, p <= 0 or NaN) after the update");
+  if (err) AW_FAIL(AW_ESTATE, "inconsistent mesh detected on the device (error word %d)", err);
+  return AW_OK;
+}
+
+// regrid pre-pass (at a synchronisation time): WENO polynomials of the active cells of levels
+// 0..lmax-1 top-down, virtual children of levels 1..lmax-1 filled from their mothers' WENO
+// polynomials; then the indicator on levels 0..lmax-1
+static int regrid_prepass(aw_solver* s, int init_mode) {
+  if (!init_mode) {
+    for (int l = 0; l < s->lmax; l++) {
+      HotArgs a = make_args(s, l, 0);
+      s->launches += s->ops.weno(a, s->stream);
+      if (l + 1 < s->lmax) {
+        HotArgs b = make_args(s, l + 1, 0);
+        s->launches += s->ops.project(b, s->lev[l + 1].vlist, s->lev[l + 1].nv, s->lev[l].wh, 0, nullptr, 1, s->stream);
+      }
+    }
+  }
+  for (int l = 0; l < s->lmax; l++) {
+    Level& L = s->lev[l];
+    k_indicator<<<nblk(L.n, 256), 256, 0, s->stream>>>(view(s, l), bc6_of(s), s->D, s->cfg.eps_ind, L.chi);
+    s->launches++;
+  }
+  CK(cudaGetLastError());
+  return AW_OK;
+}
+
+static IcArgs ic_args(const aw_solver* s) {
+  IcArgs I;
+  memset(&I, 0, sizeof I);
+  I.kind = s->ic;
+  I.np = (int)std::min<size_t>(s->icp.size(), 128);
+  for (int i = 0; i < I.np; i++) I.p[i] = s->icp[i];
+  I.R = rtphys(s);
+  for (int a = 0; a < 3; a++) { I.lo[a] = s->cfg.lo[a]; I.hi[a] = s->cfg.hi[a]; }
+  for (int i = 0; i < s->N; i++) { I.x[i] = s->T.x[i]; I.w[i] = s->T.w[i]; }
+  I.N = s->N;
+  return I;
+}
+
+// apply the dense flags of every level (L.flag) and rebuild the tree
+static int apply_flags(aw_solver* s, int init_mode) {
+  const int lmax = s->lmax;
+  if (lmax == 0) return AW_OK;
+  Bc6 bc = bc6_of(s);
+  for (int l = 0; l <= lmax; l++) {
+    Level& L = s->lev[l];
+    LevelView Lc = l < lmax ? view(s, l + 1) : view(s, l);
+    LevelView Lg = l + 2 <= lmax ? view(s, l + 2) : view(s, l);
+    const int8_t* cflag = l < lmax ? s->lev[l + 1].flag : L.flag;
+    k_rinit<<<nblk(L.n, 256), 256, 0, s->stream>>>(view(s, l), Lc, Lg, L.flag, cflag, l < lmax, l + 2 <= lmax, s->D,
+                                                   s->r, L.R);
+    s->launches++;
+  }
+  for (int l = lmax - 1; l >= 1; l--) {
+    k_closure<<<nblk(s->lev[l].n, 256), 256, 0, s->stream>>>(view(s, l), view(s, l - 1), bc, s->lev[l].R,
+                                                             s->lev[l - 1].R, s->D, s->r);
+    s->launches++;
+  }
+  for (int l = 0; l <= lmax; l++) {
+    Level& L = s->lev[l];
+    const Level& Lm = s->lev[l > 0 ? l - 1 : 0];
+    k_newstatus<<<nblk(L.n, 256), 256, 0, s->stream>>>(view(s, l), view(s, l > 0 ? l - 1 : 0), bc, L.R, Lm.R, Lm.nst,
+                                                       l, s->D, s->r, L.nst);
+    s->launches++;
+  }
+  CK(cudaGetLastError());
+  // values of cells that change role (the pre-edit statuses and active ids are still in place)
+  IcArgs I = ic_args(s);
+  for (int l = 1; l <= lmax; l++) {
+    Level& L = s->lev[l];
+    if (init_mode) k_ic<<<nblk(L.n, 128), 128, 0, s->stream>>>(view(s, l), I, L.st, L.nst, 1);
+    else
+      k_newvalues<<<nblk(L.n, 128), 128, 0, s->stream>>>(view(s, l), view(s, l - 1), L.nst, s->lev[l - 1].wh, s->T,
+                                                         s->D, s->V, s->d_err);
+    s->launches++;
+  }
+  for (int l = 0; l <= lmax; l++) {
+    Level& L = s->lev[l];
+    k_commit<<<nblk(L.n, 256), 256, 0, s->stream>>>(view(s, l), L.nst, L.st, s->V);
+    s->launches++;
+  }
+  if (!init_mode)
+    for (int l = 1; l <= lmax; l++) {
+      k_virtual_from_mother<<<nblk(s->lev[l].n, 256), 256, 0, s->stream>>>(view(s, l), view(s, l - 1), s->D, s->V,
+                                                                           s->r);
+      s->launches++;
+    }
+  CK(cudaGetLastError());
+  TRY(rebuild_lists(s));
+  TRY(average_all(s));
+  return AW_OK;
+}
+
+static int flags_from_chi(aw_solver* s) {
+  for (int l = 0; l <= s->lmax; l++) {
+    Level& L = s->lev[l];
+    k_flags_from_chi<<<nblk(L.n, 256), 256, 0, s->stream>>>(view(s, l), L.chi, l < s->lmax, s->cfg.chi_ref,
+                                                            s->cfg.chi_rec, L.flag);
+    s->launches++;
+  }
+  CK(cudaGetLastError());
+  return AW_OK;
+}
+
+static int regrid(aw_solver* s, int init_mode) {
+  if (s->lmax == 0) return AW_OK;
+  TRY(regrid_prepass(s, init_mode));
+  TRY(flags_from_chi(s));
+  return apply_flags(s, init_mode);
+}
+
+static int64_t total_cells(const aw_solver* s) {
+  int64_t n = 0;
+  for (int l = 0; l <= s->lmax; l++) n += s->lev[l].nc;
+  return n;
+}
+
+static void free_solver(aw_solver* s) {
+  harvest_events(s);
+  for (auto e : s->ev_free) cudaEventDestroy(e);
+  s->ev_free.clear();
+  for (int l = 0; l < MAXL; l++) {
+    Level& L = s->lev[l];
+    cudaFree(L.st); cudaFree(L.R); cudaFree(L.nst); cudaFree(L.flag); cudaFree(L.u); cudaFree(L.chi);
+    cudaFree(L.aid); cudaFree(L.alist); cudaFree(L.vlist); cudaFree(L.mlist); cudaFree(L.clist);
+    cudaFree(L.tflag); cudaFree(L.tiles); cudaFree(L.wh); cudaFree(L.qh); cudaFree(L.fl); cudaFree(L.mem);
+  }
+  cudaFree(s->d_dtl); cudaFree(s->d_dtmin); cudaFree(s->d_err); cudaFree(s->d_cnt); cudaFree(s->d_bcnt);
+  cudaFree(s->d_buf);
+  cudaFreeHost(s->h_cnt); cudaFreeHost(s->h_dtl);
+}
+
+// ------------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------------
+extern "C" {
+
+const char* aw_last_error(void) { return g_err.c_str(); }
+
+int aw_num_vars(const aw_solver* s) { return s ? s->V : 0; }
+
+int64_t aw_kernel_launches(const aw_solver* s) { return s ? s->launches : 0; }
+
+int aw_create(const aw_config* cfg, uintptr_t stream, aw_solver** out) {
+  if (!cfg || !out) AW_FAIL(AW_EINVAL, "null argument");
+  *out = nullptr;
+  const aw_config& c = *cfg;
+  if (c.dim != 2 && c.dim != 3) AW_FAIL(AW_EINVAL, "dim must be 2 or 3");
+  if (c.M < 2 || c.M > 3) AW_FAIL(AW_EINVAL, "M must be 2 or 3");
+  if (c.pde < 0 || c.pde > 2) AW_FAIL(AW_EINVAL, "unknown pde %d", c.pde);
+  if (c.lmax < 0 || c.lmax >= MAXL) AW_FAIL(AW_EINVAL, "lmax must be in 0..%d", MAXL - 1);
+  int r = c.lmax > 0 ? c.refine_factor : (c.refine_factor > 0 ? c.refine_factor : 2);
+  if (c.lmax > 0 && (r < 2 || r < c.M || r > MAXR)) AW_FAIL(AW_EINVAL, "refine_factor must satisfy max(2, M) <= r <= %d", MAXR);
+  if (r > MAXR) r = MAXR;
+  if (c.nx < 1 || c.ny < 1 || (c.dim == 3 && c.nz < 1)) AW_FAIL(AW_EINVAL, "grid size must be positive");
+  for (int a = 0; a < c.dim; a++) {
+    if (!(c.hi[a] > c.lo[a])) AW_FAIL(AW_EINVAL, "empty domain on axis %d", a);
+    if ((c.bc[2 * a] == AW_BC_PERIODIC) != (c.bc[2 * a + 1] == AW_BC_PERIODIC))
+      AW_FAIL(AW_EINVAL, "periodic boundaries must pair up on axis %d", a);
+    for (int sd = 0; sd < 2; sd++)
+      if (c.bc[2 * a + sd] != AW_BC_PERIODIC && c.bc[2 * a + sd] != AW_BC_TRANSMISSIVE)
+        AW_FAIL(AW_EINVAL, "unknown boundary condition %d", c.bc[2 * a + sd]);
+  }
+  if (!(c.cfl > 0.0)) AW_FAIL(AW_EINVAL, "cfl must be positive");
+  if (c.flux != AW_FLUX_RUSANOV) AW_FAIL(AW_EINVAL, "only the Rusanov flux is available");
+  aw_solver* s = new aw_solver();
+  s->cfg = c;
+  s->D = c.dim;
+  s->M = c.M;
+  s->N = c.M + 1;
+  s->r = r;
+  s->lmax = c.lmax;
+  s->V = nvars(c.dim, c.pde);
+  s->NSP = ipow(s->N, s->D);
+  s->NST = s->NSP * s->N;
+  s->P = c.picard_iters > 0 ? c.picard_iters : c.M + 1;
+  s->stream = (cudaStream_t)stream;
+  s->phys.gamma = c.gamma;
+  s->phys.c_h = c.c_h;
+  for (int a = 0; a < 3; a++) s->phys.adv[a] = c.adv[a];
+  if (!get_ops(c.dim, c.M, c.pde, &s->ops)) {
+    delete s;
+    AW_FAIL(AW_EINVAL, "configuration dim=%d M=%d pde=%d is not compiled in", c.dim, c.M, c.pde);
+  }
+  if (!build_tables(c.M, r, &s->T)) {
+    delete s;
+    AW_FAIL(AW_EINVAL, "table construction failed");
+  }
+  int rc = AW_OK;
+  auto alloc = [&](void** p, size_t bytes) {
+    if (rc != AW_OK) return;
+    if (cudaMalloc(p, bytes ? bytes : 1) != cudaSuccess) {
+      rc = AW_ENOMEM;
+      char b[200];
+      snprintf(b, sizeof b, "device allocation of %zu bytes failed", bytes);
+      g_err = b;
+    }
+  };
+  long long rr = 1;
+  for (int l = 0; l <= s->lmax; l++) {
+    Level& L = s->lev[l];
+    L.L[0] = (int)(c.nx * rr);
+    L.L[1] = (int)(c.ny * rr);
+    L.L[2] = s->D == 3 ? (int)(c.nz * rr) : 1;
+    L.n = (long long)L.L[0] * L.L[1] * L.L[2];
+    L.dx[0] = (c.hi[0] - c.lo[0]) / c.nx;
+    L.dx[1] = (c.hi[1] - c.lo[1]) / c.ny;
+    L.dx[2] = s->D == 3 ? (c.hi[2] - c.lo[2]) / c.nz : 1.0;
+    for (int k = 0; k < l; k++)
+      for (int a = 0; a < s->D; a++) L.dx[a] /= s->r;
+    int TS = s->ops.wenoTS;
+    for (int a = 0; a < 3; a++) L.tdim[a] = a < s->D ? (L.L[a] + TS - 1) / TS : 1;
+    L.ntd = (long long)L.tdim[0] * L.tdim[1] * L.tdim[2];
+    alloc((void**)&L.st, L.n);
+    alloc((void**)&L.R, L.n);
+    alloc((void**)&L.nst, L.n);
+    alloc((void**)&L.flag, L.n);
+    alloc((void**)&L.u, L.n * s->V * sizeof(double));
+    alloc((void**)&L.chi, L.n * sizeof(double));
+    alloc((void**)&L.aid, L.n * sizeof(int32_t));
+    alloc((void**)&L.alist, L.n * sizeof(int32_t));
+    alloc((void**)&L.vlist, L.n * sizeof(int32_t));
+    alloc((void**)&L.mlist, L.n * sizeof(int32_t));
+    alloc((void**)&L.clist, L.n * sizeof(int32_t));
+    alloc((void**)&L.tflag, L.ntd);
+    alloc((void**)&L.tiles, L.ntd * sizeof(int32_t));
+    rr *= s->r;
+  }
+  alloc((void**)&s->d_dtl, sizeof(double) * MAXL);
+  alloc((void**)&s->d_dtmin, sizeof(double));
+  alloc((void**)&s->d_err, sizeof(int));
+  alloc((void**)&s->d_cnt, sizeof(int) * (5 * MAXL + 8));
+  if (rc == AW_OK && (cudaMallocHost((void**)&s->h_cnt, sizeof(int) * (5 * MAXL + 8)) != cudaSuccess ||
+                      cudaMallocHost((void**)&s->h_dtl, sizeof(double) * MAXL) != cudaSuccess)) {
+    rc = AW_ENOMEM;
+    g_err = "pinned host allocation failed";
+  }
+  if (rc != AW_OK) {
+    free_solver(s);
+    delete s;
+    return rc;
+  }
+  for (int l = 0; l <= s->lmax; l++) {
+    Level& L = s->lev[l];
+    cudaMemsetAsync(L.st, l == 0 ? 0 : ST_NONE, L.n, s->stream);
+    cudaMemsetAsync(L.u, 0, L.n * s->V * sizeof(double), s->stream);
+    cudaMemsetAsync(L.chi, 0, L.n * sizeof(double), s->stream);
+    cudaMemsetAsync(L.flag, 0, L.n, s->stream);
+    cudaMemsetAsync(L.nst, ST_NONE, L.n, s->stream);
+  }
+  cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream);
+  rc = rebuild_lists(s);
+  if (rc != AW_OK) {
+    free_solver(s);
+    delete s;
+    return rc;
+  }
+  *out = s;
+  return AW_OK;
+}
+
+void aw_destroy(aw_solver* s) {
+  if (!s) return;
+  cudaStreamSynchronize(s->stream);
+  free_solver(s);
+  delete s;
+}
+
+int aw_reset(aw_solver* s) {
+  if (!s) AW_FAIL(AW_EINVAL, "null solver");
+  for (int l = 0; l <= s->lmax; l++) {
+    Level& L = s->lev[l];
+    CK(cudaMemsetAsync(L.st, l == 0 ? 0 : ST_NONE, L.n, s->stream));
+    CK(cudaMemsetAsync(L.u, 0, L.n * s->V * sizeof(double), s->stream));
+  }
+  TRY(rebuild_lists(s));
+  s->t = 0.0;
+  return AW_OK;
+}
+
+int aw_set_profiling(aw_solver* s, int32_t on) {
+  if (!s) AW_FAIL(AW_EINVAL, "null solver");
+  s->prof = on ? 1 : 0;
+  return AW_OK;
+}
+
+int aw_kernel_times(aw_solver* s, double* ms, int64_t* launches) {
+  if (!s || !ms || !launches) AW_FAIL(AW_EINVAL, "null argument");
+  CK(cudaStreamSynchronize(s->stream));
+  harvest_events(s);
+  for (int k = 0; k < 8; k++) {
+    ms[k] = s->kind_ms[k];
+    launches[k] = s->kind_n[k];
+    s->kind_ms[k] = 0.0;
+    s->kind_n[k] = 0;
+  }
+  return AW_OK;
+}
+
+int aw_sync(aw_solver* s) {
+  if (!s) AW_FAIL(AW_EINVAL, "null solver");
+  CK(cudaStreamSynchronize(s->stream));
+  return AW_OK;
+}
+
+int aw_set_initial(aw_solver* s, int32_t ic_kind, const double* params, int32_t nparams, int32_t nrefine) {
+  if (!s) AW_FAIL(AW_EINVAL, "null solver");
+  if (ic_kind < AW_IC_CONST || ic_kind > AW_IC_FOURIER) AW_FAIL(AW_EINVAL, "unknown initial condition %d", ic_kind);
+  if (nparams < 0 || nparams > 128 || (nparams > 0 && !params)) AW_FAIL(AW_EINVAL, "bad parameter array");
+  if ((ic_kind == AW_IC_VORTEX || ic_kind == AW_IC_RP4) && s->D != 2) AW_FAIL(AW_EINVAL, "initial condition is 2D");
+  if (ic_kind == AW_IC_OT && s->cfg.pde != AW_PDE_MHD_GLM) AW_FAIL(AW_EINVAL, "Orszag-Tang data needs the MHD system");
+  s->ic = ic_kind;
+  s->icp.assign(params, params + nparams);
+  s->icp.resize(128, 0.0);
+  IcArgs I = ic_args(s);
+  for (int l = 0; l <= s->lmax; l++) {
+    k_ic<<<nblk(s->lev[l].n, 128), 128, 0, s->stream>>>(view(s, l), I, nullptr, nullptr, 0);
+    s->launches++;
+  }
+  CK(cudaGetLastError());
+  TRY(average_all(s));
+  s->t = 0.0;
+  int passes = nrefine < 0 ? s->lmax : nrefine;
+  for (int p = 0; p < passes; p++) TRY(regrid(s, 1));
+  CK(cudaStreamSynchronize(s->stream));
+  return AW_OK;
+}
+
+int aw_set_cell_averages(aw_solver* s, const double* u_host, int64_t n) {
+  if (!s || (!u_host && n > 0)) AW_FAIL(AW_EINVAL, "null argument");
+  int64_t nc = total_cells(s);
+  if (n != nc) AW_FAIL(AW_EINVAL, "expected %lld cells, got %lld", (long long)nc, (long long)n);
+  TRY(ensure_buf(s, nc * s->V));
+  CK(cudaMemcpyAsync(s->d_buf, u_host, sizeof(double) * nc * s->V, cudaMemcpyHostToDevice, s->stream));
+  long long off = 0;
+  for (int l = 0; l <= s->lmax; l++) {
+    const Level& L = s->lev[l];
+    if (L.nc > 0) {
+      k_scatter<<<nblk(L.nc, 256), 256, 0, s->stream>>>(view(s, l), L.clist, L.nc, s->V, s->d_buf + off * s->V);
+      s->launches++;
+    }
+    off += L.nc;
+  }
+  CK(cudaGetLastError());
+  TRY(average_all(s));
+  CK(cudaStreamSynchronize(s->stream));
+  return AW_OK;
+}
+
+int aw_compute_dt(aw_solver* s, double* dt0) {
+  if (!s || !dt0) AW_FAIL(AW_EINVAL, "null argument");
+  return compute_dt(s, dt0);
+}
+
+int aw_step_dt(aw_solver* s, double dt0, aw_stats* st) {
+  if (!s) AW_FAIL(AW_EINVAL, "null solver");
+  if (!(dt0 > 0.0)) AW_FAIL(AW_EINVAL, "dt0 must be positive");
+  if (st) memset(st, 0, sizeof *st);
+  int rc = step_dt(s, dt0, st);
+  s->t += dt0;
+  if (st) st->t = s->t;
+  return rc;
+}
+
+static int step_cfl(aw_solver* s, double t_end, aw_stats* st) {
+  double dt;
+  TRY(compute_dt(s, &dt));
+  bool clip = s->t + dt >= t_end;
+  if (clip) dt = t_end - s->t;
+  int rc = step_dt(s, dt, st);
+  s->t = clip ? t_end : s->t + dt;
+  if (rc != AW_OK) return rc;
+  if (s->cfg.auto_regrid && s->lmax > 0) TRY(regrid(s, 0));
+  return AW_OK;
+}
+
+int aw_step(aw_solver* s, double t_end, aw_stats* st) {
+  if (!s) AW_FAIL(AW_EINVAL, "null solver");
+  if (st) memset(st, 0, sizeof *st);
+  if (!(t_end > s->t)) AW_FAIL(AW_EINVAL, "t_end %g is not after t %g", t_end, s->t);
+  int rc = step_cfl(s, t_end, st);
+  if (st) st->t = s->t;
+  return rc;
+}
+
+int aw_advance_to(aw_solver* s, double t_end, aw_stats* st) {
+  if (!s) AW_FAIL(AW_EINVAL, "null solver");
+  if (st) memset(st, 0, sizeof *st);
+  while (s->t < t_end) {
+    int rc = step_cfl(s, t_end, st);
+    if (rc != AW_OK) {
+      if (st) st->t = s->t;
+      return rc;
+    }
+  }
+  if (st) st->t = s->t;
+  return AW_OK;
+}
+
+int aw_regrid(aw_solver* s, int32_t init_mode) {
+  if (!s) AW_FAIL(AW_EINVAL, "null solver");
+  if (init_mode && s->ic < 0) AW_FAIL(AW_ESTATE, "initial-condition regrid before aw_set_initial");
+  TRY(regrid(s, init_mode));
+  CK(cudaStreamSynchronize(s->stream));
+  return AW_OK;
+}
+
+int aw_compute_flags(aw_solver* s, int32_t init_mode, int8_t* flags, int64_t cap, int64_t* n) {
+  if (!s || !n) AW_FAIL(AW_EINVAL, "null argument");
+  int64_t nc = total_cells(s);
+  *n = nc;
+  if (cap < nc) AW_FAIL(AW_EINVAL, "capacity %lld < %lld cells", (long long)cap, (long long)nc);
+  if (s->lmax == 0) {
+    memset(flags, 0, nc);
+    return AW_OK;
+  }
+  TRY(regrid_prepass(s, init_mode));
+  TRY(flags_from_chi(s));
+  TRY(ensure_buf(s, nc / 8 + 1));
+  int8_t* d = (int8_t*)s->d_buf;
+  long long off = 0;
+  for (int l = 0; l <= s->lmax; l++) {
+    const Level& L = s->lev[l];
+    if (L.nc > 0) {
+      k_gather_i8<<<nblk(L.nc, 256), 256, 0, s->stream>>>(L.flag, L.clist, L.nc, d + off);
+      s->launches++;
+    }
+    off += L.nc;
+  }
+  CK(cudaMemcpyAsync(flags, d, nc, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return AW_OK;
+}
+
+int aw_regrid_with_flags(aw_solver* s, const int8_t* flags, int64_t n, int32_t init_mode) {
+  if (!s || (!flags && n > 0)) AW_FAIL(AW_EINVAL, "null argument");
+  int64_t nc = total_cells(s);
+  if (n != nc) AW_FAIL(AW_EINVAL, "expected %lld flags, got %lld", (long long)nc, (long long)n);
+  if (init_mode && s->ic < 0) AW_FAIL(AW_ESTATE, "initial-condition regrid before aw_set_initial");
+  if (s->lmax == 0) return AW_OK;
+  TRY(regrid_prepass(s, init_mode));
+  TRY(ensure_buf(s, nc / 8 + 1));
+  int8_t* d = (int8_t*)s->d_buf;
+  CK(cudaMemcpyAsync(d, flags, nc, cudaMemcpyHostToDevice, s->stream));
+  long long off = 0;
+  for (int l = 0; l <= s->lmax; l++) {
+    const Level& L = s->lev[l];
+    CK(cudaMemsetAsync(L.flag, 0, L.n, s->stream));
+    if (L.nc > 0) {
+      k_scatter_i8<<<nblk(L.nc, 256), 256, 0, s->stream>>>(L.flag, L.clist, L.nc, d + off);
+      s->launches++;
+    }
+    off += L.nc;
+  }
+  CK(cudaGetLastError());
+  TRY(apply_flags(s, init_mode));
+  CK(cudaStreamSynchronize(s->stream));
+  return AW_OK;
+}
+
+int aw_get_counts(aw_solver* s, int64_t* n_cells, int64_t* n_active, int64_t* cpl, int64_t* apl) {
+  if (!s) AW_FAIL(AW_EINVAL, "null solver");
+  int64_t nc = 0, na = 0;
+  for (int l = 0; l < 8; l++) {
+    int64_t c = l <= s->lmax ? s->lev[l].nc : 0, a = l <= s->lmax ? s->lev[l].na : 0;
+    if (cpl) cpl[l] = c;
+    if (apl) apl[l] = a;
+    nc += c;
+    na += a;
+  }
+  if (n_cells) *n_cells = nc;
+  if (n_active) *n_active = na;
+  return AW_OK;
+}
+
+int aw_read_cells(aw_solver* s, aw_cell* meta, double* u, int64_t cap, int64_t* n) {
+  if (!s || !n) AW_FAIL(AW_EINVAL, "null argument");
+  int64_t nc = total_cells(s);
+  *n = nc;
+  if (cap < nc) AW_FAIL(AW_EINVAL, "capacity %lld < %lld cells", (long long)cap, (long long)nc);
+  long long words = nc * s->V + (nc * (long long)sizeof(aw_cell) + 7) / 8;
+  TRY(ensure_buf(s, words + 1));
+  double* du = s->d_buf;
+  aw_cell* dm = (aw_cell*)(s->d_buf + nc * s->V);
+  long long off = 0;
+  for (int l = 0; l <= s->lmax; l++) {
+    const Level& L = s->lev[l];
+    if (L.nc > 0) {
+      k_gather<<<nblk(L.nc, 256), 256, 0, s->stream>>>(view(s, l), L.clist, L.nc, s->V, du + off * s->V, dm + off, l);
+      s->launches++;
+    }
+    off += L.nc;
+  }
+  CK(cudaGetLastError());
+  if (u) CK(cudaMemcpyAsync(u, du, sizeof(double) * nc * s->V, cudaMemcpyDeviceToHost, s->stream));
+  if (meta) CK(cudaMemcpyAsync(meta, dm, sizeof(aw_cell) * nc, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return AW_OK;
+}
+
+int aw_read_internal(aw_solver* s, int32_t what, int32_t level, double* buf, int64_t cap, int64_t* n) {
+  if (!s || !n) AW_FAIL(AW_EINVAL, "null argument");
+  if (level < 0 || level > s->lmax) AW_FAIL(AW_EINVAL, "level out of range");
+  const Level& L = s->lev[level];
+  int64_t cnt;
+  const double* src = nullptr;
+  switch (what) {
+    case AW_INTERNAL_WENO: cnt = (int64_t)L.na * s->V * s->NSP; src = L.wh; break;
+    case AW_INTERNAL_PREDICTOR: cnt = (int64_t)L.na * s->V * s->NST; src = L.qh; break;
+    case AW_INTERNAL_FLUX: cnt = (int64_t)L.na * 2 * s->D * s->V; src = L.fl; break;
+    case AW_INTERNAL_CHI: cnt = L.nc; break;
+    default: AW_FAIL(AW_EINVAL, "unknown selector %d", what);
+  }
+  *n = cnt;
+  if (cap < cnt) AW_FAIL(AW_EINVAL, "capacity %lld < %lld", (long long)cap, (long long)cnt);
+  if (cnt == 0) return AW_OK;
+  if (what == AW_INTERNAL_CHI) {
+    TRY(ensure_buf(s, cnt));
+    k_gather_d<<<nblk(cnt, 256), 256, 0, s->stream>>>(L.chi, L.clist, L.nc, s->d_buf);
+    s->launches++;
+    src = s->d_buf;
+  }
+  CK(cudaMemcpyAsync(buf, src, sizeof(double) * cnt, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return AW_OK;
+}
+
+int aw_get_time(aw_solver* s, double* t) {
+  if (!s || !t) AW_FAIL(AW_EINVAL, "null argument");
+  *t = s->t;
+  return AW_OK;
+}
+
+int aw_totals(aw_solver* s, double* tot) {
+  if (!s || !tot) AW_FAIL(AW_EINVAL, "null argument");
+  for (int v = 0; v < s->V; v++) tot[v] = 0.0;
+  for (int l = 0; l <= s->lmax; l++) {
+    const Level& L = s->lev[l];
+    if (L.na == 0) continue;
+    int nb = (int)nblk(L.na, 256);
+    TRY(ensure_buf(s, (long long)nb * s->V));
+    k_partial<<<nb, 256, 0, s->stream>>>(view(s, l), L.alist, L.na, s->V, s->d_buf);
+    s->launches++;
+    std::vector<double> h((size_t)nb * s->V);
+    CK(cudaMemcpyAsync(h.data(), s->d_buf, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s->stream));
+    CK(cudaStreamSynchronize(s->stream));
+    double vol = 1.0;
+    for (int a = 0; a < s->D; a++) vol *= L.dx[a];
+    for (int v = 0; v < s->V; v++) {
+      double acc = 0.0;
+      for (int b = 0; b < nb; b++) acc += h[(size_t)b * s->V + v];
+      tot[v] += vol * acc;
+    }
+  }
+  return AW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,48 @@
+"""The N>1 path of bench.py: independent replicas, job time = slowest rank (gloo, CPU, 2 ranks)."""
+import os
+
+import pytest
+import torch
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _worker(rank, ws, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+
+    def max_reduce(x):
+        t = torch.tensor([x], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    ms = 100.0 + 50.0 * rank        # rank 1 is slower
+    value, job_ms = bench.combine_replicas(1_000_000, ms, ws, max_reduce)
+    dist.barrier()
+    q.put((rank, value, job_ms))
+    dist.destroy_process_group()
+
+
+def test_two_replicas_gloo():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = 29500 + (os.getpid() % 1000)
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+        assert p.exitcode == 0
+    res = sorted(q.get() for _ in range(2))
+    for rank, value, job_ms in res:
+        assert job_ms == 150.0
+        assert value == pytest.approx(2 * 1_000_000 / 0.150)
+
+
+def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setattr("sys.argv", ["bench.py", "--impl", "reference", "--gpus", "2"])
+    assert bench.main() == 0
