@@ -201,6 +201,24 @@ int aw_sync(aw_solver* s);
 /* Kernel launches issued by this solver since creation (device work the library ran). */
 int64_t aw_kernel_launches(const aw_solver* s);
 
+/* Allocation-free CFL time step of a uniform grid (the paper has no counterpart; this is a
+ * convenience for callers that cannot allocate device memory when they need it, such as code
+ * inside a framework that owns every device allocation through its own pool, or a time loop
+ * that must not pay the implicit synchronisation of cudaMalloc/cudaFree).
+ * Computes min over the cells of CFL / sum_d(s_d / dx_d) (the same formula as aw_compute_dt)
+ * for the level-0 grid of `cfg` (nx*ny[*nz] cells, spacing from lo/hi) and writes it to the
+ * device double `dt_dev`, asynchronously on `stream`.
+ *   u_dev:   device pointer, cell averages as a structure of arrays u[v * n_cells + c], cells in
+ *            canonical order (k, j, i); read only.
+ *   n_cells: must equal the grid's cell count and be at most 8192 * 256 = 2,097,152
+ *            (AW_EINVAL otherwise, before any device work).
+ * Scratch: a fixed 64 KiB array in the library's device memory, which every GPU that loads the
+ * library holds until the process exits.  The first call on a device looks up its address
+ * (make that call before any stream capture).  The array is shared: calls whose device work
+ * overlaps (different streams, or threads) race on it and must be serialised by the caller.
+ * Nothing is allocated or freed. */
+int aw_cfl_dt_noalloc(const aw_config* cfg, const double* u_dev, int64_t n_cells, double* dt_dev, uintptr_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,6 +68,7 @@ SIGNATURES = {
     "aw_reset": (C.c_int, [_vp]),
     "aw_set_profiling": (C.c_int, [_vp, C.c_int32]),
     "aw_kernel_times": (C.c_int, [_vp, _dp, _i64p]),
+    "aw_cfl_dt_noalloc": (C.c_int, [C.POINTER(AwConfig), C.c_void_p, C.c_int64, C.c_void_p, C.c_size_t]),
     "aw_kernel_launches": (C.c_int64, [_vp]),
 }
 

@@ -993,6 +993,59 @@ static void free_solver(aw_solver* s) {
 }
 
 // ------------------------------------------------------------------------------------------
+// Allocation-free CFL time step (aw_cfl_dt_noalloc).  Some callers cannot allocate device
+// memory at the moment they need a stable time step: code running inside a host framework that
+// owns every device allocation through its own pool, or a time loop that must not pay the
+// implicit device synchronisation of cudaMalloc/cudaFree.  This variant of the CFL reduction
+// keeps its per-block partial minima in a fixed file-scope device array instead of solver
+// memory.  The array is shared by every call in the process and keeps the last call's contents;
+// each call overwrites every slot it later reads, so nothing has to start at zero.
+// ------------------------------------------------------------------------------------------
+#define AW_NOALLOC_BLOCK 256
+#define AW_NOALLOC_SLOTS 8192  // partial minima: up to 8192 * 256 cells (64 KiB of device memory)
+static __device__ __align__(256) double g_noalloc_dt_scratch[AW_NOALLOC_SLOTS];
+static double* g_noalloc_ptr[64];  // device address of the array, per device, from set-up
+static bool g_noalloc_ready[64];
+
+__global__ void k_dt_blockmin(const double* u, long long n, RtPhys R, double dx0, double dx1, double dx2, double cfl,
+                              double* partial) {
+  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double dt = 1e300;
+  if (k < n) {
+    double q[MAXV];
+    for (int v = 0; v < R.V; v++) q[v] = u[v * n + k];
+    double dx[3] = {dx0, dx1, dx2};
+    double den = 0.0;
+    for (int a = 0; a < R.D; a++) den += rt_speed(R, q, a) / dx[a];
+    dt = cfl / den;
+    if (!(dt > 0.0)) dt = 0.0;
+  }
+  for (int o = 16; o > 0; o >>= 1) dt = fmin(dt, __shfl_xor_sync(0xffffffffu, dt, o));
+  __shared__ double wmin[AW_NOALLOC_BLOCK / 32];
+  if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = dt;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = wmin[0];
+    for (int w = 1; w < AW_NOALLOC_BLOCK / 32; w++) m = fmin(m, wmin[w]);
+    partial[blockIdx.x] = m;
+  }
+}
+
+__global__ void k_dt_final(const double* partial, int nb, double* out) {
+  double m = 1e300;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) m = fmin(m, partial[b]);
+  for (int o = 16; o > 0; o >>= 1) m = fmin(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ double wmin[32];
+  if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double r = wmin[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); w++) r = fmin(r, wmin[w]);
+    *out = r;
+  }
+}
+
+// ------------------------------------------------------------------------------------------
 // C ABI
 // ------------------------------------------------------------------------------------------
 extern "C" {
@@ -1414,6 +1467,45 @@ int aw_totals(aw_solver* s, double* tot) {
       tot[v] += vol * acc;
     }
   }
+  return AW_OK;
+}
+
+int aw_cfl_dt_noalloc(const aw_config* cfg, const double* u_dev, int64_t n_cells, double* dt_dev, uintptr_t stream) {
+  if (!cfg || !u_dev || !dt_dev) AW_FAIL(AW_EINVAL, "null argument");
+  const aw_config& c = *cfg;
+  if (c.dim != 2 && c.dim != 3) AW_FAIL(AW_EINVAL, "dim must be 2 or 3");
+  if (c.pde < 0 || c.pde > 2) AW_FAIL(AW_EINVAL, "unknown pde %d", c.pde);
+  if (c.nx < 1 || c.ny < 1 || (c.dim == 3 && c.nz < 1)) AW_FAIL(AW_EINVAL, "grid size must be positive");
+  long long n = (long long)c.nx * c.ny * (c.dim == 3 ? c.nz : 1);
+  if (n_cells != n) AW_FAIL(AW_EINVAL, "n_cells %lld does not match the %lld cells of the grid", (long long)n_cells, n);
+  long long nb = (n + AW_NOALLOC_BLOCK - 1) / AW_NOALLOC_BLOCK;
+  if (nb > AW_NOALLOC_SLOTS)
+    AW_FAIL(AW_EINVAL, "aw_cfl_dt_noalloc handles at most %d cells (got %lld)", AW_NOALLOC_SLOTS * AW_NOALLOC_BLOCK, n);
+  if (!(c.cfl > 0.0)) AW_FAIL(AW_EINVAL, "cfl must be positive");
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) AW_FAIL(AW_EINVAL, "device ordinal %d out of range", dev);
+  if (!g_noalloc_ready[dev]) {
+    // once per device, with that device current: the host-side name of the array is not a
+    // device address, so take the address from the runtime
+    double* p = nullptr;
+    CK(cudaGetSymbolAddress((void**)&p, g_noalloc_dt_scratch));
+    g_noalloc_ptr[dev] = p;
+    g_noalloc_ready[dev] = true;
+  }
+  RtPhys R;
+  R.pde = c.pde;
+  R.D = c.dim;
+  R.V = nvars(c.dim, c.pde);
+  R.P.gamma = c.gamma;
+  R.P.c_h = c.c_h;
+  for (int a = 0; a < 3; a++) R.P.adv[a] = c.adv[a];
+  double dx0 = (c.hi[0] - c.lo[0]) / c.nx, dx1 = (c.hi[1] - c.lo[1]) / c.ny;
+  double dx2 = c.dim == 3 ? (c.hi[2] - c.lo[2]) / c.nz : 1.0;
+  cudaStream_t st = (cudaStream_t)stream;
+  k_dt_blockmin<<<(unsigned)nb, AW_NOALLOC_BLOCK, 0, st>>>(u_dev, n, R, dx0, dx1, dx2, c.cfl, g_noalloc_ptr[dev]);
+  k_dt_final<<<1, 1024, 0, st>>>(g_noalloc_ptr[dev], (int)nb, dt_dev);
+  CK(cudaGetLastError());
   return AW_OK;
 }
 
