@@ -125,7 +125,7 @@ def run_reference(args):
     threads = os.cpu_count() or 1
     times, updates = [], []
     for i in range(args.warmup + args.steps):
-        o = oracle.Oracle(oracle.make_cfg(dim=2, M=3, n=(100, 100, 1), lo=CFG["lo"], hi=CFG["hi"],
+        o = oracle.Oracle(oracle.make_cfg(dim=2, M=3, n=CFG["n"], lo=CFG["lo"], hi=CFG["hi"],
                                           bc=oracle.BC_TRANSMISSIVE, r=3, lmax=2, cfl=0.6, auto_regrid=1),
                           threads=threads)
         o.set_initial(oracle.IC_EXPLOSION, aw_inputs.EXPLOSION)
@@ -153,7 +153,7 @@ def cpu_baseline_sample():
     import oracle
     import aw_inputs
     threads = os.cpu_count() or 1
-    o = oracle.Oracle(oracle.make_cfg(dim=2, M=3, n=(100, 100, 1), lo=CFG["lo"], hi=CFG["hi"],
+    o = oracle.Oracle(oracle.make_cfg(dim=2, M=3, n=CFG["n"], lo=CFG["lo"], hi=CFG["hi"],
                                       bc=oracle.BC_TRANSMISSIVE, r=3, lmax=2, cfl=0.6, auto_regrid=1),
                       threads=threads)
     o.set_initial(oracle.IC_EXPLOSION, aw_inputs.EXPLOSION)
@@ -174,7 +174,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--base", type=int, default=100, help="level-0 cells per direction (workload: 100)")
+    ap.add_argument("--t-end", type=float, default=T_END, help="end time (workload: 0.25)")
     args = ap.parse_args()
+    if args.base != 100 or args.t_end != T_END:
+        CFG["n"] = (args.base, args.base, 1)
+        globals()["T_END"] = args.t_end
+        globals()["WORKLOAD"] = WORKLOAD.replace("base 100x100", f"base {args.base}x{args.base}").replace(
+            "t_end=0.25", f"t_end={args.t_end}")
     ws, rank, local = dist_setup()
     if args.impl == "reference":
         if rank != 0:
