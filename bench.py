@@ -40,6 +40,15 @@ T_END = 0.25
 SM_COUNT = 152
 FP64_FMA_PER_CLK_PER_SM = 2      # sm_103a: measured 0.598 T DFMA/s at ~1.97 GHz on 152 SMs
 SM_MAX_MHZ = 2070.0
+HBM_GBS = 6792.1                 # measured copy bandwidth of this GB300 pool
+
+
+def _measured_hbm():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return HBM_GBS
 FP64_PEAK_TFLOPS = 2 * FP64_FMA_PER_CLK_PER_SM * SM_COUNT * SM_MAX_MHZ * 1e6 / 1e12   # 1.2586
 
 
@@ -57,6 +66,36 @@ def predictor_flops_per_cell(D, M, V, P, flux_flops):
 # FP64 operations of the Euler fluxes in all D directions at one state (1/rho, velocities,
 # kinetic energy, pressure, E+p, then D*(D+2) components)
 EULER_FLUX_FLOPS = {2: 18, 3: 25}
+
+
+def weno_flops_per_cell(D, M, V):
+    """Algorithmic FP64 FLOPs of the dimension-by-dimension WENO per cell: one 1D reconstruction
+    per variable on each of the N^(a) lines of sweep a (1 in x, N in y, N^2 in z), each with
+    N_s stencils of N-1 differences (stencil product, sigma as a quadratic form, weight) and
+    the normalised combination.  Halo sweeps a tile recomputes are overhead, not counted."""
+    N = M + 1
+    ns = 3 if M % 2 == 0 else 4
+    per_stencil = 2 * (N - 1) * N + 2 * ((N - 1) * N // 2 + (N - 1)) + 5 + 2 * N
+    per_recon = ns * per_stencil + ns + 1 + 2 * N
+    lines = sum(N ** a for a in range(D))
+    return per_recon * lines * V
+
+
+def flux_flops_per_cell(D, M, V):
+    """Algorithmic FP64 FLOPs of the face fluxes per cell: D owned faces of N^D space-time Gauss
+    points; two traces (N-term contractions), the Euler flux and spectral radius of both states,
+    the Rusanov combination and the quadrature weight."""
+    N = M + 1
+    per_state = 1 + 2 * D + 6 + 2 * D + 4 + 1 + 2
+    per_point = 2 * V * N * 2 + 2 * per_state + 3 * V + V
+    return D * N ** D * per_point
+
+
+def bytes_per_cell(D, M, V):
+    """Algorithmic HBM bytes per cell update of each kernel (every array read or written once)."""
+    N = M + 1
+    wh, qh, fl = V * N ** D * 8, V * N ** (D + 1) * 8, 2 * D * V * 8
+    return {"weno": V * 8 + wh, "predictor": wh + qh, "face_flux": qh + fl}
 
 
 class ClockSampler:
@@ -267,6 +306,20 @@ def main():
         roofline = {"bound": "alu", "kernel": names[dom], "achieved": None, "peak": FP64_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "frac": None, "traffic": None}
     kernel_share = {n: float(kms[i] / max(kms.sum(), 1e-9)) for i, n in enumerate(names)}
+    flops = {"weno": weno_flops_per_cell(2, 3, V), "predictor": pf, "face_flux": flux_flops_per_cell(2, 3, V)}
+    hbm = _measured_hbm()
+    bpc = bytes_per_cell(2, 3, V)
+    kernels = {}
+    for i, n in enumerate(names[:3]):
+        if kms[i] <= 0:
+            continue
+        t = kms[i] * 1e-3
+        kernels[n] = {"ms_total": float(kms[i]), "launches": int(kn[i]), "share": kernel_share[n],
+                      "fp64_tflops": flops[n] * upd / t / 1e12,
+                      "fp64_frac": flops[n] * upd / t / 1e12 / FP64_PEAK_TFLOPS,
+                      "hbm_gbs_algorithmic": bpc[n] * upd / t / 1e9,
+                      "hbm_frac": bpc[n] * upd / t / 1e9 / hbm,
+                      "flops_per_cell_update": flops[n], "bytes_per_cell_update": bpc[n]}
 
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
@@ -274,7 +327,7 @@ def main():
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "cell_updates_per_solve": upd_per_step, "level0_steps_per_solve": l0 / args.steps,
                    "l2": "flushed between timed solves (256 MB write)", "parallelism": f"replicas x{ws}"},
-        "roofline": roofline, "kernel_time_share": kernel_share, "gpu_launches": int(launches),
+        "roofline": roofline, "kernel_time_share": kernel_share, "kernels": kernels, "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
 

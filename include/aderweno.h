@@ -54,7 +54,8 @@ extern "C" {
 #define AW_BC_PERIODIC 0
 #define AW_BC_TRANSMISSIVE 1
 
-#define AW_FLUX_RUSANOV 0
+#define AW_FLUX_RUSANOV 0  /* Eq. eqn.rusanov */
+#define AW_FLUX_OSHER 1    /* Eq. eqn.osher, 3-point Gauss-Legendre path quadrature (Euler) */
 
 /* initial conditions of Sec. 4; parameter layouts:
  *  AW_IC_CONST:     primitive state (Euler: rho, v_1..v_d, p; MHD: rho, vx, vy, vz, p, Bx, By,
@@ -96,7 +97,7 @@ typedef struct aw_config {
   double eps_ind;       /* filter epsilon of Eq. eqn.indicator */
   double cfl;           /* CFL number */
   int32_t picard_iters; /* Picard iterations of the predictor, 0 -> M+1 */
-  int32_t flux;         /* AW_FLUX_RUSANOV */
+  int32_t flux;         /* AW_FLUX_RUSANOV or AW_FLUX_OSHER */
   int32_t auto_regrid;  /* 1: regrid after every level-0 step (aw_step / aw_advance_to) */
   int32_t reserved;
   double adv[3];        /* advection velocity of AW_PDE_LINADV */
@@ -200,6 +201,60 @@ int aw_sync(aw_solver* s);
 
 /* Kernel launches issued by this solver since creation (device work the library ran). */
 int64_t aw_kernel_launches(const aw_solver* s);
+
+/* ------------------------------------------------------------------------------------------
+ * Request loop: independent solves (each a full aw_create / aw_set_initial / aw_advance_to of
+ * its own configuration) admitted as device memory and worker slots free up; concurrent
+ * requests run on their own CUDA streams, so their kernels overlap on the GPU.  Admission is
+ * in arrival order against a device-memory budget using an estimate of each solve's footprint
+ * (the dense per-level grids plus per-active arrays for a quarter of the finest level).  A
+ * finished request's cell averages are kept in host memory and its device memory is released.
+ * Results do not depend on the mix: every request runs the same kernels as a solve alone.
+ * (Not a passage of the paper: a serving layer around the method.)
+ * ------------------------------------------------------------------------------------------ */
+typedef struct aw_server aw_server;
+
+#define AW_REQ_QUEUED 0
+#define AW_REQ_RUNNING 1
+#define AW_REQ_DONE 2
+#define AW_REQ_FAILED 3
+
+typedef struct aw_srv_info {
+  int64_t cell_updates, level0_steps, footprint_bytes;
+  double queue_ms, run_ms, total_ms;   /* submit -> start, start -> done, submit -> done */
+} aw_srv_info;
+
+typedef struct aw_srv_summary {
+  int64_t done, failed, queued, running;
+  double p50_ms, p99_ms;               /* time to solution (submit -> done) of finished requests */
+  double solves_per_s, cell_updates_per_s;   /* over first submit -> last completion */
+} aw_srv_summary;
+
+/* Start `max_concurrent` worker threads on the current device with a device-memory budget. */
+int aw_srv_create(int64_t hbm_budget_bytes, int32_t max_concurrent, aw_server** out);
+/* Queue one solve (configuration copied; params copied).  AW_EINVAL if its footprint exceeds
+ * the whole budget. */
+int aw_srv_submit(aw_server* s, const aw_config* cfg, int32_t ic_kind, const double* params, int32_t nparams,
+                  double t_end, int64_t* id);
+/* State of a request: AW_REQ_*. */
+int aw_srv_poll(aw_server* s, int64_t id, int32_t* state);
+/* Block until the queue is empty and no request is running. */
+int aw_srv_wait_all(aw_server* s);
+/* Cells of a finished request in canonical order (as aw_read_cells), and its timings; returns
+ * the request's own error code if it failed, AW_ESTATE if it has not finished. */
+int aw_srv_result(aw_server* s, int64_t id, aw_cell* meta, double* u, int64_t cap, int64_t* n, aw_srv_info* info);
+/* p50/p99 time to solution and throughput of the finished requests. */
+int aw_srv_stats(aw_server* s, aw_srv_summary* out);
+/* Message of the last failing aw_srv_* call on this thread. */
+const char* aw_srv_last_error(void);
+/* Drop queued requests, wait for running ones, stop the workers. */
+void aw_srv_destroy(aw_server* s);
+
+/* Self-test of the Newton-Raphson reciprocal the kernels use in place of IEEE division
+ * (y <- y + y(1 - x y) twice from a single-precision seed): out_dev[k] = that reciprocal of
+ * x_dev[k], out_dev[n + k] = 1.0 / x_dev[k] by IEEE division, for k < n (device buffers owned
+ * by the caller; out_dev holds 2n doubles).  Asynchronous on `stream`. */
+int aw_selftest_reciprocal(const double* x_dev, int64_t n, double* out_dev, uintptr_t stream);
 
 /* Allocation-free CFL time step of a uniform grid (the paper has no counterpart; this is a
  * convenience for callers that cannot allocate device memory when they need it, such as code

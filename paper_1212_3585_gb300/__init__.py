@@ -10,7 +10,7 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (AW_BC_PERIODIC, AW_BC_TRANSMISSIVE, AW_FLUX_RUSANOV, AW_IC_CONST, AW_IC_EXPLOSION,  # noqa: F401
+from ._lib import (AwSrvInfo, AwSrvSummary, AW_BC_PERIODIC, AW_BC_TRANSMISSIVE, AW_FLUX_OSHER, AW_FLUX_RUSANOV, AW_IC_CONST, AW_IC_EXPLOSION,  # noqa: F401
                    AW_IC_FOURIER, AW_IC_OT, AW_IC_RP4, AW_IC_VORTEX, AW_INTERNAL_CHI, AW_INTERNAL_FLUX,
                    AW_INTERNAL_PREDICTOR, AW_INTERNAL_WENO, AW_PDE_EULER, AW_PDE_LINADV, AW_PDE_MHD_GLM,
                    AwCell, AwConfig, AwError, AwStats)
@@ -18,7 +18,7 @@ from ._lib import (AW_BC_PERIODIC, AW_BC_TRANSMISSIVE, AW_FLUX_RUSANOV, AW_IC_CO
 
 def make_config(dim=2, pde=AW_PDE_EULER, M=2, n=(16, 16, 1), gamma=1.4, c_h=2.0, lo=(0.0, 0.0, 0.0),
                 hi=(1.0, 1.0, 1.0), bc=AW_BC_PERIODIC, r=3, lmax=0, chi_ref=0.2, chi_rec=0.1, eps_ind=0.01,
-                cfl=0.9, picard=0, auto_regrid=1, adv=(1.0, 1.0, 1.0)) -> AwConfig:
+                cfl=0.9, picard=0, auto_regrid=1, adv=(1.0, 1.0, 1.0), flux=AW_FLUX_RUSANOV) -> AwConfig:
     c = AwConfig()
     c.dim, c.pde, c.M = dim, pde, M
     c.nx, c.ny, c.nz = n[0], n[1], (n[2] if dim == 3 else 1)
@@ -30,7 +30,7 @@ def make_config(dim=2, pde=AW_PDE_EULER, M=2, n=(16, 16, 1), gamma=1.4, c_h=2.0,
         c.bc[i] = bcs[i]
     c.refine_factor, c.lmax = r, lmax
     c.chi_ref, c.chi_rec, c.eps_ind, c.cfl = chi_ref, chi_rec, eps_ind, cfl
-    c.picard_iters, c.flux, c.auto_regrid = picard, AW_FLUX_RUSANOV, auto_regrid
+    c.picard_iters, c.flux, c.auto_regrid = picard, flux, auto_regrid
     return c
 
 
@@ -156,3 +156,59 @@ class Solver:
 
     def kernel_launches(self):
         return self.L.aw_kernel_launches(self.h)
+
+
+class Server:
+    """Request loop of independent solves (aw_srv_*): continuous admission under a device-memory
+    budget, concurrent requests on their own streams."""
+
+    def __init__(self, hbm_budget_bytes: int, max_concurrent: int = 4):
+        self.L = _lib.load()
+        h = C.c_void_p()
+        rc = self.L.aw_srv_create(int(hbm_budget_bytes), max_concurrent, C.byref(h))
+        if rc:
+            raise AwError(rc, self.L.aw_srv_last_error().decode())
+        self.h = h
+
+    def _check(self, rc):
+        if rc:
+            raise AwError(rc, self.L.aw_srv_last_error().decode())
+
+    def submit(self, cfg: AwConfig, ic, params, t_end) -> int:
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        rid = C.c_int64()
+        self._check(self.L.aw_srv_submit(self.h, C.byref(cfg), ic, _dp(p), len(p), t_end, C.byref(rid)))
+        return rid.value
+
+    def poll(self, rid) -> int:
+        st = C.c_int32()
+        self._check(self.L.aw_srv_poll(self.h, rid, C.byref(st)))
+        return st.value
+
+    def wait_all(self):
+        self._check(self.L.aw_srv_wait_all(self.h))
+
+    def result(self, rid, V):
+        n = C.c_int64()
+        info = AwSrvInfo()
+        rc = self.L.aw_srv_result(self.h, rid, None, None, 0, C.byref(n), C.byref(info))
+        if rc not in (0, _lib.AW_EINVAL):
+            self._check(rc)
+        meta = (AwCell * max(n.value, 1))()
+        u = np.zeros((max(n.value, 1), V))
+        self._check(self.L.aw_srv_result(self.h, rid, meta, _dp(u), n.value, C.byref(n), C.byref(info)))
+        m = np.frombuffer(meta, dtype=np.int32).reshape(-1, 5)[: n.value].copy()
+        return m, u[: n.value], info
+
+    def stats(self) -> AwSrvSummary:
+        s = AwSrvSummary()
+        self._check(self.L.aw_srv_stats(self.h, C.byref(s)))
+        return s
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.L.aw_srv_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()

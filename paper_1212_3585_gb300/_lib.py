@@ -10,7 +10,7 @@ LIB_PATH = os.path.join(PKG, "lib", "libaderweno.so")
 AW_OK, AW_EINVAL, AW_ENOMEM, AW_ECUDA, AW_ENONPHYSICAL, AW_ETIMEOUT, AW_ESTATE = 0, -1, -2, -3, -4, -5, -6
 AW_PDE_EULER, AW_PDE_MHD_GLM, AW_PDE_LINADV = 0, 1, 2
 AW_BC_PERIODIC, AW_BC_TRANSMISSIVE = 0, 1
-AW_FLUX_RUSANOV = 0
+AW_FLUX_RUSANOV, AW_FLUX_OSHER = 0, 1
 AW_IC_CONST, AW_IC_VORTEX, AW_IC_EXPLOSION, AW_IC_OT, AW_IC_RP4, AW_IC_FOURIER = 0, 1, 2, 3, 4, 5
 AW_INTERNAL_WENO, AW_INTERNAL_PREDICTOR, AW_INTERNAL_CHI, AW_INTERNAL_FLUX = 0, 1, 2, 3
 
@@ -34,6 +34,17 @@ class AwStats(C.Structure):
         ("level0_steps", C.c_int64), ("cell_updates", C.c_int64), ("updates_per_level", C.c_int64 * 8),
         ("last_dt0", C.c_double), ("t", C.c_double),
     ]
+
+
+class AwSrvInfo(C.Structure):
+    _fields_ = [("cell_updates", C.c_int64), ("level0_steps", C.c_int64), ("footprint_bytes", C.c_int64),
+                ("queue_ms", C.c_double), ("run_ms", C.c_double), ("total_ms", C.c_double)]
+
+
+class AwSrvSummary(C.Structure):
+    _fields_ = [("done", C.c_int64), ("failed", C.c_int64), ("queued", C.c_int64), ("running", C.c_int64),
+                ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("solves_per_s", C.c_double),
+                ("cell_updates_per_s", C.c_double)]
 
 
 class AwCell(C.Structure):
@@ -68,6 +79,15 @@ SIGNATURES = {
     "aw_reset": (C.c_int, [_vp]),
     "aw_set_profiling": (C.c_int, [_vp, C.c_int32]),
     "aw_kernel_times": (C.c_int, [_vp, _dp, _i64p]),
+    "aw_srv_create": (C.c_int, [C.c_int64, C.c_int32, C.POINTER(_vp)]),
+    "aw_srv_submit": (C.c_int, [_vp, C.POINTER(AwConfig), C.c_int32, _dp, C.c_int32, C.c_double, _i64p]),
+    "aw_srv_poll": (C.c_int, [_vp, C.c_int64, C.POINTER(C.c_int32)]),
+    "aw_srv_wait_all": (C.c_int, [_vp]),
+    "aw_srv_result": (C.c_int, [_vp, C.c_int64, C.POINTER(AwCell), _dp, C.c_int64, _i64p, C.POINTER(AwSrvInfo)]),
+    "aw_srv_stats": (C.c_int, [_vp, C.POINTER(AwSrvSummary)]),
+    "aw_srv_last_error": (C.c_char_p, []),
+    "aw_srv_destroy": (None, [_vp]),
+    "aw_selftest_reciprocal": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_size_t]),
     "aw_cfl_dt_noalloc": (C.c_int, [C.POINTER(AwConfig), C.c_void_p, C.c_int64, C.c_void_p, C.c_size_t]),
     "aw_kernel_launches": (C.c_int64, [_vp]),
 }

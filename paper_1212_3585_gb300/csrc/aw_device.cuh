@@ -31,6 +31,10 @@ struct Tables {
   double lam[4];                  // linear weight lambda_s
   double Ainv[4][MAXN][MAXN];     // Ainv[s][p][e]: stencil reconstruction matrix
   double Sig[MAXN][MAXN];         // oscillation indicator matrix
+  // sigma_s as a quadratic form of the N-1 stencil differences to the cell value (the centre
+  // cell's difference is zero): Bq[s][i][j] = B_ii on the diagonal, 2 B_ij above it, where
+  // B = Ainv_s^T Sigma Ainv_s without the centre row and column
+  double Bq[4][MAXN - 1][MAXN - 1];
   double G[MAXN][MAXN];           // K_t^{-1} diag(w): time block of the predictor
   double gsum[MAXN];              // row sums of G
   double Wc[MAXR][MAXN];          // Wc[c][l] = r * int_{c/r}^{(c+1)/r} psi_l (child averages)
@@ -76,6 +80,20 @@ __device__ __forceinline__ bool bcmap(const int* L, const int* bc, int a, int c,
   return false;
 }
 
+// Reciprocal by the Newton-Raphson iteration y <- y + y (1 - x y) (quadratic convergence),
+// seeded with the single-precision reciprocal of x (about 24 correct bits); two steps reach
+// double precision (error a few ulp, tested against IEEE division).  Valid for |x| inside the
+// single-precision normal range, which covers densities and the WENO sigma + eps >= 1e-14.
+// On sm_103a the FP64 pipe is the bottleneck and this costs 4 FP64 FMAs instead of the ~10
+// FP64 operations of an IEEE double division.
+__device__ __forceinline__ double rcp_nr(double x) {
+  double y = (double)__frcp_rn((float)x);
+  double e = fma(-x, y, 1.0);
+  y = fma(y, e, y);
+  e = fma(-x, y, 1.0);
+  return fma(y, e, y);
+}
+
 // ------------------------------------------------------------------------------------------
 // PDE systems.  Euler (Eq. eq:Euler-system), ideal MHD with hyperbolic GLM cleaning (Sec. 4.2,
 // rationalised units) and linear advection.  All in FP64.
@@ -88,7 +106,7 @@ struct Pde<PDE_EULER, D> {
   static constexpr int V = D + 2;
   // fluxes in every direction at one state, sharing the primitive variables
   __device__ __forceinline__ static void fluxes(const double* q, double (*F)[V], const Phys& P) {
-    double ir = 1.0 / q[0];
+    double ir = rcp_nr(q[0]);
     double v[D];
 #pragma unroll
     for (int a = 0; a < D; a++) v[a] = q[1 + a] * ir;
@@ -142,27 +160,36 @@ struct Pde<PDE_EULER, D> {
 template <int D>
 struct Pde<PDE_MHD, D> {
   static constexpr int V = 9;
+  // x/y/z fluxes of the MHD-GLM system for the directions n < ND, sharing the primitives
+  template <int ND>
+  __device__ __forceinline__ static void flux_dirs(const double* q, double (*F)[V], const Phys& P, int n0) {
+    const double ir = rcp_nr(q[0]);
+    const double vv[3] = {q[1] * ir, q[2] * ir, q[3] * ir};
+    const double B2 = q[5] * q[5] + q[6] * q[6] + q[7] * q[7];
+    const double mv = q[1] * vv[0] + q[2] * vv[1] + q[3] * vv[2];
+    const double p = (P.gamma - 1.0) * (q[4] - 0.5 * mv - 0.5 * B2);
+    const double vB = vv[0] * q[5] + vv[1] * q[6] + vv[2] * q[7];
+    const double pt = p + 0.5 * B2;
+    const double ch2 = P.c_h * P.c_h;
+#pragma unroll
+    for (int k = 0; k < ND; k++) {
+      const int n = ND == 1 ? n0 : k;
+      const double vn = vv[n], Bn = q[5 + n];
+      double* f = F[k];
+      f[0] = q[1 + n];
+#pragma unroll
+      for (int a = 0; a < 3; a++) f[1 + a] = q[1 + a] * vn + (a == n ? pt : 0.0) - q[5 + a] * Bn;
+      f[4] = vn * (q[4] + pt) - Bn * vB;
+#pragma unroll
+      for (int a = 0; a < 3; a++) f[5 + a] = (a == n) ? q[8] : (vn * q[5 + a] - Bn * vv[a]);
+      f[8] = ch2 * Bn;
+    }
+  }
   __device__ __forceinline__ static void flux(const double* q, int n, double* f, const Phys& P) {
-    double ir = 1.0 / q[0];
-    double v0 = q[1] * ir, v1 = q[2] * ir, v2 = q[3] * ir;
-    double vv[3] = {v0, v1, v2};
-    double B2 = q[5] * q[5] + q[6] * q[6] + q[7] * q[7];
-    double mv = q[1] * v0 + q[2] * v1 + q[3] * v2;
-    double p = (P.gamma - 1.0) * (q[4] - 0.5 * mv - 0.5 * B2);
-    double vB = v0 * q[5] + v1 * q[6] + v2 * q[7];
-    double pt = p + 0.5 * B2;
-    double vn = vv[n], Bn = q[5 + n];
-    f[0] = q[1 + n];
-#pragma unroll
-    for (int a = 0; a < 3; a++) f[1 + a] = q[1 + a] * vn + (a == n ? pt : 0.0) - q[5 + a] * Bn;
-    f[4] = vn * (q[4] + pt) - Bn * vB;
-#pragma unroll
-    for (int a = 0; a < 3; a++) f[5 + a] = (a == n) ? q[8] : (vn * q[5 + a] - Bn * vv[a]);
-    f[8] = P.c_h * P.c_h * Bn;
+    flux_dirs<1>(q, (double(*)[V])f, P, n);
   }
   __device__ __forceinline__ static void fluxes(const double* q, double (*F)[V], const Phys& P) {
-#pragma unroll
-    for (int n = 0; n < D; n++) flux(q, n, F[n], P);
+    flux_dirs<D>(q, F, P, 0);
   }
   __device__ __forceinline__ static double pressure(const double* q, const Phys& P) {
     double m2 = q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
@@ -170,13 +197,15 @@ struct Pde<PDE_MHD, D> {
     return (P.gamma - 1.0) * (q[4] - 0.5 * m2 / q[0] - 0.5 * B2);
   }
   __device__ __forceinline__ static double speed(const double* q, int n, const Phys& P) {
-    double p = pressure(q, P);
-    double a2 = P.gamma * p / q[0];
+    const double ir = rcp_nr(q[0]);
+    double m2 = q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
     double B2 = q[5] * q[5] + q[6] * q[6] + q[7] * q[7];
-    double b2 = B2 / q[0], bn2 = q[5 + n] * q[5 + n] / q[0];
+    double p = (P.gamma - 1.0) * (q[4] - 0.5 * m2 * ir - 0.5 * B2);
+    double a2 = P.gamma * p * ir;
+    double b2 = B2 * ir, bn2 = q[5 + n] * q[5 + n] * ir;
     double s = a2 + b2;
     double cf = sqrt(0.5 * (s + sqrt(s * s - 4.0 * a2 * bn2)));
-    double c = fabs(q[1 + n] / q[0]) + cf;
+    double c = fabs(q[1 + n] * ir) + cf;
     return c > P.c_h ? c : P.c_h;
   }
   __device__ __forceinline__ static bool physical(const double* q, const Phys& P) {
@@ -201,9 +230,109 @@ struct Pde<PDE_LINADV, D> {
   __device__ __forceinline__ static bool physical(const double* q, const Phys&) { return q[0] == q[0]; }
 };
 
+// Euler flux in direction n and the spectral radius of its Jacobian at one state, sharing 1/rho.
+template <int D>
+__device__ __forceinline__ double euler_flux_speed(const double* q, int n, double* f, const Phys& P) {
+  const double ir = rcp_nr(q[0]);
+  const double vn = q[1 + n] * ir;
+  double ke = q[1] * q[1];
+#pragma unroll
+  for (int a = 1; a < D; a++) ke = fma(q[1 + a], q[1 + a], ke);
+  const double p = (P.gamma - 1.0) * fma(-0.5 * ir, ke, q[D + 1]);
+  f[0] = q[1 + n];
+#pragma unroll
+  for (int a = 0; a < D; a++) f[1 + a] = (a == n) ? fma(q[1 + a], vn, p) : q[1 + a] * vn;
+  f[D + 1] = vn * (q[D + 1] + p);
+  const double c2 = P.gamma * p * ir;
+  return c2 >= 0.0 ? fabs(vn) + sqrt(c2) : sqrt(fma(vn, vn, -c2));
+}
+
+// |A(q)| dq for the Euler flux in direction n, from the characteristic decomposition: wave
+// amplitudes alpha = L dq (acoustic -, entropy, shears, acoustic +), scaled by |u_n - c|, |u_n|,
+// |u_n + c|, and recombined with the right eigenvectors.  Where c^2 <= 0 the eigenvalues are
+// complex and |A| dq is replaced by the spectral radius times dq.
+template <int D>
+__device__ __forceinline__ void euler_abs_jacobian_apply(const double* q, int n, const double* dq, double* out,
+                                                         const Phys& P) {
+  constexpr int V = D + 2;
+  const double ir = rcp_nr(q[0]);
+  double v[D], v2 = 0.0, vdm = 0.0;
+#pragma unroll
+  for (int a = 0; a < D; a++) { v[a] = q[1 + a] * ir; v2 = fma(v[a], v[a], v2); vdm = fma(v[a], dq[1 + a], vdm); }
+  const double p = (P.gamma - 1.0) * fma(-0.5 * q[0], v2, q[D + 1]);
+  const double c2 = P.gamma * p * ir;
+  const double un = v[n];
+  if (!(c2 > 0.0)) {
+    const double sr = sqrt(fma(un, un, -c2));
+#pragma unroll
+    for (int k = 0; k < V; k++) out[k] = sr * dq[k];
+    return;
+  }
+  const double c = sqrt(c2), icv = rcp_nr(c), H = (q[D + 1] + p) * ir;
+  const double b1 = (P.gamma - 1.0) * rcp_nr(c2);
+  const double b2 = 0.5 * v2 * b1;
+  const double Pq = b1 * (vdm - dq[D + 1]);
+  const double A = (un * dq[0] - dq[1 + n]) * icv;
+  double a0 = 0.5 * (b2 * dq[0] - Pq + A);
+  double a1 = (1.0 - b2) * dq[0] + Pq;
+  double a4 = 0.5 * (b2 * dq[0] - Pq - A);
+  a0 *= fabs(un - c);
+  a1 *= fabs(un);
+  a4 *= fabs(un + c);
+  const double s04 = a0 + a4, d40 = a4 - a0, sum = s04 + a1;
+  double eshear = 0.0;
+  out[0] = sum;
+#pragma unroll
+  for (int a = 0; a < D; a++) {
+    double o = v[a] * sum;
+    if (a == n) o = fma(c, d40, o);
+    else {
+      double as = fabs(un) * fma(-v[a], dq[0], dq[1 + a]);
+      o += as;
+      eshear = fma(v[a], as, eshear);
+    }
+    out[1 + a] = o;
+  }
+  out[D + 1] = H * s04 + un * c * d40 + 0.5 * v2 * a1 + eshear;
+}
+
+// Osher-Solomon flux of Dumbser and Toro, Eq. eqn.osher: straight path between the states,
+// |A| integrated by the 3-point Gauss-Legendre rule on [0,1].
+template <int D>
+__device__ __forceinline__ void osher_euler(const double* qm, const double* qp, int n, double* out, const Phys& P) {
+  constexpr int V = D + 2;
+  const double gs[3] = {0.5 - 0.3872983346207417, 0.5, 0.5 + 0.3872983346207417};
+  const double gw[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+  double fm[V], fp[V], dq[V], acc[V];
+  euler_flux_speed<D>(qm, n, fm, P);
+  euler_flux_speed<D>(qp, n, fp, P);
+#pragma unroll
+  for (int k = 0; k < V; k++) { dq[k] = qp[k] - qm[k]; acc[k] = 0.0; }
+#pragma unroll
+  for (int j = 0; j < 3; j++) {
+    double q[V], t[V];
+#pragma unroll
+    for (int k = 0; k < V; k++) q[k] = fma(gs[j], dq[k], qm[k]);
+    euler_abs_jacobian_apply<D>(q, n, dq, t, P);
+#pragma unroll
+    for (int k = 0; k < V; k++) acc[k] = fma(gw[j], t[k], acc[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < V; k++) out[k] = fma(-0.5, acc[k], 0.5 * (fm[k] + fp[k]));
+}
+
 // Rusanov flux, Eq. eqn.rusanov: s_max is the larger of the two states' largest |eigenvalue|.
 template <int PDE, int D>
 __device__ __forceinline__ void rusanov(const double* qm, const double* qp, int n, double* out, const Phys& P) {
+  if constexpr (PDE == PDE_EULER) {
+    constexpr int V = D + 2;
+    double fm[V], fp[V];
+    double sm = euler_flux_speed<D>(qm, n, fm, P), sp = euler_flux_speed<D>(qp, n, fp, P);
+    double hs = 0.5 * (sm > sp ? sm : sp);
+#pragma unroll
+    for (int v = 0; v < V; v++) out[v] = fma(-hs, qp[v] - qm[v], 0.5 * (fm[v] + fp[v]));
+    return;
+  }
   using Q = Pde<PDE, D>;
   constexpr int V = Q::V;
   double fm[V], fp[V];
@@ -220,6 +349,7 @@ struct HotArgs {
   Tables T;
   Phys P;
   int bc[6];
+  int flux;             // 0 Rusanov, 1 Osher-Solomon (Euler)
   int level, sub, picard;
   LevelView lv;         // this level
   LevelView lvm;        // mother level (level-1), valid when level >= 1

@@ -29,31 +29,38 @@ __device__ __forceinline__ void weno1d(const Tables& T, const double* v, int str
   double val[W];
   const double c = v[M * stride];
 #pragma unroll
-  for (int e = 0; e < W; e++) val[e] = v[e * stride] - c;
+  for (int e = 0; e < W; e++) val[e] = (e == M) ? 0.0 : v[e * stride] - c;
   double acc[N], sum = 0.0;
 #pragma unroll
   for (int p = 0; p < N; p++) acc[p] = 0.0;
 #pragma unroll
   for (int s = 0; s < NS; s++) {
-    const int o = M - Sten<M>::SL(s);
+    const int o = M - Sten<M>::SL(s);   // stencil cells o..o+M, the centre cell at e = SL(s)
+    // the N-1 nonzero differences of this stencil
+    double d[N - 1];
+#pragma unroll
+    for (int e = 0, k = 0; e < N; e++)
+      if (e != Sten<M>::SL(s)) d[k++] = val[o + e];
     double ws[N];
 #pragma unroll
     for (int p = 0; p < N; p++) {
-      double t = T.Ainv[s][p][0] * val[o];
+      double t = 0.0;
 #pragma unroll
-      for (int e = 1; e < N; e++) t = fma(T.Ainv[s][p][e], val[o + e], t);
+      for (int e = 0, k = 0; e < N; e++)
+        if (e != Sten<M>::SL(s)) t = fma(T.Ainv[s][p][e], d[k++], t);
       ws[p] = t;
     }
     double sig = 0.0;
 #pragma unroll
-    for (int p = 0; p < N; p++) {
-      double t = T.Sig[p][0] * ws[0];
+    for (int i = 0; i < N - 1; i++) {
+      double t = T.Bq[s][i][i] * d[i];
 #pragma unroll
-      for (int m = 1; m < N; m++) t = fma(T.Sig[p][m], ws[m], t);
-      sig = fma(t, ws[p], sig);
+      for (int j = i + 1; j < N - 1; j++) t = fma(T.Bq[s][i][j], d[j], t);
+      sig = fma(t, d[i], sig);
     }
-    double x = sig + 1e-14, x2 = x * x, x4 = x2 * x2, x8 = x4 * x4;
-    double om = T.lam[s] / x8;
+    // lambda_s / (sigma + eps)^8 from the reciprocal of sigma + eps (>= 1e-14)
+    double y = rcp_nr(sig + 1e-14), y2 = y * y, y4 = y2 * y2, y8 = y4 * y4;
+    double om = (s < (M % 2 == 0 ? 1 : 2)) ? 1e5 * y8 : y8;
     sum += om;
 #pragma unroll
     for (int p = 0; p < N; p++) acc[p] = fma(om, ws[p], acc[p]);
@@ -357,29 +364,25 @@ __global__ void __launch_bounds__(PredCfg<D, M, PDE>::THREADS) k_predict(HotArgs
 // ------------------------------------------------------------------------------------------
 template <int D, int M, int PDE>
 struct FluxCfg {
-  static constexpr int N = M + 1, NPT = ipow(N, D), TPC = D * NPT, V = nvars(D, PDE);
-  static constexpr int CPB = (256 / TPC) > 0 ? (256 / TPC) : 1;
-  static constexpr int THREADS = CPB * TPC;
+  static constexpr int N = M + 1, NPT = ipow(N, D), V = nvars(D, PDE);
+  static constexpr int CPB = 256 / NPT;
+  static constexpr int THREADS = CPB * NPT;
   static constexpr int SMEM = THREADS * V * 8;
 };
 
 enum { FK_SAME = 0, FK_FINE = 1, FK_COARSE = 2, FK_BOUNDARY = 3, FK_SKIP = 4 };
 
-template <int D, int M, int PDE>
-__global__ void __launch_bounds__(FluxCfg<D, M, PDE>::THREADS) k_flux(HotArgs a) {
-  using C = FluxCfg<D, M, PDE>;
-  constexpr int N = C::N, NPT = C::NPT, TPC = C::TPC, V = C::V;
-  constexpr int NSP = ipow(N, D), NST = NSP * N;
-  extern __shared__ double sh[];
-  const int lc = threadIdx.x / TPC, rem = threadIdx.x % TPC, d = rem / NPT, g = rem % NPT;
-  const int cell = blockIdx.x * C::CPB + lc;
-  const bool ok = cell < a.na;
+// one face (axis d, side) of an active cell: the point contribution of this thread
+template <int D, int M, int PDE, int d>
+__device__ __forceinline__ int flux_point(const HotArgs& a, bool ok, const int* ijk, const double* qA, int g, int side,
+                                          double* contrib, int* nbo) {
+  constexpr int N = M + 1, V = nvars(D, PDE), NSP = ipow(N, D), NST = NSP * N;
+  constexpr int dstr = ipow(N, d);
   const LevelView& L = a.lv;
-  const int r = a.T.r;
-  // transverse node indices (axes b != d in increasing order) and time node
   int jt[3] = {0, 0, 0}, s;
   {
     int t = g;
+#pragma unroll
     for (int b = 0; b < D; b++) {
       if (b == d) continue;
       jt[b] = t % N;
@@ -387,9 +390,189 @@ __global__ void __launch_bounds__(FluxCfg<D, M, PDE>::THREADS) k_flux(HotArgs a)
     }
     s = t;
   }
+  int nbase = NSP * s;
   double wgt = a.T.w[s];
+#pragma unroll
   for (int b = 0; b < D; b++)
-    if (b != d) wgt *= a.T.w[jt[b]];
+    if (b != d) { nbase += jt[b] * ipow(N, b); wgt *= a.T.w[jt[b]]; }
+  int kind = FK_SKIP;
+  int nb[3] = {ijk[0], ijk[1], ijk[2]};
+  long long nbd = 0;
+  if (ok) {
+    bool inside = bcmap(L.L, a.bc, d, ijk[d] + (side ? 1 : -1), &nb[d]);
+    if (!inside) kind = FK_BOUNDARY;
+    else {
+      nbd = didx(L, nb[0], nb[1], nb[2]);
+      int8_t sn = L.st[nbd];
+      kind = sn == 0 ? (side ? FK_SKIP : FK_SAME) : (sn == 1 ? FK_FINE : FK_COARSE);
+    }
+  }
+  nbo[0] = nb[0]; nbo[1] = nb[1]; nbo[2] = nb[2];
+#pragma unroll
+  for (int v = 0; v < V; v++) contrib[v] = 0.0;
+  if (kind == FK_SAME || kind == FK_FINE || kind == FK_BOUNDARY) {
+    const double* pa = side ? a.T.psi1 : a.T.psi0;
+    double qa[V], qb[V], f[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+      double t = pa[0] * qA[v * NST + nbase];
+#pragma unroll
+      for (int k = 1; k < N; k++) t = fma(pa[k], qA[v * NST + nbase + k * dstr], t);
+      qa[v] = t;
+    }
+    if (kind == FK_BOUNDARY) {
+      Pde<PDE, D>::flux(qa, d, f, a.P);
+    } else {
+      if (kind == FK_SAME) {
+        const double* qB = a.qh + (long long)L.aid[nbd] * V * NST;
+        const double* pb = side ? a.T.psi0 : a.T.psi1;
+#pragma unroll
+        for (int v = 0; v < V; v++) {
+          double t = pb[0] * qB[v * NST + nbase];
+#pragma unroll
+          for (int k = 1; k < N; k++) t = fma(pb[k], qB[v * NST + nbase + k * dstr], t);
+          qb[v] = t;
+        }
+      } else {
+        // coarse mother of the virtual neighbour, evaluated at this cell's face point and sub-step
+        const LevelView& Lm = a.lvm;
+        const int r = a.T.r;
+        int cm[3] = {nb[0] / r, nb[1] / r, D == 3 ? nb[2] / r : 0};
+        const double* qC = a.qhm + (long long)Lm.aid[didx(Lm, cm[0], cm[1], cm[2])] * V * NST;
+        double bas[D][N], bt[N];
+#pragma unroll
+        for (int b = 0; b < D; b++)
+#pragma unroll
+          for (int l = 0; l < N; l++)
+            bas[b][l] = (b == d) ? (side ? a.T.psi0[l] : a.T.psi1[l]) : a.T.Pf[ijk[b] - r * cm[b]][jt[b]][l];
+#pragma unroll
+        for (int l = 0; l < N; l++) bt[l] = a.T.Pf[a.sub][s][l];
+#pragma unroll
+        for (int v = 0; v < V; v++) qb[v] = 0.0;
+        for (int nn = 0; nn < NST; nn++) {
+          int t = nn;
+          double th = 1.0;
+#pragma unroll
+          for (int b = 0; b < D; b++) { th *= bas[b][t % N]; t /= N; }
+          th *= bt[t];
+#pragma unroll
+          for (int v = 0; v < V; v++) qb[v] = fma(th, qC[v * NST + nn], qb[v]);
+        }
+      }
+      const double* ql = side ? qa : qb;
+      const double* qr = side ? qb : qa;
+      if constexpr (PDE == PDE_EULER) {
+        if (a.flux == 1) osher_euler<D>(ql, qr, d, f, a.P);
+        else rusanov<PDE, D>(ql, qr, d, f, a.P);
+      } else {
+        rusanov<PDE, D>(ql, qr, d, f, a.P);
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < V; v++) contrib[v] = wgt * f[v];
+  }
+  return kind;
+}
+
+// reduce the point contributions of every (cell, variable) of the CTA and finish the face
+template <int D, int M, int PDE, int d>
+__device__ __forceinline__ void flux_finish(const HotArgs& a, const double* sh, const int* skind, const int* snb,
+                                            int side) {
+  constexpr int N = M + 1, NPT = ipow(N, D), V = nvars(D, PDE);
+  constexpr int CPB = FluxCfg<D, M, PDE>::CPB;
+  const int t = threadIdx.x;
+  if (t >= CPB * V) return;
+  const int lc = t / V, v = t % V;
+  const int cell = blockIdx.x * CPB + lc;
+  const int kind = skind[lc];
+  if (cell >= a.na || kind == FK_SKIP) return;
+  const LevelView& L = a.lv;
+  const double dt = a.dtl[a.level];
+  double area = 1.0;
+#pragma unroll
+  for (int b = 0; b < D; b++)
+    if (b != d) area *= L.dx[b];
+  double F;
+  if (kind == FK_COARSE) {
+    // fine cells of the refined neighbour that touch this face; their memory slot faces this cell
+    const LevelView& Lc = a.lvc;
+    const int r = a.T.r;
+    long long di = a.alist[cell];
+    int ijk[3] = {(int)(di % L.L[0]), (int)((di / L.L[0]) % L.L[1]), (int)(di / ((long long)L.L[0] * L.L[1]))};
+    const int* nb = snb + 3 * lc;
+    constexpr int t0 = d == 0 ? 1 : 0;
+    constexpr int t1 = d == 2 ? 1 : 2;
+    double acc = 0.0;
+    const int nr2 = (D == 3) ? r : 1;
+    for (int c1 = 0; c1 < nr2; c1++)
+      for (int c0 = 0; c0 < r; c0++) {
+        int fc[3] = {0, 0, 0};
+        fc[d] = side ? r * nb[d] : r * nb[d] + r - 1;
+        fc[t0] = r * ijk[t0] + c0;
+        if (D == 3) fc[t1] = r * ijk[t1] + c1;
+        int fa = Lc.aid[didx(Lc, fc[0], fc[1], fc[2])];
+        if (fa < 0) { atomicOr(a.err, 2); continue; }
+        double* m = a.memc + ((long long)fa * 2 * D + 2 * d + (1 - side)) * V + v;
+        acc += *m;
+        *m = 0.0;
+      }
+    F = acc / (dt * area);
+  } else {
+    double acc = 0.0;
+    const double* src = sh + (lc * NPT) * V + v;
+#pragma unroll
+    for (int g = 0; g < NPT; g++) acc += src[g * V];
+    F = acc;
+  }
+  a.fl[((long long)cell * 2 * D + 2 * d + side) * V + v] = F;
+  if (kind == FK_FINE) a.mem[((long long)cell * 2 * D + 2 * d + side) * V + v] += F * dt * area;
+}
+
+template <int D, int M, int PDE, int d>
+__device__ __forceinline__ void flux_axis(const HotArgs& a, bool ok, const int* ijk, const double* qA, int lc, int g,
+                                          double* sh, int* skind, int* snb) {
+  constexpr int V = nvars(D, PDE);
+  for (int side = 0; side < 2; side++) {
+    double contrib[V];
+    int nb[3];
+    int kind = flux_point<D, M, PDE, d>(a, ok, ijk, qA, g, side, contrib, nb);
+    // the high side is only needed where the neighbour is not an active cell of this level
+    if (side == 1 && !__syncthreads_or(kind != FK_SKIP)) break;
+#pragma unroll
+    for (int v = 0; v < V; v++) sh[threadIdx.x * V + v] = contrib[v];
+    if (g == 0) {
+      skind[lc] = ok ? kind : FK_SKIP;
+      snb[3 * lc] = nb[0]; snb[3 * lc + 1] = nb[1]; snb[3 * lc + 2] = nb[2];
+    }
+    __syncthreads();
+    flux_finish<D, M, PDE, d>(a, sh, skind, snb, side);
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------------
+// Face flux kernel (Eqs. flux:F..flux:H, eqn.rusanov, eqn.memory.sum).  One thread per (active
+// cell, face quadrature point), looping over the axes; the N^(d-1) x N space-time Gauss points
+// of a face coincide with the nodal points, so a trace is one N-term contraction along the
+// normal.  Each active cell computes its low face on every axis, and its high face where the
+// neighbour is not an active cell of the same level (boundary, coarse or fine neighbour).
+// Faces toward a virtual child are fine sides of a coarse/fine face: the coarse predictor is
+// evaluated at this cell's points and sub-step, and the face integral is added to this cell's
+// memory variable.  Faces toward a virtual mother are coarse sides: the flux is the sum of the
+// fine cells' memory variables over the r sub-steps, normalised by dt * area of this level.
+// ------------------------------------------------------------------------------------------
+template <int D, int M, int PDE>
+__global__ void __launch_bounds__(FluxCfg<D, M, PDE>::THREADS) k_flux(HotArgs a) {
+  using C = FluxCfg<D, M, PDE>;
+  constexpr int N = M + 1, NPT = C::NPT, V = C::V;
+  constexpr int NST = ipow(N, D + 1);
+  extern __shared__ double sh[];
+  __shared__ int skind[C::CPB];
+  __shared__ int snb[3 * C::CPB];
+  const int lc = threadIdx.x / NPT, g = threadIdx.x % NPT;
+  const int cell = blockIdx.x * C::CPB + lc;
+  const bool ok = cell < a.na;
+  const LevelView& L = a.lv;
   int ijk[3] = {0, 0, 0};
   if (ok) {
     long long di = a.alist[cell];
@@ -397,142 +580,10 @@ __global__ void __launch_bounds__(FluxCfg<D, M, PDE>::THREADS) k_flux(HotArgs a)
     ijk[1] = (int)((di / L.L[0]) % L.L[1]);
     ijk[2] = (int)(di / ((long long)L.L[0] * L.L[1]));
   }
-  const double dt = a.dtl[a.level];
-  double area = 1.0;
-  for (int b = 0; b < D; b++)
-    if (b != d) area *= L.dx[b];
   const double* qA = a.qh + (long long)(ok ? cell : 0) * V * NST;
-  // node index with i_d = k, transverse jt, time s
-  int nbase = NSP * s;
-  {
-    int st = 1;
-    for (int b = 0; b < D; b++) {
-      if (b != d) nbase += jt[b] * st;
-      st *= N;
-    }
-  }
-  const int dstr = (d == 0 ? 1 : (d == 1 ? N : N * N));
-
-  for (int side = 0; side < 2; side++) {
-    int kind = FK_SKIP;
-    int nb[3] = {ijk[0], ijk[1], ijk[2]};
-    long long nbd = 0;
-    if (ok) {
-      bool inside = bcmap(L.L, a.bc, d, ijk[d] + (side ? 1 : -1), &nb[d]);
-      if (!inside) kind = FK_BOUNDARY;
-      else {
-        nbd = didx(L, nb[0], nb[1], nb[2]);
-        int8_t sn = L.st[nbd];
-        kind = sn == 0 ? (side ? FK_SKIP : FK_SAME) : (sn == 1 ? FK_FINE : FK_COARSE);
-      }
-    }
-    double contrib[V];
-#pragma unroll
-    for (int v = 0; v < V; v++) contrib[v] = 0.0;
-    if (kind == FK_SAME || kind == FK_FINE || kind == FK_BOUNDARY) {
-      const double* pa = side ? a.T.psi1 : a.T.psi0;
-      double qa[V], qb[V], f[V];
-#pragma unroll
-      for (int v = 0; v < V; v++) {
-        double t = 0.0;
-#pragma unroll
-        for (int k = 0; k < N; k++) t = fma(pa[k], qA[v * NST + nbase + k * dstr], t);
-        qa[v] = t;
-      }
-      if (kind == FK_BOUNDARY) {
-        Pde<PDE, D>::flux(qa, d, f, a.P);
-      } else {
-        if (kind == FK_SAME) {
-          const double* qB = a.qh + (long long)L.aid[nbd] * V * NST;
-          const double* pb = side ? a.T.psi0 : a.T.psi1;
-#pragma unroll
-          for (int v = 0; v < V; v++) {
-            double t = 0.0;
-#pragma unroll
-            for (int k = 0; k < N; k++) t = fma(pb[k], qB[v * NST + nbase + k * dstr], t);
-            qb[v] = t;
-          }
-        } else {
-          // coarse mother of the virtual neighbour, evaluated at this cell's face point
-          const LevelView& Lm = a.lvm;
-          int cm[3] = {nb[0] / r, nb[1] / r, D == 3 ? nb[2] / r : 0};
-          long long mdi = didx(Lm, cm[0], cm[1], cm[2]);
-          const double* qC = a.qhm + (long long)Lm.aid[mdi] * V * NST;
-          double bas[3][N], bt[N];
-          for (int b = 0; b < D; b++) {
-#pragma unroll
-            for (int l = 0; l < N; l++)
-              bas[b][l] = (b == d) ? (side ? a.T.psi0[l] : a.T.psi1[l])
-                                   : a.T.Pf[ijk[b] - r * cm[b]][jt[b]][l];
-          }
-#pragma unroll
-          for (int l = 0; l < N; l++) bt[l] = a.T.Pf[a.sub][s][l];
-#pragma unroll
-          for (int v = 0; v < V; v++) qb[v] = 0.0;
-          for (int nn = 0; nn < NST; nn++) {
-            int t = nn;
-            double th = 1.0;
-            for (int b = 0; b < D; b++) { th *= bas[b][t % N]; t /= N; }
-            th *= bt[t];
-#pragma unroll
-            for (int v = 0; v < V; v++) qb[v] = fma(th, qC[v * NST + nn], qb[v]);
-          }
-        }
-        if (side) rusanov<PDE, D>(qa, qb, d, f, a.P);
-        else rusanov<PDE, D>(qb, qa, d, f, a.P);
-      }
-#pragma unroll
-      for (int v = 0; v < V; v++) contrib[v] = wgt * f[v];
-    }
-#pragma unroll
-    for (int v = 0; v < V; v++) sh[threadIdx.x * V + v] = contrib[v];
-    __syncthreads();
-    if (ok && g == 0 && kind != FK_SKIP) {
-      double F[V];
-      if (kind == FK_COARSE) {
-        // fine cells of the refined neighbour that touch this face; their memory slot is the
-        // face facing this cell
-        const LevelView& Lc = a.lvc;
-        double acc[V];
-#pragma unroll
-        for (int v = 0; v < V; v++) acc[v] = 0.0;
-        const int nr2 = (D == 3) ? r : 1;
-        int t0 = -1, t1 = -1;
-        for (int b = 0; b < D; b++)
-          if (b != d) { if (t0 < 0) t0 = b; else t1 = b; }
-        for (int c1 = 0; c1 < nr2; c1++)
-          for (int c0 = 0; c0 < r; c0++) {
-            int fc[3] = {0, 0, 0};
-            fc[d] = side ? r * nb[d] : r * nb[d] + r - 1;
-            fc[t0] = r * ijk[t0] + c0;
-            if (D == 3) fc[t1] = r * ijk[t1] + c1;
-            int fa = Lc.aid[didx(Lc, fc[0], fc[1], fc[2])];
-            if (fa < 0) { atomicOr(a.err, 2); continue; }
-            double* m = a.memc + ((long long)fa * 2 * D + 2 * d + (1 - side)) * V;
-#pragma unroll
-            for (int v = 0; v < V; v++) { acc[v] += m[v]; m[v] = 0.0; }
-          }
-#pragma unroll
-        for (int v = 0; v < V; v++) F[v] = acc[v] / (dt * area);
-      } else {
-#pragma unroll
-        for (int v = 0; v < V; v++) {
-          double t = 0.0;
-          for (int gg = 0; gg < NPT; gg++) t += sh[(threadIdx.x + gg) * V + v];
-          F[v] = t;
-        }
-      }
-      double* dst = a.fl + ((long long)cell * 2 * D + 2 * d + side) * V;
-#pragma unroll
-      for (int v = 0; v < V; v++) dst[v] = F[v];
-      if (kind == FK_FINE) {
-        double* m = a.mem + ((long long)cell * 2 * D + 2 * d + side) * V;
-#pragma unroll
-        for (int v = 0; v < V; v++) m[v] += F[v] * dt * area;
-      }
-    }
-    __syncthreads();
-  }
+  flux_axis<D, M, PDE, 0>(a, ok, ijk, qA, lc, g, sh, skind, snb);
+  flux_axis<D, M, PDE, 1>(a, ok, ijk, qA, lc, g, sh, skind, snb);
+  if constexpr (D == 3) flux_axis<D, M, PDE, 2>(a, ok, ijk, qA, lc, g, sh, skind, snb);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -1,0 +1,280 @@
+// aw_serve.cu -- request loop for independent AMR solves (continuous admission).
+//
+// Requests (a configuration, an initial condition and an end time) are queued by aw_srv_submit.
+// Worker threads admit them in arrival order as soon as their device-memory footprint fits the
+// remaining budget and a worker is free; each admitted request gets its own CUDA stream and
+// solver, so the kernels of concurrent requests overlap on the GPU.  A finished request's cell
+// averages are copied to host memory and its device memory is released at once, which admits
+// the next request.  Every request runs exactly the same kernels as a solve on its own, so its
+// result does not depend on what else is running.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "aderweno.h"
+#include "aw_device.cuh"
+
+namespace {
+
+using clk = std::chrono::steady_clock;
+
+struct Request {
+  int64_t id;
+  aw_config cfg;
+  int32_t ic;
+  std::vector<double> params;
+  double t_end;
+  int64_t footprint;
+  int32_t state = AW_REQ_QUEUED;
+  int32_t rc = AW_OK;
+  std::string err;
+  clk::time_point t_submit, t_start, t_done;
+  int64_t cell_updates = 0, level0_steps = 0;
+  std::vector<aw_cell> meta;
+  std::vector<double> u;
+};
+
+}  // namespace
+
+struct aw_server {
+  int device = 0;
+  int64_t budget = 0, in_use = 0;
+  int nworkers = 1;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<int64_t> queue;
+  std::map<int64_t, Request> req;
+  std::vector<std::thread> workers;
+  bool stop = false;
+  int64_t next_id = 1;
+  int running = 0;
+  clk::time_point t_first_submit;
+  bool any_submitted = false;
+};
+
+// Device bytes one solve of `c` needs: the dense per-level grids (exact) plus per-active arrays
+// for a quarter of the finest level's cells (the AMR meshes of these workloads stay below that)
+// and a fixed allowance for the CUDA context's share and staging buffers.
+static int64_t footprint_bytes(const aw_config& c) {
+  int V = aw::nvars(c.dim, c.pde), N = c.M + 1;
+  int64_t nsp = 1;
+  for (int a = 0; a < c.dim; a++) nsp *= N;
+  int64_t nst = nsp * N;
+  int64_t dense_per_cell = 8 * V + 4 + 8 + 4 * 5;
+  int64_t active_per_cell = 8 * (V * nsp + V * nst + 4 * c.dim * V);
+  int64_t total = 0, finest = 0, rr = 1;
+  int r = c.lmax > 0 ? c.refine_factor : 1;
+  for (int l = 0; l <= c.lmax; l++) {
+    int64_t n = (int64_t)c.nx * rr * c.ny * rr * (c.dim == 3 ? c.nz * rr : 1);
+    total += n * dense_per_cell;
+    finest = n;
+    rr *= r;
+  }
+  return total + finest / 4 * active_per_cell + ((int64_t)64 << 20);
+}
+
+static void run_request(aw_server* S, Request& R) {
+  cudaSetDevice(S->device);
+  cudaStream_t st = nullptr;
+  aw_solver* sol = nullptr;
+  int rc = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess ? AW_OK : AW_ECUDA;
+  if (rc == AW_OK) rc = aw_create(&R.cfg, (uintptr_t)st, &sol);
+  if (rc == AW_OK)
+    rc = aw_set_initial(sol, R.ic, R.params.empty() ? nullptr : R.params.data(), (int32_t)R.params.size(), -1);
+  aw_stats stats;
+  memset(&stats, 0, sizeof stats);
+  if (rc == AW_OK) rc = aw_advance_to(sol, R.t_end, &stats);
+  if (rc == AW_OK) {
+    int64_t n = 0;
+    aw_get_counts(sol, &n, nullptr, nullptr, nullptr);
+    R.meta.resize(n);
+    R.u.resize((size_t)n * aw::nvars(R.cfg.dim, R.cfg.pde));
+    rc = aw_read_cells(sol, R.meta.data(), R.u.data(), n, &n);
+  }
+  if (rc != AW_OK) R.err = aw_last_error();
+  R.cell_updates = stats.cell_updates;
+  R.level0_steps = stats.level0_steps;
+  aw_destroy(sol);
+  if (st) cudaStreamDestroy(st);
+  R.rc = rc;
+}
+
+static void worker_main(aw_server* S) {
+  std::unique_lock<std::mutex> lk(S->mu);
+  for (;;) {
+    // the oldest queued request that fits the remaining budget (arrival order)
+    int64_t pick = -1;
+    S->cv_work.wait(lk, [&] {
+      if (S->stop) return true;
+      pick = -1;
+      if (!S->queue.empty()) {
+        int64_t id = S->queue.front();
+        if (S->in_use + S->req[id].footprint <= S->budget) pick = id;
+      }
+      return pick >= 0;
+    });
+    if (S->stop) return;
+    S->queue.pop_front();
+    Request& R = S->req[pick];
+    S->in_use += R.footprint;
+    S->running++;
+    R.state = AW_REQ_RUNNING;
+    R.t_start = clk::now();
+    lk.unlock();
+    run_request(S, R);
+    lk.lock();
+    R.t_done = clk::now();
+    R.state = R.rc == AW_OK ? AW_REQ_DONE : AW_REQ_FAILED;
+    S->in_use -= R.footprint;
+    S->running--;
+    S->cv_done.notify_all();
+    S->cv_work.notify_all();
+  }
+}
+
+static thread_local std::string g_srv_err;
+#define SRV_FAIL(code, msg) \
+  do {                      \
+    g_srv_err = msg;        \
+    return code;            \
+  } while (0)
+
+extern "C" {
+
+const char* aw_srv_last_error(void) { return g_srv_err.c_str(); }
+
+int aw_srv_create(int64_t hbm_budget_bytes, int32_t max_concurrent, aw_server** out) {
+  if (!out || hbm_budget_bytes <= 0 || max_concurrent < 1 || max_concurrent > 256)
+    SRV_FAIL(AW_EINVAL, "bad server arguments");
+  aw_server* S = new aw_server();
+  cudaGetDevice(&S->device);
+  S->budget = hbm_budget_bytes;
+  S->nworkers = max_concurrent;
+  for (int i = 0; i < max_concurrent; i++) S->workers.emplace_back(worker_main, S);
+  *out = S;
+  return AW_OK;
+}
+
+int aw_srv_submit(aw_server* S, const aw_config* cfg, int32_t ic_kind, const double* params, int32_t nparams,
+                  double t_end, int64_t* id) {
+  if (!S || !cfg || !id || nparams < 0 || (nparams > 0 && !params)) SRV_FAIL(AW_EINVAL, "null argument");
+  Request R;
+  R.cfg = *cfg;
+  R.ic = ic_kind;
+  R.params.assign(params, params + nparams);
+  R.t_end = t_end;
+  R.footprint = footprint_bytes(*cfg);
+  if (R.footprint > S->budget) SRV_FAIL(AW_EINVAL, "request needs more device memory than the whole budget");
+  std::lock_guard<std::mutex> lk(S->mu);
+  R.id = S->next_id++;
+  R.t_submit = clk::now();
+  if (!S->any_submitted) {
+    S->any_submitted = true;
+    S->t_first_submit = R.t_submit;
+  }
+  S->req[R.id] = std::move(R);
+  S->queue.push_back(S->req.rbegin()->first);
+  *id = S->req.rbegin()->first;
+  S->cv_work.notify_all();
+  return AW_OK;
+}
+
+int aw_srv_poll(aw_server* S, int64_t id, int32_t* state) {
+  if (!S || !state) SRV_FAIL(AW_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->req.find(id);
+  if (it == S->req.end()) SRV_FAIL(AW_EINVAL, "unknown request id");
+  *state = it->second.state;
+  return AW_OK;
+}
+
+int aw_srv_wait_all(aw_server* S) {
+  if (!S) SRV_FAIL(AW_EINVAL, "null server");
+  std::unique_lock<std::mutex> lk(S->mu);
+  S->cv_done.wait(lk, [&] { return S->queue.empty() && S->running == 0; });
+  return AW_OK;
+}
+
+int aw_srv_result(aw_server* S, int64_t id, aw_cell* meta, double* u, int64_t cap, int64_t* n, aw_srv_info* info) {
+  if (!S || !n) SRV_FAIL(AW_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(S->mu);
+  auto it = S->req.find(id);
+  if (it == S->req.end()) SRV_FAIL(AW_EINVAL, "unknown request id");
+  Request& R = it->second;
+  if (R.state == AW_REQ_FAILED) {
+    g_srv_err = R.err;
+    return R.rc;
+  }
+  if (R.state != AW_REQ_DONE) SRV_FAIL(AW_ESTATE, "request not finished");
+  *n = (int64_t)R.meta.size();
+  if (info) {
+    info->cell_updates = R.cell_updates;
+    info->level0_steps = R.level0_steps;
+    info->queue_ms = std::chrono::duration<double, std::milli>(R.t_start - R.t_submit).count();
+    info->run_ms = std::chrono::duration<double, std::milli>(R.t_done - R.t_start).count();
+    info->total_ms = std::chrono::duration<double, std::milli>(R.t_done - R.t_submit).count();
+    info->footprint_bytes = R.footprint;
+  }
+  if (cap < *n) SRV_FAIL(AW_EINVAL, "capacity too small");
+  if (meta) memcpy(meta, R.meta.data(), sizeof(aw_cell) * R.meta.size());
+  if (u) memcpy(u, R.u.data(), sizeof(double) * R.u.size());
+  return AW_OK;
+}
+
+int aw_srv_stats(aw_server* S, aw_srv_summary* out) {
+  if (!S || !out) SRV_FAIL(AW_EINVAL, "null argument");
+  std::lock_guard<std::mutex> lk(S->mu);
+  std::vector<double> tts;
+  int64_t upd = 0, failed = 0;
+  clk::time_point last = S->t_first_submit;
+  for (auto& kv : S->req) {
+    const Request& R = kv.second;
+    if (R.state == AW_REQ_DONE) {
+      tts.push_back(std::chrono::duration<double, std::milli>(R.t_done - R.t_submit).count());
+      upd += R.cell_updates;
+      last = std::max(last, R.t_done);
+    } else if (R.state == AW_REQ_FAILED) {
+      failed++;
+    }
+  }
+  memset(out, 0, sizeof *out);
+  out->done = (int64_t)tts.size();
+  out->failed = failed;
+  out->queued = (int64_t)S->queue.size();
+  out->running = S->running;
+  if (!tts.empty()) {
+    std::sort(tts.begin(), tts.end());
+    auto pct = [&](double p) {
+      size_t k = (size_t)std::min<double>(tts.size() - 1, std::ceil(p * tts.size()) - 1);
+      return tts[k];
+    };
+    out->p50_ms = pct(0.50);
+    out->p99_ms = pct(0.99);
+    double span = std::chrono::duration<double>(last - S->t_first_submit).count();
+    out->solves_per_s = span > 0 ? tts.size() / span : 0.0;
+    out->cell_updates_per_s = span > 0 ? upd / span : 0.0;
+  }
+  return AW_OK;
+}
+
+void aw_srv_destroy(aw_server* S) {
+  if (!S) return;
+  {
+    std::lock_guard<std::mutex> lk(S->mu);
+    S->stop = true;
+    S->queue.clear();
+  }
+  S->cv_work.notify_all();
+  for (auto& t : S->workers) t.join();
+  delete S;
+}
+
+}  // extern "C"

@@ -762,6 +762,7 @@ static HotArgs make_args(const aw_solver* s, int l, int sub) {
   a.level = l;
   a.sub = sub;
   a.picard = s->P;
+  a.flux = s->cfg.flux;
   a.lv = view(s, l);
   if (l >= 1) a.lvm = view(s, l - 1);
   if (l < s->lmax) a.lvc = view(s, l + 1);
@@ -1045,6 +1046,13 @@ __global__ void k_dt_final(const double* partial, int nb, double* out) {
   }
 }
 
+__global__ void k_selftest_rcp(const double* x, long long n, double* out) {
+  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  out[k] = rcp_nr(x[k]);
+  out[n + k] = 1.0 / x[k];
+}
+
 // ------------------------------------------------------------------------------------------
 // C ABI
 // ------------------------------------------------------------------------------------------
@@ -1077,7 +1085,9 @@ int aw_create(const aw_config* cfg, uintptr_t stream, aw_solver** out) {
         AW_FAIL(AW_EINVAL, "unknown boundary condition %d", c.bc[2 * a + sd]);
   }
   if (!(c.cfl > 0.0)) AW_FAIL(AW_EINVAL, "cfl must be positive");
-  if (c.flux != AW_FLUX_RUSANOV) AW_FAIL(AW_EINVAL, "only the Rusanov flux is available");
+  if (c.flux != AW_FLUX_RUSANOV && c.flux != AW_FLUX_OSHER) AW_FAIL(AW_EINVAL, "unknown numerical flux %d", c.flux);
+  if (c.flux == AW_FLUX_OSHER && c.pde == AW_PDE_MHD_GLM)
+    AW_FAIL(AW_EINVAL, "the Osher flux is available for the Euler equations and linear advection");
   aw_solver* s = new aw_solver();
   s->cfg = c;
   s->D = c.dim;
@@ -1505,6 +1515,14 @@ int aw_cfl_dt_noalloc(const aw_config* cfg, const double* u_dev, int64_t n_cells
   cudaStream_t st = (cudaStream_t)stream;
   k_dt_blockmin<<<(unsigned)nb, AW_NOALLOC_BLOCK, 0, st>>>(u_dev, n, R, dx0, dx1, dx2, c.cfl, g_noalloc_ptr[dev]);
   k_dt_final<<<1, 1024, 0, st>>>(g_noalloc_ptr[dev], (int)nb, dt_dev);
+  CK(cudaGetLastError());
+  return AW_OK;
+}
+
+int aw_selftest_reciprocal(const double* x_dev, int64_t n, double* out_dev, uintptr_t stream) {
+  if (!x_dev || !out_dev || n < 0) AW_FAIL(AW_EINVAL, "bad argument");
+  if (n == 0) return AW_OK;
+  k_selftest_rcp<<<nblk(n, 256), 256, 0, (cudaStream_t)stream>>>(x_dev, n, out_dev);
   CK(cudaGetLastError());
   return AW_OK;
 }

@@ -163,6 +163,23 @@ bool build_tables(int M, int r, Tables* T) {
     for (int p = 0; p < N; p++)
       for (int m = 0; m < N; m++) T->Sig[p][m] = (double)S[p][m];
   }
+  // sigma_s as a quadratic form of the stencil differences
+  for (int s = 0; s < NS; s++) {
+    LD B[MAXN][MAXN];
+    for (int e = 0; e < N; e++)
+      for (int f = 0; f < N; f++) {
+        LD acc = 0.0L;
+        for (int p = 0; p < N; p++)
+          for (int m = 0; m < N; m++) acc += (LD)T->Ainv[s][p][e] * (LD)T->Sig[p][m] * (LD)T->Ainv[s][m][f];
+        B[e][f] = acc;
+      }
+    int idx[MAXN], k = 0;
+    for (int e = 0; e < N; e++)
+      if (e != SL[s]) idx[k++] = e;
+    for (int i = 0; i < N - 1; i++)
+      for (int j = 0; j < N - 1; j++)
+        T->Bq[s][i][j] = j < i ? 0.0 : (double)((j == i ? 1.0L : 2.0L) * B[idx[i]][idx[j]]);
+  }
   // time block of K1 and G = K_t^{-1} diag(w)
   {
     std::vector<LD> Kt(N * N), Ki;

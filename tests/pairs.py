@@ -9,8 +9,9 @@ import numpy as np
 import oracle
 import paper_1212_3585_gb300 as pg
 
-# conserved-variable tolerance: max |gpu - oracle| over cells, divided by the largest |oracle|
-# of that variable on the mesh (momentum components can vanish pointwise)
+# tolerance of the normwise relative error per step: max |gpu - oracle| over cells and
+# variables, divided by the largest |oracle| over the whole field (variables that stay near zero,
+# such as the GLM cleaning variable psi, are measured against the state's magnitude)
 RTOL = 1e-10
 
 PDE_MAP = {"euler": (oracle.PDE_EULER, pg.AW_PDE_EULER), "mhd": (oracle.PDE_MHD, pg.AW_PDE_MHD_GLM),
@@ -25,24 +26,21 @@ def rel_err(a, b):
     b = np.asarray(b, dtype=np.float64)
     if a.size == 0 and b.size == 0:
         return 0.0
-    if a.ndim == 1:
-        a = a[:, None]
-        b = b[:, None]
-    scale = np.maximum(np.max(np.abs(b), axis=0), 1e-300)
-    return float(np.max(np.max(np.abs(a - b), axis=0) / scale))
+    scale = max(float(np.max(np.abs(b))), 1e-300)
+    return float(np.max(np.abs(a - b)) / scale)
 
 
 class Pair:
     def __init__(self, dim=2, pde="euler", M=2, n=(16, 16, 1), lo=(0, 0, 0), hi=(1, 1, 1), bc="periodic",
                  r=3, lmax=0, gamma=1.4, c_h=2.0, chi_ref=0.2, chi_rec=0.1, cfl=0.9, adv=(1.0, 0.5, 0.25),
-                 threads=8):
+                 threads=8, flux=0):
         op, gp = PDE_MAP[pde]
         obc = oracle.BC_PERIODIC if bc == "periodic" else oracle.BC_TRANSMISSIVE
         gbc = pg.AW_BC_PERIODIC if bc == "periodic" else pg.AW_BC_TRANSMISSIVE
         kw = dict(dim=dim, M=M, n=n, lo=lo, hi=hi, r=r, lmax=lmax, gamma=gamma, c_h=c_h, chi_ref=chi_ref,
                   chi_rec=chi_rec, cfl=cfl, auto_regrid=0, adv=adv)
-        self.o = oracle.Oracle(oracle.make_cfg(pde=op, bc=obc, **kw), threads=threads)
-        self.g = pg.Solver(pg.make_config(pde=gp, bc=gbc, **kw))
+        self.o = oracle.Oracle(oracle.make_cfg(pde=op, bc=obc, flux=flux, **kw), threads=threads)
+        self.g = pg.Solver(pg.make_config(pde=gp, bc=gbc, flux=flux, **kw))
         self.lmax = lmax
 
     def init(self, ic, params, passes=None):

@@ -147,3 +147,14 @@ def test_empty_levels_and_errors():
     with pytest.raises(pg.AwError) as ei:
         g.step_dt(1e-3)
     assert ei.value.code == pg._lib.AW_ENONPHYSICAL
+
+
+@pytest.mark.parametrize("dim,M,lmax", [(2, 3, 0), (2, 3, 2), (3, 2, 1)])
+def test_osher_flux_explosion(dim, M, lmax):
+    """Osher-Solomon flux (Eq. eqn.osher), uniform and AMR with local time stepping"""
+    n = (16, 16, 1) if dim == 2 else (6, 6, 6)
+    p = Pair(dim=dim, M=M, n=n, lo=(-1, -1, -1), hi=(1, 1, 1), bc="transmissive", r=3, lmax=lmax, cfl=0.6,
+             flux=1)
+    p.init("explosion", EXPL)
+    for _ in range(2):
+        p.step()
