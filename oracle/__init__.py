@@ -30,6 +30,7 @@ class OrcCfg(C.Structure):
         ("chi_ref", C.c_double), ("chi_rec", C.c_double), ("eps_ind", C.c_double), ("cfl", C.c_double),
         ("picard", C.c_int), ("auto_regrid", C.c_int),
         ("adv", C.c_double * 3),
+        ("flux", C.c_int),
     ]
 
 
@@ -82,6 +83,8 @@ def lib():
         L.orc_max_speed.restype = C.c_double
         L.orc_max_speed.argtypes = [C.c_void_p, dp, C.c_int]
         L.orc_rusanov.argtypes = [C.c_void_p, dp, dp, C.c_int, dp]
+        L.orc_osher.argtypes = [C.c_void_p, dp, dp, C.c_int, dp]
+        L.orc_abs_jacobian_apply.argtypes = [C.c_void_p, dp, C.c_int, dp, dp]
         L.orc_eval_st.argtypes = [C.c_void_p, dp, dp, C.c_double, dp]
         L.orc_eval_sp.argtypes = [C.c_void_p, dp, dp, dp]
         L.orc_project_st.argtypes = [C.c_void_p, dp, ip, C.c_double, dp]
@@ -101,7 +104,7 @@ def _dp(a):
 
 def make_cfg(dim=2, pde=PDE_EULER, M=2, n=(16, 16, 1), gamma=1.4, c_h=2.0, lo=(0.0, 0.0, 0.0),
              hi=(1.0, 1.0, 1.0), bc=BC_PERIODIC, r=3, lmax=0, chi_ref=0.2, chi_rec=0.1, eps_ind=0.01,
-             cfl=0.9, picard=0, auto_regrid=1, adv=(1.0, 1.0, 1.0)):
+             cfl=0.9, picard=0, auto_regrid=1, adv=(1.0, 1.0, 1.0), flux=0):
     c = OrcCfg()
     c.dim, c.pde, c.M = dim, pde, M
     c.nx, c.ny, c.nz = n[0], n[1], (n[2] if dim == 3 else 1)
@@ -114,6 +117,7 @@ def make_cfg(dim=2, pde=PDE_EULER, M=2, n=(16, 16, 1), gamma=1.4, c_h=2.0, lo=(0
     c.r, c.lmax = r, lmax
     c.chi_ref, c.chi_rec, c.eps_ind, c.cfl = chi_ref, chi_rec, eps_ind, cfl
     c.picard, c.auto_regrid = picard, auto_regrid
+    c.flux = flux
     return c
 
 
@@ -230,6 +234,25 @@ class Oracle:
         f = np.zeros(self.V)
         self.L.orc_rusanov(self.h, _dp(qm), _dp(qp), n, _dp(f))
         return f
+
+    def osher(self, qm, qp, n):
+        qm = np.ascontiguousarray(qm, dtype=np.float64)
+        qp = np.ascontiguousarray(qp, dtype=np.float64)
+        f = np.zeros(self.V)
+        self.L.orc_osher(self.h, _dp(qm), _dp(qp), n, _dp(f))
+        return f
+
+    def abs_jacobian(self, q, n):
+        """the matrix |A(q)| (columns = |A| applied to unit vectors)"""
+        q = np.ascontiguousarray(q, dtype=np.float64)
+        out = np.zeros((self.V, self.V))
+        for j in range(self.V):
+            e = np.zeros(self.V)
+            e[j] = 1.0
+            col = np.zeros(self.V)
+            self.L.orc_abs_jacobian_apply(self.h, _dp(q), n, _dp(e), _dp(col))
+            out[:, j] = col
+        return out
 
     def eval_st(self, qh, xi, tau):
         qh = np.ascontiguousarray(qh, dtype=np.float64)

@@ -52,6 +52,7 @@ typedef struct {
   int picard;
   int auto_regrid;
   double adv[3];
+  int flux; /* 0 Rusanov, 1 Osher-Solomon (Dumbser-Toro) */
 } orc_cfg;
 
 static char g_err[512];
@@ -331,7 +332,7 @@ static void free_tables(tables *T) {
  *    cleaning (Sec. 4.2) in rationalised units (reading: the 4*pi factors dropped),
  *    plus linear advection as a test system.
  * =================================================================================== */
-typedef struct { int pde, d, V; double gamma, c_h, adv[3]; } phys;
+typedef struct { int pde, d, V, flux; double gamma, c_h, adv[3]; } phys;
 
 static void flux(const phys *P, const double *q, int n, double *f) {
   if (P->pde == PDE_LINADV) { f[0] = P->adv[n] * q[0]; return; }
@@ -410,6 +411,87 @@ static void rusanov(const phys *P, const double *qm, const double *qp, int n, do
   double sm = max_speed(P, qm, n), sp = max_speed(P, qp, n);
   double s = sm > sp ? sm : sp;
   for (int v = 0; v < P->V; v++) out[v] = 0.5 * (fm[v] + fp[v]) - 0.5 * s * (qp[v] - qm[v]);
+}
+
+/* |A(q)| applied to dq for the Euler flux in direction n: R |Lambda| L dq with the right and left
+ * eigenvectors of the Jacobian written out (eigenvalues u_n - c, u_n (d times), u_n + c).  A state
+ * with c^2 <= 0 has complex eigenvalues; there |A| dq is replaced by s dq with s the spectral
+ * radius (reading).  Linear advection: |a_n| dq. */
+static void abs_jacobian_apply(const phys *P, const double *q, int n, const double *dq, double *out) {
+  int V = P->V, d = P->d;
+  if (P->pde == PDE_LINADV) { out[0] = fabs(P->adv[n]) * dq[0]; return; }
+  double rho = q[0], vel[3] = {0, 0, 0}, v2 = 0.0;
+  for (int a = 0; a < d; a++) { vel[a] = q[1 + a] / rho; v2 += vel[a] * vel[a]; }
+  double p = pressure(P, q), c2 = P->gamma * p / rho;
+  if (!(c2 > 0.0)) {
+    double s = max_speed(P, q, n);
+    for (int v = 0; v < V; v++) out[v] = s * dq[v];
+    return;
+  }
+  double c = sqrt(c2), H = (q[d + 1] + p) / rho, un = vel[n];
+  double R[5][5] = {{0}}, L[5][5] = {{0}}, lam[5];
+  /* columns: acoustic -, entropy, shear (transverse axes), acoustic + */
+  R[0][0] = 1.0; R[d + 1][0] = H - un * c;
+  R[0][1] = 1.0; R[d + 1][1] = 0.5 * v2;
+  R[0][V - 1] = 1.0; R[d + 1][V - 1] = H + un * c;
+  for (int a = 0; a < d; a++) {
+    R[1 + a][0] = vel[a] - (a == n ? c : 0.0);
+    R[1 + a][1] = vel[a];
+    R[1 + a][V - 1] = vel[a] + (a == n ? c : 0.0);
+  }
+  double b1 = (P->gamma - 1.0) / c2, b2 = 0.5 * v2 * b1;
+  L[0][0] = 0.5 * (b2 + un / c); L[0][d + 1] = 0.5 * b1;
+  L[1][0] = 1.0 - b2; L[1][d + 1] = -b1;
+  L[V - 1][0] = 0.5 * (b2 - un / c); L[V - 1][d + 1] = 0.5 * b1;
+  for (int a = 0; a < d; a++) {
+    L[0][1 + a] = 0.5 * (-b1 * vel[a] - (a == n ? 1.0 / c : 0.0));
+    L[1][1 + a] = b1 * vel[a];
+    L[V - 1][1 + a] = 0.5 * (-b1 * vel[a] + (a == n ? 1.0 / c : 0.0));
+  }
+  lam[0] = un - c; lam[1] = un; lam[V - 1] = un + c;
+  int k = 2;
+  for (int a = 0; a < d; a++) {
+    if (a == n) continue;
+    R[1 + a][k] = 1.0; R[d + 1][k] = vel[a];
+    L[k][0] = -vel[a]; L[k][1 + a] = 1.0;
+    lam[k] = un;
+    k++;
+  }
+  double al[5];
+  for (int i = 0; i < V; i++) {
+    double t = 0.0;
+    for (int j = 0; j < V; j++) t += L[i][j] * dq[j];
+    al[i] = fabs(lam[i]) * t;
+  }
+  for (int i = 0; i < V; i++) {
+    double t = 0.0;
+    for (int j = 0; j < V; j++) t += R[i][j] * al[j];
+    out[i] = t;
+  }
+}
+
+/* Osher-Solomon flux of Dumbser and Toro, Eq. eqn.osher: the path integral of |A| along the
+ * straight segment between the states by 3-point Gauss-Legendre quadrature (reading: the paper
+ * asks for at least two points). */
+static void osher(const phys *P, const double *qm, const double *qp, int n, double *out) {
+  double fm[MAXV], fp[MAXV], dq[MAXV], acc[MAXV] = {0};
+  flux(P, qm, n, fm);
+  flux(P, qp, n, fp);
+  for (int v = 0; v < P->V; v++) dq[v] = qp[v] - qm[v];
+  double s[3], w[3];
+  gauss_legendre01(3, s, w);
+  for (int j = 0; j < 3; j++) {
+    double q[MAXV], t[MAXV];
+    for (int v = 0; v < P->V; v++) q[v] = qm[v] + s[j] * dq[v];
+    abs_jacobian_apply(P, q, n, dq, t);
+    for (int v = 0; v < P->V; v++) acc[v] += w[j] * t[v];
+  }
+  for (int v = 0; v < P->V; v++) out[v] = 0.5 * (fm[v] + fp[v]) - 0.5 * acc[v];
+}
+
+static void numflux(const phys *P, const double *qm, const double *qp, int n, double *out) {
+  if (P->flux == 1) osher(P, qm, qp, n, out);
+  else rusanov(P, qm, qp, n, out);
 }
 
 static int physical(const phys *P, const double *q) {
@@ -939,7 +1021,7 @@ static void face_flux(osolver *S, int lv, const int *ijk, int ia, int a, int sid
       int gs = t;
       wt *= S->T.w[gs];
       eval_st(S, qA, xi, S->T.x[gs], q);
-      rusanov(&S->P, q, q, a, f);
+      numflux(&S->P, q, q, a, f);
       for (int v = 0; v < V; v++) F[v] += wt * f[v];
     }
     return;
@@ -963,8 +1045,8 @@ static void face_flux(osolver *S, int lv, const int *ijk, int ia, int a, int sid
       wt *= S->T.w[gs];
       eval_st(S, qA, xiA, S->T.x[gs], qa);
       eval_st(S, qB, xiB, S->T.x[gs], qb);
-      if (side) rusanov(&S->P, qa, qb, a, f);
-      else rusanov(&S->P, qb, qa, a, f);
+      if (side) numflux(&S->P, qa, qb, a, f);
+      else numflux(&S->P, qb, qa, a, f);
       for (int v = 0; v < V; v++) F[v] += wt * f[v];
     }
     return;
@@ -995,8 +1077,8 @@ static void face_flux(osolver *S, int lv, const int *ijk, int ia, int a, int sid
       wt *= S->T.w[gs];
       eval_st(S, qA, xiA, S->T.x[gs], qa);
       eval_st(S, qC, xiC, (sub + S->T.x[gs]) / r, qc);
-      if (side) rusanov(&S->P, qa, qc, a, f);
-      else rusanov(&S->P, qc, qa, a, f);
+      if (side) numflux(&S->P, qa, qc, a, f);
+      else numflux(&S->P, qc, qa, a, f);
       for (int v = 0; v < V; v++) F[v] += wt * f[v];
     }
     if (addmem) {
@@ -1363,7 +1445,8 @@ void *orc_create(const orc_cfg *c) {
   S->c = *c;
   S->d = c->dim;
   S->N = c->M + 1;
-  S->P.pde = c->pde; S->P.d = c->dim; S->P.gamma = c->gamma; S->P.c_h = c->c_h;
+  S->P.pde = c->pde; S->P.d = c->dim; S->P.gamma = c->gamma; S->P.c_h = c->c_h; S->P.flux = c->flux;
+  if (c->flux == 1 && c->pde == PDE_MHD) { seterr("the Osher flux is available for Euler and linear advection"); return NULL; }
   for (int a = 0; a < 3; a++) S->P.adv[a] = c->adv[a];
   S->V = c->pde == PDE_LINADV ? 1 : (c->pde == PDE_EULER ? c->dim + 2 : 9);
   S->P.V = S->V;
@@ -1650,6 +1733,8 @@ int orc_predictor(void *h, const double *wh, double dt, const double *dx, double
 void orc_flux(void *h, const double *q, int n, double *f) { flux(&((osolver *)h)->P, q, n, f); }
 double orc_max_speed(void *h, const double *q, int n) { return max_speed(&((osolver *)h)->P, q, n); }
 void orc_rusanov(void *h, const double *qm, const double *qp, int n, double *f) { rusanov(&((osolver *)h)->P, qm, qp, n, f); }
+void orc_osher(void *h, const double *qm, const double *qp, int n, double *f) { osher(&((osolver *)h)->P, qm, qp, n, f); }
+void orc_abs_jacobian_apply(void *h, const double *q, int n, const double *dq, double *out) { abs_jacobian_apply(&((osolver *)h)->P, q, n, dq, out); }
 void orc_eval_st(void *h, const double *qh, const double *xi, double tau, double *out) { eval_st(h, qh, xi, tau, out); }
 void orc_eval_sp(void *h, const double *wh, const double *xi, double *out) { eval_sp(h, wh, xi, out); }
 void orc_project_st(void *h, const double *qh, const int *ch, double tau, double *out) { project_st(h, qh, ch, tau, out); }
