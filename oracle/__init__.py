@@ -93,6 +93,8 @@ def lib():
         L.orc_indicator_at.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int]
         L.orc_ic_average.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_int, dp]
         L.orc_nvars.argtypes = [C.c_void_p]
+        L.orc_radial_explosion.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double,
+                                           C.c_double, C.c_int, C.c_double, C.c_double, C.c_double, dp, dp, dp]
         L.orc_totals.argtypes = [C.c_void_p, dp]
         _lib = L
     return _lib
@@ -326,3 +328,13 @@ def weno1d(M, v):
     out = np.zeros(M + 1)
     lib().orc_weno1d(M, _dp(v), _dp(out))
     return out
+
+
+def radial_explosion(d, R=0.5, rho_in=1.0, p_in=1.0, rho_out=0.125, p_out=0.1, gamma=1.4, n=10000, rmax=1.5,
+                     t_end=0.25, cfl=0.4):
+    """1D radial reference of the explosion problems (Eq. eq.1D): zone centres and (rho, u, p)"""
+    rho, u, p = np.zeros(n), np.zeros(n), np.zeros(n)
+    lib().orc_radial_explosion(d, R, rho_in, p_in, rho_out, p_out, gamma, n, rmax, t_end, cfl, _dp(rho), _dp(u),
+                               _dp(p))
+    r = (np.arange(n) + 0.5) * rmax / n
+    return r, rho, u, p

@@ -1754,3 +1754,96 @@ void orc_totals(void *h, double *tot) {
       for (int v = 0; v < S->V; v++) tot[v] += vol * L->u[(size_t)L->alist[ia] * S->V + v];
   }
 }
+
+/* ===================================================================================
+ * 12. One-dimensional radial reference solution of the explosion problems (Eq. eq.1D):
+ *     the Euler equations in the radial coordinate with the geometric source
+ *     -(d-1)/r (rho u, rho u^2, u (E + p)), solved by a second-order TVD finite volume
+ *     scheme (minmod-limited linear reconstruction of the primitive variables, Rusanov
+ *     flux, two-stage SSP Runge-Kutta) on n zones of [0, rmax]; reflection at r = 0,
+ *     transmissive at rmax.  Returns the primitive state (rho, u, p) at the zone centres.
+ *     (The paper's reference used 10000 zones and the Osher flux.)
+ * =================================================================================== */
+static double minmod(double a, double b) {
+  if (a * b <= 0.0) return 0.0;
+  return fabs(a) < fabs(b) ? a : b;
+}
+
+static void radial_rhs(int d, int n, double dr, double g, const double *U, double *L) {
+  /* U: 3 per zone (rho, m, E) */
+  double *W = malloc(sizeof(double) * 3 * (n + 4));
+  for (int i = 0; i < n + 4; i++) {
+    int j = i - 2;
+    int src = j < 0 ? -j - 1 : (j >= n ? n - 1 : j); /* mirror at 0, copy at rmax */
+    double rho = U[3 * src], m = U[3 * src + 1], E = U[3 * src + 2];
+    double u = m / rho, p = (g - 1.0) * (E - 0.5 * rho * u * u);
+    W[3 * i] = rho;
+    W[3 * i + 1] = j < 0 ? -u : u;
+    W[3 * i + 2] = p;
+  }
+  double *F = malloc(sizeof(double) * 3 * (n + 1));
+  for (int f = 0; f <= n; f++) {
+    /* face between zones f-1 and f: ghost-padded indices i = f+1 and f+2 */
+    int il = f + 1, ir = f + 2;
+    double wl[3], wr[3];
+    for (int k = 0; k < 3; k++) {
+      double sl = minmod(W[3 * il + k] - W[3 * (il - 1) + k], W[3 * (il + 1) + k] - W[3 * il + k]);
+      double sr = minmod(W[3 * ir + k] - W[3 * (ir - 1) + k], W[3 * (ir + 1) + k] - W[3 * ir + k]);
+      wl[k] = W[3 * il + k] + 0.5 * sl;
+      wr[k] = W[3 * ir + k] - 0.5 * sr;
+    }
+    double ql[3] = {wl[0], wl[0] * wl[1], wl[2] / (g - 1.0) + 0.5 * wl[0] * wl[1] * wl[1]};
+    double qr[3] = {wr[0], wr[0] * wr[1], wr[2] / (g - 1.0) + 0.5 * wr[0] * wr[1] * wr[1]};
+    double fl[3] = {ql[1], ql[1] * wl[1] + wl[2], wl[1] * (ql[2] + wl[2])};
+    double fr[3] = {qr[1], qr[1] * wr[1] + wr[2], wr[1] * (qr[2] + wr[2])};
+    double cl = fabs(wl[1]) + sqrt(g * fabs(wl[2] / wl[0])), cr = fabs(wr[1]) + sqrt(g * fabs(wr[2] / wr[0]));
+    double sm = cl > cr ? cl : cr;
+    for (int k = 0; k < 3; k++) F[3 * f + k] = 0.5 * (fl[k] + fr[k]) - 0.5 * sm * (qr[k] - ql[k]);
+  }
+  for (int i = 0; i < n; i++) {
+    double r = (i + 0.5) * dr;
+    double rho = U[3 * i], m = U[3 * i + 1], E = U[3 * i + 2], u = m / rho, p = (g - 1.0) * (E - 0.5 * rho * u * u);
+    double geo = (d - 1) / r;
+    L[3 * i] = -(F[3 * (i + 1)] - F[3 * i]) / dr - geo * m;
+    L[3 * i + 1] = -(F[3 * (i + 1) + 1] - F[3 * i + 1]) / dr - geo * m * u;
+    L[3 * i + 2] = -(F[3 * (i + 1) + 2] - F[3 * i + 2]) / dr - geo * u * (E + p);
+  }
+  free(W);
+  free(F);
+}
+
+int orc_radial_explosion(int d, double R, double rho_in, double p_in, double rho_out, double p_out, double gamma,
+                         int n, double rmax, double t_end, double cfl, double *rho_o, double *u_o, double *p_o) {
+  double dr = rmax / n, g = gamma;
+  double *U = malloc(sizeof(double) * 3 * n), *U1 = malloc(sizeof(double) * 3 * n), *L = malloc(sizeof(double) * 3 * n);
+  for (int i = 0; i < n; i++) {
+    /* exact zone averages of the piecewise constant data (the jump at R may cut a zone) */
+    double a = i * dr, b = (i + 1) * dr, f = (R <= a) ? 0.0 : (R >= b ? 1.0 : (R - a) / dr);
+    double rho = f * rho_in + (1 - f) * rho_out, p = f * p_in + (1 - f) * p_out;
+    U[3 * i] = rho; U[3 * i + 1] = 0.0; U[3 * i + 2] = p / (g - 1.0);
+  }
+  double t = 0.0;
+  while (t < t_end) {
+    double smax = 0.0;
+    for (int i = 0; i < n; i++) {
+      double rho = U[3 * i], u = U[3 * i + 1] / rho, p = (g - 1.0) * (U[3 * i + 2] - 0.5 * rho * u * u);
+      double s = fabs(u) + sqrt(g * p / rho);
+      if (s > smax) smax = s;
+    }
+    double dt = cfl * dr / smax;
+    if (t + dt > t_end) dt = t_end - t;
+    radial_rhs(d, n, dr, g, U, L);
+    for (int k = 0; k < 3 * n; k++) U1[k] = U[k] + dt * L[k];
+    radial_rhs(d, n, dr, g, U1, L);
+    for (int k = 0; k < 3 * n; k++) U[k] = 0.5 * (U[k] + U1[k] + dt * L[k]);
+    t += dt;
+  }
+  for (int i = 0; i < n; i++) {
+    double rho = U[3 * i], u = U[3 * i + 1] / rho;
+    rho_o[i] = rho;
+    u_o[i] = u;
+    p_o[i] = (g - 1.0) * (U[3 * i + 2] - 0.5 * rho * u * u);
+  }
+  free(U); free(U1); free(L);
+  return 0;
+}
