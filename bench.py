@@ -41,6 +41,10 @@ SM_COUNT = 152
 FP64_FMA_PER_CLK_PER_SM = 2      # sm_103a: measured 0.598 T DFMA/s at ~1.97 GHz on 152 SMs
 SM_MAX_MHZ = 2070.0
 HBM_GBS = 6792.1                 # measured copy bandwidth of this GB300 pool
+# DRAM bytes per cell of k_predict<2,3,Euler> from one ncu capture of a full-size level-2 launch
+# of this workload (68,832 cells: dram__bytes_read.sum 35.43 MB + dram__bytes_write.sum 77.27 MB);
+# scaled by the cells of an average launch.  Must be re-captured whenever k_predict changes.
+PREDICTOR_DRAM_BYTES_PER_CELL = (35434240 + 77272832) / 68832
 
 
 def _measured_hbm():
@@ -297,8 +301,12 @@ def main():
     roofline = None
     if names[dom] == "predictor" and kn[dom] > 0:
         ach = pf * upd / (kms[dom] * 1e-3) / 1e12
+        cells_per_launch = upd / kn[dom]
         roofline = {"bound": "alu", "kernel": "k_predict<2,3,Euler>", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS, "traffic": None,
+                    "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                    "traffic": PREDICTOR_DRAM_BYTES_PER_CELL * cells_per_launch,
+                    "traffic_note": "bytes per average launch: ncu dram read+write of a full-size launch per cell x cells per launch",
+                    "cells_per_launch": cells_per_launch,
                     "flops_per_cell_update": pf, "launches": int(kn[dom]),
                     "avg_launch_ms": float(kms[dom] / kn[dom]),
                     "peak_note": "FP64 FMA pipe: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (derived; 1.195 measured)"}
