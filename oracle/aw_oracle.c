@@ -1279,16 +1279,32 @@ static void regrid_prepass(osolver *S, int init_mode) {
   }
 }
 
-/* flags from the indicator: +1 refine (active, l < lmax, chi > chi_ref), -1 coarsen
- * (virtual mother, chi < chi_rec), 0 otherwise; dense per level */
+/* flags from the indicator: +1 refine (active, l < lmax, chi^ > chi_ref), -1 coarsen
+ * (virtual mother, chi^ < chi_rec), 0 otherwise; dense per level.  chi^ is the largest indicator
+ * over the cell and its same-level Voronoi neighbours of status <= 0 (reading: the second
+ * difference vanishes in the middle of a jump smeared over a few cells and peaks on both sides
+ * of it, so Loehner's criterion is applied to neighbourhoods, as in the block-based codes the
+ * paper cites; a cell cut by a discontinuity is thereby refined with its neighbours). */
 static void flags_from_chi(const osolver *S, int8_t **fl) {
+  int off[26][3];
+  int nv = voronoi(S->d, off);
   for (int lv = 0; lv <= S->c.lmax; lv++) {
     const olev *L = &S->lev[lv];
     for (long c = 0; c < L->n; c++) {
       int8_t f = 0;
-      if (lv < S->c.lmax) {
-        if (L->st[c] == 0 && L->chi[c] > S->c.chi_ref) f = 1;
-        if (L->st[c] == -1 && L->chi[c] < S->c.chi_rec) f = -1;
+      if (lv < S->c.lmax && (L->st[c] == 0 || L->st[c] == -1)) {
+        int ijk[3];
+        coords(L, c, ijk);
+        double chi = L->chi[c];
+        for (int o = 0; o < nv; o++) {
+          int nb[3] = {ijk[0] + off[o][0], ijk[1] + off[o][1], ijk[2] + off[o][2]}, in = 1;
+          for (int a = 0; a < S->d; a++) in &= bcmap(S, lv, a, nb[a], &nb[a]);
+          if (!in) continue;
+          long nc = didx(L, nb[0], nb[1], nb[2]);
+          if ((L->st[nc] == 0 || L->st[nc] == -1) && L->chi[nc] > chi) chi = L->chi[nc];
+        }
+        if (L->st[c] == 0 && chi > S->c.chi_ref) f = 1;
+        if (L->st[c] == -1 && chi < S->c.chi_rec) f = -1;
       }
       fl[lv][c] = f;
     }

@@ -70,8 +70,8 @@ def test_free_stream_uniform_and_amr():
 
 @pytest.mark.parametrize("M,lmax", [(2, 1), (3, 2)])
 def test_conservation_amr_lts_periodic(M, lmax):
-    cfg = oracle.make_cfg(dim=2, M=M, n=(6, 6, 1), lo=(0, 0, 0), hi=(10, 10, 1), lmax=lmax, r=3,
-                          chi_ref=0.05, chi_rec=0.01, auto_regrid=1)
+    cfg = oracle.make_cfg(dim=2, M=M, n=(12, 12, 1), lo=(0, 0, 0), hi=(10, 10, 1), lmax=lmax, r=3,
+                          chi_ref=0.1, chi_rec=0.01, auto_regrid=1)
     o = oracle.Oracle(cfg)
     o.set_initial(oracle.IC_VORTEX, VORTEX)
     n, per, act = o.counts()
