@@ -364,14 +364,35 @@ __global__ void k_indicator(LevelView L, Bc6 bc6, int D, double eps, double* chi
   chi[c] = den > 0.0 ? sqrt(num / den) : 0.0;
 }
 
-__global__ void k_flags_from_chi(LevelView L, const double* chi, int is_below_lmax, double chi_ref, double chi_rec,
-                                 int8_t* flag) {
+// flags from the indicator: +1 refine (active, below lmax, chi^ > chi_ref), -1 recoarsen (virtual
+// mother, chi^ < chi_rec); chi^ = the largest indicator over the cell and its same-level Voronoi
+// neighbours of status <= 0 (the second difference vanishes in the middle of a smeared jump and
+// peaks on both sides of it, so the criterion is applied to neighbourhoods)
+__global__ void k_flags_from_chi(LevelView L, Bc6 bc6, int D, const double* chi, int is_below_lmax, double chi_ref,
+                                 double chi_rec, int8_t* flag) {
   long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= L.n) return;
   int8_t f = 0;
-  if (is_below_lmax) {
-    if (L.st[c] == 0 && chi[c] > chi_ref) f = 1;
-    if (L.st[c] == -1 && chi[c] < chi_rec) f = -1;
+  const int8_t s = L.st[c];
+  if (is_below_lmax && (s == 0 || s == -1)) {
+    int ijk[3];
+    cell_coords(L, c, ijk);
+    double m = chi[c];
+    const int kz0 = D == 3 ? -1 : 0, kz1 = D == 3 ? 1 : 0;
+    for (int oz = kz0; oz <= kz1; oz++)
+      for (int oy = -1; oy <= 1; oy++)
+        for (int ox = -1; ox <= 1; ox++) {
+          if (!ox && !oy && !oz) continue;
+          int nb[3] = {ijk[0] + ox, ijk[1] + oy, ijk[2] + oz};
+          bool in = true;
+          for (int a = 0; a < D; a++) in &= bcmap(L.L, bc6.v, a, nb[a], &nb[a]);
+          if (!in) continue;
+          long long nd = didx(L, nb[0], nb[1], nb[2]);
+          const int8_t sn = L.st[nd];
+          if ((sn == 0 || sn == -1) && chi[nd] > m) m = chi[nd];
+        }
+    if (s == 0 && m > chi_ref) f = 1;
+    if (s == -1 && m < chi_rec) f = -1;
   }
   flag[c] = f;
 }
@@ -957,8 +978,8 @@ static int apply_flags(aw_solver* s, int init_mode) {
 static int flags_from_chi(aw_solver* s) {
   for (int l = 0; l <= s->lmax; l++) {
     Level& L = s->lev[l];
-    k_flags_from_chi<<<nblk(L.n, 256), 256, 0, s->stream>>>(view(s, l), L.chi, l < s->lmax, s->cfg.chi_ref,
-                                                            s->cfg.chi_rec, L.flag);
+    k_flags_from_chi<<<nblk(L.n, 256), 256, 0, s->stream>>>(view(s, l), bc6_of(s), s->D, L.chi, l < s->lmax,
+                                                            s->cfg.chi_ref, s->cfg.chi_rec, L.flag);
     s->launches++;
   }
   CK(cudaGetLastError());

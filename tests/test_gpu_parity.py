@@ -77,7 +77,7 @@ def test_amr_explosion_lts(M, lmax):
 
 
 def test_amr_periodic_conservation_gpu():
-    p = Pair(dim=2, M=3, n=(9, 9, 1), lo=(0, 0, 0), hi=(10, 10, 1), bc="periodic", r=3, lmax=2, chi_ref=0.05,
+    p = Pair(dim=2, M=3, n=(12, 12, 1), lo=(0, 0, 0), hi=(10, 10, 1), bc="periodic", r=3, lmax=2, chi_ref=0.1,
              chi_rec=0.01)
     p.init("vortex", VORTEX)
     t0 = p.g.totals()
