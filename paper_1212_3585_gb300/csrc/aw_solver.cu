@@ -60,6 +60,9 @@ struct Level {
   int32_t* tiles = nullptr;
   int ntiles = 0;
   double *wh = nullptr, *qh = nullptr, *fl = nullptr, *mem = nullptr;
+  int8_t* hflag = nullptr;     // per (axis, active id): the high face needs computing
+  int32_t* hflist = nullptr;   // compacted high faces, axis * na + active id
+  int nh = 0;
   long long cap = 0;
 };
 
@@ -615,6 +618,21 @@ __global__ void k_tmark(LevelView L, const int32_t* alist, int na, int TS, int t
   tflag[t] = 1;
 }
 
+// high faces that need their own flux: the +axis neighbour is outside a transmissive boundary, a
+// virtual child or a virtual mother (an active neighbour computes the face as its low face)
+__global__ void k_hmark(LevelView L, Bc6 bc6, const int32_t* alist, int na, int D, int8_t* hflag) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= na) return;
+  int ijk[3];
+  cell_coords(L, alist[k], ijk);
+  for (int d = 0; d < D; d++) {
+    int nb[3] = {ijk[0], ijk[1], ijk[2]};
+    bool in = bcmap(L.L, bc6.v, d, ijk[d] + 1, &nb[d]);
+    bool need = !in || L.st[didx(L, nb[0], nb[1], nb[2])] != 0;
+    hflag[(long long)d * na + k] = need ? 1 : 0;
+  }
+}
+
 // canonical gather / scatter of cell averages and metadata
 __global__ void k_gather(LevelView L, const int32_t* clist, int nc, int V, double* out, aw_cell* meta, int level) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -728,11 +746,14 @@ static int ensure_active_cap(aw_solver* s, int l, long long need) {
   Level& L = s->lev[l];
   if (need <= L.cap) return AW_OK;
   long long cap = std::max(need + need / 2, (long long)64);
-  cudaFree(L.wh); cudaFree(L.qh); cudaFree(L.fl); cudaFree(L.mem);
+  cudaFree(L.wh); cudaFree(L.qh); cudaFree(L.fl); cudaFree(L.mem); cudaFree(L.hflag); cudaFree(L.hflist);
   L.wh = L.qh = L.fl = L.mem = nullptr;
+  L.hflag = nullptr;
+  L.hflist = nullptr;
   L.cap = 0;
   size_t V = s->V;
-  if (cudaMalloc(&L.wh, cap * V * s->NSP * sizeof(double)) != cudaSuccess ||
+  if (cudaMalloc(&L.hflag, cap * s->D) != cudaSuccess || cudaMalloc(&L.hflist, cap * s->D * sizeof(int32_t)) != cudaSuccess ||
+      cudaMalloc(&L.wh, cap * V * s->NSP * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&L.qh, cap * V * s->NST * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&L.fl, cap * 2 * s->D * V * sizeof(double)) != cudaSuccess ||
       cudaMalloc(&L.mem, cap * 2 * s->D * V * sizeof(double)) != cudaSuccess)
@@ -745,32 +766,42 @@ static int ensure_active_cap(aw_solver* s, int l, long long need) {
 static int rebuild_lists(aw_solver* s) {
   for (int l = 0; l <= s->lmax; l++) {
     Level& L = s->lev[l];
-    TRY(compact(s, L.st, L.n, 0, 0, L.alist, L.aid, 5 * l + 0));
-    TRY(compact(s, L.st, L.n, 0, 1, L.vlist, nullptr, 5 * l + 1));
-    TRY(compact(s, L.st, L.n, 0, -1, L.mlist, nullptr, 5 * l + 2));
-    TRY(compact(s, L.st, L.n, 1, 0, L.clist, nullptr, 5 * l + 3));
+    TRY(compact(s, L.st, L.n, 0, 0, L.alist, L.aid, 6 * l + 0));
+    TRY(compact(s, L.st, L.n, 0, 1, L.vlist, nullptr, 6 * l + 1));
+    TRY(compact(s, L.st, L.n, 0, -1, L.mlist, nullptr, 6 * l + 2));
+    TRY(compact(s, L.st, L.n, 1, 0, L.clist, nullptr, 6 * l + 3));
   }
-  CK(cudaMemcpyAsync(s->h_cnt, s->d_cnt, sizeof(int) * 5 * MAXL, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(s->h_cnt, s->d_cnt, sizeof(int) * 6 * MAXL, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
   for (int l = 0; l <= s->lmax; l++) {
     Level& L = s->lev[l];
-    L.na = s->h_cnt[5 * l + 0];
-    L.nv = s->h_cnt[5 * l + 1];
-    L.nm = s->h_cnt[5 * l + 2];
-    L.nc = s->h_cnt[5 * l + 3];
+    L.na = s->h_cnt[6 * l + 0];
+    L.nv = s->h_cnt[6 * l + 1];
+    L.nm = s->h_cnt[6 * l + 2];
+    L.nc = s->h_cnt[6 * l + 3];
     CK(cudaMemsetAsync(L.tflag, 0, L.ntd, s->stream));
     if (L.na > 0) {
       k_tmark<<<nblk(L.na, 256), 256, 0, s->stream>>>(view(s, l), L.alist, L.na, s->ops.wenoTS, L.tdim[0], L.tdim[1],
                                                       L.tflag);
       s->launches++;
     }
-    TRY(compact(s, L.tflag, L.ntd, 2, 0, L.tiles, nullptr, 5 * l + 4));
+    TRY(compact(s, L.tflag, L.ntd, 2, 0, L.tiles, nullptr, 6 * l + 4));
     TRY(ensure_active_cap(s, l, L.na));
+    if (L.na > 0) {
+      k_hmark<<<nblk(L.na, 256), 256, 0, s->stream>>>(view(s, l), bc6_of(s), L.alist, L.na, s->D, L.hflag);
+      s->launches++;
+      TRY(compact(s, L.hflag, (long long)s->D * L.na, 2, 0, L.hflist, nullptr, 6 * l + 5));
+    } else {
+      CK(cudaMemsetAsync(s->d_cnt + 6 * l + 5, 0, sizeof(int), s->stream));
+    }
     CK(cudaMemsetAsync(L.mem, 0, (size_t)L.cap * 2 * s->D * s->V * sizeof(double), s->stream));
   }
-  CK(cudaMemcpyAsync(s->h_cnt, s->d_cnt, sizeof(int) * 5 * MAXL, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(s->h_cnt, s->d_cnt, sizeof(int) * 6 * MAXL, cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
-  for (int l = 0; l <= s->lmax; l++) s->lev[l].ntiles = s->h_cnt[5 * l + 4];
+  for (int l = 0; l <= s->lmax; l++) {
+    s->lev[l].ntiles = s->h_cnt[6 * l + 4];
+    s->lev[l].nh = s->h_cnt[6 * l + 5];
+  }
   return AW_OK;
 }
 
@@ -790,6 +821,8 @@ static HotArgs make_args(const aw_solver* s, int l, int sub) {
   const Level& L = s->lev[l];
   a.alist = L.alist;
   a.na = L.na;
+  a.hflist = L.hflist;
+  a.nh = L.nh;
   a.tiles = L.tiles;
   a.ntiles = L.ntiles;
   for (int i = 0; i < 3; i++) a.tdim[i] = L.tdim[i];
@@ -870,9 +903,9 @@ static int step_dt(aw_solver* s, double dt0, aw_stats* st) {
   CK(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream));
   TRY(advance(s, 0, 0));
   int err = 0;
-  CK(cudaMemcpyAsync(s->h_cnt + 5 * MAXL, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(s->h_cnt + 6 * MAXL, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
-  err = s->h_cnt[5 * MAXL];
+  err = s->h_cnt[6 * MAXL];
   int64_t rl = 1;
   for (int l = 0; l <= s->lmax; l++) {
     int64_t u = (int64_t)s->lev[l].na * rl;
@@ -1008,6 +1041,7 @@ static void free_solver(aw_solver* s) {
     cudaFree(L.st); cudaFree(L.R); cudaFree(L.nst); cudaFree(L.flag); cudaFree(L.u); cudaFree(L.chi);
     cudaFree(L.aid); cudaFree(L.alist); cudaFree(L.vlist); cudaFree(L.mlist); cudaFree(L.clist);
     cudaFree(L.tflag); cudaFree(L.tiles); cudaFree(L.wh); cudaFree(L.qh); cudaFree(L.fl); cudaFree(L.mem);
+    cudaFree(L.hflag); cudaFree(L.hflist);
   }
   cudaFree(s->d_dtl); cudaFree(s->d_dtmin); cudaFree(s->d_err); cudaFree(s->d_cnt); cudaFree(s->d_bcnt);
   cudaFree(s->d_buf);
@@ -1175,8 +1209,8 @@ int aw_create(const aw_config* cfg, uintptr_t stream, aw_solver** out) {
   alloc((void**)&s->d_dtl, sizeof(double) * MAXL);
   alloc((void**)&s->d_dtmin, sizeof(double));
   alloc((void**)&s->d_err, sizeof(int));
-  alloc((void**)&s->d_cnt, sizeof(int) * (5 * MAXL + 8));
-  if (rc == AW_OK && (cudaMallocHost((void**)&s->h_cnt, sizeof(int) * (5 * MAXL + 8)) != cudaSuccess ||
+  alloc((void**)&s->d_cnt, sizeof(int) * (6 * MAXL + 8));
+  if (rc == AW_OK && (cudaMallocHost((void**)&s->h_cnt, sizeof(int) * (6 * MAXL + 8)) != cudaSuccess ||
                       cudaMallocHost((void**)&s->h_dtl, sizeof(double) * MAXL) != cudaSuccess)) {
     rc = AW_ENOMEM;
     g_err = "pinned host allocation failed";
