@@ -153,6 +153,85 @@ def combine_replicas(updates, ms, world_size, max_reduce):
     return world_size * updates / (job_ms * 1e-3), job_ms
 
 
+def serve_requests(n, base_max, seed=20121213):
+    """Seeded stream shaped like the serving workload: 2D Euler four-quadrant Riemann problems on
+    [-0.5, 0.5]^2, base grid uniform in 32..base_max, M in {2, 3}, l_max in {0, 1, 2}, r = 3,
+    per-quadrant rho, p ~ U[0.1, 1.5], u, v ~ U[-1, 1] (aw_inputs.rp4_params)."""
+    import numpy as np
+    import aw_inputs
+    import paper_1212_3585_gb300 as pg
+    rng = np.random.default_rng(seed)
+    out = []
+    for k in range(n):
+        base = int(rng.integers(32, base_max + 1))
+        M = int(rng.choice([2, 3]))
+        lmax = int(rng.integers(0, 3))
+        cfg = pg.make_config(dim=2, M=M, n=(base, base, 1), lo=(-0.5, -0.5, 0), hi=(0.5, 0.5, 1),
+                             bc=pg.AW_BC_TRANSMISSIVE, r=3, lmax=lmax, cfl=0.5)
+        out.append((cfg, aw_inputs.rp4_params(seed + k)))
+    return out
+
+
+def run_serve(args):
+    """Continuous admission (aw_srv_*, concurrent requests on their own streams) against
+    one-at-a-time plain solves, on the same seeded requests and arrival times."""
+    import threading
+    import numpy as np
+    import torch
+    import paper_1212_3585_gb300 as pg
+    torch.cuda.set_device(0)
+    reqs = serve_requests(args.requests, args.serve_base_max)
+    t_end = args.serve_t_end
+
+    def plain(arrivals):
+        t0 = time.perf_counter()
+        tts, done, upd = [], 0.0, 0
+        for (cfg, p), a in zip(reqs, arrivals):
+            now = time.perf_counter() - t0
+            if now < a:
+                time.sleep(a - now)
+            s = pg.Solver(cfg)
+            s.set_initial(pg.AW_IC_RP4, p, -1)
+            st = s.advance_to(t_end)
+            s.cells()
+            s.close()
+            upd += st.cell_updates
+            done = time.perf_counter() - t0
+            tts.append(1e3 * (done - a))
+        return {"solves_per_s": len(reqs) / done, "p50_ms": float(np.percentile(tts, 50)),
+                "p99_ms": float(np.percentile(tts, 99)), "cell_updates_per_s": upd / done}
+
+    def batched(arrivals):
+        srv = pg.Server(hbm_budget_bytes=int(args.serve_budget_gb * (1 << 30)), max_concurrent=args.concurrency)
+        t0 = time.perf_counter()
+        ids = []
+        for (cfg, p), a in zip(reqs, arrivals):
+            now = time.perf_counter() - t0
+            if now < a:
+                time.sleep(a - now)
+            ids.append(srv.submit(cfg, pg.AW_IC_RP4, p, t_end))
+        srv.wait_all()
+        st = srv.stats()
+        out = {"solves_per_s": st.solves_per_s, "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
+               "cell_updates_per_s": st.cell_updates_per_s, "failed": int(st.failed)}
+        srv.close()
+        return out
+
+    burst = [0.0] * len(reqs)
+    res = {"burst": {"plain": plain(burst), "batched": batched(burst)}}
+    lam = 0.8 * res["burst"]["batched"]["solves_per_s"]
+    rng = np.random.default_rng(7)
+    arr = list(np.cumsum(rng.exponential(1.0 / lam, len(reqs))))
+    res["poisson"] = {"rate_per_s": lam, "plain": plain(arr), "batched": batched(arr)}
+    print(json.dumps({"metric": "batched solves/s + p50/p99 time to solution vs plain", "unit": "solves/s",
+                      "higher_is_better": True, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": f"{len(reqs)} 2D Euler four-quadrant Riemann AMR solves, base 32..{args.serve_base_max}, "
+                                             f"M in {{2,3}}, l_max in {{0,1,2}}, r=3, CFL 0.5, t_end={t_end}",
+                                 "concurrency": args.concurrency, "budget_gb": args.serve_budget_gb},
+                      **res}))
+    return 0
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -218,6 +297,12 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--base", type=int, default=100, help="level-0 cells per direction (workload: 100)")
+    ap.add_argument("--serve", action="store_true", help="request-stream benchmark of the serving loop")
+    ap.add_argument("--requests", type=int, default=48)
+    ap.add_argument("--serve-base-max", type=int, default=96)
+    ap.add_argument("--serve-t-end", type=float, default=0.05)
+    ap.add_argument("--concurrency", type=int, default=8)
+    ap.add_argument("--serve-budget-gb", type=float, default=160.0)
     ap.add_argument("--t-end", type=float, default=T_END, help="end time (workload: 0.25)")
     args = ap.parse_args()
     if args.base != 100 or args.t_end != T_END:
@@ -226,6 +311,8 @@ def main():
         globals()["WORKLOAD"] = WORKLOAD.replace("base 100x100", f"base {args.base}x{args.base}").replace(
             "t_end=0.25", f"t_end={args.t_end}")
     ws, rank, local = dist_setup()
+    if args.serve:
+        return run_serve(args) if rank == 0 else 0
     if args.impl == "reference":
         if rank != 0:
             return 0

@@ -116,11 +116,17 @@ struct Pde<PDE_EULER, D> {
     const double gm1 = P.gamma - 1.0;
     double p = gm1 * (q[D + 1] - 0.5 * ke);
     double Ep = q[D + 1] + p;
+    // the off-diagonal momentum fluxes rho v_a v_n are symmetric in (a, n): computed once
+    double mv[D][D];
+#pragma unroll
+    for (int n = 0; n < D; n++)
+#pragma unroll
+      for (int a = 0; a <= n; a++) mv[n][a] = mv[a][n] = (a == n) ? fma(q[1 + a], v[n], p) : q[1 + a] * v[n];
 #pragma unroll
     for (int n = 0; n < D; n++) {
       F[n][0] = q[1 + n];
 #pragma unroll
-      for (int a = 0; a < D; a++) F[n][1 + a] = q[1 + a] * v[n] + (a == n ? p : 0.0);
+      for (int a = 0; a < D; a++) F[n][1 + a] = mv[n][a];
       F[n][D + 1] = v[n] * Ep;
     }
   }
@@ -356,6 +362,8 @@ struct HotArgs {
   LevelView lvc;        // child level (level+1), valid when level < lmax
   const int32_t* alist; // active cells of this level (dense indices), canonical order
   int na;
+  const int32_t* hflist; // high faces to compute: axis * na + active id, axis-major, where the +axis
+  int nh;                // neighbour is not an active cell of this level
   const int32_t* tiles; // tile origins (tile linear index on the level's tile grid)
   int ntiles;
   int tdim[3];          // tiles per direction

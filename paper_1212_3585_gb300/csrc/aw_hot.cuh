@@ -250,7 +250,7 @@ struct PredCfg {
   static constexpr int N = M + 1, NSP = ipow(N, D), NST = NSP * N, V = nvars(D, PDE);
   static constexpr int CPB = (NSP == 9) ? 32 : (NSP == 16 ? 16 : (NSP == 27 ? 16 : 4));
   static constexpr int THREADS = CPB * NSP;
-  static constexpr int SMEM = CPB * D * V * NSP * 8;
+  static constexpr int SMEM = CPB * D * V * NST * 8;   // fluxes at every space-time node
 };
 
 template <int D, int M, int PDE>
@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(PredCfg<D, M, PDE>::THREADS) k_predict(HotArgs
   using C = PredCfg<D, M, PDE>;
   using Q = Pde<PDE, D>;
   constexpr int N = C::N, NSP = C::NSP, NST = C::NST, V = C::V;
-  extern __shared__ double sh[];  // [CPB][D][V][NSP]
+  extern __shared__ double sh[];  // [CPB][D][V][NST]
   const int lc = threadIdx.x / NSP, node = threadIdx.x % NSP;
   const int cell = blockIdx.x * C::CPB + lc;
   const bool ok = cell < a.na;
@@ -280,16 +280,16 @@ __global__ void __launch_bounds__(PredCfg<D, M, PDE>::THREADS) k_predict(HotArgs
   const double* wsrc = a.wh + (long long)(ok ? cell : 0) * V * NSP;
 #pragma unroll
   for (int v = 0; v < V; v++) w[v] = wsrc[v * NSP + node];
-  double* shc = sh + lc * D * V * NSP;
+  double* shc = sh + lc * D * V * NST;
   double q[V][N], R[V][N];
-  // first Picard iteration from q = w
+  // first Picard iteration from q = w, constant in time: one flux evaluation per node
   {
     double F[D][V];
     Q::fluxes(w, F, a.P);
 #pragma unroll
     for (int d = 0; d < D; d++)
 #pragma unroll
-      for (int v = 0; v < V; v++) shc[(d * V + v) * NSP + node] = F[d][v];
+      for (int v = 0; v < V; v++) shc[(d * V + v) * NST + node] = F[d][v];
     __syncthreads();
 #pragma unroll
     for (int v = 0; v < V; v++) {
@@ -299,7 +299,7 @@ __global__ void __launch_bounds__(PredCfg<D, M, PDE>::THREADS) k_predict(HotArgs
         const int st = (d == 0 ? 1 : (d == 1 ? N : N * N));
         const int base = node - ix[d] * st;
 #pragma unroll
-        for (int k = 0; k < N; k++) r = fma(Dr[d][k], shc[(d * V + v) * NSP + base + k * st], r);
+        for (int k = 0; k < N; k++) r = fma(Dr[d][k], shc[(d * V + v) * NST + base + k * st], r);
       }
 #pragma unroll
       for (int s = 0; s < N; s++) q[v][s] = fma(-a.T.gsum[s], r, w[v]);
@@ -307,6 +307,7 @@ __global__ void __launch_bounds__(PredCfg<D, M, PDE>::THREADS) k_predict(HotArgs
     __syncthreads();
   }
   for (int it = 1; it < a.picard; it++) {
+    // fluxes at all N time nodes of this thread's spatial node
 #pragma unroll
     for (int s = 0; s < N; s++) {
       double qs[V], F[D][V];
@@ -316,22 +317,24 @@ __global__ void __launch_bounds__(PredCfg<D, M, PDE>::THREADS) k_predict(HotArgs
 #pragma unroll
       for (int d = 0; d < D; d++)
 #pragma unroll
-        for (int v = 0; v < V; v++) shc[(d * V + v) * NSP + node] = F[d][v];
-      __syncthreads();
+        for (int v = 0; v < V; v++) shc[(d * V + v) * NST + node + NSP * s] = F[d][v];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < N; s++)
 #pragma unroll
       for (int v = 0; v < V; v++) {
         double r = 0.0;
 #pragma unroll
         for (int d = 0; d < D; d++) {
           const int st = (d == 0 ? 1 : (d == 1 ? N : N * N));
-          const int base = node - ix[d] * st;
+          const int base = node - ix[d] * st + NSP * s;
 #pragma unroll
-          for (int k = 0; k < N; k++) r = fma(Dr[d][k], shc[(d * V + v) * NSP + base + k * st], r);
+          for (int k = 0; k < N; k++) r = fma(Dr[d][k], shc[(d * V + v) * NST + base + k * st], r);
         }
         R[v][s] = r;
       }
-      __syncthreads();
-    }
+    __syncthreads();
 #pragma unroll
     for (int v = 0; v < V; v++)
 #pragma unroll
@@ -351,21 +354,11 @@ __global__ void __launch_bounds__(PredCfg<D, M, PDE>::THREADS) k_predict(HotArgs
   }
 }
 
-// ------------------------------------------------------------------------------------------
-// Face flux kernel (Eqs. flux:F..flux:H, eqn.rusanov, eqn.memory.sum).  One thread per
-// (active cell, axis, face quadrature point); the N^(d-1) x N space-time Gauss points of a face
-// coincide with the nodal points, so a trace is one N-term contraction along the normal.  Each
-// active cell computes its low face on every axis, and its high face where the neighbour is not
-// an active cell of the same level (boundary, coarse or fine neighbour).  Faces toward a
-// virtual child are fine sides of a coarse/fine face: the coarse predictor is evaluated at this
-// cell's points and sub-step, and the face integral is added to this cell's memory variable.
-// Faces toward a virtual mother are coarse sides: the flux is the sum of the fine cells' memory
-// variables over the r sub-steps, normalised by dt * area of this level.
-// ------------------------------------------------------------------------------------------
+// Face flux configuration: IPB face items of N^d quadrature points per CTA.
 template <int D, int M, int PDE>
 struct FluxCfg {
   static constexpr int N = M + 1, NPT = ipow(N, D), V = nvars(D, PDE);
-  static constexpr int CPB = 256 / NPT;
+  static constexpr int CPB = 256 / NPT;   // face items per CTA
   static constexpr int THREADS = CPB * NPT;
   static constexpr int SMEM = THREADS * V * 8;
 };
@@ -475,17 +468,18 @@ __device__ __forceinline__ int flux_point(const HotArgs& a, bool ok, const int* 
 }
 
 // reduce the point contributions of every (cell, variable) of the CTA and finish the face
-template <int D, int M, int PDE, int d>
-__device__ __forceinline__ void flux_finish(const HotArgs& a, const double* sh, const int* skind, const int* snb,
-                                            int side) {
+// reduce the point contributions of every (face item, variable) of the CTA and finish the face
+template <int D, int M, int PDE>
+__device__ __forceinline__ void flux_finish(const HotArgs& a, const double* sh, const int* sitem, const int* skind,
+                                            const int* snb) {
   constexpr int N = M + 1, NPT = ipow(N, D), V = nvars(D, PDE);
-  constexpr int CPB = FluxCfg<D, M, PDE>::CPB;
+  constexpr int IPB = FluxCfg<D, M, PDE>::CPB;
   const int t = threadIdx.x;
-  if (t >= CPB * V) return;
-  const int lc = t / V, v = t % V;
-  const int cell = blockIdx.x * CPB + lc;
-  const int kind = skind[lc];
-  if (cell >= a.na || kind == FK_SKIP) return;
+  if (t >= IPB * V) return;
+  const int li = t / V, v = t % V;
+  const int kind = skind[li];
+  if (kind == FK_SKIP) return;
+  const int cell = sitem[3 * li], d = sitem[3 * li + 1], side = sitem[3 * li + 2];
   const LevelView& L = a.lv;
   const double dt = a.dtl[a.level];
   double area = 1.0;
@@ -499,9 +493,9 @@ __device__ __forceinline__ void flux_finish(const HotArgs& a, const double* sh, 
     const int r = a.T.r;
     long long di = a.alist[cell];
     int ijk[3] = {(int)(di % L.L[0]), (int)((di / L.L[0]) % L.L[1]), (int)(di / ((long long)L.L[0] * L.L[1]))};
-    const int* nb = snb + 3 * lc;
-    constexpr int t0 = d == 0 ? 1 : 0;
-    constexpr int t1 = d == 2 ? 1 : 2;
+    const int* nb = snb + 3 * li;
+    const int t0 = d == 0 ? 1 : 0;
+    const int t1 = d == 2 ? 1 : 2;
     double acc = 0.0;
     const int nr2 = (D == 3) ? r : 1;
     for (int c1 = 0; c1 < nr2; c1++)
@@ -519,7 +513,7 @@ __device__ __forceinline__ void flux_finish(const HotArgs& a, const double* sh, 
     F = acc / (dt * area);
   } else {
     double acc = 0.0;
-    const double* src = sh + (lc * NPT) * V + v;
+    const double* src = sh + (li * NPT) * V + v;
 #pragma unroll
     for (int g = 0; g < NPT; g++) acc += src[g * V];
     F = acc;
@@ -528,38 +522,16 @@ __device__ __forceinline__ void flux_finish(const HotArgs& a, const double* sh, 
   if (kind == FK_FINE) a.mem[((long long)cell * 2 * D + 2 * d + side) * V + v] += F * dt * area;
 }
 
-template <int D, int M, int PDE, int d>
-__device__ __forceinline__ void flux_axis(const HotArgs& a, bool ok, const int* ijk, const double* qA, int lc, int g,
-                                          double* sh, int* skind, int* snb) {
-  constexpr int V = nvars(D, PDE);
-  for (int side = 0; side < 2; side++) {
-    double contrib[V];
-    int nb[3];
-    int kind = flux_point<D, M, PDE, d>(a, ok, ijk, qA, g, side, contrib, nb);
-    // the high side is only needed where the neighbour is not an active cell of this level
-    if (side == 1 && !__syncthreads_or(kind != FK_SKIP)) break;
-#pragma unroll
-    for (int v = 0; v < V; v++) sh[threadIdx.x * V + v] = contrib[v];
-    if (g == 0) {
-      skind[lc] = ok ? kind : FK_SKIP;
-      snb[3 * lc] = nb[0]; snb[3 * lc + 1] = nb[1]; snb[3 * lc + 2] = nb[2];
-    }
-    __syncthreads();
-    flux_finish<D, M, PDE, d>(a, sh, skind, snb, side);
-    __syncthreads();
-  }
-}
-
 // ------------------------------------------------------------------------------------------
-// Face flux kernel (Eqs. flux:F..flux:H, eqn.rusanov, eqn.memory.sum).  One thread per (active
-// cell, face quadrature point), looping over the axes; the N^(d-1) x N space-time Gauss points
-// of a face coincide with the nodal points, so a trace is one N-term contraction along the
-// normal.  Each active cell computes its low face on every axis, and its high face where the
-// neighbour is not an active cell of the same level (boundary, coarse or fine neighbour).
-// Faces toward a virtual child are fine sides of a coarse/fine face: the coarse predictor is
-// evaluated at this cell's points and sub-step, and the face integral is added to this cell's
-// memory variable.  Faces toward a virtual mother are coarse sides: the flux is the sum of the
-// fine cells' memory variables over the r sub-steps, normalised by dt * area of this level.
+// Face flux kernel (Eqs. flux:F..flux:H, eqn.rusanov, eqn.osher, eqn.memory.sum).  Work items are
+// faces: the low face of every active cell on every axis (axis-major), then the listed high faces
+// whose neighbour is not an active cell of this level (boundary, coarse or fine neighbour).  One
+// thread per (face, quadrature point); the N^(d-1) x N space-time Gauss points of a face coincide
+// with the nodal points, so a trace is one N-term contraction along the normal.  Faces toward a
+// virtual child are fine sides of a coarse/fine face: the coarse predictor is evaluated at this
+// cell's points and sub-step, and the face integral is added to this cell's memory variable.
+// Faces toward a virtual mother are coarse sides: the flux is the sum of the fine cells' memory
+// variables over the r sub-steps, normalised by dt * area of this level.
 // ------------------------------------------------------------------------------------------
 template <int D, int M, int PDE>
 __global__ void __launch_bounds__(FluxCfg<D, M, PDE>::THREADS) k_flux(HotArgs a) {
@@ -569,9 +541,18 @@ __global__ void __launch_bounds__(FluxCfg<D, M, PDE>::THREADS) k_flux(HotArgs a)
   extern __shared__ double sh[];
   __shared__ int skind[C::CPB];
   __shared__ int snb[3 * C::CPB];
-  const int lc = threadIdx.x / NPT, g = threadIdx.x % NPT;
-  const int cell = blockIdx.x * C::CPB + lc;
-  const bool ok = cell < a.na;
+  __shared__ int sitem[3 * C::CPB];
+  const int li = threadIdx.x / NPT, g = threadIdx.x % NPT;
+  const long long item = (long long)blockIdx.x * C::CPB + li;
+  const long long nlo = (long long)D * a.na;
+  const bool ok = item < nlo + a.nh;
+  int cell = 0, d = 0, side = 0;
+  if (ok) {
+    long long e = item < nlo ? item : a.hflist[item - nlo];
+    d = (int)(e / a.na);
+    cell = (int)(e - (long long)d * a.na);
+    side = item < nlo ? 0 : 1;
+  }
   const LevelView& L = a.lv;
   int ijk[3] = {0, 0, 0};
   if (ok) {
@@ -580,10 +561,22 @@ __global__ void __launch_bounds__(FluxCfg<D, M, PDE>::THREADS) k_flux(HotArgs a)
     ijk[1] = (int)((di / L.L[0]) % L.L[1]);
     ijk[2] = (int)(di / ((long long)L.L[0] * L.L[1]));
   }
-  const double* qA = a.qh + (long long)(ok ? cell : 0) * V * NST;
-  flux_axis<D, M, PDE, 0>(a, ok, ijk, qA, lc, g, sh, skind, snb);
-  flux_axis<D, M, PDE, 1>(a, ok, ijk, qA, lc, g, sh, skind, snb);
-  if constexpr (D == 3) flux_axis<D, M, PDE, 2>(a, ok, ijk, qA, lc, g, sh, skind, snb);
+  const double* qA = a.qh + (long long)cell * V * NST;
+  double contrib[V];
+  int nb[3];
+  int kind;
+  if (d == 0) kind = flux_point<D, M, PDE, 0>(a, ok, ijk, qA, g, side, contrib, nb);
+  else if (D == 2 || d == 1) kind = flux_point<D, M, PDE, 1>(a, ok, ijk, qA, g, side, contrib, nb);
+  else kind = flux_point<D, M, PDE, (D == 3 ? 2 : 1)>(a, ok, ijk, qA, g, side, contrib, nb);
+#pragma unroll
+  for (int v = 0; v < V; v++) sh[threadIdx.x * V + v] = contrib[v];
+  if (g == 0) {
+    skind[li] = ok ? kind : FK_SKIP;
+    snb[3 * li] = nb[0]; snb[3 * li + 1] = nb[1]; snb[3 * li + 2] = nb[2];
+    sitem[3 * li] = cell; sitem[3 * li + 1] = d; sitem[3 * li + 2] = side;
+  }
+  __syncthreads();
+  flux_finish<D, M, PDE>(a, sh, sitem, skind, snb);
 }
 
 // ------------------------------------------------------------------------------------------
