@@ -14,7 +14,7 @@ import numpy as np
 from . import build as _build
 
 PDE_EULER, PDE_MHD, PDE_LINADV = 0, 1, 2
-BC_PERIODIC, BC_TRANSMISSIVE = 0, 1
+BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE = 0, 1, 2
 IC_CONST, IC_VORTEX, IC_EXPLOSION, IC_OT, IC_RP4, IC_FOURIER = 0, 1, 2, 3, 4, 5
 ST_NONE = -2
 

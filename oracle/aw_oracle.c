@@ -39,7 +39,7 @@
 #define ST_NONE ((int8_t)-2)
 
 enum { PDE_EULER = 0, PDE_MHD = 1, PDE_LINADV = 2 };
-enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1 };
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2 };
 enum { IC_CONST = 0, IC_VORTEX = 1, IC_EXPLOSION = 2, IC_OT = 3, IC_RP4 = 4, IC_FOURIER = 5 };
 
 typedef struct {
@@ -543,9 +543,18 @@ static long didx(const olev *L, int i, int j, int k) { return ((long)k * L->L[1]
 static int bcmap(const osolver *S, int lv, int a, int c, int *out) {
   int n = S->lev[lv].L[a];
   if (c >= 0 && c < n) { *out = c; return 1; }
-  if (S->c.bc[2 * a + (c < 0 ? 0 : 1)] == BC_PERIODIC) { *out = ((c % n) + n) % n; return 1; }
+  int bc = S->c.bc[2 * a + (c < 0 ? 0 : 1)];
+  if (bc == BC_PERIODIC) { *out = ((c % n) + n) % n; return 1; }
+  if (bc == BC_REFLECTIVE) { *out = c < 0 ? -1 - c : 2 * n - 1 - c; return 0; }  /* mirror image */
   *out = c < 0 ? 0 : n - 1;
   return 0;
+}
+
+/* is coordinate c of axis a beyond a reflective boundary? */
+static int reflected(const osolver *S, int lv, int a, int c) {
+  int n = S->lev[lv].L[a];
+  if (c >= 0 && c < n) return 0;
+  return S->c.bc[2 * a + (c < 0 ? 0 : 1)] == BC_REFLECTIVE;
 }
 
 static double dxl(const osolver *S, int lv, int a) {
@@ -751,12 +760,18 @@ static void weno1d(const tables *T, const double *v, double *out) {
   for (int p = 0; p < N; p++) out[p] += c;
 }
 
-/* value at level lv of the cell at integer coordinates c[] (through the BCs) */
-static const double *uval(const osolver *S, int lv, const int *c) {
+/* averages at level lv of the cell at integer coordinates c[], through the BCs: periodic wrap,
+ * transmissive clamp, reflective mirror image with the normal momentum negated (reading: a
+ * reflecting wall is the mirror image of the interior, for the Euler equations) */
+static void uget(const osolver *S, int lv, const int *c, double *out) {
   const olev *L = &S->lev[lv];
   int m[3] = {0, 0, 0};
   for (int a = 0; a < S->d; a++) bcmap(S, lv, a, c[a], &m[a]);
-  return L->u + didx(L, m[0], m[1], m[2]) * S->V;
+  const double *u = L->u + didx(L, m[0], m[1], m[2]) * S->V;
+  for (int v = 0; v < S->V; v++) out[v] = u[v];
+  if (S->P.pde == PDE_EULER)
+    for (int a = 0; a < S->d; a++)
+      if (reflected(S, lv, a, c[a])) out[1 + a] = -out[1 + a];
 }
 
 /* WENO polynomial of cell ijk at level lv: wh[v*nsp + (p + N q + N^2 r)] */
@@ -770,7 +785,9 @@ static void weno_cell(const osolver *S, int lv, const int *ijk, double *wh) {
         double line[2 * MAXN + 1];
         for (int f = -M; f <= M; f++) {
           int c[3] = {ijk[0] + f, ijk[1] + e, 0};
-          line[f + M] = uval(S, lv, c)[v];
+          double tmp[MAXV];
+          uget(S, lv, c, tmp);
+          line[f + M] = tmp[v];
         }
         weno1d(&S->T, line, wx[e + M][v]);
       }
@@ -793,7 +810,9 @@ static void weno_cell(const osolver *S, int lv, const int *ijk, double *wh) {
         double line[2 * MAXN + 1];
         for (int f = -M; f <= M; f++) {
           int c[3] = {ijk[0] + f, ijk[1] + ey, ijk[2] + ez};
-          line[f + M] = uval(S, lv, c)[v];
+          double tmp[MAXV];
+          uget(S, lv, c, tmp);
+          line[f + M] = tmp[v];
         }
         weno1d(&S->T, line, wx[ez + M][ey + M][v]);
       }
@@ -1011,6 +1030,24 @@ static void face_flux(osolver *S, int lv, const int *ijk, int ia, int a, int sid
     if (b != a) tdir[nt++] = b;
   int npt = 1;
   for (int b = 0; b < nt; b++) npt *= N;
+  if (!inside && S->c.bc[2 * a + side] == BC_REFLECTIVE) {
+    /* reflecting wall: the outer state is the mirror image of the inner trace */
+    for (int g = 0; g < npt * N; g++) {
+      int t = g;
+      double xi[3], wt = 1.0, q[MAXV], qm[MAXV], f[MAXV];
+      xi[a] = side ? 1.0 : 0.0;
+      for (int b = 0; b < nt; b++) { int gi = t % N; t /= N; xi[tdir[b]] = S->T.x[gi]; wt *= S->T.w[gi]; }
+      int gs = t;
+      wt *= S->T.w[gs];
+      eval_st(S, qA, xi, S->T.x[gs], q);
+      for (int v = 0; v < V; v++) qm[v] = q[v];
+      if (S->P.pde == PDE_EULER) qm[1 + a] = -qm[1 + a];
+      if (side) numflux(&S->P, q, qm, a, f);
+      else numflux(&S->P, qm, q, a, f);
+      for (int v = 0; v < V; v++) F[v] += wt * f[v];
+    }
+    return;
+  }
   if (!inside) {
     /* transmissive boundary face: q+ = q- (reading), Rusanov reduces to f(q-) */
     for (int g = 0; g < npt * N; g++) {
@@ -1196,7 +1233,9 @@ static double phi_at(const osolver *S, int lv, const int *ijk, int a, int sa, in
   int c[3] = {ijk[0], ijk[1], ijk[2]};
   c[a] += sa;
   c[b] += sb;
-  return uval(S, lv, c)[0];
+  double tmp[MAXV];
+  uget(S, lv, c, tmp);
+  return tmp[0];
 }
 static double indicator(const osolver *S, int lv, const int *ijk) {
   int d = S->d;
@@ -1463,6 +1502,8 @@ void *orc_create(const orc_cfg *c) {
   S->N = c->M + 1;
   S->P.pde = c->pde; S->P.d = c->dim; S->P.gamma = c->gamma; S->P.c_h = c->c_h; S->P.flux = c->flux;
   if (c->flux == 1 && c->pde == PDE_MHD) { seterr("the Osher flux is available for Euler and linear advection"); return NULL; }
+  for (int i = 0; i < 6; i++)
+    if (c->bc[i] == BC_REFLECTIVE && c->pde == PDE_MHD) { seterr("reflective walls are available for Euler and linear advection"); return NULL; }
   for (int a = 0; a < 3; a++) S->P.adv[a] = c->adv[a];
   S->V = c->pde == PDE_LINADV ? 1 : (c->pde == PDE_EULER ? c->dim + 2 : 9);
   S->P.V = S->V;
