@@ -53,6 +53,7 @@ extern "C" {
 
 #define AW_BC_PERIODIC 0
 #define AW_BC_TRANSMISSIVE 1
+#define AW_BC_REFLECTIVE 2   /* wall: mirror image with the normal momentum negated (Euler, linear advection) */
 
 #define AW_FLUX_RUSANOV 0  /* Eq. eqn.rusanov */
 #define AW_FLUX_OSHER 1    /* Eq. eqn.osher, 3-point Gauss-Legendre path quadrature (Euler) */

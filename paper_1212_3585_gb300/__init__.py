@@ -10,7 +10,7 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (AwSrvInfo, AwSrvSummary, AW_BC_PERIODIC, AW_BC_TRANSMISSIVE, AW_FLUX_OSHER, AW_FLUX_RUSANOV, AW_IC_CONST, AW_IC_EXPLOSION,  # noqa: F401
+from ._lib import (AwSrvInfo, AwSrvSummary, AW_BC_PERIODIC, AW_BC_REFLECTIVE, AW_BC_TRANSMISSIVE, AW_FLUX_OSHER, AW_FLUX_RUSANOV, AW_IC_CONST, AW_IC_EXPLOSION,  # noqa: F401
                    AW_IC_FOURIER, AW_IC_OT, AW_IC_RP4, AW_IC_VORTEX, AW_INTERNAL_CHI, AW_INTERNAL_FLUX,
                    AW_INTERNAL_PREDICTOR, AW_INTERNAL_WENO, AW_PDE_EULER, AW_PDE_LINADV, AW_PDE_MHD_GLM,
                    AwCell, AwConfig, AwError, AwStats)

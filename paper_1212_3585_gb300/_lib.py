@@ -9,7 +9,7 @@ LIB_PATH = os.path.join(PKG, "lib", "libaderweno.so")
 
 AW_OK, AW_EINVAL, AW_ENOMEM, AW_ECUDA, AW_ENONPHYSICAL, AW_ETIMEOUT, AW_ESTATE = 0, -1, -2, -3, -4, -5, -6
 AW_PDE_EULER, AW_PDE_MHD_GLM, AW_PDE_LINADV = 0, 1, 2
-AW_BC_PERIODIC, AW_BC_TRANSMISSIVE = 0, 1
+AW_BC_PERIODIC, AW_BC_TRANSMISSIVE, AW_BC_REFLECTIVE = 0, 1, 2
 AW_FLUX_RUSANOV, AW_FLUX_OSHER = 0, 1
 AW_IC_CONST, AW_IC_VORTEX, AW_IC_EXPLOSION, AW_IC_OT, AW_IC_RP4, AW_IC_FOURIER = 0, 1, 2, 3, 4, 5
 AW_INTERNAL_WENO, AW_INTERNAL_PREDICTOR, AW_INTERNAL_CHI, AW_INTERNAL_FLUX = 0, 1, 2, 3

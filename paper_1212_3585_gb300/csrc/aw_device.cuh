@@ -13,7 +13,7 @@ constexpr int MAXV = 9;
 constexpr int8_t ST_NONE = -2;
 
 enum { PDE_EULER = 0, PDE_MHD = 1, PDE_LINADV = 2 };
-enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1 };
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2 };
 
 __host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
 __host__ __device__ constexpr int nvars(int D, int PDE) {
@@ -67,17 +67,24 @@ __host__ __device__ inline long long didx(const LevelView& L, int i, int j, int 
 
 // Map coordinate c of axis a through the boundary conditions.  Returns true inside (possibly
 // wrapped), false outside a transmissive boundary, where *out is clamped (ghost layers copy the
-// adjacent interior cell of the same level).
+// adjacent interior cell of the same level), or outside a reflective wall, where *out is the
+// mirror image (the caller negates the normal momentum).
 __device__ __forceinline__ bool bcmap(const int* L, const int* bc, int a, int c, int* out) {
   int n = L[a];
   if (c >= 0 && c < n) { *out = c; return true; }
-  if (bc[2 * a + (c < 0 ? 0 : 1)] == BC_PERIODIC) {
+  int b = bc[2 * a + (c < 0 ? 0 : 1)];
+  if (b == BC_PERIODIC) {
     int m = c % n;
     *out = m < 0 ? m + n : m;
     return true;
   }
+  if (b == BC_REFLECTIVE) { *out = c < 0 ? -1 - c : 2 * n - 1 - c; return false; }
   *out = c < 0 ? 0 : n - 1;
   return false;
+}
+
+__device__ __forceinline__ bool reflected(const int* L, const int* bc, int a, int c) {
+  return (c < 0 || c >= L[a]) && bc[2 * a + (c < 0 ? 0 : 1)] == BC_REFLECTIVE;
 }
 
 // Reciprocal by the Newton-Raphson iteration y <- y + y (1 - x y) (quadratic convergence),

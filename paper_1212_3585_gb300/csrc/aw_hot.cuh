@@ -125,17 +125,23 @@ __global__ void __launch_bounds__(256) k_weno(HotArgs a) {
     int t = tile;
     for (int d = 0; d < D; d++) { org[d] = (t % a.tdim[d]) * TS; t /= a.tdim[d]; }
   }
-  // stage the box
+  // stage the box (reflective walls: mirror image with the normal momentum negated)
   for (int idx = threadIdx.x; idx < NB; idx += blockDim.x) {
     int t = idx, c[3] = {0, 0, 0};
+    unsigned flip = 0;
     for (int d = 0; d < D; d++) {
       int b = t % B;
       t /= B;
+      if (reflected(L.L, a.bc, d, org[d] - M + b)) flip |= 1u << d;
       bcmap(L.L, a.bc, d, org[d] - M + b, &c[d]);
     }
     long long di = didx(L, c[0], c[1], c[2]);
 #pragma unroll
-    for (int v = 0; v < V; v++) box[v * NB + idx] = L.u[v * L.n + di];
+    for (int v = 0; v < V; v++) {
+      double x = L.u[v * L.n + di];
+      if (PDE == PDE_EULER && v >= 1 && v <= D && (flip >> (v - 1) & 1u)) x = -x;
+      box[v * NB + idx] = x;
+    }
   }
   for (int idx = threadIdx.x; idx < C::NC; idx += blockDim.x) {
     int t = idx, c[3] = {0, 0, 0};
@@ -413,7 +419,21 @@ __device__ __forceinline__ int flux_point(const HotArgs& a, bool ok, const int* 
       for (int k = 1; k < N; k++) t = fma(pa[k], qA[v * NST + nbase + k * dstr], t);
       qa[v] = t;
     }
-    if (kind == FK_BOUNDARY) {
+    if (kind == FK_BOUNDARY && a.bc[2 * d + side] == BC_REFLECTIVE) {
+      // reflecting wall: the outer state is the mirror image of the trace
+      double qm[V];
+#pragma unroll
+      for (int v = 0; v < V; v++) qm[v] = qa[v];
+      if constexpr (PDE == PDE_EULER) qm[1 + d] = -qm[1 + d];
+      const double* ql = side ? qa : qm;
+      const double* qr = side ? qm : qa;
+      if constexpr (PDE == PDE_EULER) {
+        if (a.flux == 1) osher_euler<D>(ql, qr, d, f, a.P);
+        else rusanov<PDE, D>(ql, qr, d, f, a.P);
+      } else {
+        rusanov<PDE, D>(ql, qr, d, f, a.P);
+      }
+    } else if (kind == FK_BOUNDARY) {
       Pde<PDE, D>::flux(qa, d, f, a.P);
     } else {
       if (kind == FK_SAME) {

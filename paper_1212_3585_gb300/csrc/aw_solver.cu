@@ -1135,9 +1135,13 @@ int aw_create(const aw_config* cfg, uintptr_t stream, aw_solver** out) {
     if (!(c.hi[a] > c.lo[a])) AW_FAIL(AW_EINVAL, "empty domain on axis %d", a);
     if ((c.bc[2 * a] == AW_BC_PERIODIC) != (c.bc[2 * a + 1] == AW_BC_PERIODIC))
       AW_FAIL(AW_EINVAL, "periodic boundaries must pair up on axis %d", a);
-    for (int sd = 0; sd < 2; sd++)
-      if (c.bc[2 * a + sd] != AW_BC_PERIODIC && c.bc[2 * a + sd] != AW_BC_TRANSMISSIVE)
-        AW_FAIL(AW_EINVAL, "unknown boundary condition %d", c.bc[2 * a + sd]);
+    for (int sd = 0; sd < 2; sd++) {
+      int b = c.bc[2 * a + sd];
+      if (b != AW_BC_PERIODIC && b != AW_BC_TRANSMISSIVE && b != AW_BC_REFLECTIVE)
+        AW_FAIL(AW_EINVAL, "unknown boundary condition %d", b);
+      if (b == AW_BC_REFLECTIVE && c.pde == AW_PDE_MHD_GLM)
+        AW_FAIL(AW_EINVAL, "reflective walls are available for the Euler equations and linear advection");
+    }
   }
   if (!(c.cfl > 0.0)) AW_FAIL(AW_EINVAL, "cfl must be positive");
   if (c.flux != AW_FLUX_RUSANOV && c.flux != AW_FLUX_OSHER) AW_FAIL(AW_EINVAL, "unknown numerical flux %d", c.flux);

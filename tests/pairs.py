@@ -35,8 +35,11 @@ class Pair:
                  r=3, lmax=0, gamma=1.4, c_h=2.0, chi_ref=0.2, chi_rec=0.1, cfl=0.9, adv=(1.0, 0.5, 0.25),
                  threads=8, flux=0):
         op, gp = PDE_MAP[pde]
-        obc = oracle.BC_PERIODIC if bc == "periodic" else oracle.BC_TRANSMISSIVE
-        gbc = pg.AW_BC_PERIODIC if bc == "periodic" else pg.AW_BC_TRANSMISSIVE
+        if isinstance(bc, (list, tuple)):
+            obc = gbc = list(bc)   # per-face codes, identical numbering on both sides
+        else:
+            obc = oracle.BC_PERIODIC if bc == "periodic" else oracle.BC_TRANSMISSIVE
+            gbc = pg.AW_BC_PERIODIC if bc == "periodic" else pg.AW_BC_TRANSMISSIVE
         kw = dict(dim=dim, M=M, n=n, lo=lo, hi=hi, r=r, lmax=lmax, gamma=gamma, c_h=c_h, chi_ref=chi_ref,
                   chi_rec=chi_rec, cfl=cfl, auto_regrid=0, adv=adv)
         self.o = oracle.Oracle(oracle.make_cfg(pde=op, bc=obc, flux=flux, **kw), threads=threads)
