@@ -240,6 +240,57 @@ def run_serve(args):
     return 0
 
 
+def run_efficiency(args):
+    """Cost per cell update of the second- to fourth-order schemes (M = 1, 2, 3) on a uniform
+    grid and on the AMR grid (r = 4, l_max = 2) of the 2D explosion, normalised by the
+    second-order scheme on the uniform grid: the measurement of the paper's Sec. 3.2 efficiency
+    table (whole solve, ghost projection, averaging and regrid included) on this GPU."""
+    import torch
+    import aw_inputs
+    import paper_1212_3585_gb300 as pg
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    B, r, lmax = args.eff_base, 4, 2
+    rows = []
+    for M in (1, 2, 3):
+        for grid in ("uniform", "amr"):
+            n = B * r ** lmax if grid == "uniform" else B
+            cfg = pg.make_config(dim=2, M=M, n=(n, n, 1), lo=(-1.0, -1.0, 0.0), hi=(1.0, 1.0, 1.0),
+                                 bc=pg.AW_BC_TRANSMISSIVE, r=r, lmax=0 if grid == "uniform" else lmax,
+                                 cfl=0.6, auto_regrid=1)
+            s = pg.Solver(cfg, stream.cuda_stream)
+            times, upd = [], 0
+            for i in range(args.warmup + args.steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record(stream)
+                s.reset()
+                s.set_initial(pg.AW_IC_EXPLOSION, aw_inputs.EXPLOSION, -1)
+                st = s.advance_to(args.eff_t_end)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if i >= args.warmup:
+                    times.append(e0.elapsed_time(e1))
+                    upd += st.cell_updates
+            s.close()
+            ns = 1e6 * sum(times) / upd
+            rows.append({"order": M + 1, "M": M, "grid": grid, "ns_per_cell_update": ns,
+                         "cell_updates_per_solve": upd // args.steps, "ms_per_solve": sum(times) / len(times)})
+    ref = rows[0]["ns_per_cell_update"]
+    table = {}
+    for M in (1, 2, 3):
+        u = next(x for x in rows if x["M"] == M and x["grid"] == "uniform")["ns_per_cell_update"]
+        a = next(x for x in rows if x["M"] == M and x["grid"] == "amr")["ns_per_cell_update"]
+        table[f"O{M + 1}"] = {"uniform": u / ref, "amr": a / ref, "amr_overhead_pct": 100 * (a / u - 1)}
+    print(json.dumps({"metric": "normalised time per cell update (second-order uniform = 1)", "unit": "ratio",
+                      "higher_is_better": False, "dtype": "f64", "data": "synthetic",
+                      "config": {"workload": f"2D Euler explosion, [-1,1]^2, CFL 0.6, t_end={args.eff_t_end}; "
+                                             f"AMR: base {B}x{B}, r={r}, l_max={lmax}; uniform: {B * r ** lmax}^2",
+                                 "steps": args.steps, "warmup": args.warmup},
+                      "table": table, "rows": rows}))
+    return 0
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -312,6 +363,10 @@ def main():
     ap.add_argument("--concurrency", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=float, default=160.0)
     ap.add_argument("--t-end", type=float, default=T_END, help="end time (workload: 0.25)")
+    ap.add_argument("--efficiency", action="store_true",
+                    help="cost per cell update of orders 2-4, uniform vs AMR (r=4, l_max=2)")
+    ap.add_argument("--eff-base", type=int, default=25)
+    ap.add_argument("--eff-t-end", type=float, default=0.1)
     args = ap.parse_args()
     if args.base != 100 or args.t_end != T_END:
         CFG["n"] = (args.base, args.base, 1)
@@ -321,6 +376,8 @@ def main():
     ws, rank, local = dist_setup()
     if args.serve:
         return run_serve(args) if rank == 0 else 0
+    if args.efficiency:
+        return run_efficiency(args) if rank == 0 else 0
     if args.impl == "reference":
         if rank != 0:
             return 0

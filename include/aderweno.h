@@ -85,7 +85,7 @@ extern "C" {
 typedef struct aw_config {
   int32_t dim;          /* 2 or 3 */
   int32_t pde;          /* AW_PDE_* */
-  int32_t M;            /* polynomial degree of the reconstruction, 2 or 3 (order M+1) */
+  int32_t M;            /* polynomial degree of the reconstruction, 1, 2 or 3 (order M+1); M = 1 for 2D Euler and linear advection only */
   int32_t nx, ny, nz;   /* level-0 cells per direction (nz ignored when dim == 2) */
   double gamma;         /* ratio of specific heats */
   double c_h;           /* GLM cleaning speed (MHD) */

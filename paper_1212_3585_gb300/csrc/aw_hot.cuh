@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(256) k_weno(HotArgs a) {
 template <int D, int M, int PDE>
 struct PredCfg {
   static constexpr int N = M + 1, NSP = ipow(N, D), NST = NSP * N, V = nvars(D, PDE);
-  static constexpr int CPB = (NSP == 9) ? 32 : (NSP == 16 ? 16 : (NSP == 27 ? 16 : 4));
+  static constexpr int CPB = (NSP == 4) ? 64 : (NSP == 9) ? 32 : (NSP == 16 ? 16 : (NSP == 27 ? 16 : 4));
   static constexpr int THREADS = CPB * NSP;
   static constexpr int SMEM = CPB * D * V * NST * 8;   // fluxes at every space-time node
 };
@@ -367,6 +367,7 @@ struct FluxCfg {
   static constexpr int CPB = 256 / NPT;   // face items per CTA
   static constexpr int THREADS = CPB * NPT;
   static constexpr int SMEM = THREADS * V * 8;
+  static_assert(CPB * V <= THREADS, "flux_finish needs one thread per (face item, variable)");
 };
 
 enum { FK_SAME = 0, FK_FINE = 1, FK_COARSE = 2, FK_BOUNDARY = 3, FK_SKIP = 4 };
@@ -487,7 +488,6 @@ __device__ __forceinline__ int flux_point(const HotArgs& a, bool ok, const int* 
   return kind;
 }
 
-// reduce the point contributions of every (cell, variable) of the CTA and finish the face
 // reduce the point contributions of every (face item, variable) of the CTA and finish the face
 template <int D, int M, int PDE>
 __device__ __forceinline__ void flux_finish(const HotArgs& a, const double* sh, const int* sitem, const int* skind,
@@ -544,14 +544,15 @@ __device__ __forceinline__ void flux_finish(const HotArgs& a, const double* sh, 
 
 // ------------------------------------------------------------------------------------------
 // Face flux kernel (Eqs. flux:F..flux:H, eqn.rusanov, eqn.osher, eqn.memory.sum).  Work items are
-// faces: the low face of every active cell on every axis (axis-major), then the listed high faces
-// whose neighbour is not an active cell of this level (boundary, coarse or fine neighbour).  One
-// thread per (face, quadrature point); the N^(d-1) x N space-time Gauss points of a face coincide
-// with the nodal points, so a trace is one N-term contraction along the normal.  Faces toward a
-// virtual child are fine sides of a coarse/fine face: the coarse predictor is evaluated at this
-// cell's points and sub-step, and the face integral is added to this cell's memory variable.
-// Faces toward a virtual mother are coarse sides: the flux is the sum of the fine cells' memory
-// variables over the r sub-steps, normalised by dt * area of this level.
+// faces: the low face of every active cell on every axis (by chunks of cells, the axes of a chunk
+// in turn), then the listed high faces whose neighbour is not an active cell of this level
+// (boundary, coarse or fine neighbour).  One thread per (face, quadrature point); the
+// N^(d-1) x N space-time Gauss points of a face coincide with the nodal points, so a trace is
+// one N-term contraction along the normal.  Faces toward a virtual child are fine sides of a
+// coarse/fine face: the coarse predictor is evaluated at this cell's points and sub-step, and
+// the face integral is added to this cell's memory variable.  Faces toward a virtual mother are
+// coarse sides: the flux is the sum of the fine cells' memory variables over the r sub-steps,
+// normalised by dt * area of this level.
 // ------------------------------------------------------------------------------------------
 template <int D, int M, int PDE>
 __global__ void __launch_bounds__(FluxCfg<D, M, PDE>::THREADS) k_flux(HotArgs a) {
@@ -563,15 +564,27 @@ __global__ void __launch_bounds__(FluxCfg<D, M, PDE>::THREADS) k_flux(HotArgs a)
   __shared__ int snb[3 * C::CPB];
   __shared__ int sitem[3 * C::CPB];
   const int li = threadIdx.x / NPT, g = threadIdx.x % NPT;
-  const long long item = (long long)blockIdx.x * C::CPB + li;
-  const long long nlo = (long long)D * a.na;
-  const bool ok = item < nlo + a.nh;
+  // CTAs 0..D*nchunk-1 take the low faces: chunk c of CPB active cells, axis d = CTA mod D, so
+  // the D passes over a chunk run back to back and share its predictor data in L2.  The rest
+  // take the listed high faces (item e = d * na + cell).
+  const long long nlob = (long long)D * ((a.na + C::CPB - 1) / C::CPB);
+  bool ok;
   int cell = 0, d = 0, side = 0;
-  if (ok) {
-    long long e = item < nlo ? item : a.hflist[item - nlo];
-    d = (int)(e / a.na);
-    cell = (int)(e - (long long)d * a.na);
-    side = item < nlo ? 0 : 1;
+  if (blockIdx.x < nlob) {
+    const long long chunk = blockIdx.x / D;
+    d = (int)(blockIdx.x - chunk * D);
+    const long long c = chunk * C::CPB + li;
+    ok = c < a.na;
+    cell = ok ? (int)c : 0;
+  } else {
+    const long long h = (blockIdx.x - nlob) * C::CPB + li;
+    ok = h < a.nh;
+    if (ok) {
+      const long long e = a.hflist[h];
+      d = (int)(e / a.na);
+      cell = (int)(e - (long long)d * a.na);
+      side = 1;
+    }
   }
   const LevelView& L = a.lv;
   int ijk[3] = {0, 0, 0};

@@ -38,8 +38,8 @@ struct Launch {
       cudaFuncSetAttribute(k_flux<D, M, PDE>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
       init = true;
     }
-    long long items = (long long)D * a.na + a.nh;
-    int blocks = (int)((items + C::CPB - 1) / C::CPB);
+    long long blocks_lo = (long long)D * ((a.na + C::CPB - 1) / C::CPB);
+    int blocks = (int)(blocks_lo + (a.nh + C::CPB - 1) / C::CPB);
     k_flux<D, M, PDE><<<blocks, C::THREADS, C::SMEM, st>>>(a);
     return 1;
   }

@@ -2,6 +2,8 @@
 #include "aw_ops.h"
 
 namespace aw {
+HotOps ops_2_1_0();
+HotOps ops_2_1_2();
 HotOps ops_2_2_0();
 HotOps ops_2_3_0();
 HotOps ops_3_2_0();
@@ -14,6 +16,8 @@ HotOps ops_3_2_2();
 bool get_ops(int D, int M, int PDE, HotOps* out) {
   int key = D * 100 + M * 10 + PDE;
   switch (key) {
+    case 210: *out = ops_2_1_0(); return true;
+    case 212: *out = ops_2_1_2(); return true;
     case 220: *out = ops_2_2_0(); return true;
     case 230: *out = ops_2_3_0(); return true;
     case 320: *out = ops_3_2_0(); return true;

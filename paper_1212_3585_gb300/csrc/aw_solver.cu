@@ -1124,7 +1124,7 @@ int aw_create(const aw_config* cfg, uintptr_t stream, aw_solver** out) {
   *out = nullptr;
   const aw_config& c = *cfg;
   if (c.dim != 2 && c.dim != 3) AW_FAIL(AW_EINVAL, "dim must be 2 or 3");
-  if (c.M < 2 || c.M > 3) AW_FAIL(AW_EINVAL, "M must be 2 or 3");
+  if (c.M < 1 || c.M > 3) AW_FAIL(AW_EINVAL, "M must be 1, 2 or 3");
   if (c.pde < 0 || c.pde > 2) AW_FAIL(AW_EINVAL, "unknown pde %d", c.pde);
   if (c.lmax < 0 || c.lmax >= MAXL) AW_FAIL(AW_EINVAL, "lmax must be in 0..%d", MAXL - 1);
   int r = c.lmax > 0 ? c.refine_factor : (c.refine_factor > 0 ? c.refine_factor : 2);

@@ -28,7 +28,7 @@ def by_var(buf, what, V, per=None):
 VORTEX = [5.0, 5.0, 5.0, 1.0, 1.0, 1.0, 1.0]
 
 
-@pytest.mark.parametrize("M", [2, 3])
+@pytest.mark.parametrize("M", [1, 2, 3])
 @pytest.mark.parametrize("bc", ["periodic", "transmissive"])
 def test_uniform_euler_kernels(M, bc):
     """WENO dofs, predictor dofs, face fluxes and averages after one step of a uniform grid."""
@@ -55,7 +55,7 @@ def test_vortex_config_full_size_20_steps():
         p.step()
 
 
-@pytest.mark.parametrize("pde,M,dim", [("linadv", 2, 2), ("linadv", 3, 2), ("linadv", 2, 3), ("euler", 2, 3)])
+@pytest.mark.parametrize("pde,M,dim", [("linadv", 1, 2), ("linadv", 2, 2), ("linadv", 3, 2), ("linadv", 2, 3), ("euler", 2, 3)])
 def test_uniform_other_systems(pde, M, dim):
     n = (9, 7, 6) if dim == 3 else (13, 10, 1)
     p = Pair(dim=dim, pde=pde, M=M, n=n, bc="periodic")
@@ -64,7 +64,7 @@ def test_uniform_other_systems(pde, M, dim):
         p.step()
 
 
-@pytest.mark.parametrize("M,lmax", [(3, 2), (2, 1)])
+@pytest.mark.parametrize("M,lmax", [(3, 2), (2, 1), (1, 2)])
 def test_amr_explosion_lts(M, lmax):
     """Explosion shaped like the 2D AMR configuration at a small base grid: tree bit-exact,
     averages within tolerance after each level-0 step with local time stepping and regrids."""
@@ -149,7 +149,7 @@ def test_empty_levels_and_errors():
     assert ei.value.code == pg._lib.AW_ENONPHYSICAL
 
 
-@pytest.mark.parametrize("dim,M,lmax", [(2, 3, 0), (2, 3, 2), (3, 2, 1)])
+@pytest.mark.parametrize("dim,M,lmax", [(2, 3, 0), (2, 3, 2), (3, 2, 1), (2, 1, 2)])
 def test_osher_flux_explosion(dim, M, lmax):
     """Osher-Solomon flux (Eq. eqn.osher), uniform and AMR with local time stepping"""
     n = (16, 16, 1) if dim == 2 else (6, 6, 6)
@@ -160,7 +160,7 @@ def test_osher_flux_explosion(dim, M, lmax):
         p.step()
 
 
-@pytest.mark.parametrize("dim,M,lmax,flux", [(2, 3, 1, 0), (2, 2, 2, 1), (3, 2, 1, 0)])
+@pytest.mark.parametrize("dim,M,lmax,flux", [(2, 3, 1, 0), (2, 2, 2, 1), (3, 2, 1, 0), (2, 1, 1, 1)])
 def test_reflective_walls(dim, M, lmax, flux):
     """walls on the low faces, transmissive high faces: the quadrant of the centred explosion"""
     R, T = pg.AW_BC_REFLECTIVE, pg.AW_BC_TRANSMISSIVE

@@ -178,8 +178,10 @@ def _linadv_err(M, n, t_end):
     return math.sqrt(np.mean((u[:, 0].reshape(n, n) - ex) ** 2))
 
 
-@pytest.mark.parametrize("M,lo_order", [(2, 2.85), (3, 3.8)])
-def test_linear_advection_design_order(M, lo_order):
-    e = [_linadv_err(M, n, 0.5) for n in (10, 20, 40)]
+# M = 1: the two-cell stencils' weights (exponent 8) switch near the extrema of the sine wave, so
+# the second order is reached only slowly (1.67, 1.69, 1.81 from 20 to 160 cells)
+@pytest.mark.parametrize("M,grids,lo_order", [(1, (40, 80, 160), 1.65), (2, (10, 20, 40), 2.85), (3, (10, 20, 40), 3.8)])
+def test_linear_advection_design_order(M, grids, lo_order):
+    e = [_linadv_err(M, n, 0.5) for n in grids]
     orders = [math.log(e[i] / e[i + 1], 2) for i in range(2)]
     assert min(orders) > lo_order, (e, orders)
