@@ -14,7 +14,7 @@ import numpy as np
 from . import build as _build
 
 PDE_EULER, PDE_MHD, PDE_LINADV = 0, 1, 2
-BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE = 0, 1, 2
+BC_PERIODIC, BC_TRANSMISSIVE, BC_REFLECTIVE, BC_INFLOW = 0, 1, 2, 3
 IC_CONST, IC_VORTEX, IC_EXPLOSION, IC_OT, IC_RP4, IC_FOURIER = 0, 1, 2, 3, 4, 5
 ST_NONE = -2
 
@@ -31,6 +31,7 @@ class OrcCfg(C.Structure):
         ("picard", C.c_int), ("auto_regrid", C.c_int),
         ("adv", C.c_double * 3),
         ("flux", C.c_int),
+        ("inflow", C.c_double * 9),
     ]
 
 
@@ -106,7 +107,7 @@ def _dp(a):
 
 def make_cfg(dim=2, pde=PDE_EULER, M=2, n=(16, 16, 1), gamma=1.4, c_h=2.0, lo=(0.0, 0.0, 0.0),
              hi=(1.0, 1.0, 1.0), bc=BC_PERIODIC, r=3, lmax=0, chi_ref=0.2, chi_rec=0.1, eps_ind=0.01,
-             cfl=0.9, picard=0, auto_regrid=1, adv=(1.0, 1.0, 1.0), flux=0):
+             cfl=0.9, picard=0, auto_regrid=1, adv=(1.0, 1.0, 1.0), flux=0, inflow=()):
     c = OrcCfg()
     c.dim, c.pde, c.M = dim, pde, M
     c.nx, c.ny, c.nz = n[0], n[1], (n[2] if dim == 3 else 1)
@@ -120,6 +121,8 @@ def make_cfg(dim=2, pde=PDE_EULER, M=2, n=(16, 16, 1), gamma=1.4, c_h=2.0, lo=(0
     c.chi_ref, c.chi_rec, c.eps_ind, c.cfl = chi_ref, chi_rec, eps_ind, cfl
     c.picard, c.auto_regrid = picard, auto_regrid
     c.flux = flux
+    for v, q in enumerate(inflow):
+        c.inflow[v] = q
     return c
 
 

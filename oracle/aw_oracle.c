@@ -39,7 +39,7 @@
 #define ST_NONE ((int8_t)-2)
 
 enum { PDE_EULER = 0, PDE_MHD = 1, PDE_LINADV = 2 };
-enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2 };
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2, BC_INFLOW = 3 };
 enum { IC_CONST = 0, IC_VORTEX = 1, IC_EXPLOSION = 2, IC_OT = 3, IC_RP4 = 4, IC_FOURIER = 5 };
 
 typedef struct {
@@ -53,6 +53,7 @@ typedef struct {
   int auto_regrid;
   double adv[3];
   int flux; /* 0 Rusanov, 1 Osher-Solomon (Dumbser-Toro) */
+  double inflow[MAXV]; /* conserved state held by the ghost cells beyond BC_INFLOW faces */
 } orc_cfg;
 
 static char g_err[512];
@@ -537,9 +538,10 @@ typedef struct {
 static long didx(const olev *L, int i, int j, int k) { return ((long)k * L->L[1] + j) * L->L[0] + i; }
 
 /* map coordinate c in direction a at level lv through the boundary conditions.
- * Returns 1 if inside (possibly wrapped periodically), 0 if outside a transmissive
- * boundary; *out is then the clamped coordinate (reading: transmissive ghost layers copy
- * the adjacent interior cell of the same level). */
+ * Returns 1 if inside (possibly wrapped periodically), 0 if outside a non-periodic boundary;
+ * *out is then the clamped coordinate (reading: transmissive ghost layers copy the adjacent
+ * interior cell of the same level), or the mirror image beyond a reflective wall.  Beyond an
+ * inflow face uget replaces the value by the inflow state. */
 static int bcmap(const osolver *S, int lv, int a, int c, int *out) {
   int n = S->lev[lv].L[a];
   if (c >= 0 && c < n) { *out = c; return 1; }
@@ -763,8 +765,22 @@ static void weno1d(const tables *T, const double *v, double *out) {
 /* averages at level lv of the cell at integer coordinates c[], through the BCs: periodic wrap,
  * transmissive clamp, reflective mirror image with the normal momentum negated (reading: a
  * reflecting wall is the mirror image of the interior, for the Euler equations) */
+/* is coordinate c of axis a beyond an inflow boundary? */
+static int beyond_inflow(const osolver *S, int lv, int a, int c) {
+  int n = S->lev[lv].L[a];
+  if (c >= 0 && c < n) return 0;
+  return S->c.bc[2 * a + (c < 0 ? 0 : 1)] == BC_INFLOW;
+}
+
+/* average of cell c of level lv through the boundary conditions (reading: a ghost cell beyond
+ * an inflow face, in any direction, holds the inflow state) */
 static void uget(const osolver *S, int lv, const int *c, double *out) {
   const olev *L = &S->lev[lv];
+  for (int a = 0; a < S->d; a++)
+    if (beyond_inflow(S, lv, a, c[a])) {
+      for (int v = 0; v < S->V; v++) out[v] = S->c.inflow[v];
+      return;
+    }
   int m[3] = {0, 0, 0};
   for (int a = 0; a < S->d; a++) bcmap(S, lv, a, c[a], &m[a]);
   const double *u = L->u + didx(L, m[0], m[1], m[2]) * S->V;
@@ -1030,6 +1046,23 @@ static void face_flux(osolver *S, int lv, const int *ijk, int ia, int a, int sid
     if (b != a) tdir[nt++] = b;
   int npt = 1;
   for (int b = 0; b < nt; b++) npt *= N;
+  if (!inside && S->c.bc[2 * a + side] == BC_INFLOW) {
+    /* inflow face: the outer state is the prescribed inflow state (reading) */
+    const double *qi = S->c.inflow;
+    for (int g = 0; g < npt * N; g++) {
+      int t = g;
+      double xi[3], wt = 1.0, q[MAXV], f[MAXV];
+      xi[a] = side ? 1.0 : 0.0;
+      for (int b = 0; b < nt; b++) { int gi = t % N; t /= N; xi[tdir[b]] = S->T.x[gi]; wt *= S->T.w[gi]; }
+      int gs = t;
+      wt *= S->T.w[gs];
+      eval_st(S, qA, xi, S->T.x[gs], q);
+      if (side) numflux(&S->P, q, qi, a, f);
+      else numflux(&S->P, qi, q, a, f);
+      for (int v = 0; v < V; v++) F[v] += wt * f[v];
+    }
+    return;
+  }
   if (!inside && S->c.bc[2 * a + side] == BC_REFLECTIVE) {
     /* reflecting wall: the outer state is the mirror image of the inner trace */
     for (int g = 0; g < npt * N; g++) {

@@ -1,0 +1,71 @@
+"""Pins of the oracle's inflow boundaries (reading: the ghost cells beyond an inflow face hold the
+prescribed conserved state, and the face flux is the numerical flux between that state and the
+interior trace).
+
+* Linear advection entering a constant state: the total changes at exactly a (c_in - c_0) L_y per
+  unit time while the front is inside the domain (the inflow face flux of the upwind scheme is
+  a c_in, the outflow face still sees c_0).
+* A supersonic channel: a contact discontinuity enters with the inflow state and leaves the
+  channel filled with it (a transmissive boundary would keep the initial state).
+* An inflow state equal to the adjacent constant state gives the transmissive solution.
+"""
+import numpy as np
+import pytest
+
+import aw_inputs
+import oracle
+
+
+@pytest.mark.parametrize("M", [2, 3])
+def test_linear_advection_inflow_balance(M):
+    c0, c1, a, Ly = 0.3, 1.0, 1.0, 0.25
+    cfg = oracle.make_cfg(dim=2, pde=oracle.PDE_LINADV, M=M, n=(64, 4, 1), lo=(0, 0, 0), hi=(1.0, Ly, 1),
+                          bc=[oracle.BC_INFLOW, oracle.BC_TRANSMISSIVE, oracle.BC_PERIODIC, oracle.BC_PERIODIC,
+                              oracle.BC_PERIODIC, oracle.BC_PERIODIC],
+                          adv=(a, 0.0, 0.0), inflow=(c1,), cfl=0.9)
+    o = oracle.Oracle(cfg, threads=4)
+    o.set_initial(oracle.IC_CONST, [c0], nrefine=0)
+    tot0 = o.totals()[0]
+    t_end = 0.15
+    while o.t < t_end:
+        rc, _ = o.step(t_end)
+        assert rc == 0
+    assert abs(o.totals()[0] - (tot0 + a * (c1 - c0) * Ly * t_end)) < 1e-13
+    _, u = o.cells()
+    assert np.max(np.abs(u[:, 0].reshape(4, 64)[:, -8:] - c0)) < 1e-15   # the outflow end untouched
+
+
+def test_supersonic_channel_fills_with_inflow_state():
+    g = 1.4
+    rho0, rho1, u, p = 0.5, 1.0, 3.0, 1.0
+    cons = lambda rho: [rho, rho * u, 0.0, p / (g - 1) + 0.5 * rho * u * u]
+    cfg = oracle.make_cfg(dim=2, M=3, n=(24, 4, 1), lo=(0, 0, 0), hi=(1.0, 1.0 / 6, 1),
+                          bc=[oracle.BC_INFLOW, oracle.BC_TRANSMISSIVE, oracle.BC_PERIODIC, oracle.BC_PERIODIC,
+                              oracle.BC_PERIODIC, oracle.BC_PERIODIC],
+                          inflow=cons(rho1), cfl=0.9, gamma=g)
+    o = oracle.Oracle(cfg, threads=4)
+    o.set_initial(oracle.IC_CONST, [rho0, u, 0.0, p], nrefine=0)   # primitive variables
+    t_end = 1.0     # the contact (speed u) has left by t = 1/3; u - c = 1.8 flushes the rest
+    while o.t < t_end:
+        rc, _ = o.step(t_end)
+        assert rc == 0
+    _, q = o.cells()
+    assert np.max(np.abs(q - np.array(cons(rho1)))) < 1e-9 * cons(rho1)[3]
+
+
+def test_inflow_of_the_boundary_state_equals_transmissive():
+    """the explosion on [-1.5, 1.5]^2 for three steps, while even its numerical precursor is far
+    from the boundary: an inflow face holding the outer state changes nothing"""
+    E = aw_inputs.EXPLOSION
+    outer = [E[3], 0.0, 0.0, E[4] / 0.4]
+    runs = []
+    for left in (oracle.BC_TRANSMISSIVE, oracle.BC_INFLOW):
+        cfg = oracle.make_cfg(dim=2, M=3, n=(30, 30, 1), lo=(-1.5, -1.5, 0), hi=(1.5, 1.5, 1),
+                              bc=[left] + [oracle.BC_TRANSMISSIVE] * 5, inflow=outer, cfl=0.6, r=3, lmax=1)
+        o = oracle.Oracle(cfg, threads=4)
+        o.set_initial(oracle.IC_EXPLOSION, E)
+        for _ in range(3):
+            assert o.step(1.0)[0] == 0
+        runs.append(o.cells())
+    assert np.array_equal(runs[0][0], runs[1][0])
+    assert np.max(np.abs(runs[0][1] - runs[1][1])) < 1e-14
