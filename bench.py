@@ -154,19 +154,19 @@ def combine_replicas(updates, ms, world_size, max_reduce):
     return world_size * updates / (job_ms * 1e-3), job_ms
 
 
-def serve_requests(n, base_max, seed=20121213):
+def serve_requests(n, base_max, seed=20121213, base_min=32, lmax_max=2):
     """Seeded stream shaped like the serving workload: 2D Euler four-quadrant Riemann problems on
-    [-0.5, 0.5]^2, base grid uniform in 32..base_max, M in {2, 3}, l_max in {0, 1, 2}, r = 3,
-    per-quadrant rho, p ~ U[0.1, 1.5], u, v ~ U[-1, 1] (aw_inputs.rp4_params)."""
+    [-0.5, 0.5]^2, base grid uniform in base_min..base_max, M in {2, 3}, l_max in 0..lmax_max,
+    r = 3, per-quadrant rho, p ~ U[0.1, 1.5], u, v ~ U[-1, 1] (aw_inputs.rp4_params)."""
     import numpy as np
     import aw_inputs
     import paper_1212_3585_gb300 as pg
     rng = np.random.default_rng(seed)
     out = []
     for k in range(n):
-        base = int(rng.integers(32, base_max + 1))
+        base = int(rng.integers(base_min, base_max + 1))
         M = int(rng.choice([2, 3]))
-        lmax = int(rng.integers(0, 3))
+        lmax = int(rng.integers(0, lmax_max + 1))
         cfg = pg.make_config(dim=2, M=M, n=(base, base, 1), lo=(-0.5, -0.5, 0), hi=(0.5, 0.5, 1),
                              bc=pg.AW_BC_TRANSMISSIVE, r=3, lmax=lmax, cfl=0.5)
         out.append((cfg, aw_inputs.rp4_params(seed + k)))
@@ -174,14 +174,16 @@ def serve_requests(n, base_max, seed=20121213):
 
 
 def run_serve(args):
-    """Continuous admission (aw_srv_*, concurrent requests on their own streams) against
-    one-at-a-time plain solves, on the same seeded requests and arrival times."""
+    """Continuous admission (aw_srv_*, concurrent requests on their own streams), with and without
+    cross-request batching, against one-at-a-time plain solves, on the same seeded requests and
+    arrival times."""
     import threading
     import numpy as np
     import torch
     import paper_1212_3585_gb300 as pg
     torch.cuda.set_device(0)
-    reqs = serve_requests(args.requests, args.serve_base_max)
+    reqs = serve_requests(args.requests, args.serve_base_max, base_min=args.serve_base_min,
+                          lmax_max=args.serve_lmax_max)
     t_end = args.serve_t_end
 
     def plain(arrivals):
@@ -209,8 +211,9 @@ def run_serve(args):
         return {"solves_per_s": len(tts) / done, "p50_ms": float(np.percentile(tts, 50)),
                 "p99_ms": float(np.percentile(tts, 99)), "cell_updates_per_s": upd / done, "failed": failed}
 
-    def batched(arrivals):
-        srv = pg.Server(hbm_budget_bytes=int(args.serve_budget_gb * (1 << 30)), max_concurrent=args.concurrency)
+    def loop(arrivals, max_batch=1):
+        srv = pg.Server(hbm_budget_bytes=int(args.serve_budget_gb * (1 << 30)), max_concurrent=args.concurrency,
+                        max_batch=max_batch)
         t0 = time.perf_counter()
         ids = []
         for (cfg, p), a in zip(reqs, arrivals):
@@ -226,16 +229,18 @@ def run_serve(args):
         return out
 
     burst = [0.0] * len(reqs)
-    res = {"burst": {"plain": plain(burst), "batched": batched(burst)}}
-    lam = 0.8 * res["burst"]["batched"]["solves_per_s"]
+    B = args.serve_batch
+    res = {"burst": {"plain": plain(burst), "loop": loop(burst), f"loop_batch{B}": loop(burst, B)}}
+    lam = 0.8 * max(res["burst"]["loop"]["solves_per_s"], res["burst"][f"loop_batch{B}"]["solves_per_s"])
     rng = np.random.default_rng(7)
     arr = list(np.cumsum(rng.exponential(1.0 / lam, len(reqs))))
-    res["poisson"] = {"rate_per_s": lam, "plain": plain(arr), "batched": batched(arr)}
-    print(json.dumps({"metric": "batched solves/s + p50/p99 time to solution vs plain", "unit": "solves/s",
+    res["poisson"] = {"rate_per_s": lam, "plain": plain(arr), "loop": loop(arr), f"loop_batch{B}": loop(arr, B)}
+    print(json.dumps({"metric": "request-loop solves/s + p50/p99 time to solution vs plain", "unit": "solves/s",
                       "higher_is_better": True, "dtype": "f64", "data": "synthetic",
-                      "config": {"workload": f"{len(reqs)} 2D Euler four-quadrant Riemann AMR solves, base 32..{args.serve_base_max}, "
-                                             f"M in {{2,3}}, l_max in {{0,1,2}}, r=3, CFL 0.5, t_end={t_end}",
-                                 "concurrency": args.concurrency, "budget_gb": args.serve_budget_gb},
+                      "config": {"workload": f"{len(reqs)} 2D Euler four-quadrant Riemann AMR solves, "
+                                             f"base {args.serve_base_min}..{args.serve_base_max}, M in {{2,3}}, "
+                                             f"l_max in 0..{args.serve_lmax_max}, r=3, CFL 0.5, t_end={t_end}",
+                                 "concurrency": args.concurrency, "budget_gb": args.serve_budget_gb, "batch": args.serve_batch},
                       **res}))
     return 0
 
@@ -359,9 +364,12 @@ def main():
     ap.add_argument("--serve", action="store_true", help="request-stream benchmark of the serving loop")
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--serve-base-max", type=int, default=96)
+    ap.add_argument("--serve-base-min", type=int, default=32)
+    ap.add_argument("--serve-lmax-max", type=int, default=2)
     ap.add_argument("--serve-t-end", type=float, default=0.05)
     ap.add_argument("--concurrency", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=float, default=160.0)
+    ap.add_argument("--serve-batch", type=int, default=8, help="batch size of the batched request loop")
     ap.add_argument("--t-end", type=float, default=T_END, help="end time (workload: 0.25)")
     ap.add_argument("--efficiency", action="store_true",
                     help="cost per cell update of orders 2-4, uniform vs AMR (r=4, l_max=2)")

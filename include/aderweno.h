@@ -54,6 +54,7 @@ extern "C" {
 #define AW_BC_PERIODIC 0
 #define AW_BC_TRANSMISSIVE 1
 #define AW_BC_REFLECTIVE 2   /* wall: mirror image with the normal momentum negated (Euler, linear advection) */
+#define AW_BC_INFLOW 3       /* ghost cells hold the constant conserved state inflow[]; face flux against it */
 
 #define AW_FLUX_RUSANOV 0  /* Eq. eqn.rusanov */
 #define AW_FLUX_OSHER 1    /* Eq. eqn.osher, 3-point Gauss-Legendre path quadrature (Euler) */
@@ -102,6 +103,7 @@ typedef struct aw_config {
   int32_t auto_regrid;  /* 1: regrid after every level-0 step (aw_step / aw_advance_to) */
   int32_t reserved;
   double adv[3];        /* advection velocity of AW_PDE_LINADV */
+  double inflow[9];     /* conserved state beyond AW_BC_INFLOW faces (first V entries used) */
 } aw_config;
 
 typedef struct aw_stats {
@@ -120,10 +122,13 @@ typedef struct aw_solver aw_solver;
 
 /* Create a solver on the current CUDA device.  Allocates the dense per-level grids (Sec. 3.1:
  * level l has n*r^l cells per direction) and installs a uniform level-0 mesh of active cells
- * with zero averages.  Errors: AW_EINVAL (bad config), AW_ENOMEM, AW_ECUDA. */
+ * with zero averages.  All device work and device memory of the solver are ordered on `stream`
+ * (memory from the device's default pool, allocated and freed in stream order, so creating and
+ * destroying solvers does not synchronise the device); the stream must outlive the solver.
+ * Errors: AW_EINVAL (bad config), AW_ENOMEM, AW_ECUDA. */
 int aw_create(const aw_config* cfg, uintptr_t stream, aw_solver** out);
 
-/* Release every device buffer of the solver.  Safe on NULL. */
+/* Wait for the solver's stream, then release every buffer of the solver.  Safe on NULL. */
 void aw_destroy(aw_solver* s);
 
 /* Message of the last failing call on this thread (never NULL). */
@@ -150,6 +155,23 @@ int aw_step_dt(aw_solver* s, double dt0, aw_stats* stats);
 
 /* Level-0 steps (with regrids if auto_regrid) until t reaches t_end. */
 int aw_advance_to(aw_solver* s, double t_end, aw_stats* stats);
+
+/* Cross-request batching (no counterpart in the paper, which advances one mesh): advances the n
+ * independent solvers (1 <= n <= AW_BATCH_MAX) each to t_end, as aw_advance_to does, in lockstep
+ * level-0 steps whose hot kernels (WENO, predictor, face flux, update, projection of virtual
+ * children) of one level and sub-step run as ONE launch over the cells of all members.  Each
+ * member keeps its own mesh, state, CFL time step, regrids and errors, and computes exactly what
+ * aw_advance_to would.  The members must agree in dim, pde, M, flux and refine_factor (grid,
+ * domain, lmax, boundaries, physics and data may differ) and be distinct.  All device work of the
+ * call is ordered on `stream` (the members' own streams are synchronised first and restored on
+ * return).  stats and rc (arrays of n entries, either may be NULL) receive each member's
+ * statistics and status.  A member that fails (AW_ENONPHYSICAL, ...) stops; the others go on.
+ * Returns AW_OK when every member reached t_end, else the first member's failure, or a failure of
+ * the batch as a whole (AW_ECUDA).  Kernel timing (aw_set_profiling) does not cover batched
+ * launches; they are counted in aw_kernel_launches of the first live member. */
+#define AW_BATCH_MAX 8
+int aw_advance_batch(aw_solver* const* solvers, int32_t n, double t_end, uintptr_t stream, aw_stats* stats,
+                     int32_t* rc);
 
 /* Stable level-0 time step of the current state (CFL condition over all active cells). */
 int aw_compute_dt(aw_solver* s, double* dt0);
@@ -233,6 +255,13 @@ typedef struct aw_srv_summary {
 
 /* Start `max_concurrent` worker threads on the current device with a device-memory budget. */
 int aw_srv_create(int64_t hbm_budget_bytes, int32_t max_concurrent, aw_server** out);
+
+/* Cross-request batching in the loop: a worker that admits the oldest queued request also admits
+ * up to max_batch - 1 further queued requests (in arrival order) that agree with it in dim, pde,
+ * M, flux, refine_factor and end time and fit the remaining budget, and advances the group with
+ * aw_advance_batch.  1 (the default) turns batching off.  Applies to requests admitted after the
+ * call.  AW_EINVAL unless 1 <= max_batch <= AW_BATCH_MAX. */
+int aw_srv_set_batching(aw_server* srv, int32_t max_batch);
 /* Queue one solve (configuration copied; params copied).  AW_EINVAL if its footprint exceeds
  * the whole budget. */
 int aw_srv_submit(aw_server* s, const aw_config* cfg, int32_t ic_kind, const double* params, int32_t nparams,

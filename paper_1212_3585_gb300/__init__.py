@@ -10,7 +10,7 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (AwSrvInfo, AwSrvSummary, AW_BC_PERIODIC, AW_BC_REFLECTIVE, AW_BC_TRANSMISSIVE, AW_FLUX_OSHER, AW_FLUX_RUSANOV, AW_IC_CONST, AW_IC_EXPLOSION,  # noqa: F401
+from ._lib import (AwSrvInfo, AwSrvSummary, AW_BATCH_MAX, AW_BC_INFLOW, AW_BC_PERIODIC, AW_BC_REFLECTIVE, AW_BC_TRANSMISSIVE, AW_FLUX_OSHER, AW_FLUX_RUSANOV, AW_IC_CONST, AW_IC_EXPLOSION,  # noqa: F401
                    AW_IC_FOURIER, AW_IC_OT, AW_IC_RP4, AW_IC_VORTEX, AW_INTERNAL_CHI, AW_INTERNAL_FLUX,
                    AW_INTERNAL_PREDICTOR, AW_INTERNAL_WENO, AW_PDE_EULER, AW_PDE_LINADV, AW_PDE_MHD_GLM,
                    AwCell, AwConfig, AwError, AwStats)
@@ -18,7 +18,7 @@ from ._lib import (AwSrvInfo, AwSrvSummary, AW_BC_PERIODIC, AW_BC_REFLECTIVE, AW
 
 def make_config(dim=2, pde=AW_PDE_EULER, M=2, n=(16, 16, 1), gamma=1.4, c_h=2.0, lo=(0.0, 0.0, 0.0),
                 hi=(1.0, 1.0, 1.0), bc=AW_BC_PERIODIC, r=3, lmax=0, chi_ref=0.2, chi_rec=0.1, eps_ind=0.01,
-                cfl=0.9, picard=0, auto_regrid=1, adv=(1.0, 1.0, 1.0), flux=AW_FLUX_RUSANOV) -> AwConfig:
+                cfl=0.9, picard=0, auto_regrid=1, adv=(1.0, 1.0, 1.0), flux=AW_FLUX_RUSANOV, inflow=()) -> AwConfig:
     c = AwConfig()
     c.dim, c.pde, c.M = dim, pde, M
     c.nx, c.ny, c.nz = n[0], n[1], (n[2] if dim == 3 else 1)
@@ -31,6 +31,8 @@ def make_config(dim=2, pde=AW_PDE_EULER, M=2, n=(16, 16, 1), gamma=1.4, c_h=2.0,
     c.refine_factor, c.lmax = r, lmax
     c.chi_ref, c.chi_rec, c.eps_ind, c.cfl = chi_ref, chi_rec, eps_ind, cfl
     c.picard_iters, c.flux, c.auto_regrid = picard, flux, auto_regrid
+    for v, q in enumerate(inflow):
+        c.inflow[v] = q
     return c
 
 
@@ -158,17 +160,34 @@ class Solver:
         return self.L.aw_kernel_launches(self.h)
 
 
+def advance_batch(solvers, t_end, stream: int = 0):
+    """aw_advance_batch: advance independent solvers of one kernel configuration to t_end with
+    their hot kernels batched per level and sub-step.  Returns (stats, rc) per solver; raises
+    AwError with the first failure."""
+    n = len(solvers)
+    arr = (C.c_void_p * n)(*[s.h.value for s in solvers])
+    st = (AwStats * n)()
+    rc = (C.c_int32 * n)()
+    code = _lib.load().aw_advance_batch(arr, n, t_end, stream, st, rc)
+    out = list(st), list(rc)
+    _lib.check(code)
+    return out
+
+
 class Server:
     """Request loop of independent solves (aw_srv_*): continuous admission under a device-memory
-    budget, concurrent requests on their own streams."""
+    budget, concurrent requests on their own streams; with max_batch > 1, compatible queued
+    requests are advanced together with batched launches (aw_srv_set_batching)."""
 
-    def __init__(self, hbm_budget_bytes: int, max_concurrent: int = 4):
+    def __init__(self, hbm_budget_bytes: int, max_concurrent: int = 4, max_batch: int = 1):
         self.L = _lib.load()
         h = C.c_void_p()
         rc = self.L.aw_srv_create(int(hbm_budget_bytes), max_concurrent, C.byref(h))
         if rc:
             raise AwError(rc, self.L.aw_srv_last_error().decode())
         self.h = h
+        if max_batch != 1:
+            self._check(self.L.aw_srv_set_batching(self.h, max_batch))
 
     def _check(self, rc):
         if rc:

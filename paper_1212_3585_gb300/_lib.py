@@ -9,10 +9,11 @@ LIB_PATH = os.path.join(PKG, "lib", "libaderweno.so")
 
 AW_OK, AW_EINVAL, AW_ENOMEM, AW_ECUDA, AW_ENONPHYSICAL, AW_ETIMEOUT, AW_ESTATE = 0, -1, -2, -3, -4, -5, -6
 AW_PDE_EULER, AW_PDE_MHD_GLM, AW_PDE_LINADV = 0, 1, 2
-AW_BC_PERIODIC, AW_BC_TRANSMISSIVE, AW_BC_REFLECTIVE = 0, 1, 2
+AW_BC_PERIODIC, AW_BC_TRANSMISSIVE, AW_BC_REFLECTIVE, AW_BC_INFLOW = 0, 1, 2, 3
 AW_FLUX_RUSANOV, AW_FLUX_OSHER = 0, 1
 AW_IC_CONST, AW_IC_VORTEX, AW_IC_EXPLOSION, AW_IC_OT, AW_IC_RP4, AW_IC_FOURIER = 0, 1, 2, 3, 4, 5
 AW_INTERNAL_WENO, AW_INTERNAL_PREDICTOR, AW_INTERNAL_CHI, AW_INTERNAL_FLUX = 0, 1, 2, 3
+AW_BATCH_MAX = 8
 
 
 class AwConfig(C.Structure):
@@ -26,6 +27,7 @@ class AwConfig(C.Structure):
         ("chi_ref", C.c_double), ("chi_rec", C.c_double), ("eps_ind", C.c_double), ("cfl", C.c_double),
         ("picard_iters", C.c_int32), ("flux", C.c_int32), ("auto_regrid", C.c_int32), ("reserved", C.c_int32),
         ("adv", C.c_double * 3),
+        ("inflow", C.c_double * 9),
     ]
 
 
@@ -80,6 +82,7 @@ SIGNATURES = {
     "aw_set_profiling": (C.c_int, [_vp, C.c_int32]),
     "aw_kernel_times": (C.c_int, [_vp, _dp, _i64p]),
     "aw_srv_create": (C.c_int, [C.c_int64, C.c_int32, C.POINTER(_vp)]),
+    "aw_srv_set_batching": (C.c_int, [_vp, C.c_int32]),
     "aw_srv_submit": (C.c_int, [_vp, C.POINTER(AwConfig), C.c_int32, _dp, C.c_int32, C.c_double, _i64p]),
     "aw_srv_poll": (C.c_int, [_vp, C.c_int64, C.POINTER(C.c_int32)]),
     "aw_srv_wait_all": (C.c_int, [_vp]),
@@ -90,6 +93,8 @@ SIGNATURES = {
     "aw_selftest_reciprocal": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_size_t]),
     "aw_cfl_dt_noalloc": (C.c_int, [C.POINTER(AwConfig), C.c_void_p, C.c_int64, C.c_void_p, C.c_size_t]),
     "aw_kernel_launches": (C.c_int64, [_vp]),
+    "aw_advance_batch": (C.c_int, [C.POINTER(_vp), C.c_int32, C.c_double, C.c_size_t, C.POINTER(AwStats),
+                                   C.POINTER(C.c_int32)]),
 }
 
 _lib = None

@@ -13,7 +13,7 @@ constexpr int MAXV = 9;
 constexpr int8_t ST_NONE = -2;
 
 enum { PDE_EULER = 0, PDE_MHD = 1, PDE_LINADV = 2 };
-enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2 };
+enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2, BC_INFLOW = 3 };
 
 __host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
 __host__ __device__ constexpr int nvars(int D, int PDE) {
@@ -45,10 +45,12 @@ struct Tables {
 struct Phys {
   double gamma, c_h;
   double adv[3];
+  double inflow[9];   // conserved state of the ghost cells beyond inflow faces
 };
 
 struct Bc6 {
-  int v[6];  // boundary condition of faces x-, x+, y-, y+, z-, z+
+  int v[6];           // boundary condition of faces x-, x+, y-, y+, z-, z+
+  double inflow_rho;  // density of the inflow state (refinement indicator)
 };
 
 // One level of the mesh: dense status/average/active-id grids over the whole level box.
@@ -85,6 +87,11 @@ __device__ __forceinline__ bool bcmap(const int* L, const int* bc, int a, int c,
 
 __device__ __forceinline__ bool reflected(const int* L, const int* bc, int a, int c) {
   return (c < 0 || c >= L[a]) && bc[2 * a + (c < 0 ? 0 : 1)] == BC_REFLECTIVE;
+}
+
+// beyond an inflow face: the ghost cell holds the inflow state, whatever the other directions
+__device__ __forceinline__ bool beyond_inflow(const int* L, const int* bc, int a, int c) {
+  return (c < 0 || c >= L[a]) && bc[2 * a + (c < 0 ? 0 : 1)] == BC_INFLOW;
 }
 
 // Reciprocal by the Newton-Raphson iteration y <- y + y (1 - x y) (quadratic convergence),
@@ -382,6 +389,18 @@ struct HotArgs {
   double* memc;         // memory variables of the child level
   const double* dtl;    // device array: dt of each level
   int* err;             // device error word
+  const int32_t* vlist; // virtual children of this level (dense indices), projected from qhm
+  int nv;
+};
+
+// Several independent solves of the same kernel configuration in one launch: member m owns CTAs
+// start[m] .. start[m+1]-1 and runs them with its own arguments (passed as one grid-constant
+// kernel parameter, 20.8 KB for 8 members).
+constexpr int MAXB = 8;
+struct HotBatch {
+  int n;
+  int start[MAXB + 1];
+  HotArgs a[MAXB];
 };
 
 }  // namespace aw

@@ -104,7 +104,7 @@ struct WenoCfg {
 };
 
 template <int D, int M, int PDE, int TS>
-__global__ void __launch_bounds__(256) k_weno(HotArgs a) {
+__device__ __forceinline__ void weno_body(const HotArgs& a, const int bid) {
   using C = WenoCfg<D, M, PDE, TS>;
   constexpr int N = C::N, V = C::V, B = C::B, NB = C::NB, NSP = ipow(N, D);
   extern __shared__ double smem[];
@@ -119,21 +119,29 @@ __global__ void __launch_bounds__(256) k_weno(HotArgs a) {
   __shared__ uint8_t needxy[(C::NYC > 0) ? C::NYC : 1];
 
   const LevelView& L = a.lv;
-  const int tile = a.tiles[blockIdx.x];
+  const int tile = a.tiles[bid];
   int org[3] = {0, 0, 0};
   {
     int t = tile;
     for (int d = 0; d < D; d++) { org[d] = (t % a.tdim[d]) * TS; t /= a.tdim[d]; }
   }
-  // stage the box (reflective walls: mirror image with the normal momentum negated)
+  // stage the box (reflective walls: mirror image with the normal momentum negated; beyond an
+  // inflow face: the inflow state)
   for (int idx = threadIdx.x; idx < NB; idx += blockDim.x) {
     int t = idx, c[3] = {0, 0, 0};
     unsigned flip = 0;
+    bool inflow = false;
     for (int d = 0; d < D; d++) {
       int b = t % B;
       t /= B;
       if (reflected(L.L, a.bc, d, org[d] - M + b)) flip |= 1u << d;
+      inflow |= beyond_inflow(L.L, a.bc, d, org[d] - M + b);
       bcmap(L.L, a.bc, d, org[d] - M + b, &c[d]);
+    }
+    if (inflow) {
+#pragma unroll
+      for (int v = 0; v < V; v++) box[v * NB + idx] = a.P.inflow[v];
+      continue;
     }
     long long di = didx(L, c[0], c[1], c[2]);
 #pragma unroll
@@ -240,6 +248,11 @@ __global__ void __launch_bounds__(256) k_weno(HotArgs a) {
   }
 }
 
+template <int D, int M, int PDE, int TS>
+__global__ void __launch_bounds__(256) k_weno(const __grid_constant__ HotArgs a) {
+  weno_body<D, M, PDE, TS>(a, blockIdx.x);
+}
+
 // ------------------------------------------------------------------------------------------
 // Predictor kernel (Sec. 2.3, Eq. eqn.stdg.final).  One thread per (active cell, spatial node);
 // the thread holds the time column of q_h at its node for all variables.  With the nodal
@@ -260,13 +273,13 @@ struct PredCfg {
 };
 
 template <int D, int M, int PDE>
-__global__ void __launch_bounds__(PredCfg<D, M, PDE>::THREADS) k_predict(HotArgs a) {
+__device__ __forceinline__ void predict_body(const HotArgs& a, const int bid) {
   using C = PredCfg<D, M, PDE>;
   using Q = Pde<PDE, D>;
   constexpr int N = C::N, NSP = C::NSP, NST = C::NST, V = C::V;
   extern __shared__ double sh[];  // [CPB][D][V][NST]
   const int lc = threadIdx.x / NSP, node = threadIdx.x % NSP;
-  const int cell = blockIdx.x * C::CPB + lc;
+  const int cell = bid * C::CPB + lc;
   const bool ok = cell < a.na;
   int ix[D];
   {
@@ -360,6 +373,11 @@ __global__ void __launch_bounds__(PredCfg<D, M, PDE>::THREADS) k_predict(HotArgs
   }
 }
 
+template <int D, int M, int PDE>
+__global__ void __launch_bounds__(PredCfg<D, M, PDE>::THREADS) k_predict(const __grid_constant__ HotArgs a) {
+  predict_body<D, M, PDE>(a, blockIdx.x);
+}
+
 // Face flux configuration: IPB face items of N^d quadrature points per CTA.
 template <int D, int M, int PDE>
 struct FluxCfg {
@@ -420,7 +438,17 @@ __device__ __forceinline__ int flux_point(const HotArgs& a, bool ok, const int* 
       for (int k = 1; k < N; k++) t = fma(pa[k], qA[v * NST + nbase + k * dstr], t);
       qa[v] = t;
     }
-    if (kind == FK_BOUNDARY && a.bc[2 * d + side] == BC_REFLECTIVE) {
+    if (kind == FK_BOUNDARY && a.bc[2 * d + side] == BC_INFLOW) {
+      // inflow face: the outer state is the prescribed inflow state
+      const double* ql = side ? qa : a.P.inflow;
+      const double* qr = side ? a.P.inflow : qa;
+      if constexpr (PDE == PDE_EULER) {
+        if (a.flux == 1) osher_euler<D>(ql, qr, d, f, a.P);
+        else rusanov<PDE, D>(ql, qr, d, f, a.P);
+      } else {
+        rusanov<PDE, D>(ql, qr, d, f, a.P);
+      }
+    } else if (kind == FK_BOUNDARY && a.bc[2 * d + side] == BC_REFLECTIVE) {
       // reflecting wall: the outer state is the mirror image of the trace
       double qm[V];
 #pragma unroll
@@ -555,7 +583,7 @@ __device__ __forceinline__ void flux_finish(const HotArgs& a, const double* sh, 
 // normalised by dt * area of this level.
 // ------------------------------------------------------------------------------------------
 template <int D, int M, int PDE>
-__global__ void __launch_bounds__(FluxCfg<D, M, PDE>::THREADS) k_flux(HotArgs a) {
+__device__ __forceinline__ void flux_body(const HotArgs& a, const int bid) {
   using C = FluxCfg<D, M, PDE>;
   constexpr int N = M + 1, NPT = C::NPT, V = C::V;
   constexpr int NST = ipow(N, D + 1);
@@ -570,14 +598,14 @@ __global__ void __launch_bounds__(FluxCfg<D, M, PDE>::THREADS) k_flux(HotArgs a)
   const long long nlob = (long long)D * ((a.na + C::CPB - 1) / C::CPB);
   bool ok;
   int cell = 0, d = 0, side = 0;
-  if (blockIdx.x < nlob) {
-    const long long chunk = blockIdx.x / D;
-    d = (int)(blockIdx.x - chunk * D);
+  if (bid < nlob) {
+    const long long chunk = bid / D;
+    d = (int)(bid - chunk * D);
     const long long c = chunk * C::CPB + li;
     ok = c < a.na;
     cell = ok ? (int)c : 0;
   } else {
-    const long long h = (blockIdx.x - nlob) * C::CPB + li;
+    const long long h = (bid - nlob) * C::CPB + li;
     ok = h < a.nh;
     if (ok) {
       const long long e = a.hflist[h];
@@ -612,14 +640,19 @@ __global__ void __launch_bounds__(FluxCfg<D, M, PDE>::THREADS) k_flux(HotArgs a)
   flux_finish<D, M, PDE>(a, sh, sitem, skind, snb);
 }
 
+template <int D, int M, int PDE>
+__global__ void __launch_bounds__(FluxCfg<D, M, PDE>::THREADS) k_flux(const __grid_constant__ HotArgs a) {
+  flux_body<D, M, PDE>(a, blockIdx.x);
+}
+
 // ------------------------------------------------------------------------------------------
 // Update kernel, Eq. eq:finite_vol (source zero): one thread per active cell.  The high face of
 // axis d is the low face of the +d neighbour when that neighbour is active on this level.
 // ------------------------------------------------------------------------------------------
 template <int D, int M, int PDE>
-__global__ void k_update(HotArgs a) {
+__device__ __forceinline__ void update_body(const HotArgs& a, const int bid) {
   constexpr int V = nvars(D, PDE);
-  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
+  const int cell = bid * blockDim.x + threadIdx.x;
   if (cell >= a.na) return;
   const LevelView& L = a.lv;
   long long di = a.alist[cell];
@@ -645,16 +678,21 @@ __global__ void k_update(HotArgs a) {
   if (!Pde<PDE, D>::physical(u, a.P)) atomicOr(a.err, 1);
 }
 
+template <int D, int M, int PDE>
+__global__ void k_update(const __grid_constant__ HotArgs a) {
+  update_body<D, M, PDE>(a, blockIdx.x);
+}
+
 // ------------------------------------------------------------------------------------------
 // Projection of virtual children (Sec. 3.1.3): child-box average of the mother's space-time
 // polynomial at mother time tau = sub / r; one thread per (virtual cell, variable).
 // With spatial dofs only (predictor == false) the mother's WENO polynomial is projected.
 // ------------------------------------------------------------------------------------------
 template <int D, int M, int PDE>
-__global__ void k_project(HotArgs a, const int32_t* vlist, int nv, const double* src, int spacetime,
-                          double* out_u, int write_dense) {
+__device__ __forceinline__ void project_body(const HotArgs& a, const int32_t* vlist, int nv, const double* src,
+                                             int spacetime, double* out_u, int write_dense, const int bid) {
   constexpr int N = M + 1, V = nvars(D, PDE), NSP = ipow(N, D), NST = NSP * N;
-  const int it = blockIdx.x * blockDim.x + threadIdx.x;
+  const int it = bid * blockDim.x + threadIdx.x;
   if (it >= nv * V) return;
   const int k = it / V, v = it % V;
   const LevelView& L = a.lv;
@@ -687,6 +725,53 @@ __global__ void k_project(HotArgs a, const int32_t* vlist, int nv, const double*
   }
   if (write_dense) L.u[v * L.n + di] = acc;
   else out_u[(long long)k * V + v] = acc;
+}
+
+template <int D, int M, int PDE>
+__global__ void k_project(const __grid_constant__ HotArgs a, const int32_t* vlist, int nv, const double* src,
+                          int spacetime, double* out_u, int write_dense) {
+  project_body<D, M, PDE>(a, vlist, nv, src, spacetime, out_u, write_dense, blockIdx.x);
+}
+
+// ------------------------------------------------------------------------------------------
+// Batched launches: the same bodies over the CTAs of several solves (cross-request batching).
+// ------------------------------------------------------------------------------------------
+__device__ __forceinline__ int batch_member(const HotBatch& b, int blk) {
+  int m = 0;
+  while (m + 1 < b.n && blk >= b.start[m + 1]) m++;
+  return m;
+}
+
+template <int D, int M, int PDE, int TS>
+__global__ void __launch_bounds__(256) k_weno_batch(const __grid_constant__ HotBatch b) {
+  const int m = batch_member(b, blockIdx.x);
+  weno_body<D, M, PDE, TS>(b.a[m], blockIdx.x - b.start[m]);
+}
+
+template <int D, int M, int PDE>
+__global__ void __launch_bounds__(PredCfg<D, M, PDE>::THREADS) k_predict_batch(const __grid_constant__ HotBatch b) {
+  const int m = batch_member(b, blockIdx.x);
+  predict_body<D, M, PDE>(b.a[m], blockIdx.x - b.start[m]);
+}
+
+template <int D, int M, int PDE>
+__global__ void __launch_bounds__(FluxCfg<D, M, PDE>::THREADS) k_flux_batch(const __grid_constant__ HotBatch b) {
+  const int m = batch_member(b, blockIdx.x);
+  flux_body<D, M, PDE>(b.a[m], blockIdx.x - b.start[m]);
+}
+
+template <int D, int M, int PDE>
+__global__ void k_update_batch(const __grid_constant__ HotBatch b) {
+  const int m = batch_member(b, blockIdx.x);
+  update_body<D, M, PDE>(b.a[m], blockIdx.x - b.start[m]);
+}
+
+// virtual children of every member from their mothers' predictor at tau = sub / r
+template <int D, int M, int PDE>
+__global__ void k_project_batch(const __grid_constant__ HotBatch b) {
+  const int m = batch_member(b, blockIdx.x);
+  const HotArgs& a = b.a[m];
+  project_body<D, M, PDE>(a, a.vlist, a.nv, a.qhm, 1, nullptr, 1, blockIdx.x - b.start[m]);
 }
 
 template <int D, int M, int PDE>

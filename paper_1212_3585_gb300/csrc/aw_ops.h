@@ -5,6 +5,7 @@
 
 namespace aw {
 struct HotArgs;
+struct HotBatch;
 
 struct HotOps {
   int D, M, PDE, V, wenoTS;
@@ -17,6 +18,13 @@ struct HotOps {
   // else spatial WENO dofs), into the dense averages (dense != 0) or into out[k*V + v]
   int (*project)(const HotArgs&, const int32_t* vlist, int nv, const double* src, int spacetime,
                  double* out, int dense, cudaStream_t);
+  // the same kernels over all members of a batch (b.n and b.a[] set by the caller; the launcher
+  // fills b.start); the projection takes each member's vlist/nv and mother predictor qhm
+  int (*weno_b)(HotBatch&, cudaStream_t);
+  int (*predict_b)(HotBatch&, cudaStream_t);
+  int (*flux_b)(HotBatch&, cudaStream_t);
+  int (*update_b)(HotBatch&, cudaStream_t);
+  int (*project_b)(HotBatch&, cudaStream_t);
 };
 
 // returns false when the configuration is not compiled in

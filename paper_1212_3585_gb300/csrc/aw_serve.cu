@@ -7,6 +7,11 @@
 // averages are copied to host memory and its device memory is released at once, which admits
 // the next request.  Every request runs exactly the same kernels as a solve on its own, so its
 // result does not depend on what else is running.
+//
+// With batching on (aw_srv_set_batching), a worker that admits the oldest request also admits
+// queued requests of the same kernel configuration and end time (up to the batch size, in arrival
+// order, while the budget allows) and advances them together with aw_advance_batch: one launch
+// per hot kernel, level and sub-step for the whole group.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -48,6 +53,7 @@ struct aw_server {
   int device = 0;
   int64_t budget = 0, in_use = 0;
   int nworkers = 1;
+  int max_batch = 1;
   std::mutex mu;
   std::condition_variable cv_work, cv_done;
   std::deque<int64_t> queue;
@@ -107,6 +113,59 @@ static void run_request(aw_server* S, Request& R) {
   R.rc = rc;
 }
 
+// a batch of requests on one stream: each member created and initialised on its own, then all
+// advanced together
+static void run_batch(aw_server* S, std::vector<Request*>& G) {
+  cudaSetDevice(S->device);
+  const int n = (int)G.size();
+  cudaStream_t st = nullptr;
+  int rc0 = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess ? AW_OK : AW_ECUDA;
+  std::vector<aw_solver*> sol(n, nullptr);
+  std::vector<aw_solver*> run;
+  std::vector<int> idx;
+  for (int i = 0; i < n; i++) {
+    Request& R = *G[i];
+    int rc = rc0;
+    if (rc == AW_OK) rc = aw_create(&R.cfg, (uintptr_t)st, &sol[i]);
+    if (rc == AW_OK)
+      rc = aw_set_initial(sol[i], R.ic, R.params.empty() ? nullptr : R.params.data(), (int32_t)R.params.size(), -1);
+    R.rc = rc;
+    if (rc != AW_OK) R.err = rc0 == AW_OK ? aw_last_error() : "stream creation failed";
+    else { run.push_back(sol[i]); idx.push_back(i); }
+  }
+  if (!run.empty()) {
+    std::vector<aw_stats> stats(run.size());
+    std::vector<int32_t> rcs(run.size(), AW_OK);
+    int rc = aw_advance_batch(run.data(), (int32_t)run.size(), G[idx[0]]->t_end, (uintptr_t)st, stats.data(), rcs.data());
+    std::string msg = rc != AW_OK ? aw_last_error() : "";
+    for (size_t k = 0; k < run.size(); k++) {
+      Request& R = *G[idx[k]];
+      R.cell_updates = stats[k].cell_updates;
+      R.level0_steps = stats[k].level0_steps;
+      int r = rcs[k];
+      if (r == AW_OK) {
+        int64_t nc = 0;
+        aw_get_counts(run[k], &nc, nullptr, nullptr, nullptr);
+        R.meta.resize(nc);
+        R.u.resize((size_t)nc * aw::nvars(R.cfg.dim, R.cfg.pde));
+        r = aw_read_cells(run[k], R.meta.data(), R.u.data(), nc, &nc);
+        if (r != AW_OK) R.err = aw_last_error();
+      } else {
+        R.err = msg.empty() ? "failed in a batch" : "failed in a batch (first failure of the batch: " + msg + ")";
+      }
+      R.rc = r;
+    }
+  }
+  for (int i = 0; i < n; i++) aw_destroy(sol[i]);
+  if (st) cudaStreamDestroy(st);
+}
+
+// requests that can share batched launches with R
+static bool batchable(const Request& R, const Request& Q) {
+  return R.cfg.dim == Q.cfg.dim && R.cfg.pde == Q.cfg.pde && R.cfg.M == Q.cfg.M && R.cfg.flux == Q.cfg.flux &&
+         R.cfg.refine_factor == Q.cfg.refine_factor && R.t_end == Q.t_end;
+}
+
 static void worker_main(aw_server* S) {
   std::unique_lock<std::mutex> lk(S->mu);
   for (;;) {
@@ -123,18 +182,37 @@ static void worker_main(aw_server* S) {
     });
     if (S->stop) return;
     S->queue.pop_front();
-    Request& R = S->req[pick];
-    S->in_use += R.footprint;
-    S->running++;
-    R.state = AW_REQ_RUNNING;
-    R.t_start = clk::now();
+    std::vector<Request*> G{&S->req[pick]};
+    int64_t need = G[0]->footprint;
+    // batching: compatible queued requests, in arrival order, while the budget allows
+    for (auto it = S->queue.begin(); it != S->queue.end() && (int)G.size() < S->max_batch;) {
+      Request& Q = S->req[*it];
+      if (batchable(*G[0], Q) && S->in_use + need + Q.footprint <= S->budget) {
+        G.push_back(&Q);
+        need += Q.footprint;
+        it = S->queue.erase(it);
+      } else {
+        ++it;
+      }
+    }
+    S->in_use += need;
+    S->running += (int)G.size();
+    const clk::time_point t0 = clk::now();
+    for (Request* R : G) {
+      R->state = AW_REQ_RUNNING;
+      R->t_start = t0;
+    }
     lk.unlock();
-    run_request(S, R);
+    if (G.size() == 1) run_request(S, *G[0]);
+    else run_batch(S, G);
     lk.lock();
-    R.t_done = clk::now();
-    R.state = R.rc == AW_OK ? AW_REQ_DONE : AW_REQ_FAILED;
-    S->in_use -= R.footprint;
-    S->running--;
+    const clk::time_point t1 = clk::now();
+    for (Request* R : G) {
+      R->t_done = t1;
+      R->state = R->rc == AW_OK ? AW_REQ_DONE : AW_REQ_FAILED;
+    }
+    S->in_use -= need;
+    S->running -= (int)G.size();
     S->cv_done.notify_all();
     S->cv_work.notify_all();
   }
@@ -160,6 +238,13 @@ int aw_srv_create(int64_t hbm_budget_bytes, int32_t max_concurrent, aw_server** 
   S->nworkers = max_concurrent;
   for (int i = 0; i < max_concurrent; i++) S->workers.emplace_back(worker_main, S);
   *out = S;
+  return AW_OK;
+}
+
+int aw_srv_set_batching(aw_server* S, int32_t max_batch) {
+  if (!S || max_batch < 1 || max_batch > AW_BATCH_MAX) SRV_FAIL(AW_EINVAL, "max_batch must be 1..AW_BATCH_MAX");
+  std::lock_guard<std::mutex> lk(S->mu);
+  S->max_batch = max_batch;
   return AW_OK;
 }
 
@@ -274,6 +359,12 @@ void aw_srv_destroy(aw_server* S) {
   }
   S->cv_work.notify_all();
   for (auto& t : S->workers) t.join();
+  // give the memory the solves kept in the device's pool back
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, S->device) == cudaSuccess) {
+    cudaDeviceSynchronize();
+    cudaMemPoolTrimTo(pool, 0);
+  }
   delete S;
 }
 

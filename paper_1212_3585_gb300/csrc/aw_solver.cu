@@ -8,10 +8,17 @@
 // are rebuilt after every regrid by an order-preserving stream compaction, so every list is in
 // canonical order (k, j, i) and every result is deterministic.  The per-active FP64 arrays
 // (WENO dofs, predictor dofs, face fluxes, memory variables) are indexed by the active id.
+//
+// Device memory is stream-ordered (cudaMallocAsync / cudaFreeAsync on the solver's stream, from
+// the device's default pool, which keeps freed blocks for reuse): creating or destroying a solver
+// does not synchronise the device, so the solves of a request loop keep running while others
+// start and finish.  The two small pinned host buffers of a solver come from a process-wide free
+// list for the same reason.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -45,6 +52,46 @@ static thread_local std::string g_err = "";
   } while (0)
 
 static const int CHUNK = 4096;
+
+// stream-ordered device allocation on the solver's stream
+static cudaError_t dalloc(cudaStream_t st, void** p, size_t bytes) { return cudaMallocAsync(p, bytes ? bytes : 1, st); }
+static void dfree(cudaStream_t st, void* p) {
+  if (p) cudaFreeAsync(p, st);
+}
+
+// the default pool of a device keeps freed memory for reuse instead of returning it at every
+// synchronisation (set once per device)
+static std::mutex g_pool_mu;
+static bool g_pool_ready[64];
+static void keep_pool(int dev) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (dev < 0 || dev >= 64 || g_pool_ready[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  g_pool_ready[dev] = true;
+}
+
+// 256-byte pinned host blocks, allocated once per process and recycled
+static std::mutex g_pin_mu;
+static std::vector<void*> g_pin_free;
+static void* pinned_block() {
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  if (!g_pin_free.empty()) {
+    void* p = g_pin_free.back();
+    g_pin_free.pop_back();
+    return p;
+  }
+  void* p = nullptr;
+  return cudaMallocHost(&p, 256) == cudaSuccess ? p : nullptr;
+}
+static void pinned_release(void* p) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pin_mu);
+  g_pin_free.push_back(p);
+}
 
 struct Level {
   int L[3] = {1, 1, 1};
@@ -326,13 +373,16 @@ __global__ void k_average(LevelView L, LevelView Lc, const int32_t* mlist, int n
 
 // ---- refinement indicator (Eq. eqn.indicator), Phi = rho, undivided differences on the 3^d
 // same-level box; see the solver documentation for the discrete form ----
-__device__ __forceinline__ double phi(const LevelView& L, const int* bc, const int* ijk, int D, int a, int sa, int b,
+__device__ __forceinline__ double phi(const LevelView& L, const Bc6& bc6, const int* ijk, int D, int a, int sa, int b,
                                       int sb) {
   int c[3] = {ijk[0], ijk[1], ijk[2]};
   c[a] += sa;
   c[b] += sb;
   int m[3] = {0, 0, 0};
-  for (int e = 0; e < D; e++) bcmap(L.L, bc, e, c[e], &m[e]);
+  for (int e = 0; e < D; e++) {
+    if (beyond_inflow(L.L, bc6.v, e, c[e])) return bc6.inflow_rho;
+    bcmap(L.L, bc6.v, e, c[e], &m[e]);
+  }
   return L.u[didx(L, m[0], m[1], m[2])];
 }
 
@@ -343,19 +393,18 @@ __global__ void k_indicator(LevelView L, Bc6 bc6, int D, double eps, double* chi
   if (s != 0 && s != -1) { chi[c] = 0.0; return; }
   int ijk[3];
   cell_coords(L, c, ijk);
-  const int* bc = bc6.v;
   double P0 = L.u[c], num = 0.0, den = 0.0;
   for (int k = 0; k < D; k++)
     for (int l = 0; l < D; l++) {
       double d2, g, a;
       if (k == l) {
-        double Pp = phi(L, bc, ijk, D, k, 1, k, 0), Pm = phi(L, bc, ijk, D, k, -1, k, 0);
+        double Pp = phi(L, bc6, ijk, D, k, 1, k, 0), Pm = phi(L, bc6, ijk, D, k, -1, k, 0);
         d2 = Pp - 2.0 * P0 + Pm;
         g = fabs(Pp - P0) + fabs(P0 - Pm);
         a = fabs(Pp) + 2.0 * fabs(P0) + fabs(Pm);
       } else {
-        double Ppp = phi(L, bc, ijk, D, k, 1, l, 1), Ppm = phi(L, bc, ijk, D, k, 1, l, -1);
-        double Pmp = phi(L, bc, ijk, D, k, -1, l, 1), Pmm = phi(L, bc, ijk, D, k, -1, l, -1);
+        double Ppp = phi(L, bc6, ijk, D, k, 1, l, 1), Ppm = phi(L, bc6, ijk, D, k, 1, l, -1);
+        double Pmp = phi(L, bc6, ijk, D, k, -1, l, 1), Pmm = phi(L, bc6, ijk, D, k, -1, l, -1);
         d2 = (Ppp - Ppm - Pmp + Pmm) / 4.0;
         g = (fabs(Ppp - Pmp) + fabs(Ppm - Pmm)) / 4.0;
         a = (fabs(Ppp) + fabs(Ppm) + fabs(Pmp) + fabs(Pmm)) / 4.0;
@@ -702,6 +751,7 @@ static LevelView view(const aw_solver* s, int l) {
 static Bc6 bc6_of(const aw_solver* s) {
   Bc6 b;
   for (int i = 0; i < 6; i++) b.v[i] = s->cfg.bc[i];
+  b.inflow_rho = s->cfg.inflow[0];
   return b;
 }
 
@@ -716,10 +766,11 @@ static RtPhys rtphys(const aw_solver* s) {
 
 static int ensure_buf(aw_solver* s, long long ndouble) {
   if (ndouble <= s->buf_cap) return AW_OK;
-  if (s->d_buf) cudaFree(s->d_buf);
+  dfree(s->stream, s->d_buf);
   s->d_buf = nullptr;
   long long cap = std::max(ndouble, (long long)1024);
-  if (cudaMalloc(&s->d_buf, cap * sizeof(double)) != cudaSuccess) AW_FAIL(AW_ENOMEM, "staging buffer of %lld doubles", cap);
+  if (dalloc(s->stream, (void**)&s->d_buf, cap * sizeof(double)) != cudaSuccess)
+    AW_FAIL(AW_ENOMEM, "staging buffer of %lld doubles", cap);
   s->buf_cap = cap;
   return AW_OK;
 }
@@ -729,9 +780,9 @@ static int compact(aw_solver* s, const int8_t* a, long long n, int mode, int val
                    int slot) {
   long long nb = (n + CHUNK - 1) / CHUNK;
   if (nb > s->bcnt_cap) {
-    if (s->d_bcnt) cudaFree(s->d_bcnt);
+    dfree(s->stream, s->d_bcnt);
     s->d_bcnt = nullptr;
-    if (cudaMalloc(&s->d_bcnt, nb * sizeof(int)) != cudaSuccess) AW_FAIL(AW_ENOMEM, "scan scratch");
+    if (dalloc(s->stream, (void**)&s->d_bcnt, nb * sizeof(int)) != cudaSuccess) AW_FAIL(AW_ENOMEM, "scan scratch");
     s->bcnt_cap = nb;
   }
   k_ccount<<<(unsigned)nb, 256, 0, s->stream>>>(a, n, mode, val, s->d_bcnt);
@@ -746,24 +797,29 @@ static int ensure_active_cap(aw_solver* s, int l, long long need) {
   Level& L = s->lev[l];
   if (need <= L.cap) return AW_OK;
   long long cap = std::max(need + need / 2, (long long)64);
-  cudaFree(L.wh); cudaFree(L.qh); cudaFree(L.fl); cudaFree(L.mem); cudaFree(L.hflag); cudaFree(L.hflist);
+  for (void* p : {(void*)L.wh, (void*)L.qh, (void*)L.fl, (void*)L.mem, (void*)L.hflag, (void*)L.hflist})
+    dfree(s->stream, p);
   L.wh = L.qh = L.fl = L.mem = nullptr;
   L.hflag = nullptr;
   L.hflist = nullptr;
   L.cap = 0;
   size_t V = s->V;
-  if (cudaMalloc(&L.hflag, cap * s->D) != cudaSuccess || cudaMalloc(&L.hflist, cap * s->D * sizeof(int32_t)) != cudaSuccess ||
-      cudaMalloc(&L.wh, cap * V * s->NSP * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&L.qh, cap * V * s->NST * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&L.fl, cap * 2 * s->D * V * sizeof(double)) != cudaSuccess ||
-      cudaMalloc(&L.mem, cap * 2 * s->D * V * sizeof(double)) != cudaSuccess)
+  cudaStream_t st = s->stream;
+  if (dalloc(st, (void**)&L.hflag, cap * s->D) != cudaSuccess ||
+      dalloc(st, (void**)&L.hflist, cap * s->D * sizeof(int32_t)) != cudaSuccess ||
+      dalloc(st, (void**)&L.wh, cap * V * s->NSP * sizeof(double)) != cudaSuccess ||
+      dalloc(st, (void**)&L.qh, cap * V * s->NST * sizeof(double)) != cudaSuccess ||
+      dalloc(st, (void**)&L.fl, cap * 2 * s->D * V * sizeof(double)) != cudaSuccess ||
+      dalloc(st, (void**)&L.mem, cap * 2 * s->D * V * sizeof(double)) != cudaSuccess)
     AW_FAIL(AW_ENOMEM, "per-active arrays of level %d (%lld cells)", l, cap);
   L.cap = cap;
   return AW_OK;
 }
 
-// rebuild every per-level list and read the counts back
-static int rebuild_lists(aw_solver* s) {
+// Rebuild every per-level list and read the counts back, in three phases around two host
+// synchronisations (lists_issue; sync; lists_mid; sync; lists_finish), so that a batch of solvers
+// can share the synchronisations.
+static int lists_issue(aw_solver* s) {
   for (int l = 0; l <= s->lmax; l++) {
     Level& L = s->lev[l];
     TRY(compact(s, L.st, L.n, 0, 0, L.alist, L.aid, 6 * l + 0));
@@ -772,7 +828,10 @@ static int rebuild_lists(aw_solver* s) {
     TRY(compact(s, L.st, L.n, 1, 0, L.clist, nullptr, 6 * l + 3));
   }
   CK(cudaMemcpyAsync(s->h_cnt, s->d_cnt, sizeof(int) * 6 * MAXL, cudaMemcpyDeviceToHost, s->stream));
-  CK(cudaStreamSynchronize(s->stream));
+  return AW_OK;
+}
+
+static int lists_mid(aw_solver* s) {
   for (int l = 0; l <= s->lmax; l++) {
     Level& L = s->lev[l];
     L.na = s->h_cnt[6 * l + 0];
@@ -797,11 +856,22 @@ static int rebuild_lists(aw_solver* s) {
     CK(cudaMemsetAsync(L.mem, 0, (size_t)L.cap * 2 * s->D * s->V * sizeof(double), s->stream));
   }
   CK(cudaMemcpyAsync(s->h_cnt, s->d_cnt, sizeof(int) * 6 * MAXL, cudaMemcpyDeviceToHost, s->stream));
-  CK(cudaStreamSynchronize(s->stream));
+  return AW_OK;
+}
+
+static void lists_finish(aw_solver* s) {
   for (int l = 0; l <= s->lmax; l++) {
     s->lev[l].ntiles = s->h_cnt[6 * l + 4];
     s->lev[l].nh = s->h_cnt[6 * l + 5];
   }
+}
+
+static int rebuild_lists(aw_solver* s) {
+  TRY(lists_issue(s));
+  CK(cudaStreamSynchronize(s->stream));
+  TRY(lists_mid(s));
+  CK(cudaStreamSynchronize(s->stream));
+  lists_finish(s);
   return AW_OK;
 }
 
@@ -834,6 +904,8 @@ static HotArgs make_args(const aw_solver* s, int l, int sub) {
   if (l < s->lmax) a.memc = s->lev[l + 1].mem;
   a.dtl = s->d_dtl;
   a.err = s->d_err;
+  a.vlist = L.vlist;
+  a.nv = L.nv;
   return a;
 }
 
@@ -872,7 +944,8 @@ static int advance(aw_solver* s, int l, int sub) {
   return AW_OK;
 }
 
-static int compute_dt(aw_solver* s, double* dt) {
+// dt0 (reading R11): issue the reduction and the copy of its result to host slot h_dtl[MAXL]
+static int dt_issue(aw_solver* s) {
   double big = 1e300;
   CK(cudaMemcpyAsync(s->d_dtmin, &big, sizeof(double), cudaMemcpyHostToDevice, s->stream));
   double rl = 1.0;
@@ -885,15 +958,26 @@ static int compute_dt(aw_solver* s, double* dt) {
     rl *= s->r;
   }
   CK(cudaGetLastError());
-  double h;
-  CK(cudaMemcpyAsync(&h, s->d_dtmin, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-  CK(cudaStreamSynchronize(s->stream));
+  CK(cudaMemcpyAsync(s->h_dtl + MAXL, s->d_dtmin, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  return AW_OK;
+}
+
+// after the stream has reached the copy of dt_issue
+static int dt_finish(aw_solver* s, double* dt) {
+  double h = s->h_dtl[MAXL];
   if (!(h > 0.0) || h >= 1e300) AW_FAIL(AW_ENONPHYSICAL, "no positive stable time step (dt = %g)", h);
   *dt = h;
   return AW_OK;
 }
 
-static int step_dt(aw_solver* s, double dt0, aw_stats* st) {
+static int compute_dt(aw_solver* s, double* dt) {
+  TRY(dt_issue(s));
+  CK(cudaStreamSynchronize(s->stream));
+  return dt_finish(s, dt);
+}
+
+// level time steps dt0 / r^l to the device and a cleared error word
+static int step_begin(aw_solver* s, double dt0) {
   double dt = dt0;
   for (int l = 0; l < MAXL; l++) {
     s->h_dtl[l] = dt;
@@ -901,11 +985,12 @@ static int step_dt(aw_solver* s, double dt0, aw_stats* st) {
   }
   CK(cudaMemcpyAsync(s->d_dtl, s->h_dtl, sizeof(double) * MAXL, cudaMemcpyHostToDevice, s->stream));
   CK(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream));
-  TRY(advance(s, 0, 0));
-  int err = 0;
-  CK(cudaMemcpyAsync(s->h_cnt + 6 * MAXL, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
-  CK(cudaStreamSynchronize(s->stream));
-  err = s->h_cnt[6 * MAXL];
+  return AW_OK;
+}
+
+// after the stream has reached the copy of the error word to h_cnt[6 * MAXL]: statistics, errors
+static int step_finish(aw_solver* s, double dt0, aw_stats* st) {
+  const int err = s->h_cnt[6 * MAXL];
   int64_t rl = 1;
   for (int l = 0; l <= s->lmax; l++) {
     int64_t u = (int64_t)s->lev[l].na * rl;
@@ -916,6 +1001,14 @@ static int step_dt(aw_solver* s, double dt0, aw_stats* st) {
   if (err & 1) AW_FAIL(AW_ENONPHYSICAL, "non-physical state (rho <= 0, p <= 0 or NaN) after the update");
   if (err) AW_FAIL(AW_ESTATE, "inconsistent mesh detected on the device (error word %d)", err);
   return AW_OK;
+}
+
+static int step_dt(aw_solver* s, double dt0, aw_stats* st) {
+  TRY(step_begin(s, dt0));
+  TRY(advance(s, 0, 0));
+  CK(cudaMemcpyAsync(s->h_cnt + 6 * MAXL, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return step_finish(s, dt0, st);
 }
 
 // regrid pre-pass (at a synchronisation time): WENO polynomials of the active cells of levels
@@ -955,9 +1048,9 @@ static IcArgs ic_args(const aw_solver* s) {
 }
 
 // apply the dense flags of every level (L.flag) and rebuild the tree
-static int apply_flags(aw_solver* s, int init_mode) {
+// the tree edit of the flags on the device, up to (not including) the list rebuild
+static int apply_flags_issue(aw_solver* s, int init_mode) {
   const int lmax = s->lmax;
-  if (lmax == 0) return AW_OK;
   Bc6 bc = bc6_of(s);
   for (int l = 0; l <= lmax; l++) {
     Level& L = s->lev[l];
@@ -1003,6 +1096,12 @@ static int apply_flags(aw_solver* s, int init_mode) {
       s->launches++;
     }
   CK(cudaGetLastError());
+  return AW_OK;
+}
+
+static int apply_flags(aw_solver* s, int init_mode) {
+  if (s->lmax == 0) return AW_OK;
+  TRY(apply_flags_issue(s, init_mode));
   TRY(rebuild_lists(s));
   TRY(average_all(s));
   return AW_OK;
@@ -1036,16 +1135,22 @@ static void free_solver(aw_solver* s) {
   harvest_events(s);
   for (auto e : s->ev_free) cudaEventDestroy(e);
   s->ev_free.clear();
+  // stream-ordered: after the solver's last work on its stream
+  cudaStream_t st = s->stream;
   for (int l = 0; l < MAXL; l++) {
     Level& L = s->lev[l];
-    cudaFree(L.st); cudaFree(L.R); cudaFree(L.nst); cudaFree(L.flag); cudaFree(L.u); cudaFree(L.chi);
-    cudaFree(L.aid); cudaFree(L.alist); cudaFree(L.vlist); cudaFree(L.mlist); cudaFree(L.clist);
-    cudaFree(L.tflag); cudaFree(L.tiles); cudaFree(L.wh); cudaFree(L.qh); cudaFree(L.fl); cudaFree(L.mem);
-    cudaFree(L.hflag); cudaFree(L.hflist);
+    for (void* p : {(void*)L.st, (void*)L.R, (void*)L.nst, (void*)L.flag, (void*)L.u, (void*)L.chi, (void*)L.aid,
+                    (void*)L.alist, (void*)L.vlist, (void*)L.mlist, (void*)L.clist, (void*)L.tflag, (void*)L.tiles,
+                    (void*)L.wh, (void*)L.qh, (void*)L.fl, (void*)L.mem, (void*)L.hflag, (void*)L.hflist})
+      dfree(st, p);
   }
-  cudaFree(s->d_dtl); cudaFree(s->d_dtmin); cudaFree(s->d_err); cudaFree(s->d_cnt); cudaFree(s->d_bcnt);
-  cudaFree(s->d_buf);
-  cudaFreeHost(s->h_cnt); cudaFreeHost(s->h_dtl);
+  for (void* p : {(void*)s->d_dtl, (void*)s->d_dtmin, (void*)s->d_err, (void*)s->d_cnt, (void*)s->d_bcnt,
+                  (void*)s->d_buf})
+    dfree(st, p);
+  // the host blocks may still be the target of copies in flight
+  cudaStreamSynchronize(st);
+  pinned_release(s->h_cnt);
+  pinned_release(s->h_dtl);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1137,7 +1242,7 @@ int aw_create(const aw_config* cfg, uintptr_t stream, aw_solver** out) {
       AW_FAIL(AW_EINVAL, "periodic boundaries must pair up on axis %d", a);
     for (int sd = 0; sd < 2; sd++) {
       int b = c.bc[2 * a + sd];
-      if (b != AW_BC_PERIODIC && b != AW_BC_TRANSMISSIVE && b != AW_BC_REFLECTIVE)
+      if (b != AW_BC_PERIODIC && b != AW_BC_TRANSMISSIVE && b != AW_BC_REFLECTIVE && b != AW_BC_INFLOW)
         AW_FAIL(AW_EINVAL, "unknown boundary condition %d", b);
       if (b == AW_BC_REFLECTIVE && c.pde == AW_PDE_MHD_GLM)
         AW_FAIL(AW_EINVAL, "reflective walls are available for the Euler equations and linear advection");
@@ -1162,6 +1267,7 @@ int aw_create(const aw_config* cfg, uintptr_t stream, aw_solver** out) {
   s->phys.gamma = c.gamma;
   s->phys.c_h = c.c_h;
   for (int a = 0; a < 3; a++) s->phys.adv[a] = c.adv[a];
+  for (int v = 0; v < 9; v++) s->phys.inflow[v] = c.inflow[v];
   if (!get_ops(c.dim, c.M, c.pde, &s->ops)) {
     delete s;
     AW_FAIL(AW_EINVAL, "configuration dim=%d M=%d pde=%d is not compiled in", c.dim, c.M, c.pde);
@@ -1171,9 +1277,12 @@ int aw_create(const aw_config* cfg, uintptr_t stream, aw_solver** out) {
     AW_FAIL(AW_EINVAL, "table construction failed");
   }
   int rc = AW_OK;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  keep_pool(dev);
   auto alloc = [&](void** p, size_t bytes) {
     if (rc != AW_OK) return;
-    if (cudaMalloc(p, bytes ? bytes : 1) != cudaSuccess) {
+    if (dalloc(s->stream, p, bytes) != cudaSuccess) {
       rc = AW_ENOMEM;
       char b[200];
       snprintf(b, sizeof b, "device allocation of %zu bytes failed", bytes);
@@ -1214,10 +1323,14 @@ int aw_create(const aw_config* cfg, uintptr_t stream, aw_solver** out) {
   alloc((void**)&s->d_dtmin, sizeof(double));
   alloc((void**)&s->d_err, sizeof(int));
   alloc((void**)&s->d_cnt, sizeof(int) * (6 * MAXL + 8));
-  if (rc == AW_OK && (cudaMallocHost((void**)&s->h_cnt, sizeof(int) * (6 * MAXL + 8)) != cudaSuccess ||
-                      cudaMallocHost((void**)&s->h_dtl, sizeof(double) * MAXL) != cudaSuccess)) {
-    rc = AW_ENOMEM;
-    g_err = "pinned host allocation failed";
+  static_assert(sizeof(int) * (6 * MAXL + 8) <= 256 && sizeof(double) * (MAXL + 1) <= 256, "pinned blocks");
+  if (rc == AW_OK) {
+    s->h_cnt = (int*)pinned_block();
+    s->h_dtl = (double*)pinned_block();
+    if (!s->h_cnt || !s->h_dtl) {
+      rc = AW_ENOMEM;
+      g_err = "pinned host allocation failed";
+    }
   }
   if (rc != AW_OK) {
     free_solver(s);
@@ -1379,6 +1492,184 @@ int aw_advance_to(aw_solver* s, double t_end, aw_stats* st) {
   }
   if (st) st->t = s->t;
   return AW_OK;
+}
+
+// ------------------------------------------------------------------------------------------
+// Cross-request batching: independent solves of one kernel configuration advanced in lockstep
+// level-0 steps; every hot kernel of a (level, sub-step) runs once for all members.
+// ------------------------------------------------------------------------------------------
+}  // extern "C"
+
+static_assert(AW_BATCH_MAX <= MAXB, "a batch fits one kernel parameter block");
+
+// one step of level l (the recursion of advance()) for every live member whose finest level is
+// at least l; *launches counts the batched launches
+static int advance_batch(aw_solver* const* S, int n, const bool* live, int l, int sub, cudaStream_t st,
+                         int64_t* launches) {
+  HotBatch b;
+  b.n = 0;
+  int idx[MAXB];
+  bool deeper = false;
+  for (int m = 0; m < n; m++) {
+    if (!live[m] || S[m]->lmax < l) continue;
+    idx[b.n] = m;
+    b.a[b.n++] = make_args(S[m], l, sub);
+    if (S[m]->lmax > l) deeper = true;
+  }
+  if (b.n == 0) return AW_OK;
+  const HotOps& ops = S[idx[0]]->ops;
+  const int r = S[idx[0]]->r;
+  if (l >= 1) *launches += ops.project_b(b, st);
+  *launches += ops.weno_b(b, st);
+  *launches += ops.predict_b(b, st);
+  CK(cudaGetLastError());
+  if (deeper)
+    for (int k = 0; k < r; k++) TRY(advance_batch(S, n, live, l + 1, k, st, launches));
+  *launches += ops.flux_b(b, st);
+  *launches += ops.update_b(b, st);
+  CK(cudaGetLastError());
+  if (l >= 1 && sub == r - 1)
+    for (int k = 0; k < b.n; k++) TRY(average_into(S[idx[k]], l - 1));
+  return AW_OK;
+}
+
+// Returns a failure of the batch as a whole (CUDA errors); a member's own failure (non-physical
+// state, no stable time step) stops that member only and is reported through rcs[m], *first and
+// *first_err.
+static int batch_run(aw_solver* const* S, int n, double t_end, cudaStream_t st, aw_stats* stats, int32_t* rcs,
+                     int* first, std::string* first_err) {
+  bool live[MAXB];
+  auto fail = [&](int m, int rc) {
+    live[m] = false;
+    rcs[m] = rc;
+    if (*first == AW_OK) {
+      *first = rc;
+      *first_err = g_err;
+    }
+  };
+  for (int m = 0; m < n; m++) {
+    live[m] = S[m]->t < t_end;
+    rcs[m] = AW_OK;
+  }
+  double dt[MAXB];
+  bool clip[MAXB];
+  for (;;) {
+    int nlive = 0;
+    for (int m = 0; m < n; m++) nlive += live[m];
+    if (!nlive) break;
+    // the time step of every member, one synchronisation
+    for (int m = 0; m < n; m++) if (live[m]) TRY(dt_issue(S[m]));
+    CK(cudaStreamSynchronize(st));
+    for (int m = 0; m < n; m++) {
+      if (!live[m]) continue;
+      int rc = dt_finish(S[m], &dt[m]);
+      if (rc != AW_OK) { fail(m, rc); continue; }
+      clip[m] = S[m]->t + dt[m] >= t_end;
+      if (clip[m]) dt[m] = t_end - S[m]->t;
+      TRY(step_begin(S[m], dt[m]));
+    }
+    // the step of every member, the hot kernels batched
+    int64_t nl = 0;
+    int rc = advance_batch(S, n, live, 0, 0, st, &nl);
+    for (int m = 0; m < n; m++)
+      if (live[m]) { S[m]->launches += nl; break; }
+    TRY(rc);
+    for (int m = 0; m < n; m++)
+      if (live[m]) CK(cudaMemcpyAsync(S[m]->h_cnt + 6 * MAXL, S[m]->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int m = 0; m < n; m++) {
+      if (!live[m]) continue;
+      aw_stats one;
+      memset(&one, 0, sizeof one);
+      rc = step_finish(S[m], dt[m], &one);
+      S[m]->t = clip[m] ? t_end : S[m]->t + dt[m];
+      if (stats) {
+        stats[m].level0_steps += one.level0_steps;
+        stats[m].cell_updates += one.cell_updates;
+        for (int l = 0; l < 8; l++) stats[m].updates_per_level[l] += one.updates_per_level[l];
+        stats[m].last_dt0 = one.last_dt0;
+        stats[m].t = S[m]->t;
+      }
+      if (rc != AW_OK) { fail(m, rc); continue; }
+    }
+    // regrids of the live members (the same device work as regrid(), the two host
+    // synchronisations of the list rebuild shared by all members)
+    bool rg[MAXB];
+    int nrg = 0;
+    for (int m = 0; m < n; m++) {
+      rg[m] = live[m] && S[m]->cfg.auto_regrid && S[m]->lmax > 0;
+      if (!rg[m]) continue;
+      nrg++;
+      TRY(regrid_prepass(S[m], 0));
+      TRY(flags_from_chi(S[m]));
+      TRY(apply_flags_issue(S[m], 0));
+      TRY(lists_issue(S[m]));
+    }
+    if (nrg) {
+      CK(cudaStreamSynchronize(st));
+      for (int m = 0; m < n; m++) {
+        if (!rg[m]) continue;
+        rc = lists_mid(S[m]);
+        if (rc != AW_OK) { fail(m, rc); rg[m] = false; }
+      }
+      CK(cudaStreamSynchronize(st));
+      for (int m = 0; m < n; m++) {
+        if (!rg[m]) continue;
+        lists_finish(S[m]);
+        TRY(average_all(S[m]));
+      }
+    }
+    for (int m = 0; m < n; m++)
+      if (live[m] && !(S[m]->t < t_end)) live[m] = false;
+  }
+  return AW_OK;
+}
+
+extern "C" {
+
+int aw_advance_batch(aw_solver* const* solvers, int32_t n, double t_end, uintptr_t stream, aw_stats* stats,
+                     int32_t* rc_out) {
+  if (!solvers || n < 1 || n > AW_BATCH_MAX) AW_FAIL(AW_EINVAL, "need 1 <= n <= %d solvers", AW_BATCH_MAX);
+  for (int m = 0; m < n; m++) {
+    const aw_solver* a = solvers[m];
+    if (!a) AW_FAIL(AW_EINVAL, "null solver %d", m);
+    const aw_solver* z = solvers[0];
+    if (a->D != z->D || a->cfg.pde != z->cfg.pde || a->M != z->M || a->cfg.flux != z->cfg.flux || a->r != z->r)
+      AW_FAIL(AW_EINVAL, "solver %d differs from solver 0 in dim, pde, M, flux or refine_factor", m);
+    for (int k = 0; k < m; k++)
+      if (solvers[k] == a) AW_FAIL(AW_EINVAL, "solver %d appears twice", m);
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaStream_t own[MAXB];
+  for (int m = 0; m < n; m++) {
+    CK(cudaStreamSynchronize(solvers[m]->stream));
+    own[m] = solvers[m]->stream;
+    solvers[m]->stream = st;
+  }
+  if (stats) memset(stats, 0, sizeof(aw_stats) * n);
+  int32_t rcs[MAXB];
+  for (int m = 0; m < n; m++) rcs[m] = AW_OK;
+  int first = AW_OK;
+  std::string first_err;
+  int fatal = batch_run(solvers, n, t_end, st, stats, rcs, &first, &first_err);
+  std::string fatal_err = g_err;
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (fatal == AW_OK && e != cudaSuccess) {
+    fatal = AW_ECUDA;
+    fatal_err = std::string("batched advance: ") + cudaGetErrorString(e);
+  }
+  for (int m = 0; m < n; m++) {
+    solvers[m]->stream = own[m];
+    if (stats) stats[m].t = solvers[m]->t;
+    if (fatal != AW_OK && rcs[m] == AW_OK && solvers[m]->t < t_end) rcs[m] = fatal;
+    if (rc_out) rc_out[m] = rcs[m];
+  }
+  if (fatal != AW_OK) {
+    g_err = fatal_err;
+    return fatal;
+  }
+  if (first != AW_OK) g_err = first_err;
+  return first;
 }
 
 int aw_regrid(aw_solver* s, int32_t init_mode) {

@@ -33,7 +33,7 @@ def rel_err(a, b):
 class Pair:
     def __init__(self, dim=2, pde="euler", M=2, n=(16, 16, 1), lo=(0, 0, 0), hi=(1, 1, 1), bc="periodic",
                  r=3, lmax=0, gamma=1.4, c_h=2.0, chi_ref=0.2, chi_rec=0.1, cfl=0.9, adv=(1.0, 0.5, 0.25),
-                 threads=8, flux=0):
+                 threads=8, flux=0, inflow=()):
         op, gp = PDE_MAP[pde]
         if isinstance(bc, (list, tuple)):
             obc = gbc = list(bc)   # per-face codes, identical numbering on both sides
@@ -41,7 +41,7 @@ class Pair:
             obc = oracle.BC_PERIODIC if bc == "periodic" else oracle.BC_TRANSMISSIVE
             gbc = pg.AW_BC_PERIODIC if bc == "periodic" else pg.AW_BC_TRANSMISSIVE
         kw = dict(dim=dim, M=M, n=n, lo=lo, hi=hi, r=r, lmax=lmax, gamma=gamma, c_h=c_h, chi_ref=chi_ref,
-                  chi_rec=chi_rec, cfl=cfl, auto_regrid=0, adv=adv)
+                  chi_rec=chi_rec, cfl=cfl, auto_regrid=0, adv=adv, inflow=inflow)
         self.o = oracle.Oracle(oracle.make_cfg(pde=op, bc=obc, flux=flux, **kw), threads=threads)
         self.g = pg.Solver(pg.make_config(pde=gp, bc=gbc, flux=flux, **kw))
         self.lmax = lmax

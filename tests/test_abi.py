@@ -44,8 +44,25 @@ def test_binding_loads_and_rejects_bad_config_without_gpu():
     assert rc == _lib.AW_EINVAL and b"dim" in L.aw_last_error()
 
 
-def test_struct_layouts_match_header():
-    # sizes implied by the header's field list (natural alignment)
-    assert ctypes.sizeof(pg.AwConfig) == 4 * 6 + 8 * 2 + 8 * 6 + 4 * 6 + 4 * 2 + 8 * 4 + 4 * 4 + 8 * 3
-    assert ctypes.sizeof(pg.AwCell) == 20
-    assert ctypes.sizeof(pg.AwStats) == 8 * 10 + 8 * 2
+def test_struct_layouts_match_header(tmp_path):
+    """sizes and field offsets of the ctypes structures equal those the C compiler gives the
+    header's structures"""
+    structs = {"aw_config": pg.AwConfig, "aw_stats": pg.AwStats, "aw_cell": pg.AwCell,
+               "aw_srv_info": pg.AwSrvInfo, "aw_srv_summary": pg.AwSrvSummary}
+    lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "aderweno.h"', "int main(void) {"]
+    for cname, py in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for fname, _ in py._fields_:
+            lines.append(f'printf("{cname} {fname} %zu\\n", offsetof({cname}, {fname}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    c_layout = {tuple(l.split()[:2]): int(l.split()[2]) for l in got if l}
+    for cname, py in structs.items():
+        assert c_layout[(cname, "size")] == ctypes.sizeof(py), cname
+        for fname, _ in py._fields_:
+            assert c_layout[(cname, fname)] == getattr(py, fname).offset, (cname, fname)

@@ -2,7 +2,8 @@
 
 Tolerance: 1e-10 relative per step for cell averages and kernel outputs (normalised by the
 largest magnitude of each variable); the mesh (levels, statuses, indices) must be identical
-given identical refinement flags.  Sizes span several 4^d WENO tiles and a ragged tail.
+given identical refinement flags.  Sizes span several WENO tiles (8x8 in 2D, 4x4x4 in 3D) and
+a ragged tail.
 """
 import numpy as np
 import pytest
@@ -170,3 +171,26 @@ def test_reflective_walls(dim, M, lmax, flux):
     p.init("explosion", EXPL)
     for _ in range(2):
         p.step()
+
+
+@pytest.mark.parametrize("dim,M,lmax,flux", [(2, 3, 2, 0), (2, 2, 1, 1), (3, 2, 1, 0)])
+def test_inflow_boundary(dim, M, lmax, flux):
+    """a Mach-3 shock entering through an inflow face into gas at rest (the post-shock state is the
+    inflow state), transmissive elsewhere, with AMR and local time stepping"""
+    g = 1.4
+    # Rankine-Hugoniot post-shock state of a Mach-3 shock running into rho = 1.4, p = 1, u = 0
+    rho1, p1, ms = 1.4, 1.0, 3.0
+    rho2 = rho1 * (g + 1) * ms ** 2 / ((g - 1) * ms ** 2 + 2)
+    p2 = p1 * (2 * g * ms ** 2 - (g - 1)) / (g + 1)
+    u2 = ms * (1 - rho1 / rho2)                      # sound speed 1 ahead of the shock
+    E2 = p2 / (g - 1) + 0.5 * rho2 * u2 ** 2
+    qin = [rho2, rho2 * u2] + [0.0] * (dim - 1) + [E2]
+    I, T = pg.AW_BC_INFLOW, pg.AW_BC_TRANSMISSIVE
+    n = (16, 12, 1) if dim == 2 else (8, 6, 6)
+    p = Pair(dim=dim, M=M, n=n, lo=(0, 0, 0), hi=(1, 0.75, 0.75), bc=[I, T, T, T, T, T], r=3, lmax=lmax,
+             cfl=0.5, flux=flux, inflow=qin)
+    p.init("const", [rho1, 0.0] + [0.0] * (dim - 1) + [p1])
+    for _ in range(3):
+        p.step()
+    m, u = p.g.cells()
+    assert np.max(u[:, 0]) > 1.5 * rho1          # the shock has entered

@@ -1,6 +1,7 @@
 """Request loop: independent AMR solves of different sizes, orders and depths admitted under a
-device-memory budget and run concurrently; each result is bitwise identical to the same solve
-run alone, and the loop reports p50/p99 time to solution."""
+device-memory budget and run concurrently (and, with batching on, advanced together with batched
+launches); each result is bitwise identical to the same solve run alone, and the loop reports
+p50/p99 time to solution."""
 import numpy as np
 import pytest
 
@@ -39,6 +40,40 @@ def test_results_identical_alone_and_in_the_mix():
         assert np.array_equal(u, u2)
         assert info.cell_updates > 0
     srv.close()
+
+
+def test_batched_loop_results_identical_to_solo():
+    """with batching on, compatible requests share launches; every result still equals its solo
+    solve bit for bit"""
+    rng = np.random.default_rng(77)
+    reqs = []
+    for k in range(9):
+        base = int(rng.integers(12, 33))
+        M = int(rng.choice([2, 3]))
+        lmax = int(rng.integers(0, 3))
+        reqs.append((rp_config(base, M, lmax), aw_inputs.rp4_params(2000 + k)))
+    srv = pg.Server(hbm_budget_bytes=8 << 30, max_concurrent=2, max_batch=4)
+    ids = [srv.submit(cfg, pg.AW_IC_RP4, p, 0.02) for cfg, p in reqs]
+    srv.wait_all()
+    st = srv.stats()
+    assert st.done + st.failed == len(reqs)
+    for rid, (cfg, p) in zip(ids, reqs):
+        s = pg.Solver(cfg)
+        s.set_initial(pg.AW_IC_RP4, p, -1)
+        try:
+            s.advance_to(0.02)
+        except pg.AwError:
+            with pytest.raises(pg.AwError):
+                srv.result(rid, 4)
+            continue
+        m2, u2 = s.cells()
+        m, u, info = srv.result(rid, 4)
+        assert np.array_equal(m, m2)
+        assert np.array_equal(u, u2)
+        s.close()
+    srv.close()
+    with pytest.raises(pg.AwError):
+        pg.Server(hbm_budget_bytes=1 << 30, max_concurrent=1, max_batch=pg.AW_BATCH_MAX + 1)
 
 
 def test_budget_rejects_oversized_request():
