@@ -296,6 +296,78 @@ def run_efficiency(args):
     return 0
 
 
+def run_configs(args):
+    """Throughput of the other configurations (one JSON line each, device time with CUDA events on
+    the solver's stream, after a warm-up solve): the vortex at 32^2 (20 steps) and its labelled
+    scaled variants at 1024^2 and 2048^2, the 3D explosion (64^3 base, l_max = 2) on a time-boxed
+    sample of level-0 steps after the initial refinement, and the MHD Orszag-Tang run to t = 0.5."""
+    import numpy as np
+    import torch
+    import aw_inputs
+    import paper_1212_3585_gb300 as pg
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    names = ["weno", "predictor", "face_flux", "update", "projection"]
+
+    def measure(name, cfg, ic, params, steps=None, t_end=None, flops=None):
+        s = pg.Solver(cfg, stream.cuda_stream)
+        s.set_initial(ic, params, -1)      # warm-up: module loading, first launches
+        s.step(1e300)
+        s.reset()
+        s.set_initial(ic, params, -1)
+        torch.cuda.synchronize()
+        s.set_profiling(True)
+        s.kernel_times()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        upd, l0 = 0, 0
+        with ClockSampler(0) as clk:
+            e0.record(stream)
+            if steps is not None:
+                for _ in range(steps):
+                    st = s.step(1e300)
+                    upd += st.cell_updates
+                    l0 += st.level0_steps
+            else:
+                st = s.advance_to(t_end)
+                upd, l0 = st.cell_updates, st.level0_steps
+            e1.record(stream)
+            torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        kms, kn = s.kernel_times()
+        n, na, cpl, apl = s.counts()
+        s.close()
+        line = {"config": name, "metric": "cell-updates/s", "value": upd / (ms * 1e-3), "cell_updates": int(upd),
+                "level0_steps": int(l0), "ms": ms, "active_cells_per_level": [int(a) for a in apl],
+                "kernel_share": {k: float(kms[i] / max(kms.sum(), 1e-9)) for i, k in enumerate(names)},
+                "clocks": clk.summary()}
+        if flops is not None and kn[1] > 0:
+            ach = flops * upd / (kms[1] * 1e-3) / 1e12
+            line["predictor"] = {"fp64_tflops": ach, "frac": ach / FP64_PEAK_TFLOPS,
+                                 "flops_per_cell_update": flops}
+        print(json.dumps(line), flush=True)
+
+    T, P = pg.AW_BC_TRANSMISSIVE, pg.AW_BC_PERIODIC
+    vortex = [5.0, 5.0, 5.0, 1.0, 1.0, 1.0, 1.0]
+    f2 = predictor_flops_per_cell(2, 2, 4, 3, EULER_FLUX_FLOPS[2])
+    for n, label in ((32, "vortex 32^2 (configuration)"), (1024, "vortex 1024^2 (scaled variant)"),
+                     (2048, "vortex 2048^2 (scaled variant)")):
+        cfg = pg.make_config(dim=2, M=2, n=(n, n, 1), lo=(0, 0, 0), hi=(10, 10, 1), bc=P, cfl=0.9)
+        measure(f"{label}: 2D Euler M=2 periodic [0,10]^2, CFL 0.9, 20 steps", cfg, pg.AW_IC_VORTEX, vortex,
+                steps=20, flops=f2)
+    cfg = pg.make_config(dim=2, pde=pg.AW_PDE_MHD_GLM, M=3, n=(128, 128, 1), lo=(0, 0, 0),
+                         hi=(2 * np.pi, 2 * np.pi, 1), bc=P, r=3, lmax=1, gamma=5.0 / 3.0, c_h=2.0, cfl=0.6,
+                         auto_regrid=1)
+    measure("MHD-GLM Orszag-Tang type: M=3, base 128^2 on [0,2pi]^2, r=3, l_max=1, CFL 0.6, t_end=0.5", cfg,
+            pg.AW_IC_OT, [], t_end=0.5)
+    cfg = pg.make_config(dim=3, M=2, n=(64, 64, 64), lo=(-1, -1, -1), hi=(1, 1, 1), bc=T, r=3, lmax=2, cfl=0.6,
+                         auto_regrid=1)
+    f3 = predictor_flops_per_cell(3, 2, 5, 3, EULER_FLUX_FLOPS[3])
+    measure(f"3D explosion: Euler M=2, base 64^3 on [-1,1]^3, r=3, l_max=2, CFL 0.6; sample: the first "
+            f"{args.cfg3_steps} level-0 steps after the initial refinement", cfg, pg.AW_IC_EXPLOSION,
+            aw_inputs.EXPLOSION, steps=args.cfg3_steps, flops=f3)
+    return 0
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -335,7 +407,9 @@ def run_reference(args):
     }
 
 
-def cpu_baseline_sample():
+def cpu_baseline_sample(level0_steps=4):
+    """The oracle as it stands on all host cores (OpenMP over cells), timed on the first
+    level-0 steps of the workload (about 10 s of CPU work); setup untimed."""
     import oracle
     import aw_inputs
     threads = os.cpu_count() or 1
@@ -345,11 +419,12 @@ def cpu_baseline_sample():
     o.set_initial(oracle.IC_EXPLOSION, aw_inputs.EXPLOSION)
     u0 = o.updates()[0]
     t0 = time.perf_counter()
-    o.step(T_END)
+    for _ in range(level0_steps):
+        o.step(T_END)
     el = time.perf_counter() - t0
     n = o.updates()[0] - u0
     return {"value": n / el, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"first level-0 step of the workload ({n} cell updates, {el:.1f} s)"}
+            "sample": f"first {level0_steps} level-0 steps of the workload ({n} cell updates, {el:.1f} s)"}
 
 
 def main():
@@ -374,6 +449,8 @@ def main():
     ap.add_argument("--efficiency", action="store_true",
                     help="cost per cell update of orders 2-4, uniform vs AMR (r=4, l_max=2)")
     ap.add_argument("--eff-base", type=int, default=25)
+    ap.add_argument("--configs", action="store_true", help="throughput of the other configurations")
+    ap.add_argument("--cfg3-steps", type=int, default=2)
     ap.add_argument("--eff-t-end", type=float, default=0.1)
     args = ap.parse_args()
     if args.base != 100 or args.t_end != T_END:
@@ -386,6 +463,8 @@ def main():
         return run_serve(args) if rank == 0 else 0
     if args.efficiency:
         return run_efficiency(args) if rank == 0 else 0
+    if args.configs:
+        return run_configs(args) if rank == 0 else 0
     if args.impl == "reference":
         if rank != 0:
             return 0
@@ -489,13 +568,20 @@ def main():
                       "hbm_frac": bpc[n] * upd / t / 1e9 / hbm,
                       "flops_per_cell_update": flops[n], "bytes_per_cell_update": bpc[n]}
 
+    # the whole step: algorithmic FP64 work of WENO, predictor and face flux per cell update over
+    # the timed device time of the solve (bookkeeping, projection and host gaps included)
+    step_flops = sum(flops.values()) * upd / args.steps
+    step_tf = step_flops / (ms / args.steps * 1e-3) / 1e12
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD, "cell_updates_per_solve": upd_per_step, "level0_steps_per_solve": l0 / args.steps,
                    "l2": "flushed between timed solves (256 MB write)", "parallelism": f"replicas x{ws}"},
-        "roofline": roofline, "kernel_time_share": kernel_share, "kernels": kernels, "gpu_launches": int(launches),
+        "roofline": roofline,
+        "step_fp64": {"achieved": step_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": step_tf / FP64_PEAK_TFLOPS,
+                      "flops_per_cell_update": sum(flops.values())},
+        "kernel_time_share": kernel_share, "kernels": kernels, "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
 
