@@ -354,6 +354,33 @@ def run_configs(args):
         cfg = pg.make_config(dim=2, M=2, n=(n, n, 1), lo=(0, 0, 0), hi=(10, 10, 1), bc=P, cfl=0.9)
         measure(f"{label}: 2D Euler M=2 periodic [0,10]^2, CFL 0.9, 20 steps", cfg, pg.AW_IC_VORTEX, vortex,
                 steps=20, flops=f2)
+    # configuration 1 again through the latency path (device-side dt, CUDA graph of 20 steps):
+    # the end time is the host path's time after 20 steps, so exactly the same 20 steps are taken
+    cfg = pg.make_config(dim=2, M=2, n=(32, 32, 1), lo=(0, 0, 0), hi=(10, 10, 1), bc=P, cfl=0.9)
+    s = pg.Solver(cfg, stream.cuda_stream)
+    s.set_initial(pg.AW_IC_VORTEX, vortex, -1)
+    for _ in range(20):
+        s.step(1e300)
+    t20 = s.t
+    s.set_initial(pg.AW_IC_VORTEX, vortex, -1)
+    s.advance_graph(t20, 20)                     # warm-up (capture, module loading)
+    times = []
+    for _ in range(5):
+        s.set_initial(pg.AW_IC_VORTEX, vortex, -1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        st = s.advance_graph(t20, 20)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+        assert st.level0_steps == 20
+    ms = statistics.median(times)
+    print(json.dumps({"config": "vortex 32^2 (configuration), latency path: aw_advance_graph, device-side dt, "
+                                "one CUDA graph of 20 steps", "metric": "cell-updates/s",
+                      "value": st.cell_updates / (ms * 1e-3), "cell_updates": int(st.cell_updates),
+                      "level0_steps": int(st.level0_steps), "ms": ms, "ms_runs": times}), flush=True)
+    s.close()
     cfg = pg.make_config(dim=2, pde=pg.AW_PDE_MHD_GLM, M=3, n=(128, 128, 1), lo=(0, 0, 0),
                          hi=(2 * np.pi, 2 * np.pi, 1), bc=P, r=3, lmax=1, gamma=5.0 / 3.0, c_h=2.0, cfl=0.6,
                          auto_regrid=1)

@@ -173,6 +173,16 @@ int aw_advance_to(aw_solver* s, double t_end, aw_stats* stats);
 int aw_advance_batch(aw_solver* const* solvers, int32_t n, double t_end, uintptr_t stream, aw_stats* stats,
                      int32_t* rc);
 
+/* Latency path for a uniform mesh (lmax = 0; no counterpart in the paper): advances to t_end as
+ * aw_advance_to does, with the CFL time step reduced, clipped at t_end and turned into the level
+ * time steps on the device, so that `chunk` (1..256) level-0 steps run between two host
+ * synchronisations; the steps are captured into a CUDA graph (on a stream of the solver's own,
+ * ordered after `stream`), kept by the solver while its launch arguments stay the same, and
+ * replayed.  Steps past t_end within the last chunk have
+ * dt = 0 and change nothing.  Computes exactly what aw_advance_to computes (same kernels, same
+ * time steps).  AW_EINVAL if lmax > 0 or chunk is out of range; AW_ENONPHYSICAL as aw_step. */
+int aw_advance_graph(aw_solver* s, double t_end, int32_t chunk, aw_stats* stats);
+
 /* Stable level-0 time step of the current state (CFL condition over all active cells). */
 int aw_compute_dt(aw_solver* s, double* dt0);
 

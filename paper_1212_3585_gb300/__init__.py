@@ -84,6 +84,12 @@ class Solver:
         _lib.check(self.L.aw_advance_to(self.h, t_end, C.byref(st)))
         return st
 
+    def advance_graph(self, t_end, chunk=16):
+        """aw_advance_graph: uniform meshes, device-side time step, graph replay."""
+        st = AwStats()
+        _lib.check(self.L.aw_advance_graph(self.h, t_end, chunk, C.byref(st)))
+        return st
+
     def compute_dt(self):
         d = C.c_double()
         _lib.check(self.L.aw_compute_dt(self.h, C.byref(d)))

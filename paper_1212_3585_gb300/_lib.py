@@ -67,6 +67,7 @@ SIGNATURES = {
     "aw_step": (C.c_int, [_vp, C.c_double, C.POINTER(AwStats)]),
     "aw_step_dt": (C.c_int, [_vp, C.c_double, C.POINTER(AwStats)]),
     "aw_advance_to": (C.c_int, [_vp, C.c_double, C.POINTER(AwStats)]),
+    "aw_advance_graph": (C.c_int, [_vp, C.c_double, C.c_int32, C.POINTER(AwStats)]),
     "aw_compute_dt": (C.c_int, [_vp, _dp]),
     "aw_regrid": (C.c_int, [_vp, C.c_int32]),
     "aw_regrid_with_flags": (C.c_int, [_vp, _i8p, C.c_int64, C.c_int32]),

@@ -658,6 +658,7 @@ __device__ __forceinline__ void update_body(const HotArgs& a, const int bid) {
   long long di = a.alist[cell];
   int ijk[3] = {(int)(di % L.L[0]), (int)((di / L.L[0]) % L.L[1]), (int)(di / ((long long)L.L[0] * L.L[1]))};
   const double dt = a.dtl[a.level];
+  if (dt == 0.0) return;   // a step of length zero leaves the averages as they are
   double u[V];
 #pragma unroll
   for (int v = 0; v < V; v++) u[v] = L.u[v * L.n + di];

@@ -1,5 +1,7 @@
 // aw_inst.cuh -- launchers of the hot kernels for one configuration; included by aw_inst_*.cu.
 #pragma once
+#include <mutex>
+
 #include "aw_hot.cuh"
 
 namespace aw {
@@ -25,19 +27,16 @@ struct Launch {
   static int update_ctas(const HotArgs& a) { return a.na > 0 ? (a.na + 127) / 128 : 0; }
   static int project_ctas(int nv) { return nv > 0 ? (int)(((long long)nv * V + 127) / 128) : 0; }
 
-  // the dynamic shared memory attribute, once per kernel
+  // the dynamic shared memory attribute, once per kernel (request-loop workers launch concurrently)
   template <class K>
-  static void smem_attr(K kernel, int bytes, bool& done) {
-    if (!done) {
-      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-      done = true;
-    }
+  static void smem_attr(K kernel, int bytes, std::once_flag& once) {
+    std::call_once(once, [&] { cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); });
   }
 
   static int weno(const HotArgs& a, cudaStream_t st) {
     const int blocks = weno_ctas(a);
     if (!blocks) return 0;
-    static bool init = false;
+    static std::once_flag init;
     smem_attr(k_weno<D, M, PDE, TS>, CW::SMEM, init);
     k_weno<D, M, PDE, TS><<<blocks, 256, CW::SMEM, st>>>(a);
     return 1;
@@ -45,7 +44,7 @@ struct Launch {
   static int predict(const HotArgs& a, cudaStream_t st) {
     const int blocks = predict_ctas(a);
     if (!blocks) return 0;
-    static bool init = false;
+    static std::once_flag init;
     smem_attr(k_predict<D, M, PDE>, CP::SMEM, init);
     k_predict<D, M, PDE><<<blocks, CP::THREADS, CP::SMEM, st>>>(a);
     return 1;
@@ -53,7 +52,7 @@ struct Launch {
   static int flux(const HotArgs& a, cudaStream_t st) {
     const int blocks = flux_ctas(a);
     if (!blocks) return 0;
-    static bool init = false;
+    static std::once_flag init;
     smem_attr(k_flux<D, M, PDE>, CF::SMEM, init);
     k_flux<D, M, PDE><<<blocks, CF::THREADS, CF::SMEM, st>>>(a);
     return 1;
@@ -86,7 +85,7 @@ struct Launch {
   static int weno_b(HotBatch& b, cudaStream_t st) {
     const int blocks = fill_starts(b, weno_ctas);
     if (!blocks) return 0;
-    static bool init = false;
+    static std::once_flag init;
     smem_attr(k_weno_batch<D, M, PDE, TS>, CW::SMEM, init);
     k_weno_batch<D, M, PDE, TS><<<blocks, 256, CW::SMEM, st>>>(b);
     return 1;
@@ -94,7 +93,7 @@ struct Launch {
   static int predict_b(HotBatch& b, cudaStream_t st) {
     const int blocks = fill_starts(b, predict_ctas);
     if (!blocks) return 0;
-    static bool init = false;
+    static std::once_flag init;
     smem_attr(k_predict_batch<D, M, PDE>, CP::SMEM, init);
     k_predict_batch<D, M, PDE><<<blocks, CP::THREADS, CP::SMEM, st>>>(b);
     return 1;
@@ -102,7 +101,7 @@ struct Launch {
   static int flux_b(HotBatch& b, cudaStream_t st) {
     const int blocks = fill_starts(b, flux_ctas);
     if (!blocks) return 0;
-    static bool init = false;
+    static std::once_flag init;
     smem_attr(k_flux_batch<D, M, PDE>, CF::SMEM, init);
     k_flux_batch<D, M, PDE><<<blocks, CF::THREADS, CF::SMEM, st>>>(b);
     return 1;

@@ -113,6 +113,13 @@ struct Level {
   long long cap = 0;
 };
 
+// device-side time stepping state of aw_advance_graph (see k_dt_commit)
+struct GState {
+  double t, t_end, last_dt0;
+  long long nsteps;
+  int stop;
+};
+
 struct aw_solver {
   aw_config cfg;
   int D, V, N, M, r, lmax, NSP, NST, P;
@@ -126,6 +133,12 @@ struct aw_solver {
   std::vector<double> icp;
   double* d_dtl = nullptr;
   unsigned long long* d_dtmin = nullptr;
+  GState* d_gs = nullptr;           // device-side time stepping of aw_advance_graph
+  GState* h_gs = nullptr;
+  cudaStream_t gstream = nullptr;   // capture and replay stream of aw_advance_graph
+  cudaGraphExec_t gexec = nullptr;  // its instantiated graph, reused while the arguments match
+  HotArgs gargs;
+  int gchunk = 0;
   int* d_err = nullptr;
   int* d_cnt = nullptr;
   int* h_cnt = nullptr;
@@ -349,6 +362,35 @@ __global__ void k_dt(LevelView L, const int32_t* alist, int na, RtPhys R, double
   }
   for (int o = 16; o > 0; o >>= 1) dt = fmin(dt, __shfl_xor_sync(0xffffffffu, dt, o));
   if ((threadIdx.x & 31) == 0 && dt < 1e300) atomicMin(out, (unsigned long long)__double_as_longlong(dt));
+}
+
+// ---- device-side time step of a uniform mesh (aw_advance_graph): the host logic of step_cfl on
+// one thread -- dt0 from the CFL reduction, clipped at t_end, the time advanced, the level time
+// steps dt0 / r^l written -- so that level-0 steps need no host synchronisation.  A step after
+// t_end, after a non-physical update or without a stable time step gets dt = 0 (k_update leaves
+// the averages unchanged) ----
+__global__ void k_dt_commit(unsigned long long* dtmin, GState* g, double* dtl, int r, int* err) {
+  const double h = __longlong_as_double((long long)*dtmin);
+  *dtmin = (unsigned long long)__double_as_longlong(1e300);
+  double dt = 0.0;
+  if (!g->stop && (*err & 1)) g->stop = 1;
+  if (!g->stop && g->t < g->t_end) {
+    if (!(h > 0.0) || h >= 1e300) {
+      atomicOr(err, 8);
+      g->stop = 1;
+    } else {
+      const double t = g->t;
+      const bool clip = t + h >= g->t_end;
+      dt = clip ? g->t_end - t : h;
+      g->t = clip ? g->t_end : t + dt;
+      g->nsteps++;
+      g->last_dt0 = dt;
+    }
+  }
+  for (int l = 0; l < MAXL; l++) {
+    dtl[l] = dt;
+    dt /= r;
+  }
 }
 
 // ---- averaging (Eq. eqn.average): virtual mothers of level l from level l+1, children summed in
@@ -1145,12 +1187,18 @@ static void free_solver(aw_solver* s) {
       dfree(st, p);
   }
   for (void* p : {(void*)s->d_dtl, (void*)s->d_dtmin, (void*)s->d_err, (void*)s->d_cnt, (void*)s->d_bcnt,
-                  (void*)s->d_buf})
+                  (void*)s->d_buf, (void*)s->d_gs})
     dfree(st, p);
   // the host blocks may still be the target of copies in flight
   cudaStreamSynchronize(st);
+  if (s->gstream) {
+    cudaStreamSynchronize(s->gstream);
+    cudaStreamDestroy(s->gstream);
+  }
+  if (s->gexec) cudaGraphExecDestroy(s->gexec);
   pinned_release(s->h_cnt);
   pinned_release(s->h_dtl);
+  pinned_release(s->h_gs);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1167,6 +1215,7 @@ static void free_solver(aw_solver* s) {
 static __device__ __align__(256) double g_noalloc_dt_scratch[AW_NOALLOC_SLOTS];
 static double* g_noalloc_ptr[64];  // device address of the array, per device, from set-up
 static bool g_noalloc_ready[64];
+static std::mutex g_noalloc_mu;
 
 __global__ void k_dt_blockmin(const double* u, long long n, RtPhys R, double dx0, double dx1, double dx2, double cfl,
                               double* partial) {
@@ -1672,6 +1721,104 @@ int aw_advance_batch(aw_solver* const* solvers, int32_t n, double t_end, uintptr
   return first;
 }
 
+int aw_advance_graph(aw_solver* s, double t_end, int32_t chunk, aw_stats* st) {
+  if (!s) AW_FAIL(AW_EINVAL, "null solver");
+  if (st) memset(st, 0, sizeof *st);
+  if (s->lmax != 0) AW_FAIL(AW_EINVAL, "the graph path needs a uniform mesh (lmax = 0)");
+  if (chunk < 1 || chunk > 256) AW_FAIL(AW_EINVAL, "chunk must be 1..256 level-0 steps");
+  if (!(t_end > s->t)) {
+    if (st) st->t = s->t;
+    return AW_OK;
+  }
+  if (!s->d_gs) {
+    if (dalloc(s->stream, (void**)&s->d_gs, sizeof(GState)) != cudaSuccess) AW_FAIL(AW_ENOMEM, "graph state");
+    s->h_gs = (GState*)pinned_block();
+    if (!s->h_gs) AW_FAIL(AW_ENOMEM, "pinned host allocation failed");
+    static_assert(sizeof(GState) <= 256, "pinned block");
+  }
+  if (!s->gstream) CK(cudaStreamCreateWithFlags(&s->gstream, cudaStreamNonBlocking));
+  cudaStream_t gs = s->gstream;
+  // the state on the device, after everything already ordered on the solver's stream
+  memset(s->h_gs, 0, sizeof(GState));
+  s->h_gs->t = s->t;
+  s->h_gs->t_end = t_end;
+  s->h_dtl[MAXL] = 1e300;
+  CK(cudaMemcpyAsync(s->d_gs, s->h_gs, sizeof(GState), cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemcpyAsync(s->d_dtmin, s->h_dtl + MAXL, sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream));
+  cudaEvent_t ev;
+  CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  CK(cudaEventRecord(ev, s->stream));
+  CK(cudaStreamWaitEvent(gs, ev, 0));
+  // `chunk` level-0 steps: CFL reduction, device-side dt, the four hot kernels; captured once and
+  // kept while the launch arguments (every pointer and size of the level) stay the same
+  const Level& L = s->lev[0];
+  HotArgs a = make_args(s, 0, 0);
+  const int per_step = 2 + (L.ntiles > 0) + 3;
+  cudaError_t ce = cudaSuccess;
+  if (!s->gexec || s->gchunk != chunk || memcmp(&s->gargs, &a, sizeof a) != 0) {
+    if (s->gexec) cudaGraphExecDestroy(s->gexec);
+    s->gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+    ce = cudaStreamBeginCapture(gs, cudaStreamCaptureModeRelaxed);
+    if (ce == cudaSuccess) {
+      for (int k = 0; k < chunk; k++) {
+        k_dt<<<nblk(L.na, 256), 256, 0, gs>>>(view(s, 0), L.alist, L.na, rtphys(s), s->cfg.cfl, 1.0, s->d_dtmin);
+        k_dt_commit<<<1, 1, 0, gs>>>(s->d_dtmin, s->d_gs, s->d_dtl, s->r, s->d_err);
+        s->ops.weno(a, gs);
+        s->ops.predict(a, gs);
+        s->ops.flux(a, gs);
+        s->ops.update(a, gs);
+      }
+      ce = cudaStreamEndCapture(gs, &graph);
+    }
+    if (ce == cudaSuccess) ce = cudaGetLastError();
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&s->gexec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+      s->gexec = nullptr;
+      cudaEventDestroy(ev);
+      AW_FAIL(AW_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
+    }
+    memcpy(&s->gargs, &a, sizeof a);   // every byte, padding included, for the memcmp above
+    s->gchunk = chunk;
+  }
+  cudaGraphExec_t exec = s->gexec;
+  // replay until the device time reaches t_end, one host synchronisation per chunk
+  int rc = AW_OK, err = 0;
+  for (;;) {
+    ce = cudaGraphLaunch(exec, gs);
+    if (ce == cudaSuccess) ce = cudaMemcpyAsync(s->h_gs, s->d_gs, sizeof(GState), cudaMemcpyDeviceToHost, gs);
+    if (ce == cudaSuccess)
+      ce = cudaMemcpyAsync(s->h_cnt + 6 * MAXL, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, gs);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(gs);
+    if (ce != cudaSuccess) {
+      rc = AW_ECUDA;
+      g_err = std::string("graph replay: ") + cudaGetErrorString(ce);
+      break;
+    }
+    s->launches += (int64_t)per_step * chunk;
+    err = s->h_cnt[6 * MAXL];
+    if (s->h_gs->stop || !(s->h_gs->t < t_end)) break;
+  }
+  cudaEventRecord(ev, gs);
+  cudaStreamWaitEvent(s->stream, ev, 0);
+  cudaEventDestroy(ev);
+  if (rc != AW_OK) return rc;
+  s->t = s->h_gs->t;
+  if (st) {
+    st->level0_steps = s->h_gs->nsteps;
+    st->cell_updates = s->h_gs->nsteps * (int64_t)L.na;
+    st->updates_per_level[0] = st->cell_updates;
+    st->last_dt0 = s->h_gs->last_dt0;
+    st->t = s->t;
+  }
+  if (err & 1) AW_FAIL(AW_ENONPHYSICAL, "non-physical state (rho <= 0, p <= 0 or NaN) after the update");
+  if (err & 8) AW_FAIL(AW_ENONPHYSICAL, "no positive stable time step");
+  if (err) AW_FAIL(AW_ESTATE, "inconsistent mesh detected on the device (error word %d)", err);
+  return AW_OK;
+}
+
 int aw_regrid(aw_solver* s, int32_t init_mode) {
   if (!s) AW_FAIL(AW_EINVAL, "null solver");
   if (init_mode && s->ic < 0) AW_FAIL(AW_ESTATE, "initial-condition regrid before aw_set_initial");
@@ -1845,13 +1992,18 @@ int aw_cfl_dt_noalloc(const aw_config* cfg, const double* u_dev, int64_t n_cells
   int dev = 0;
   CK(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) AW_FAIL(AW_EINVAL, "device ordinal %d out of range", dev);
-  if (!g_noalloc_ready[dev]) {
-    // once per device, with that device current: the host-side name of the array is not a
-    // device address, so take the address from the runtime
-    double* p = nullptr;
-    CK(cudaGetSymbolAddress((void**)&p, g_noalloc_dt_scratch));
-    g_noalloc_ptr[dev] = p;
-    g_noalloc_ready[dev] = true;
+  double* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ready[dev]) {
+      // once per device, with that device current: the host-side name of the array is not a
+      // device address, so take the address from the runtime
+      double* p = nullptr;
+      CK(cudaGetSymbolAddress((void**)&p, g_noalloc_dt_scratch));
+      g_noalloc_ptr[dev] = p;
+      g_noalloc_ready[dev] = true;
+    }
+    scratch = g_noalloc_ptr[dev];
   }
   RtPhys R;
   R.pde = c.pde;
@@ -1863,8 +2015,8 @@ int aw_cfl_dt_noalloc(const aw_config* cfg, const double* u_dev, int64_t n_cells
   double dx0 = (c.hi[0] - c.lo[0]) / c.nx, dx1 = (c.hi[1] - c.lo[1]) / c.ny;
   double dx2 = c.dim == 3 ? (c.hi[2] - c.lo[2]) / c.nz : 1.0;
   cudaStream_t st = (cudaStream_t)stream;
-  k_dt_blockmin<<<(unsigned)nb, AW_NOALLOC_BLOCK, 0, st>>>(u_dev, n, R, dx0, dx1, dx2, c.cfl, g_noalloc_ptr[dev]);
-  k_dt_final<<<1, 1024, 0, st>>>(g_noalloc_ptr[dev], (int)nb, dt_dev);
+  k_dt_blockmin<<<(unsigned)nb, AW_NOALLOC_BLOCK, 0, st>>>(u_dev, n, R, dx0, dx1, dx2, c.cfl, scratch);
+  k_dt_final<<<1, 1024, 0, st>>>(scratch, (int)nb, dt_dev);
   CK(cudaGetLastError());
   return AW_OK;
 }
