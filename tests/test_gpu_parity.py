@@ -77,6 +77,18 @@ def test_amr_explosion_lts(M, lmax):
         p.step()
 
 
+def test_vortex_amr_lts():
+    """the smooth vortex with one level of refinement around its core (chi_ref = 0.02) and local
+    time stepping: the case of the oracle's AMR convergence pin"""
+    p = Pair(dim=2, M=3, n=(16, 16, 1), lo=(0, 0, 0), hi=(10, 10, 1), bc="periodic", r=3, lmax=1, chi_ref=0.02,
+             chi_rec=0.01)
+    p.init("vortex", VORTEX)
+    n, na, cpl, apl = p.g.counts()
+    assert apl[1] > 0
+    for _ in range(4):
+        p.step()
+
+
 def test_amr_periodic_conservation_gpu():
     p = Pair(dim=2, M=3, n=(12, 12, 1), lo=(0, 0, 0), hi=(10, 10, 1), bc="periodic", r=3, lmax=2, chi_ref=0.1,
              chi_rec=0.01)
