@@ -95,13 +95,19 @@ __device__ __forceinline__ bool beyond_inflow(const int* L, const int* bc, int a
 }
 
 // Reciprocal by the Newton-Raphson iteration y <- y + y (1 - x y) (quadratic convergence),
-// seeded with the single-precision reciprocal of x (about 24 correct bits); two steps reach
-// double precision (error a few ulp, tested against IEEE division).  Valid for |x| inside the
-// single-precision normal range, which covers densities and the WENO sigma + eps >= 1e-14.
+// seeded with the hardware's approximate double-precision reciprocal (PTX rcp.approx.ftz.f64,
+// no conversions to and from single precision); two steps reach double precision (error a few
+// ulp, tested against IEEE division).  Valid for normal |x| (subnormal inputs are flushed).
 // On sm_103a the FP64 pipe is the bottleneck and this costs 4 FP64 FMAs instead of the ~10
 // FP64 operations of an IEEE double division.
+__device__ __forceinline__ double rcp_approx(double x) {
+  double y;
+  asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+  return y;
+}
+
 __device__ __forceinline__ double rcp_nr(double x) {
-  double y = (double)__frcp_rn((float)x);
+  double y = rcp_approx(x);
   double e = fma(-x, y, 1.0);
   y = fma(y, e, y);
   e = fma(-x, y, 1.0);

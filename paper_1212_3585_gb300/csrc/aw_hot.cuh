@@ -65,7 +65,9 @@ __device__ __forceinline__ void weno1d(const Tables& T, const double* v, int str
 #pragma unroll
     for (int p = 0; p < N; p++) acc[p] = fma(om, ws[p], acc[p]);
   }
-  double is = 1.0 / sum;
+  // sum >= lambda_s / (sigma_s + eps)^8 of the smoothest stencil: a normal double unless every
+  // sigma exceeds ~1e38 (IEEE division there)
+  double is = sum >= 1e-300 ? rcp_nr(sum) : 1.0 / sum;
 #pragma unroll
   for (int p = 0; p < N; p++) out[p] = fma(acc[p], is, c);
 }
