@@ -42,10 +42,10 @@ FP64_FMA_PER_CLK_PER_SM = 2      # sm_103a: measured 0.598 T DFMA/s at ~1.97 GHz
 SM_MAX_MHZ = 2070.0
 HBM_GBS = 6792.1                 # measured copy bandwidth of this GB300 pool
 # DRAM bytes per cell of k_predict<2,3,Euler> from one ncu capture of a full-size level-2 launch
-# of this workload (6264 CTAs x 16 cells: dram__bytes_read.sum 51.42 MB + dram__bytes_write.sum
-# 140.44 MB); scaled by the cells of an average launch.  Must be re-captured whenever k_predict
+# of this workload (6264 CTAs x 16 cells: dram__bytes_read.sum 51.36 MB + dram__bytes_write.sum
+# 141.52 MB); scaled by the cells of an average launch.  Must be re-captured whenever k_predict
 # changes.
-PREDICTOR_DRAM_BYTES_PER_CELL = (51423232 + 140440576) / (6264 * 16)
+PREDICTOR_DRAM_BYTES_PER_CELL = (51356416 + 141521408) / (6264 * 16)
 
 
 def _measured_hbm():
