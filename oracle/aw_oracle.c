@@ -3,10 +3,10 @@
  *
  * Plain, slow, FP64 reference implementation ("oracle") of the one-step ADER-WENO finite
  * volume scheme on space-time adaptive Cartesian meshes of Dumbser, Zanotti, Hidalgo and
- * Balsara (arXiv:1212.3585).  Only tests/, __graft_entry__.smoke() and the cpu_baseline
- * leg of bench.py may load it.  It shares no code, header, table or helper with the CUDA
- * path; it computes its own Gauss-Legendre nodes, Lagrange basis, stencil inverses,
- * oscillation matrix and space-time matrices from their definitions.
+ * Balsara (arXiv:1212.3585).  Only tests/, __graft_entry__.smoke() and bench.py (its
+ * cpu_baseline leg and its --impl reference arm) may load it.  It shares no code, header,
+ * table or helper with the CUDA path; it computes its own Gauss-Legendre nodes, Lagrange
+ * basis, stencil inverses, oscillation matrix and space-time matrices from their definitions.
  *
  * It is written for checking by eye against the paper, not for speed:
  *   - WENO: every cell reconstructs its own (2M+1)^d box, one 1D reconstruction at a time
