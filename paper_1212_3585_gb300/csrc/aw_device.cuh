@@ -397,6 +397,7 @@ struct HotArgs {
   int* err;             // device error word
   const int32_t* vlist; // virtual children of this level (dense indices), projected from qhm
   int nv;
+  int ts;               // WENO tile edge of this level
 };
 
 // Several independent solves of the same kernel configuration in one launch: member m owns CTAs

@@ -266,17 +266,19 @@ __global__ void __launch_bounds__(256) k_weno(const __grid_constant__ HotArgs a)
 // The first iteration starts from q = w, constant in time, so it needs one flux evaluation per
 // node and R is constant in time.
 // ------------------------------------------------------------------------------------------
-template <int D, int M, int PDE>
+// DIV > 1: a CTA of CPB / DIV cells, for levels too small to give every SM work otherwise
+template <int D, int M, int PDE, int DIV = 1>
 struct PredCfg {
   static constexpr int N = M + 1, NSP = ipow(N, D), NST = NSP * N, V = nvars(D, PDE);
-  static constexpr int CPB = (NSP == 4) ? 64 : (NSP == 9) ? 32 : (NSP == 16 ? 16 : (NSP == 27 ? 16 : 4));
+  static constexpr int CPB0 = (NSP == 4) ? 64 : (NSP == 9) ? 32 : (NSP == 16 ? 16 : (NSP == 27 ? 16 : 4));
+  static constexpr int CPB = CPB0 / DIV > 0 ? CPB0 / DIV : 1;
   static constexpr int THREADS = CPB * NSP;
   static constexpr int SMEM = CPB * D * V * NST * 8;   // fluxes at every space-time node
 };
 
-template <int D, int M, int PDE>
+template <int D, int M, int PDE, int DIV = 1>
 __device__ __forceinline__ void predict_body(const HotArgs& a, const int bid) {
-  using C = PredCfg<D, M, PDE>;
+  using C = PredCfg<D, M, PDE, DIV>;
   using Q = Pde<PDE, D>;
   constexpr int N = C::N, NSP = C::NSP, NST = C::NST, V = C::V;
   extern __shared__ double sh[];  // [CPB][D][V][NST]
@@ -375,16 +377,16 @@ __device__ __forceinline__ void predict_body(const HotArgs& a, const int bid) {
   }
 }
 
-template <int D, int M, int PDE>
-__global__ void __launch_bounds__(PredCfg<D, M, PDE>::THREADS) k_predict(const __grid_constant__ HotArgs a) {
-  predict_body<D, M, PDE>(a, blockIdx.x);
+template <int D, int M, int PDE, int DIV>
+__global__ void __launch_bounds__(PredCfg<D, M, PDE, DIV>::THREADS) k_predict(const __grid_constant__ HotArgs a) {
+  predict_body<D, M, PDE, DIV>(a, blockIdx.x);
 }
 
 // Face flux configuration: IPB face items of N^d quadrature points per CTA.
-template <int D, int M, int PDE>
+template <int D, int M, int PDE, int DIV = 1>
 struct FluxCfg {
   static constexpr int N = M + 1, NPT = ipow(N, D), V = nvars(D, PDE);
-  static constexpr int CPB = 256 / NPT;   // face items per CTA
+  static constexpr int CPB = 256 / NPT / DIV > 0 ? 256 / NPT / DIV : 1;   // face items per CTA
   static constexpr int THREADS = CPB * NPT;
   static constexpr int SMEM = THREADS * V * 8;
   static_assert(CPB * V <= THREADS, "flux_finish needs one thread per (face item, variable)");
@@ -519,11 +521,11 @@ __device__ __forceinline__ int flux_point(const HotArgs& a, bool ok, const int* 
 }
 
 // reduce the point contributions of every (face item, variable) of the CTA and finish the face
-template <int D, int M, int PDE>
+template <int D, int M, int PDE, int DIV>
 __device__ __forceinline__ void flux_finish(const HotArgs& a, const double* sh, const int* sitem, const int* skind,
                                             const int* snb) {
   constexpr int N = M + 1, NPT = ipow(N, D), V = nvars(D, PDE);
-  constexpr int IPB = FluxCfg<D, M, PDE>::CPB;
+  constexpr int IPB = FluxCfg<D, M, PDE, DIV>::CPB;
   const int t = threadIdx.x;
   if (t >= IPB * V) return;
   const int li = t / V, v = t % V;
@@ -584,9 +586,9 @@ __device__ __forceinline__ void flux_finish(const HotArgs& a, const double* sh, 
 // coarse sides: the flux is the sum of the fine cells' memory variables over the r sub-steps,
 // normalised by dt * area of this level.
 // ------------------------------------------------------------------------------------------
-template <int D, int M, int PDE>
+template <int D, int M, int PDE, int DIV = 1>
 __device__ __forceinline__ void flux_body(const HotArgs& a, const int bid) {
-  using C = FluxCfg<D, M, PDE>;
+  using C = FluxCfg<D, M, PDE, DIV>;
   constexpr int N = M + 1, NPT = C::NPT, V = C::V;
   constexpr int NST = ipow(N, D + 1);
   extern __shared__ double sh[];
@@ -639,12 +641,12 @@ __device__ __forceinline__ void flux_body(const HotArgs& a, const int bid) {
     sitem[3 * li] = cell; sitem[3 * li + 1] = d; sitem[3 * li + 2] = side;
   }
   __syncthreads();
-  flux_finish<D, M, PDE>(a, sh, sitem, skind, snb);
+  flux_finish<D, M, PDE, DIV>(a, sh, sitem, skind, snb);
 }
 
-template <int D, int M, int PDE>
-__global__ void __launch_bounds__(FluxCfg<D, M, PDE>::THREADS) k_flux(const __grid_constant__ HotArgs a) {
-  flux_body<D, M, PDE>(a, blockIdx.x);
+template <int D, int M, int PDE, int DIV>
+__global__ void __launch_bounds__(FluxCfg<D, M, PDE, DIV>::THREADS) k_flux(const __grid_constant__ HotArgs a) {
+  flux_body<D, M, PDE, DIV>(a, blockIdx.x);
 }
 
 // ------------------------------------------------------------------------------------------

@@ -6,26 +6,49 @@
 
 namespace aw {
 
+// SMs of the current device (launch shapes for small levels)
+inline int sm_count() {
+  static std::once_flag once;
+  static int n = 152;
+  std::call_once(once, [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      n = v;
+  });
+  return n;
+}
+
 template <int D, int M, int PDE>
 struct Launch {
-  // WENO tile edge: 8x8 cells in 2D (6 sweep passes of 256 threads per 64 cells, against 2 per 16
-  // with 4x4 tiles, whose x pass fills 160 of 256 lanes), 4x4x4 in 3D (shared memory)
-  static constexpr int TS = (D == 2) ? 8 : 4;
-  using CW = WenoCfg<D, M, PDE, TS>;
+  // WENO tiles: 8x8 cells in 2D (6 sweep passes of 256 threads per 64 cells, against 2 per 16
+  // with 4x4 tiles, whose x pass fills 160 of 256 lanes), 4x4 on levels below 20,000 cells so that
+  // their tiles still spread over the SMs; 4x4x4 in 3D (shared memory)
+  static int weno_tile(long long n) { return (D == 2 && n >= 20000) ? 8 : 4; }
   using CP = PredCfg<D, M, PDE>;
   using CF = FluxCfg<D, M, PDE>;
+  // a quarter of the cells (face items) per CTA when the full-size CTAs would give fewer than two
+  // CTAs per SM; every cell and face computes exactly the same either way
+  static constexpr int SMALL = 4;
+  using CPs = PredCfg<D, M, PDE, SMALL>;
+  using CFs = FluxCfg<D, M, PDE, SMALL>;
   static constexpr int V = nvars(D, PDE);
 
   // CTAs of each kernel for one solve's level (0 when there is no work)
   static int weno_ctas(const HotArgs& a) { return a.ntiles > 0 ? a.ntiles : 0; }
-  static int predict_ctas(const HotArgs& a) { return a.na > 0 ? (a.na + CP::CPB - 1) / CP::CPB : 0; }
-  static int flux_ctas(const HotArgs& a) {
+  template <class C>
+  static int predict_ctas_of(const HotArgs& a) { return a.na > 0 ? (a.na + C::CPB - 1) / C::CPB : 0; }
+  static int predict_ctas(const HotArgs& a) { return predict_ctas_of<CP>(a); }
+  template <class C>
+  static int flux_ctas_of(const HotArgs& a) {
     if (a.na <= 0) return 0;
-    long long lo = (long long)D * ((a.na + CF::CPB - 1) / CF::CPB);
-    return (int)(lo + (a.nh + CF::CPB - 1) / CF::CPB);
+    long long lo = (long long)D * ((a.na + C::CPB - 1) / C::CPB);
+    return (int)(lo + (a.nh + C::CPB - 1) / C::CPB);
   }
+  static int flux_ctas(const HotArgs& a) { return flux_ctas_of<CF>(a); }
   static int update_ctas(const HotArgs& a) { return a.na > 0 ? (a.na + 127) / 128 : 0; }
   static int project_ctas(int nv) { return nv > 0 ? (int)(((long long)nv * V + 127) / 128) : 0; }
+  static bool small(int ctas) { return ctas < 2 * sm_count(); }
 
   // the dynamic shared memory attribute, once per kernel (request-loop workers launch concurrently)
   template <class K>
@@ -33,28 +56,51 @@ struct Launch {
     std::call_once(once, [&] { cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes); });
   }
 
+  template <int TS>
+  static void weno_launch(const HotArgs& a, int blocks, cudaStream_t st) {
+    using C = WenoCfg<D, M, PDE, TS>;
+    static std::once_flag init;
+    smem_attr(k_weno<D, M, PDE, TS>, C::SMEM, init);
+    k_weno<D, M, PDE, TS><<<blocks, 256, C::SMEM, st>>>(a);
+  }
   static int weno(const HotArgs& a, cudaStream_t st) {
     const int blocks = weno_ctas(a);
     if (!blocks) return 0;
-    static std::once_flag init;
-    smem_attr(k_weno<D, M, PDE, TS>, CW::SMEM, init);
-    k_weno<D, M, PDE, TS><<<blocks, 256, CW::SMEM, st>>>(a);
+    if constexpr (D == 2) {
+      if (a.ts == 8) {
+        weno_launch<8>(a, blocks, st);
+        return 1;
+      }
+    }
+    weno_launch<4>(a, blocks, st);
     return 1;
   }
   static int predict(const HotArgs& a, cudaStream_t st) {
-    const int blocks = predict_ctas(a);
+    int blocks = predict_ctas_of<CP>(a);
     if (!blocks) return 0;
-    static std::once_flag init;
-    smem_attr(k_predict<D, M, PDE>, CP::SMEM, init);
-    k_predict<D, M, PDE><<<blocks, CP::THREADS, CP::SMEM, st>>>(a);
+    if (small(blocks)) {
+      static std::once_flag init;
+      smem_attr(k_predict<D, M, PDE, SMALL>, CPs::SMEM, init);
+      k_predict<D, M, PDE, SMALL><<<predict_ctas_of<CPs>(a), CPs::THREADS, CPs::SMEM, st>>>(a);
+    } else {
+      static std::once_flag init;
+      smem_attr(k_predict<D, M, PDE, 1>, CP::SMEM, init);
+      k_predict<D, M, PDE, 1><<<blocks, CP::THREADS, CP::SMEM, st>>>(a);
+    }
     return 1;
   }
   static int flux(const HotArgs& a, cudaStream_t st) {
-    const int blocks = flux_ctas(a);
+    int blocks = flux_ctas_of<CF>(a);
     if (!blocks) return 0;
-    static std::once_flag init;
-    smem_attr(k_flux<D, M, PDE>, CF::SMEM, init);
-    k_flux<D, M, PDE><<<blocks, CF::THREADS, CF::SMEM, st>>>(a);
+    if (small(blocks)) {
+      static std::once_flag init;
+      smem_attr(k_flux<D, M, PDE, SMALL>, CFs::SMEM, init);
+      k_flux<D, M, PDE, SMALL><<<flux_ctas_of<CFs>(a), CFs::THREADS, CFs::SMEM, st>>>(a);
+    } else {
+      static std::once_flag init;
+      smem_attr(k_flux<D, M, PDE, 1>, CF::SMEM, init);
+      k_flux<D, M, PDE, 1><<<blocks, CF::THREADS, CF::SMEM, st>>>(a);
+    }
     return 1;
   }
   static int update(const HotArgs& a, cudaStream_t st) {
@@ -82,13 +128,34 @@ struct Launch {
     b.start[b.n] = tot;
     return tot;
   }
-  static int weno_b(HotBatch& b, cudaStream_t st) {
+  template <int TS>
+  static int weno_b_ts(HotBatch& b, cudaStream_t st) {
     const int blocks = fill_starts(b, weno_ctas);
     if (!blocks) return 0;
+    using C = WenoCfg<D, M, PDE, TS>;
     static std::once_flag init;
-    smem_attr(k_weno_batch<D, M, PDE, TS>, CW::SMEM, init);
-    k_weno_batch<D, M, PDE, TS><<<blocks, 256, CW::SMEM, st>>>(b);
+    smem_attr(k_weno_batch<D, M, PDE, TS>, C::SMEM, init);
+    k_weno_batch<D, M, PDE, TS><<<blocks, 256, C::SMEM, st>>>(b);
     return 1;
+  }
+  // members whose level has 8x8 tiles and members with 4x4 tiles run as two launches
+  static int weno_b(HotBatch& b, cudaStream_t st) {
+    if constexpr (D == 2) {
+      bool mixed = false;
+      for (int m = 1; m < b.n; m++) mixed |= b.a[m].ts != b.a[0].ts;
+      if (!mixed) return b.a[0].ts == 8 ? weno_b_ts<8>(b, st) : weno_b_ts<4>(b, st);
+      int n = 0;
+      for (int ts : {8, 4}) {
+        HotBatch g;
+        g.n = 0;
+        for (int m = 0; m < b.n; m++)
+          if (b.a[m].ts == ts) g.a[g.n++] = b.a[m];
+        if (g.n) n += ts == 8 ? weno_b_ts<8>(g, st) : weno_b_ts<4>(g, st);
+      }
+      return n;
+    } else {
+      return weno_b_ts<4>(b, st);
+    }
   }
   static int predict_b(HotBatch& b, cudaStream_t st) {
     const int blocks = fill_starts(b, predict_ctas);
@@ -121,7 +188,8 @@ struct Launch {
 
   static HotOps ops() {
     HotOps o;
-    o.D = D; o.M = M; o.PDE = PDE; o.V = V; o.wenoTS = TS;
+    o.D = D; o.M = M; o.PDE = PDE; o.V = V;
+    o.weno_tile = &weno_tile;
     o.weno = &weno; o.predict = &predict; o.flux = &flux; o.update = &update; o.project = &project;
     o.weno_b = &weno_b; o.predict_b = &predict_b; o.flux_b = &flux_b; o.update_b = &update_b;
     o.project_b = &project_b;

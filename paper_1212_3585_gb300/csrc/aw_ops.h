@@ -8,7 +8,9 @@ struct HotArgs;
 struct HotBatch;
 
 struct HotOps {
-  int D, M, PDE, V, wenoTS;
+  int D, M, PDE, V;
+  // WENO tile edge of a level of n cells (8x8 tiles in 2D unless the level is small, 4x4x4 in 3D)
+  int (*weno_tile)(long long n);
   // each launcher returns the number of kernels it launched (0 when there was no work)
   int (*weno)(const HotArgs&, cudaStream_t);
   int (*predict)(const HotArgs&, cudaStream_t);

@@ -101,6 +101,7 @@ struct Level {
   double *u = nullptr, *chi = nullptr;
   int32_t *aid = nullptr, *alist = nullptr, *vlist = nullptr, *mlist = nullptr, *clist = nullptr;
   int na = 0, nv = 0, nm = 0, nc = 0;
+  int ts = 4;                  // WENO tile edge
   int tdim[3] = {1, 1, 1};
   long long ntd = 0;
   int8_t* tflag = nullptr;
@@ -882,7 +883,7 @@ static int lists_mid(aw_solver* s) {
     L.nc = s->h_cnt[6 * l + 3];
     CK(cudaMemsetAsync(L.tflag, 0, L.ntd, s->stream));
     if (L.na > 0) {
-      k_tmark<<<nblk(L.na, 256), 256, 0, s->stream>>>(view(s, l), L.alist, L.na, s->ops.wenoTS, L.tdim[0], L.tdim[1],
+      k_tmark<<<nblk(L.na, 256), 256, 0, s->stream>>>(view(s, l), L.alist, L.na, L.ts, L.tdim[0], L.tdim[1],
                                                       L.tflag);
       s->launches++;
     }
@@ -948,6 +949,7 @@ static HotArgs make_args(const aw_solver* s, int l, int sub) {
   a.err = s->d_err;
   a.vlist = L.vlist;
   a.nv = L.nv;
+  a.ts = L.ts;
   return a;
 }
 
@@ -1350,7 +1352,8 @@ int aw_create(const aw_config* cfg, uintptr_t stream, aw_solver** out) {
     L.dx[2] = s->D == 3 ? (c.hi[2] - c.lo[2]) / c.nz : 1.0;
     for (int k = 0; k < l; k++)
       for (int a = 0; a < s->D; a++) L.dx[a] /= s->r;
-    int TS = s->ops.wenoTS;
+    L.ts = s->ops.weno_tile(L.n);
+    int TS = L.ts;
     for (int a = 0; a < 3; a++) L.tdim[a] = a < s->D ? (L.L[a] + TS - 1) / TS : 1;
     L.ntd = (long long)L.tdim[0] * L.tdim[1] * L.tdim[2];
     alloc((void**)&L.st, L.n);
