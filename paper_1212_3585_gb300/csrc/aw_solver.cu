@@ -1749,8 +1749,14 @@ int aw_advance_graph(aw_solver* s, double t_end, int32_t chunk, aw_stats* st) {
   CK(cudaMemcpyAsync(s->d_gs, s->h_gs, sizeof(GState), cudaMemcpyHostToDevice, s->stream));
   CK(cudaMemcpyAsync(s->d_dtmin, s->h_dtl + MAXL, sizeof(double), cudaMemcpyHostToDevice, s->stream));
   CK(cudaMemsetAsync(s->d_err, 0, sizeof(int), s->stream));
-  cudaEvent_t ev;
-  CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+  struct EventHolder {
+    cudaEvent_t e = nullptr;
+    ~EventHolder() {
+      if (e) cudaEventDestroy(e);
+    }
+  } evh;
+  CK(cudaEventCreateWithFlags(&evh.e, cudaEventDisableTiming));
+  cudaEvent_t ev = evh.e;
   CK(cudaEventRecord(ev, s->stream));
   CK(cudaStreamWaitEvent(gs, ev, 0));
   // `chunk` level-0 steps: CFL reduction, device-side dt, the four hot kernels; captured once and
@@ -1780,7 +1786,6 @@ int aw_advance_graph(aw_solver* s, double t_end, int32_t chunk, aw_stats* st) {
     if (graph) cudaGraphDestroy(graph);
     if (ce != cudaSuccess) {
       s->gexec = nullptr;
-      cudaEventDestroy(ev);
       AW_FAIL(AW_ECUDA, "graph capture: %s", cudaGetErrorString(ce));
     }
     memcpy(&s->gargs, &a, sizeof a);   // every byte, padding included, for the memcmp above
@@ -1806,7 +1811,6 @@ int aw_advance_graph(aw_solver* s, double t_end, int32_t chunk, aw_stats* st) {
   }
   cudaEventRecord(ev, gs);
   cudaStreamWaitEvent(s->stream, ev, 0);
-  cudaEventDestroy(ev);
   if (rc != AW_OK) return rc;
   s->t = s->h_gs->t;
   if (st) {

@@ -156,6 +156,23 @@ def test_predictor_linear_advection_exact(M, d):
     assert np.allclose(qh, exact, rtol=1e-12, atol=1e-12)
 
 
+@pytest.mark.parametrize("M,d", [(1, 2), (2, 2), (3, 2), (2, 3)])
+def test_picard_iteration_beyond_m_plus_1_changes_nothing(M, d):
+    """for a linear flux the Picard iteration is exact after M+1 steps (the spatial derivative is
+    nilpotent on degree-M data): one more step changes the result by round-off only"""
+    adv = (0.7, -0.4, 0.3)
+    rng = np.random.default_rng(12)
+    P = _random_total_degree_poly(M, d, rng)
+    N = M + 1
+    wh = _sp_nodal(P, N, d)
+    dx = (0.5, 0.8, 0.6)[:d]
+    out = []
+    for picard in (M + 1, M + 2):
+        cfg = oracle.make_cfg(dim=d, pde=oracle.PDE_LINADV, M=M, n=(8, 8, 8), adv=adv, picard=picard)
+        out.append(oracle.Oracle(cfg).predictor(wh, 0.3, dx))
+    assert np.allclose(out[0], out[1], rtol=1e-13, atol=1e-13)
+
+
 @pytest.mark.parametrize("M", [1, 2, 3])
 def test_predictor_euler_contact_wave_exact(M):
     d = 2
