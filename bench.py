@@ -450,8 +450,20 @@ def cpu_baseline_sample(level0_steps=4):
         o.step(T_END)
     el = time.perf_counter() - t0
     n = o.updates()[0] - u0
-    return {"value": n / el, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"first {level0_steps} level-0 steps of the workload ({n} cell updates, {el:.1f} s)"}
+    out = {"value": n / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": f"first {level0_steps} level-0 steps of the workload ({n} cell updates, {el:.1f} s)"}
+    # the same oracle on one core, on the first level-0 step
+    o1 = oracle.Oracle(oracle.make_cfg(dim=2, M=3, n=CFG["n"], lo=CFG["lo"], hi=CFG["hi"],
+                                       bc=oracle.BC_TRANSMISSIVE, r=3, lmax=2, cfl=0.6, auto_regrid=1), threads=1)
+    o1.set_initial(oracle.IC_EXPLOSION, aw_inputs.EXPLOSION)
+    u1 = o1.updates()[0]
+    t1 = time.perf_counter()
+    o1.step(T_END)
+    el1 = time.perf_counter() - t1
+    n1 = o1.updates()[0] - u1
+    out["single_core"] = {"value": n1 / el1, "unit": UNIT, "cores": 1,
+                          "sample": f"first level-0 step of the workload ({n1} cell updates, {el1:.1f} s)"}
+    return out
 
 
 def main():

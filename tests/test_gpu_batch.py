@@ -128,3 +128,42 @@ def test_failing_member_stops_alone():
         assert np.array_equal(m, m0) and np.array_equal(u, u0)
         s.close()
     bad.close()
+
+
+def other_specs(kind):
+    T, P, I = pg.AW_BC_TRANSMISSIVE, pg.AW_BC_PERIODIC, pg.AW_BC_INFLOW
+    if kind == "3d":
+        return [(pg.make_config(dim=3, M=2, n=(8, 8, 8), lo=(-1, -1, -1), hi=(1, 1, 1), bc=T, r=3, lmax=1, cfl=0.6,
+                                auto_regrid=1), pg.AW_IC_EXPLOSION, EXPL),
+                (pg.make_config(dim=3, M=2, n=(7, 6, 5), bc=P, cfl=0.9), pg.AW_IC_FOURIER,
+                 aw_inputs.fourier_params(seed=8, dim=3, pde="euler", nmodes=3))]
+    if kind == "mhd":
+        return [(pg.make_config(dim=2, pde=pg.AW_PDE_MHD_GLM, M=3, n=(n, n, 1), lo=(0, 0, 0),
+                                hi=(2 * np.pi, 2 * np.pi, 1), bc=P, r=3, lmax=lm, gamma=5 / 3, c_h=2.0, cfl=0.6,
+                                auto_regrid=1), pg.AW_IC_OT, []) for n, lm in ((16, 1), (12, 0))]
+    # second order, Osher flux, inflow and reflective boundaries
+    qin = [2.0, 1.0, 0.0, 4.0]
+    return [(pg.make_config(dim=2, M=1, n=(20, 16, 1), lo=(0, 0, 0), hi=(1, 0.8, 1),
+                            bc=[I, T, pg.AW_BC_REFLECTIVE, T, T, T], r=3, lmax=2, cfl=0.6, flux=pg.AW_FLUX_OSHER,
+                            auto_regrid=1, inflow=qin), pg.AW_IC_CONST, [1.0, 0.0, 0.0, 1.0]),
+            (pg.make_config(dim=2, M=1, n=(14, 14, 1), lo=(-1, -1, 0), hi=(1, 1, 1), bc=T, r=3, lmax=1, cfl=0.6,
+                            flux=pg.AW_FLUX_OSHER, auto_regrid=1), pg.AW_IC_EXPLOSION, EXPL)]
+
+
+@pytest.mark.parametrize("kind", ["3d", "mhd", "m1_osher_inflow"])
+def test_batch_other_configurations(kind):
+    t_end = 0.02
+    specs = other_specs(kind)
+    ref = [solo(cfg, ic, p, t_end) for cfg, ic, p in specs]
+    sol = []
+    for cfg, ic, p in specs:
+        s = pg.Solver(cfg)
+        s.set_initial(ic, p, -1)
+        sol.append(s)
+    stats, rc = pg.advance_batch(sol, t_end)
+    assert rc == [0] * len(sol)
+    for s, st, (m0, u0, st0) in zip(sol, stats, ref):
+        m, u = s.cells()
+        assert np.array_equal(m, m0) and np.array_equal(u, u0)
+        assert st.cell_updates == st0.cell_updates
+        s.close()
