@@ -12,9 +12,14 @@ value   = cell updates (active cell advanced by its level's dt) per second, devi
 e2e     = the same through the C ABI with host buffers: level-0 averages uploaded from pinned
           host memory, data-driven refinement, solve, all cell averages read back
 roofline= the dominant kernel's algorithmic FP64 FLOP rate against the FP64 peak
-cpu_baseline = the FP64 CPU oracle on the host cores, on the first level-0 step of the same solve
+cpu_baseline = the FP64 CPU oracle on all host cores, on the first four level-0 steps of the same
+          solve (and on one core, on the first level-0 step)
 
 Multi-GPU: one independent replica per rank (the path has no exchange step), weak scaling.
+
+Other modes (one JSON line each, not the benchmark line): --serve (request loop, with and without
+cross-request batching, against one-at-a-time solves), --efficiency (cost per cell update of
+orders 2-4, uniform against AMR), --configs (throughput of the other configurations).
 """
 import argparse
 import ctypes as C
