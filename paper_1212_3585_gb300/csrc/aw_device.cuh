@@ -398,6 +398,12 @@ struct HotArgs {
   const int32_t* vlist; // virtual children of this level (dense indices), projected from qhm
   int nv;
   int ts;               // WENO tile edge of this level
+  // 2D WENO in two passes (null xs: tiles): rows whose x sweep feeds an active cell, the dense
+  // cell -> row slot map, and the x sweeps [slot][V][N]
+  const int32_t* xlist;
+  const int32_t* xslot;
+  double* xs;
+  int nxs;
 };
 
 // Several independent solves of the same kernel configuration in one launch: member m owns CTAs

@@ -256,6 +256,80 @@ __global__ void __launch_bounds__(256) k_weno(const __grid_constant__ HotArgs a)
 }
 
 // ------------------------------------------------------------------------------------------
+// 2D WENO in two passes (the same reconstructions as the tiles, Eqs. eqn.weno, eqn.weno.y):
+// first the x sweep of every row that feeds an active cell, once, into a buffer that stays in
+// L2; then the y sweeps of the active cells over the x sweeps of their column.  A tile instead
+// recomputes the x sweeps of its 2M halo rows.  Ghost rows map exactly: periodic and
+// transmissive rows are interior rows, a mirrored row's sweep is the sweep of its image with the
+// normal momentum negated (WENO commutes with negation), and a row beyond an inflow face is the
+// inflow state.
+// ------------------------------------------------------------------------------------------
+template <int M, int PDE>
+__global__ void __launch_bounds__(128) k_weno_x(const __grid_constant__ HotArgs a) {
+  constexpr int D = 2, N = M + 1, V = nvars(D, PDE), W = 2 * M + 1;
+  const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= (long long)a.nxs * V) return;
+  const int slot = (int)(it / V), v = (int)(it % V);
+  const LevelView& L = a.lv;
+  const long long di = a.xlist[slot];
+  const int i = (int)(di % L.L[0]), j = (int)(di / L.L[0]);
+  double val[W];
+#pragma unroll
+  for (int e = 0; e < W; e++) {
+    const int ii = i - M + e;
+    if (beyond_inflow(L.L, a.bc, 0, ii)) {
+      val[e] = a.P.inflow[v];
+      continue;
+    }
+    int im = ii;
+    bcmap(L.L, a.bc, 0, ii, &im);
+    double x = L.u[v * L.n + didx(L, im, j, 0)];
+    if (PDE == PDE_EULER && v == 1 && reflected(L.L, a.bc, 0, ii)) x = -x;
+    val[e] = x;
+  }
+  double o[N];
+  weno1d<M>(a.T, val, 1, o);
+  double* dst = a.xs + ((long long)slot * V + v) * N;
+#pragma unroll
+  for (int p = 0; p < N; p++) dst[p] = o[p];
+}
+
+template <int M, int PDE>
+__global__ void __launch_bounds__(128) k_weno_y(const __grid_constant__ HotArgs a) {
+  constexpr int D = 2, N = M + 1, V = nvars(D, PDE), W = 2 * M + 1, NSP = N * N;
+  const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= (long long)a.na * N * V) return;
+  const int k = (int)(it / (N * V)), rem = (int)(it % (N * V)), p = rem / V, v = rem % V;
+  const LevelView& L = a.lv;
+  const long long di = a.alist[k];
+  const int i = (int)(di % L.L[0]), j = (int)(di / L.L[0]);
+  double val[W];
+#pragma unroll
+  for (int e = 0; e < W; e++) {
+    const int jj = j - M + e;
+    if (beyond_inflow(L.L, a.bc, 1, jj)) {
+      val[e] = a.P.inflow[v];
+      continue;
+    }
+    int jm = jj;
+    bcmap(L.L, a.bc, 1, jj, &jm);
+    int slot = a.xslot[didx(L, i, jm, 0)];
+    if (slot < 0) {   // not marked: an inconsistent list (reported, read in bounds)
+      atomicOr(a.err, 4);
+      slot = 0;
+    }
+    double x = a.xs[((long long)slot * V + v) * N + p];
+    if (PDE == PDE_EULER && v == 2 && reflected(L.L, a.bc, 1, jj)) x = -x;
+    val[e] = x;
+  }
+  double o[N];
+  weno1d<M>(a.T, val, 1, o);
+  double* dst = a.wh + ((long long)k * V + v) * NSP;
+#pragma unroll
+  for (int q = 0; q < N; q++) dst[p + N * q] = o[q];
+}
+
+// ------------------------------------------------------------------------------------------
 // Predictor kernel (Sec. 2.3, Eq. eqn.stdg.final).  One thread per (active cell, spatial node);
 // the thread holds the time column of q_h at its node for all variables.  With the nodal
 // tensor basis the Picard step reads

@@ -67,6 +67,12 @@ struct Launch {
     const int blocks = weno_ctas(a);
     if (!blocks) return 0;
     if constexpr (D == 2) {
+      if (a.xs) {   // two passes: the x sweeps of the feeding rows, then the y sweeps
+        const long long nx = (long long)a.nxs * V, ny = (long long)a.na * (M + 1) * V;
+        k_weno_x<M, PDE><<<(unsigned)((nx + 127) / 128), 128, 0, st>>>(a);
+        k_weno_y<M, PDE><<<(unsigned)((ny + 127) / 128), 128, 0, st>>>(a);
+        return 2;
+      }
       if (a.ts == 8) {
         weno_launch<8>(a, blocks, st);
         return 1;

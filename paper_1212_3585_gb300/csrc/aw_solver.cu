@@ -52,6 +52,9 @@ static thread_local std::string g_err = "";
   } while (0)
 
 static const int CHUNK = 4096;
+// device count slots per level (active, virtual child, virtual mother, existing, tiles, high
+// faces, x-sweep rows); the error word follows the last level's slots
+static const int NSLOT = 7;
 
 // stream-ordered device allocation on the solver's stream
 static cudaError_t dalloc(cudaStream_t st, void** p, size_t bytes) { return cudaMallocAsync(p, bytes ? bytes : 1, st); }
@@ -108,6 +111,12 @@ struct Level {
   int32_t* tiles = nullptr;
   int ntiles = 0;
   double *wh = nullptr, *qh = nullptr, *fl = nullptr, *mem = nullptr;
+  int8_t* xmark = nullptr;     // 2D: rows whose x sweep feeds an active cell (dense)
+  int32_t* xslot = nullptr;    // 2D: dense cell -> position in xlist, -1 elsewhere
+  int32_t* xlist = nullptr;    // 2D: those rows (dense indices), canonical order
+  double* xs = nullptr;        // 2D: their x sweeps [slot][V][N]
+  int nx = 0;
+  long long xcap = 0;
   int8_t* hflag = nullptr;     // per (axis, active id): the high face needs computing
   int32_t* hflist = nullptr;   // compacted high faces, axis * na + active id
   int nh = 0;
@@ -701,6 +710,22 @@ __global__ void k_cscatter(const int8_t* a, long long n, int mode, int val, cons
   }
 }
 
+// 2D WENO in two passes: the rows (i, j + dj), |dj| <= M, of every active cell (i, j), mapped
+// through the y boundary (wrapped, clamped or mirrored into the level; none beyond an inflow face)
+__global__ void k_xmark(LevelView L, Bc6 bc6, const int32_t* alist, int na, int M, int8_t* xmark) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= na) return;
+  int ijk[3];
+  cell_coords(L, alist[k], ijk);
+  for (int dj = -M; dj <= M; dj++) {
+    const int j = ijk[1] + dj;
+    if (beyond_inflow(L.L, bc6.v, 1, j)) continue;
+    int jm = j;
+    bcmap(L.L, bc6.v, 1, j, &jm);
+    xmark[didx(L, ijk[0], jm, 0)] = 1;
+  }
+}
+
 __global__ void k_tmark(LevelView L, const int32_t* alist, int na, int TS, int t0, int t1, int8_t* tflag) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= na) return;
@@ -836,6 +861,33 @@ static int compact(aw_solver* s, const int8_t* a, long long n, int mode, int val
   return AW_OK;
 }
 
+// x-sweep rows of a 2D level: at most 2M+1 rows per active cell, at most the level
+static int ensure_x_cap(aw_solver* s, int l, long long need) {
+  Level& L = s->lev[l];
+  if (need <= L.xcap) return AW_OK;
+  long long cap = std::min(L.n, std::max(need + need / 2, (long long)64));
+  dfree(s->stream, L.xlist);
+  dfree(s->stream, L.xs);
+  L.xlist = nullptr;
+  L.xs = nullptr;
+  L.xcap = 0;
+  if (dalloc(s->stream, (void**)&L.xlist, cap * sizeof(int32_t)) != cudaSuccess ||
+      dalloc(s->stream, (void**)&L.xs, cap * s->V * s->N * sizeof(double)) != cudaSuccess)
+    AW_FAIL(AW_ENOMEM, "x sweeps of level %d (%lld rows)", l, cap);
+  L.xcap = cap;
+  return AW_OK;
+}
+
+// the two-pass 2D WENO applies unless an inflow face in x meets a reflective face in y: there
+// the mirrored ghost rows would need the inflow value unmirrored inside their x sweep
+static bool two_pass_weno(const aw_solver* s) {
+  if (s->D != 2) return false;
+  const int* b = s->cfg.bc;
+  bool x_inflow = b[0] == AW_BC_INFLOW || b[1] == AW_BC_INFLOW;
+  bool y_reflective = b[2] == AW_BC_REFLECTIVE || b[3] == AW_BC_REFLECTIVE;
+  return !(x_inflow && y_reflective);
+}
+
 static int ensure_active_cap(aw_solver* s, int l, long long need) {
   Level& L = s->lev[l];
   if (need <= L.cap) return AW_OK;
@@ -865,47 +917,58 @@ static int ensure_active_cap(aw_solver* s, int l, long long need) {
 static int lists_issue(aw_solver* s) {
   for (int l = 0; l <= s->lmax; l++) {
     Level& L = s->lev[l];
-    TRY(compact(s, L.st, L.n, 0, 0, L.alist, L.aid, 6 * l + 0));
-    TRY(compact(s, L.st, L.n, 0, 1, L.vlist, nullptr, 6 * l + 1));
-    TRY(compact(s, L.st, L.n, 0, -1, L.mlist, nullptr, 6 * l + 2));
-    TRY(compact(s, L.st, L.n, 1, 0, L.clist, nullptr, 6 * l + 3));
+    TRY(compact(s, L.st, L.n, 0, 0, L.alist, L.aid, NSLOT * l + 0));
+    TRY(compact(s, L.st, L.n, 0, 1, L.vlist, nullptr, NSLOT * l + 1));
+    TRY(compact(s, L.st, L.n, 0, -1, L.mlist, nullptr, NSLOT * l + 2));
+    TRY(compact(s, L.st, L.n, 1, 0, L.clist, nullptr, NSLOT * l + 3));
   }
-  CK(cudaMemcpyAsync(s->h_cnt, s->d_cnt, sizeof(int) * 6 * MAXL, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(s->h_cnt, s->d_cnt, sizeof(int) * NSLOT * MAXL, cudaMemcpyDeviceToHost, s->stream));
   return AW_OK;
 }
 
 static int lists_mid(aw_solver* s) {
   for (int l = 0; l <= s->lmax; l++) {
     Level& L = s->lev[l];
-    L.na = s->h_cnt[6 * l + 0];
-    L.nv = s->h_cnt[6 * l + 1];
-    L.nm = s->h_cnt[6 * l + 2];
-    L.nc = s->h_cnt[6 * l + 3];
+    L.na = s->h_cnt[NSLOT * l + 0];
+    L.nv = s->h_cnt[NSLOT * l + 1];
+    L.nm = s->h_cnt[NSLOT * l + 2];
+    L.nc = s->h_cnt[NSLOT * l + 3];
     CK(cudaMemsetAsync(L.tflag, 0, L.ntd, s->stream));
     if (L.na > 0) {
       k_tmark<<<nblk(L.na, 256), 256, 0, s->stream>>>(view(s, l), L.alist, L.na, L.ts, L.tdim[0], L.tdim[1],
                                                       L.tflag);
       s->launches++;
     }
-    TRY(compact(s, L.tflag, L.ntd, 2, 0, L.tiles, nullptr, 6 * l + 4));
+    TRY(compact(s, L.tflag, L.ntd, 2, 0, L.tiles, nullptr, NSLOT * l + 4));
     TRY(ensure_active_cap(s, l, L.na));
     if (L.na > 0) {
       k_hmark<<<nblk(L.na, 256), 256, 0, s->stream>>>(view(s, l), bc6_of(s), L.alist, L.na, s->D, L.hflag);
       s->launches++;
-      TRY(compact(s, L.hflag, (long long)s->D * L.na, 2, 0, L.hflist, nullptr, 6 * l + 5));
+      TRY(compact(s, L.hflag, (long long)s->D * L.na, 2, 0, L.hflist, nullptr, NSLOT * l + 5));
     } else {
-      CK(cudaMemsetAsync(s->d_cnt + 6 * l + 5, 0, sizeof(int), s->stream));
+      CK(cudaMemsetAsync(s->d_cnt + NSLOT * l + 5, 0, sizeof(int), s->stream));
     }
     CK(cudaMemsetAsync(L.mem, 0, (size_t)L.cap * 2 * s->D * s->V * sizeof(double), s->stream));
+    if (L.xmark && L.na > 0) {
+      // rows whose x sweep feeds an active cell (through the y boundary map)
+      TRY(ensure_x_cap(s, l, std::min(L.n, (long long)(2 * s->M + 1) * L.na)));
+      CK(cudaMemsetAsync(L.xmark, 0, L.n, s->stream));
+      k_xmark<<<nblk(L.na, 256), 256, 0, s->stream>>>(view(s, l), bc6_of(s), L.alist, L.na, s->M, L.xmark);
+      s->launches++;
+      TRY(compact(s, L.xmark, L.n, 2, 0, L.xlist, L.xslot, NSLOT * l + 6));
+    } else {
+      CK(cudaMemsetAsync(s->d_cnt + NSLOT * l + 6, 0, sizeof(int), s->stream));
+    }
   }
-  CK(cudaMemcpyAsync(s->h_cnt, s->d_cnt, sizeof(int) * 6 * MAXL, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(s->h_cnt, s->d_cnt, sizeof(int) * NSLOT * MAXL, cudaMemcpyDeviceToHost, s->stream));
   return AW_OK;
 }
 
 static void lists_finish(aw_solver* s) {
   for (int l = 0; l <= s->lmax; l++) {
-    s->lev[l].ntiles = s->h_cnt[6 * l + 4];
-    s->lev[l].nh = s->h_cnt[6 * l + 5];
+    s->lev[l].ntiles = s->h_cnt[NSLOT * l + 4];
+    s->lev[l].nh = s->h_cnt[NSLOT * l + 5];
+    s->lev[l].nx = s->h_cnt[NSLOT * l + 6];
   }
 }
 
@@ -950,6 +1013,12 @@ static HotArgs make_args(const aw_solver* s, int l, int sub) {
   a.vlist = L.vlist;
   a.nv = L.nv;
   a.ts = L.ts;
+  if (L.xmark) {
+    a.xlist = L.xlist;
+    a.xslot = L.xslot;
+    a.xs = L.xs;
+    a.nxs = L.nx;
+  }
   return a;
 }
 
@@ -1032,9 +1101,9 @@ static int step_begin(aw_solver* s, double dt0) {
   return AW_OK;
 }
 
-// after the stream has reached the copy of the error word to h_cnt[6 * MAXL]: statistics, errors
+// after the stream has reached the copy of the error word to h_cnt[NSLOT * MAXL]: statistics, errors
 static int step_finish(aw_solver* s, double dt0, aw_stats* st) {
-  const int err = s->h_cnt[6 * MAXL];
+  const int err = s->h_cnt[NSLOT * MAXL];
   int64_t rl = 1;
   for (int l = 0; l <= s->lmax; l++) {
     int64_t u = (int64_t)s->lev[l].na * rl;
@@ -1050,7 +1119,7 @@ static int step_finish(aw_solver* s, double dt0, aw_stats* st) {
 static int step_dt(aw_solver* s, double dt0, aw_stats* st) {
   TRY(step_begin(s, dt0));
   TRY(advance(s, 0, 0));
-  CK(cudaMemcpyAsync(s->h_cnt + 6 * MAXL, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(s->h_cnt + NSLOT * MAXL, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
   return step_finish(s, dt0, st);
 }
@@ -1185,7 +1254,8 @@ static void free_solver(aw_solver* s) {
     Level& L = s->lev[l];
     for (void* p : {(void*)L.st, (void*)L.R, (void*)L.nst, (void*)L.flag, (void*)L.u, (void*)L.chi, (void*)L.aid,
                     (void*)L.alist, (void*)L.vlist, (void*)L.mlist, (void*)L.clist, (void*)L.tflag, (void*)L.tiles,
-                    (void*)L.wh, (void*)L.qh, (void*)L.fl, (void*)L.mem, (void*)L.hflag, (void*)L.hflist})
+                    (void*)L.wh, (void*)L.qh, (void*)L.fl, (void*)L.mem, (void*)L.hflag, (void*)L.hflist,
+                    (void*)L.xmark, (void*)L.xslot, (void*)L.xlist, (void*)L.xs})
       dfree(st, p);
   }
   for (void* p : {(void*)s->d_dtl, (void*)s->d_dtmin, (void*)s->d_err, (void*)s->d_cnt, (void*)s->d_bcnt,
@@ -1369,13 +1439,17 @@ int aw_create(const aw_config* cfg, uintptr_t stream, aw_solver** out) {
     alloc((void**)&L.clist, L.n * sizeof(int32_t));
     alloc((void**)&L.tflag, L.ntd);
     alloc((void**)&L.tiles, L.ntd * sizeof(int32_t));
+    if (two_pass_weno(s)) {
+      alloc((void**)&L.xmark, L.n);
+      alloc((void**)&L.xslot, L.n * sizeof(int32_t));
+    }
     rr *= s->r;
   }
   alloc((void**)&s->d_dtl, sizeof(double) * MAXL);
   alloc((void**)&s->d_dtmin, sizeof(double));
   alloc((void**)&s->d_err, sizeof(int));
-  alloc((void**)&s->d_cnt, sizeof(int) * (6 * MAXL + 8));
-  static_assert(sizeof(int) * (6 * MAXL + 8) <= 256 && sizeof(double) * (MAXL + 1) <= 256, "pinned blocks");
+  alloc((void**)&s->d_cnt, sizeof(int) * (NSLOT * MAXL + 8));
+  static_assert(sizeof(int) * (NSLOT * MAXL + 8) <= 256 && sizeof(double) * (MAXL + 1) <= 256, "pinned blocks");
   if (rc == AW_OK) {
     s->h_cnt = (int*)pinned_block();
     s->h_dtl = (double*)pinned_block();
@@ -1627,7 +1701,7 @@ static int batch_run(aw_solver* const* S, int n, double t_end, cudaStream_t st, 
       if (live[m]) { S[m]->launches += nl; break; }
     TRY(rc);
     for (int m = 0; m < n; m++)
-      if (live[m]) CK(cudaMemcpyAsync(S[m]->h_cnt + 6 * MAXL, S[m]->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+      if (live[m]) CK(cudaMemcpyAsync(S[m]->h_cnt + NSLOT * MAXL, S[m]->d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     for (int m = 0; m < n; m++) {
       if (!live[m]) continue;
@@ -1763,7 +1837,7 @@ int aw_advance_graph(aw_solver* s, double t_end, int32_t chunk, aw_stats* st) {
   // kept while the launch arguments (every pointer and size of the level) stay the same
   const Level& L = s->lev[0];
   HotArgs a = make_args(s, 0, 0);
-  const int per_step = 2 + (L.ntiles > 0) + 3;
+  const int per_step = 2 + (L.ntiles > 0 ? (a.xs ? 2 : 1) : 0) + 3;
   cudaError_t ce = cudaSuccess;
   if (!s->gexec || s->gchunk != chunk || memcmp(&s->gargs, &a, sizeof a) != 0) {
     if (s->gexec) cudaGraphExecDestroy(s->gexec);
@@ -1798,7 +1872,7 @@ int aw_advance_graph(aw_solver* s, double t_end, int32_t chunk, aw_stats* st) {
     ce = cudaGraphLaunch(exec, gs);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(s->h_gs, s->d_gs, sizeof(GState), cudaMemcpyDeviceToHost, gs);
     if (ce == cudaSuccess)
-      ce = cudaMemcpyAsync(s->h_cnt + 6 * MAXL, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, gs);
+      ce = cudaMemcpyAsync(s->h_cnt + NSLOT * MAXL, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, gs);
     if (ce == cudaSuccess) ce = cudaStreamSynchronize(gs);
     if (ce != cudaSuccess) {
       rc = AW_ECUDA;
@@ -1806,7 +1880,7 @@ int aw_advance_graph(aw_solver* s, double t_end, int32_t chunk, aw_stats* st) {
       break;
     }
     s->launches += (int64_t)per_step * chunk;
-    err = s->h_cnt[6 * MAXL];
+    err = s->h_cnt[NSLOT * MAXL];
     if (s->h_gs->stop || !(s->h_gs->t < t_end)) break;
   }
   cudaEventRecord(ev, gs);
