@@ -67,6 +67,13 @@ __host__ __device__ inline long long didx(const LevelView& L, int i, int j, int 
   return ((long long)k * L.L[1] + j) * L.L[0] + i;
 }
 
+// coordinates of dense index di
+__device__ __forceinline__ void cell_ijk(const LevelView& L, long long di, int* c) {
+  c[0] = (int)(di % L.L[0]);
+  c[1] = (int)((di / L.L[0]) % L.L[1]);
+  c[2] = (int)(di / ((long long)L.L[0] * L.L[1]));
+}
+
 // Map coordinate c of axis a through the boundary conditions.  Returns true inside (possibly
 // wrapped), false outside a transmissive boundary, where *out is clamped (ghost layers copy the
 // adjacent interior cell of the same level), or outside a reflective wall, where *out is the
@@ -398,12 +405,17 @@ struct HotArgs {
   const int32_t* vlist; // virtual children of this level (dense indices), projected from qhm
   int nv;
   int ts;               // WENO tile edge of this level
-  // 2D WENO in two passes (null xs: tiles): rows whose x sweep feeds an active cell, the dense
-  // cell -> row slot map, and the x sweeps [slot][V][N]
+  // WENO by passes (null xs: tiles): rows whose x sweep feeds an active cell, the dense
+  // cell -> row slot map and the x sweeps [slot][V][N]; in 3D also the cells whose y sweeps feed
+  // an active cell, their slot map and the y sweeps [slot][V][N][N]
   const int32_t* xlist;
   const int32_t* xslot;
   double* xs;
   int nxs;
+  const int32_t* ylist;
+  const int32_t* yslot;
+  double* ys;
+  int nys;
 };
 
 // Several independent solves of the same kernel configuration in one launch: member m owns CTAs

@@ -294,6 +294,109 @@ __global__ void __launch_bounds__(128) k_weno_x(const __grid_constant__ HotArgs 
   for (int p = 0; p < N; p++) dst[p] = o[p];
 }
 
+// 3D: the same by three passes -- x sweeps of the rows feeding the y sweeps, y sweeps of the
+// cells feeding the z sweeps, z sweeps of the active cells -- with the same exact ghost mapping
+template <int M, int PDE>
+__global__ void __launch_bounds__(128) k_weno3_x(const __grid_constant__ HotArgs a) {
+  constexpr int D = 3, N = M + 1, V = nvars(D, PDE), W = 2 * M + 1;
+  const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= (long long)a.nxs * V) return;
+  const int slot = (int)(it / V), v = (int)(it % V);
+  const LevelView& L = a.lv;
+  int c[3];
+  cell_ijk(L, a.xlist[slot], c);
+  double val[W];
+#pragma unroll
+  for (int e = 0; e < W; e++) {
+    const int ii = c[0] - M + e;
+    if (beyond_inflow(L.L, a.bc, 0, ii)) {
+      val[e] = a.P.inflow[v];
+      continue;
+    }
+    int im = ii;
+    bcmap(L.L, a.bc, 0, ii, &im);
+    double x = L.u[v * L.n + didx(L, im, c[1], c[2])];
+    if (PDE == PDE_EULER && v == 1 && reflected(L.L, a.bc, 0, ii)) x = -x;
+    val[e] = x;
+  }
+  double o[N];
+  weno1d<M>(a.T, val, 1, o);
+  double* dst = a.xs + ((long long)slot * V + v) * N;
+#pragma unroll
+  for (int p = 0; p < N; p++) dst[p] = o[p];
+}
+
+template <int M, int PDE>
+__global__ void __launch_bounds__(128) k_weno3_y(const __grid_constant__ HotArgs a) {
+  constexpr int D = 3, N = M + 1, V = nvars(D, PDE), W = 2 * M + 1;
+  const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= (long long)a.nys * N * V) return;
+  const int ysl = (int)(it / (N * V)), rem = (int)(it % (N * V)), p = rem / V, v = rem % V;
+  const LevelView& L = a.lv;
+  int c[3];
+  cell_ijk(L, a.ylist[ysl], c);
+  double val[W];
+#pragma unroll
+  for (int e = 0; e < W; e++) {
+    const int jj = c[1] - M + e;
+    if (beyond_inflow(L.L, a.bc, 1, jj)) {
+      val[e] = a.P.inflow[v];
+      continue;
+    }
+    int jm = jj;
+    bcmap(L.L, a.bc, 1, jj, &jm);
+    int slot = a.xslot[didx(L, c[0], jm, c[2])];
+    if (slot < 0) {   // not marked: an inconsistent list (reported, read in bounds)
+      atomicOr(a.err, 4);
+      slot = 0;
+    }
+    double x = a.xs[((long long)slot * V + v) * N + p];
+    if (PDE == PDE_EULER && v == 2 && reflected(L.L, a.bc, 1, jj)) x = -x;
+    val[e] = x;
+  }
+  double o[N];
+  weno1d<M>(a.T, val, 1, o);
+  double* dst = a.ys + (((long long)ysl * V + v) * N + p) * N;
+#pragma unroll
+  for (int q = 0; q < N; q++) dst[q] = o[q];
+}
+
+template <int M, int PDE>
+__global__ void __launch_bounds__(128) k_weno3_z(const __grid_constant__ HotArgs a) {
+  constexpr int D = 3, N = M + 1, V = nvars(D, PDE), W = 2 * M + 1, NSP = N * N * N;
+  const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (it >= (long long)a.na * N * N * V) return;
+  const int k = (int)(it / (N * N * V)), rem = (int)(it % (N * N * V)), pq = rem / V, v = rem % V;
+  const int p = pq % N, q = pq / N;
+  const LevelView& L = a.lv;
+  int c[3];
+  cell_ijk(L, a.alist[k], c);
+  double val[W];
+#pragma unroll
+  for (int e = 0; e < W; e++) {
+    const int kk = c[2] - M + e;
+    if (beyond_inflow(L.L, a.bc, 2, kk)) {
+      val[e] = a.P.inflow[v];
+      continue;
+    }
+    int km = kk;
+    bcmap(L.L, a.bc, 2, kk, &km);
+    int slot = a.yslot[didx(L, c[0], c[1], km)];
+    if (slot < 0) {
+      atomicOr(a.err, 4);
+      slot = 0;
+    }
+    double x = a.ys[(((long long)slot * V + v) * N + p) * N + q];
+    if (PDE == PDE_EULER && v == 3 && reflected(L.L, a.bc, 2, kk)) x = -x;
+    val[e] = x;
+  }
+  double o[N];
+  weno1d<M>(a.T, val, 1, o);
+  double* dst = a.wh + ((long long)k * V + v) * NSP;
+#pragma unroll
+  for (int r = 0; r < N; r++) dst[p + N * q + N * N * r] = o[r];
+}
+
 template <int M, int PDE>
 __global__ void __launch_bounds__(128) k_weno_y(const __grid_constant__ HotArgs a) {
   constexpr int D = 2, N = M + 1, V = nvars(D, PDE), W = 2 * M + 1, NSP = N * N;

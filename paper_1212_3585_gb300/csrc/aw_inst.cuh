@@ -66,9 +66,19 @@ struct Launch {
   static int weno(const HotArgs& a, cudaStream_t st) {
     const int blocks = weno_ctas(a);
     if (!blocks) return 0;
+    constexpr int N = M + 1;
+    if constexpr (D == 3) {
+      if (a.xs && a.ys) {   // three passes: x sweeps of the feeding rows, y sweeps, z sweeps
+        const long long nx = (long long)a.nxs * V, ny = (long long)a.nys * N * V, nz = (long long)a.na * N * N * V;
+        k_weno3_x<M, PDE><<<(unsigned)((nx + 127) / 128), 128, 0, st>>>(a);
+        k_weno3_y<M, PDE><<<(unsigned)((ny + 127) / 128), 128, 0, st>>>(a);
+        k_weno3_z<M, PDE><<<(unsigned)((nz + 127) / 128), 128, 0, st>>>(a);
+        return 3;
+      }
+    }
     if constexpr (D == 2) {
       if (a.xs) {   // two passes: the x sweeps of the feeding rows, then the y sweeps
-        const long long nx = (long long)a.nxs * V, ny = (long long)a.na * (M + 1) * V;
+        const long long nx = (long long)a.nxs * V, ny = (long long)a.na * N * V;
         k_weno_x<M, PDE><<<(unsigned)((nx + 127) / 128), 128, 0, st>>>(a);
         k_weno_y<M, PDE><<<(unsigned)((ny + 127) / 128), 128, 0, st>>>(a);
         return 2;

@@ -53,8 +53,8 @@ static thread_local std::string g_err = "";
 
 static const int CHUNK = 4096;
 // device count slots per level (active, virtual child, virtual mother, existing, tiles, high
-// faces, x-sweep rows); the error word follows the last level's slots
-static const int NSLOT = 7;
+// faces, x-sweep rows, y-sweep cells); the error word follows the last level's slots
+static const int NSLOT = 8;
 
 // stream-ordered device allocation on the solver's stream
 static cudaError_t dalloc(cudaStream_t st, void** p, size_t bytes) { return cudaMallocAsync(p, bytes ? bytes : 1, st); }
@@ -111,12 +111,18 @@ struct Level {
   int32_t* tiles = nullptr;
   int ntiles = 0;
   double *wh = nullptr, *qh = nullptr, *fl = nullptr, *mem = nullptr;
-  int8_t* xmark = nullptr;     // 2D: rows whose x sweep feeds an active cell (dense)
-  int32_t* xslot = nullptr;    // 2D: dense cell -> position in xlist, -1 elsewhere
-  int32_t* xlist = nullptr;    // 2D: those rows (dense indices), canonical order
-  double* xs = nullptr;        // 2D: their x sweeps [slot][V][N]
+  int8_t* xmark = nullptr;     // WENO by passes: rows whose x sweep feeds an active cell (dense)
+  int32_t* xslot = nullptr;    // dense cell -> position in xlist, -1 elsewhere
+  int32_t* xlist = nullptr;    // those rows (dense indices), canonical order
+  double* xs = nullptr;        // their x sweeps [slot][V][N]
   int nx = 0;
-  long long xcap = 0;
+  long long xlcap = 0, xcap = 0;  // capacities of xlist and xs (rows)
+  int8_t* ymark = nullptr;     // 3D: cells whose y sweeps feed an active cell (dense)
+  int32_t* yslot = nullptr;
+  int32_t* ylist = nullptr;
+  double* ys = nullptr;        // their y sweeps [slot][V][N][N]
+  int ny = 0;
+  long long ylcap = 0, ycap = 0;
   int8_t* hflag = nullptr;     // per (axis, active id): the high face needs computing
   int32_t* hflist = nullptr;   // compacted high faces, axis * na + active id
   int nh = 0;
@@ -726,6 +732,29 @@ __global__ void k_xmark(LevelView L, Bc6 bc6, const int32_t* alist, int na, int 
   }
 }
 
+// 3D WENO in three passes: the cells (i, j, k + dk) whose y sweeps, and the rows (i, j + dj, k + dk)
+// whose x sweeps feed the active cell (i, j, k), |dj|, |dk| <= M, mapped through the boundaries
+__global__ void k_mark3(LevelView L, Bc6 bc6, const int32_t* alist, int na, int M, int8_t* xmark, int8_t* ymark) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= na) return;
+  int ijk[3];
+  cell_coords(L, alist[k], ijk);
+  for (int dk = -M; dk <= M; dk++) {
+    const int kk = ijk[2] + dk;
+    if (beyond_inflow(L.L, bc6.v, 2, kk)) continue;
+    int km = kk;
+    bcmap(L.L, bc6.v, 2, kk, &km);
+    ymark[didx(L, ijk[0], ijk[1], km)] = 1;
+    for (int dj = -M; dj <= M; dj++) {
+      const int jj = ijk[1] + dj;
+      if (beyond_inflow(L.L, bc6.v, 1, jj)) continue;
+      int jm = jj;
+      bcmap(L.L, bc6.v, 1, jj, &jm);
+      xmark[didx(L, ijk[0], jm, km)] = 1;
+    }
+  }
+}
+
 __global__ void k_tmark(LevelView L, const int32_t* alist, int na, int TS, int t0, int t1, int8_t* tflag) {
   int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= na) return;
@@ -861,31 +890,46 @@ static int compact(aw_solver* s, const int8_t* a, long long n, int mode, int val
   return AW_OK;
 }
 
-// x-sweep rows of a 2D level: at most 2M+1 rows per active cell, at most the level
-static int ensure_x_cap(aw_solver* s, int l, long long need) {
-  Level& L = s->lev[l];
-  if (need <= L.xcap) return AW_OK;
-  long long cap = std::min(L.n, std::max(need + need / 2, (long long)64));
-  dfree(s->stream, L.xlist);
-  dfree(s->stream, L.xs);
-  L.xlist = nullptr;
-  L.xs = nullptr;
-  L.xcap = 0;
-  if (dalloc(s->stream, (void**)&L.xlist, cap * sizeof(int32_t)) != cudaSuccess ||
-      dalloc(s->stream, (void**)&L.xs, cap * s->V * s->N * sizeof(double)) != cudaSuccess)
-    AW_FAIL(AW_ENOMEM, "x sweeps of level %d (%lld rows)", l, cap);
-  L.xcap = cap;
+// WENO by passes: a row (cell) list of at least `need` entries, allocated before the compaction
+// that fills it (need: a bound from the active count), and a sweep buffer of `count` rows times
+// `per` doubles, allocated once the count is known
+static int ensure_list(aw_solver* s, int32_t** list, long long* cap, long long need, int l) {
+  if (need <= *cap) return AW_OK;
+  long long c = std::max(need + need / 2, (long long)64);
+  c = std::min(c, s->lev[l].n);
+  dfree(s->stream, *list);
+  *list = nullptr;
+  *cap = 0;
+  if (dalloc(s->stream, (void**)list, c * sizeof(int32_t)) != cudaSuccess)
+    AW_FAIL(AW_ENOMEM, "sweep list of level %d (%lld entries)", l, c);
+  *cap = c;
   return AW_OK;
 }
 
-// the two-pass 2D WENO applies unless an inflow face in x meets a reflective face in y: there
-// the mirrored ghost rows would need the inflow value unmirrored inside their x sweep
-static bool two_pass_weno(const aw_solver* s) {
-  if (s->D != 2) return false;
+static int ensure_sweeps(aw_solver* s, double** buf, long long* cap, long long count, long long per, int l) {
+  if (count <= *cap) return AW_OK;
+  long long c = std::max(count + count / 4, (long long)64);
+  dfree(s->stream, *buf);
+  *buf = nullptr;
+  *cap = 0;
+  if (dalloc(s->stream, (void**)buf, c * per * sizeof(double)) != cudaSuccess)
+    AW_FAIL(AW_ENOMEM, "sweep buffer of level %d (%lld entries)", l, c);
+  *cap = c;
+  return AW_OK;
+}
+
+// WENO by passes (one sweep direction after the other over compact lists) applies unless an
+// inflow face on one axis meets a reflective face on a later axis: the mirrored ghost lines of
+// the later axis would need the inflow values of the earlier sweep unmirrored
+static bool weno_by_passes(const aw_solver* s) {
   const int* b = s->cfg.bc;
-  bool x_inflow = b[0] == AW_BC_INFLOW || b[1] == AW_BC_INFLOW;
-  bool y_reflective = b[2] == AW_BC_REFLECTIVE || b[3] == AW_BC_REFLECTIVE;
-  return !(x_inflow && y_reflective);
+  for (int a = 0; a < s->D; a++)
+    for (int c = a + 1; c < s->D; c++) {
+      bool inflow_a = b[2 * a] == AW_BC_INFLOW || b[2 * a + 1] == AW_BC_INFLOW;
+      bool reflective_c = b[2 * c] == AW_BC_REFLECTIVE || b[2 * c + 1] == AW_BC_REFLECTIVE;
+      if (inflow_a && reflective_c) return false;
+    }
+  return true;
 }
 
 static int ensure_active_cap(aw_solver* s, int l, long long need) {
@@ -949,27 +993,44 @@ static int lists_mid(aw_solver* s) {
       CK(cudaMemsetAsync(s->d_cnt + NSLOT * l + 5, 0, sizeof(int), s->stream));
     }
     CK(cudaMemsetAsync(L.mem, 0, (size_t)L.cap * 2 * s->D * s->V * sizeof(double), s->stream));
-    if (L.xmark && L.na > 0) {
+    const long long w = 2 * s->M + 1;
+    if (L.xmark && L.na > 0 && s->D == 2) {
       // rows whose x sweep feeds an active cell (through the y boundary map)
-      TRY(ensure_x_cap(s, l, std::min(L.n, (long long)(2 * s->M + 1) * L.na)));
+      TRY(ensure_list(s, &L.xlist, &L.xlcap, std::min(L.n, w * L.na), l));
       CK(cudaMemsetAsync(L.xmark, 0, L.n, s->stream));
       k_xmark<<<nblk(L.na, 256), 256, 0, s->stream>>>(view(s, l), bc6_of(s), L.alist, L.na, s->M, L.xmark);
       s->launches++;
       TRY(compact(s, L.xmark, L.n, 2, 0, L.xlist, L.xslot, NSLOT * l + 6));
+      CK(cudaMemsetAsync(s->d_cnt + NSLOT * l + 7, 0, sizeof(int), s->stream));
+    } else if (L.xmark && L.na > 0) {
+      // 3D: rows of the x sweeps and cells of the y sweeps that feed the active cells
+      TRY(ensure_list(s, &L.xlist, &L.xlcap, std::min(L.n, w * w * L.na), l));
+      TRY(ensure_list(s, &L.ylist, &L.ylcap, std::min(L.n, w * L.na), l));
+      CK(cudaMemsetAsync(L.xmark, 0, L.n, s->stream));
+      CK(cudaMemsetAsync(L.ymark, 0, L.n, s->stream));
+      k_mark3<<<nblk(L.na, 256), 256, 0, s->stream>>>(view(s, l), bc6_of(s), L.alist, L.na, s->M, L.xmark, L.ymark);
+      s->launches++;
+      TRY(compact(s, L.xmark, L.n, 2, 0, L.xlist, L.xslot, NSLOT * l + 6));
+      TRY(compact(s, L.ymark, L.n, 2, 0, L.ylist, L.yslot, NSLOT * l + 7));
     } else {
-      CK(cudaMemsetAsync(s->d_cnt + NSLOT * l + 6, 0, sizeof(int), s->stream));
+      CK(cudaMemsetAsync(s->d_cnt + NSLOT * l + 6, 0, 2 * sizeof(int), s->stream));
     }
   }
   CK(cudaMemcpyAsync(s->h_cnt, s->d_cnt, sizeof(int) * NSLOT * MAXL, cudaMemcpyDeviceToHost, s->stream));
   return AW_OK;
 }
 
-static void lists_finish(aw_solver* s) {
+static int lists_finish(aw_solver* s) {
   for (int l = 0; l <= s->lmax; l++) {
-    s->lev[l].ntiles = s->h_cnt[NSLOT * l + 4];
-    s->lev[l].nh = s->h_cnt[NSLOT * l + 5];
-    s->lev[l].nx = s->h_cnt[NSLOT * l + 6];
+    Level& L = s->lev[l];
+    L.ntiles = s->h_cnt[NSLOT * l + 4];
+    L.nh = s->h_cnt[NSLOT * l + 5];
+    L.nx = s->h_cnt[NSLOT * l + 6];
+    L.ny = s->h_cnt[NSLOT * l + 7];
+    if (L.xmark) TRY(ensure_sweeps(s, &L.xs, &L.xcap, L.nx, (long long)s->V * s->N, l));
+    if (L.ymark) TRY(ensure_sweeps(s, &L.ys, &L.ycap, L.ny, (long long)s->V * s->N * s->N, l));
   }
+  return AW_OK;
 }
 
 static int rebuild_lists(aw_solver* s) {
@@ -977,8 +1038,7 @@ static int rebuild_lists(aw_solver* s) {
   CK(cudaStreamSynchronize(s->stream));
   TRY(lists_mid(s));
   CK(cudaStreamSynchronize(s->stream));
-  lists_finish(s);
-  return AW_OK;
+  return lists_finish(s);
 }
 
 static HotArgs make_args(const aw_solver* s, int l, int sub) {
@@ -1018,6 +1078,12 @@ static HotArgs make_args(const aw_solver* s, int l, int sub) {
     a.xslot = L.xslot;
     a.xs = L.xs;
     a.nxs = L.nx;
+  }
+  if (L.ymark) {
+    a.ylist = L.ylist;
+    a.yslot = L.yslot;
+    a.ys = L.ys;
+    a.nys = L.ny;
   }
   return a;
 }
@@ -1255,7 +1321,8 @@ static void free_solver(aw_solver* s) {
     for (void* p : {(void*)L.st, (void*)L.R, (void*)L.nst, (void*)L.flag, (void*)L.u, (void*)L.chi, (void*)L.aid,
                     (void*)L.alist, (void*)L.vlist, (void*)L.mlist, (void*)L.clist, (void*)L.tflag, (void*)L.tiles,
                     (void*)L.wh, (void*)L.qh, (void*)L.fl, (void*)L.mem, (void*)L.hflag, (void*)L.hflist,
-                    (void*)L.xmark, (void*)L.xslot, (void*)L.xlist, (void*)L.xs})
+                    (void*)L.xmark, (void*)L.xslot, (void*)L.xlist, (void*)L.xs, (void*)L.ymark, (void*)L.yslot,
+                    (void*)L.ylist, (void*)L.ys})
       dfree(st, p);
   }
   for (void* p : {(void*)s->d_dtl, (void*)s->d_dtmin, (void*)s->d_err, (void*)s->d_cnt, (void*)s->d_bcnt,
@@ -1439,9 +1506,14 @@ int aw_create(const aw_config* cfg, uintptr_t stream, aw_solver** out) {
     alloc((void**)&L.clist, L.n * sizeof(int32_t));
     alloc((void**)&L.tflag, L.ntd);
     alloc((void**)&L.tiles, L.ntd * sizeof(int32_t));
-    if (two_pass_weno(s)) {
+    // WENO by passes from 4096 cells (on tinier levels the tiles' single launch is quicker)
+    if (weno_by_passes(s) && L.n >= 4096) {
       alloc((void**)&L.xmark, L.n);
       alloc((void**)&L.xslot, L.n * sizeof(int32_t));
+      if (s->D == 3) {
+        alloc((void**)&L.ymark, L.n);
+        alloc((void**)&L.yslot, L.n * sizeof(int32_t));
+      }
     }
     rr *= s->r;
   }
@@ -1741,7 +1813,8 @@ static int batch_run(aw_solver* const* S, int n, double t_end, cudaStream_t st, 
       CK(cudaStreamSynchronize(st));
       for (int m = 0; m < n; m++) {
         if (!rg[m]) continue;
-        lists_finish(S[m]);
+        rc = lists_finish(S[m]);
+        if (rc != AW_OK) { fail(m, rc); continue; }
         TRY(average_all(S[m]));
       }
     }
@@ -1837,7 +1910,7 @@ int aw_advance_graph(aw_solver* s, double t_end, int32_t chunk, aw_stats* st) {
   // kept while the launch arguments (every pointer and size of the level) stay the same
   const Level& L = s->lev[0];
   HotArgs a = make_args(s, 0, 0);
-  const int per_step = 2 + (L.ntiles > 0 ? (a.xs ? 2 : 1) : 0) + 3;
+  const int per_step = 2 + (L.ntiles > 0 ? (a.xs ? s->D : 1) : 0) + 3;
   cudaError_t ce = cudaSuccess;
   if (!s->gexec || s->gchunk != chunk || memcmp(&s->gargs, &a, sizeof a) != 0) {
     if (s->gexec) cudaGraphExecDestroy(s->gexec);
