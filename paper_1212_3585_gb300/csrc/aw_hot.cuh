@@ -447,7 +447,10 @@ __global__ void __launch_bounds__(128) k_weno_y(const __grid_constant__ HotArgs 
 template <int D, int M, int PDE, int DIV = 1>
 struct PredCfg {
   static constexpr int N = M + 1, NSP = ipow(N, D), NST = NSP * N, V = nvars(D, PDE);
-  static constexpr int CPB0 = (NSP == 4) ? 64 : (NSP == 9) ? 32 : (NSP == 16 ? 16 : (NSP == 27 ? 16 : 4));
+  // cells per CTA: 256 threads where the fluxes of all nodes (D V N^(d+1) doubles per cell) leave
+  // room for two CTAs per SM; halved where one CTA would fill the shared memory (MHD, 3D)
+  static constexpr int CPB1 = (NSP == 4) ? 64 : (NSP == 9) ? 32 : (NSP == 16 ? 16 : (NSP == 27 ? 16 : 4));
+  static constexpr int CPB0 = (CPB1 * D * V * NST * 8 > 113 * 1024 && CPB1 > 1) ? CPB1 / 2 : CPB1;
   static constexpr int CPB = CPB0 / DIV > 0 ? CPB0 / DIV : 1;
   static constexpr int THREADS = CPB * NSP;
   static constexpr int SMEM = CPB * D * V * NST * 8;   // fluxes at every space-time node
