@@ -76,6 +76,10 @@ def predictor_flops_per_cell(D, M, V, P, flux_flops):
 # FP64 operations of the Euler fluxes in all D directions at one state (1/rho, velocities,
 # kinetic energy, pressure, E+p, then D*(D+2) components)
 EULER_FLUX_FLOPS = {2: 18, 3: 25}
+# MHD-GLM fluxes in both 2D directions at one state: shared primitives 1/rho, v, |B|^2, rho|v|^2, p,
+# v.B, p + |B|^2/2, c_h^2 (28), then per direction momentum (10), energy (4), induction (6) and
+# cleaning (1) components (21)
+MHD_FLUX_FLOPS_2D = 28 + 2 * 21
 
 
 def weno_flops_per_cell(D, M, V):
@@ -390,7 +394,7 @@ def run_configs(args):
                          hi=(2 * np.pi, 2 * np.pi, 1), bc=P, r=3, lmax=1, gamma=5.0 / 3.0, c_h=2.0, cfl=0.6,
                          auto_regrid=1)
     measure("MHD-GLM Orszag-Tang type: M=3, base 128^2 on [0,2pi]^2, r=3, l_max=1, CFL 0.6, t_end=0.5", cfg,
-            pg.AW_IC_OT, [], t_end=0.5)
+            pg.AW_IC_OT, [], t_end=0.5, flops=predictor_flops_per_cell(2, 3, 9, 4, MHD_FLUX_FLOPS_2D))
     cfg = pg.make_config(dim=3, M=2, n=(64, 64, 64), lo=(-1, -1, -1), hi=(1, 1, 1), bc=T, r=3, lmax=2, cfl=0.6,
                          auto_regrid=1)
     f3 = predictor_flops_per_cell(3, 2, 5, 3, EULER_FLUX_FLOPS[3])
