@@ -173,11 +173,13 @@ def test_osher_flux_explosion(dim, M, lmax):
         p.step()
 
 
-@pytest.mark.parametrize("dim,M,lmax,flux", [(2, 3, 1, 0), (2, 2, 2, 1), (3, 2, 1, 0), (2, 1, 1, 1)])
-def test_reflective_walls(dim, M, lmax, flux):
-    """walls on the low faces, transmissive high faces: the quadrant of the centred explosion"""
+@pytest.mark.parametrize("dim,M,lmax,flux,n3", [(2, 3, 1, 0, 5), (2, 2, 2, 1, 5), (3, 2, 1, 0, 5), (2, 1, 1, 1, 5),
+                                                 (3, 2, 1, 1, 8)])
+def test_reflective_walls(dim, M, lmax, flux, n3):
+    """walls on the low faces, transmissive high faces: the quadrant of the centred explosion (the
+    8^3 case's level 1 is large enough for the WENO by passes, the 5^3 one keeps the tiles)"""
     R, T = pg.AW_BC_REFLECTIVE, pg.AW_BC_TRANSMISSIVE
-    n = (10, 10, 1) if dim == 2 else (5, 5, 5)
+    n = (10, 10, 1) if dim == 2 else (n3, n3, n3)
     p = Pair(dim=dim, M=M, n=n, lo=(0, 0, 0), hi=(1, 1, 1), bc=[R, T, R, T, R, T], r=3, lmax=lmax, cfl=0.6,
              flux=flux)
     p.init("explosion", EXPL)
