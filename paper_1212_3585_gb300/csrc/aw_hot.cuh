@@ -91,7 +91,9 @@ __device__ __forceinline__ void warp0_compact(int ncand, Pred pred, int16_t* lis
 // WENO kernel: one CTA per tile of TS^D cells of one level.  The (TS+2M)^D box of averages is
 // staged in shared memory through the boundary map; x sweeps run on every box line that feeds
 // an active cell of the tile, then y (and z) sweeps on the active cells only (compacted work
-// lists, Eqs. eqn.weno, eqn.weno.y, eqn.weno.z).  Output: WENO dofs per active cell.
+// lists, Eqs. eqn.weno, eqn.weno.y, eqn.weno.z).  Output: WENO dofs per active cell.  Used for
+// levels below 4096 cells and for batched launches; larger levels of a single solve run the same
+// reconstructions by passes (k_weno_x/y, k_weno3_x/y/z below), without the halo recomputation.
 // ------------------------------------------------------------------------------------------
 template <int D, int M, int PDE, int TS>
 struct WenoCfg {

@@ -21,9 +21,11 @@ inline int sm_count() {
 
 template <int D, int M, int PDE>
 struct Launch {
-  // WENO tiles: 8x8 cells in 2D (6 sweep passes of 256 threads per 64 cells, against 2 per 16
-  // with 4x4 tiles, whose x pass fills 160 of 256 lanes), 4x4 on levels below 20,000 cells so that
-  // their tiles still spread over the SMs; 4x4x4 in 3D (shared memory)
+  // WENO tiles, for levels below 4096 cells and batched launches (larger levels of a single solve
+  // run the WENO by passes, k_weno_x/y and k_weno3_x/y/z): 8x8 cells in 2D (6 sweep passes of 256
+  // threads per 64 cells, against 2 per 16 with 4x4 tiles, whose x pass fills 160 of 256 lanes),
+  // 4x4 on levels below 20,000 cells so that their tiles still spread over the SMs; 4x4x4 in 3D
+  // (shared memory)
   static int weno_tile(long long n) { return (D == 2 && n >= 20000) ? 8 : 4; }
   using CP = PredCfg<D, M, PDE>;
   using CF = FluxCfg<D, M, PDE>;
