@@ -482,7 +482,7 @@ static void osher(const phys *P, const double *qm, const double *qp, int n, doub
   double s[3], w[3];
   gauss_legendre01(3, s, w);
   for (int j = 0; j < 3; j++) {
-    double q[MAXV], t[MAXV];
+    double q[MAXV] = {0}, t[MAXV];
     for (int v = 0; v < P->V; v++) q[v] = qm[v] + s[j] * dq[v];
     abs_jacobian_apply(P, q, n, dq, t);
     for (int v = 0; v < P->V; v++) acc[v] += w[j] * t[v];
