@@ -89,6 +89,18 @@ def test_vortex_amr_lts():
         p.step()
 
 
+@pytest.mark.parametrize("M,r,lmax,n", [(3, 4, 2, 10), (2, 2, 3, 16), (1, 4, 2, 10)])
+def test_amr_deep_and_wide_refinement(M, r, lmax, n):
+    """refinement factor 4 (the paper's efficiency-table setting) and a four-level hierarchy with
+    r = 2: local time stepping over r^l_max sub-steps, memory variables on every interface"""
+    p = Pair(dim=2, M=M, n=(n, n, 1), lo=(-1, -1, 0), hi=(1, 1, 1), bc="transmissive", r=r, lmax=lmax, cfl=0.6)
+    p.init("explosion", EXPL)
+    n_, na, cpl, apl = p.g.counts()
+    assert all(a > 0 for a in apl)
+    for _ in range(2):
+        p.step()
+
+
 def test_amr_periodic_conservation_gpu():
     p = Pair(dim=2, M=3, n=(12, 12, 1), lo=(0, 0, 0), hi=(10, 10, 1), bc="periodic", r=3, lmax=2, chi_ref=0.1,
              chi_rec=0.01)
