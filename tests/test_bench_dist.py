@@ -46,3 +46,24 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
     monkeypatch.setenv("WORLD_SIZE", "2")
     monkeypatch.setattr("sys.argv", ["bench.py", "--impl", "reference", "--gpus", "2"])
     assert bench.main() == 0
+
+
+def test_reference_arm_line(monkeypatch, capsys):
+    """rank 0 of the reference arm prints one JSON line with the contract's keys (the oracle on a
+    reduced base grid, one step, to keep the CPU suite short)"""
+    import json
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    monkeypatch.setattr("sys.argv", ["bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
+                                     "--base", "24", "--t-end", "0.01"])
+    # main() rewrites these for a custom base grid and end time: restored after the test
+    monkeypatch.setitem(bench.CFG, "n", bench.CFG["n"])
+    monkeypatch.setattr(bench, "T_END", bench.T_END)
+    monkeypatch.setattr(bench, "WORKLOAD", bench.WORKLOAD)
+    assert bench.main() == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
