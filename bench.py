@@ -19,7 +19,8 @@ Multi-GPU: one independent replica per rank (the path has no exchange step), wea
 
 Other modes (one JSON line each, not the benchmark line): --serve (request loop, with and without
 cross-request batching, against one-at-a-time solves), --efficiency (cost per cell update of
-orders 2-4, uniform against AMR), --configs (throughput of the other configurations).
+orders 2-4, uniform against AMR), --configs (throughput of the other configurations), --tune (the
+launch-shape rules timed one at a time).
 """
 import argparse
 import ctypes as C
@@ -404,6 +405,64 @@ def run_configs(args):
     return 0
 
 
+def run_tune(args):
+    """The launch-shape rules (aw_set_launch_params) tuned by measurement: device time per cell
+    update of the explosion workload (to t = 0.05) and of the 32^2 vortex (20 steps) for each
+    setting of one rule at a time, the others at their defaults.  Results never depend on these
+    rules; the library's defaults are the values this sweep selects."""
+    import torch
+    import aw_inputs
+    import paper_1212_3585_gb300 as pg
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    default = pg.get_launch_params()
+
+    def ns_per_update(cfg, ic, params, steps=None, t_end=None, reps=2):
+        s = pg.Solver(cfg, stream.cuda_stream)
+        s.set_initial(ic, params, -1)
+        s.step(1e300)                     # warm-up
+        best = float("inf")
+        for _ in range(reps):
+            s.reset()
+            s.set_initial(ic, params, -1)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            upd = 0
+            if steps:
+                for _ in range(steps):
+                    upd += s.step(1e300).cell_updates
+            else:
+                upd = s.advance_to(t_end).cell_updates
+            e1.record(stream)
+            torch.cuda.synchronize()
+            best = min(best, 1e6 * e0.elapsed_time(e1) / upd)
+        s.close()
+        return best
+
+    expl = pg.make_config(bc=pg.AW_BC_TRANSMISSIVE, auto_regrid=1, **CFG)
+    vort = pg.make_config(dim=2, M=2, n=(32, 32, 1), lo=(0, 0, 0), hi=(10, 10, 1), bc=pg.AW_BC_PERIODIC, cfl=0.9)
+    vortex = [5.0, 5.0, 5.0, 1.0, 1.0, 1.0, 1.0]
+
+    def measure(**kw):
+        pg.set_launch_params(**{**default, **kw})
+        r = {"explosion_ns": ns_per_update(expl, pg.AW_IC_EXPLOSION, aw_inputs.EXPLOSION, t_end=0.05),
+             "vortex32_ns": ns_per_update(vort, pg.AW_IC_VORTEX, vortex, steps=20)}
+        return {**kw, **r}
+
+    sweeps = {"pass_min_cells": [0, 4096, 65536, 10 ** 12], "tile8_min_cells": [0, 20000, 10 ** 12],
+              "small_ctas_per_sm": [0, 1, 2, 4]}
+    out = {}
+    for knob, values in sweeps.items():
+        out[knob] = [measure(**{knob: v}) for v in values]
+    pg.set_launch_params(**default)
+    print(json.dumps({"metric": "device ns per cell update by launch-shape rule", "unit": "ns",
+                      "higher_is_better": False, "dtype": "f64", "data": "synthetic", "defaults": default,
+                      "config": {"workload": "explosion (bench workload to t=0.05) and vortex 32^2 (20 steps)"},
+                      "sweeps": out}))
+    return 0
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -498,6 +557,7 @@ def main():
                     help="cost per cell update of orders 2-4, uniform vs AMR (r=4, l_max=2)")
     ap.add_argument("--eff-base", type=int, default=25)
     ap.add_argument("--configs", action="store_true", help="throughput of the other configurations")
+    ap.add_argument("--tune", action="store_true", help="time the launch-shape rules (aw_set_launch_params)")
     ap.add_argument("--cfg3-steps", type=int, default=2)
     ap.add_argument("--eff-t-end", type=float, default=0.1)
     args = ap.parse_args()
@@ -513,6 +573,8 @@ def main():
         return run_efficiency(args) if rank == 0 else 0
     if args.configs:
         return run_configs(args) if rank == 0 else 0
+    if args.tune:
+        return run_tune(args) if rank == 0 else 0
     if args.impl == "reference":
         if rank != 0:
             return 0

@@ -183,6 +183,23 @@ int aw_advance_batch(aw_solver* const* solvers, int32_t n, double t_end, uintptr
  * time steps).  AW_EINVAL if lmax > 0 or chunk is out of range; AW_ENONPHYSICAL as aw_step. */
 int aw_advance_graph(aw_solver* s, double t_end, int32_t chunk, aw_stats* stats);
 
+/* Launch shapes (no counterpart in the paper; they change the speed, never a result):
+ * WENO by passes (x, then y, then z sweeps over compact lists) on levels of at least
+ * pass_min_cells cells (default 4096; tiles below), 2D WENO tiles of 8x8 cells on levels of at
+ * least tile8_min_cells cells (default 20000; 4x4 below), and quarter-size predictor and flux
+ * CTAs when the full-size ones would give fewer than small_ctas_per_sm CTAs per SM (default 2;
+ * 0 never).  Process-wide.  The first two are fixed per level when a solver is created, the
+ * third applies to every launch.  AW_EINVAL for negative values or small_ctas_per_sm > 64.
+ * bench.py --tune times the workload over these parameters. */
+typedef struct aw_launch_params {
+  int64_t pass_min_cells;
+  int64_t tile8_min_cells;
+  int32_t small_ctas_per_sm;
+  int32_t reserved;
+} aw_launch_params;
+int aw_get_launch_params(aw_launch_params* out);
+int aw_set_launch_params(const aw_launch_params* in);
+
 /* Stable level-0 time step of the current state (CFL condition over all active cells). */
 int aw_compute_dt(aw_solver* s, double* dt0);
 

@@ -166,6 +166,24 @@ class Solver:
         return self.L.aw_kernel_launches(self.h)
 
 
+def get_launch_params() -> dict:
+    """aw_get_launch_params: the process-wide launch-shape rules."""
+    p = _lib.AwLaunchParams()
+    _lib.check(_lib.load().aw_get_launch_params(C.byref(p)))
+    return {"pass_min_cells": p.pass_min_cells, "tile8_min_cells": p.tile8_min_cells,
+            "small_ctas_per_sm": p.small_ctas_per_sm}
+
+
+def set_launch_params(pass_min_cells=None, tile8_min_cells=None, small_ctas_per_sm=None):
+    """aw_set_launch_params: change some of the launch-shape rules (speed only, never results)."""
+    cur = get_launch_params()
+    p = _lib.AwLaunchParams()
+    p.pass_min_cells = cur["pass_min_cells"] if pass_min_cells is None else int(pass_min_cells)
+    p.tile8_min_cells = cur["tile8_min_cells"] if tile8_min_cells is None else int(tile8_min_cells)
+    p.small_ctas_per_sm = cur["small_ctas_per_sm"] if small_ctas_per_sm is None else int(small_ctas_per_sm)
+    _lib.check(_lib.load().aw_set_launch_params(C.byref(p)))
+
+
 def advance_batch(solvers, t_end, stream: int = 0):
     """aw_advance_batch: advance independent solvers of one kernel configuration to t_end with
     their hot kernels batched per level and sub-step.  Returns (stats, rc) per solver; raises

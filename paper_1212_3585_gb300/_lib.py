@@ -49,6 +49,11 @@ class AwSrvSummary(C.Structure):
                 ("cell_updates_per_s", C.c_double)]
 
 
+class AwLaunchParams(C.Structure):
+    _fields_ = [("pass_min_cells", C.c_int64), ("tile8_min_cells", C.c_int64), ("small_ctas_per_sm", C.c_int32),
+                ("reserved", C.c_int32)]
+
+
 class AwCell(C.Structure):
     _fields_ = [("level", C.c_int32), ("status", C.c_int32), ("i", C.c_int32), ("j", C.c_int32), ("k", C.c_int32)]
 
@@ -68,6 +73,8 @@ SIGNATURES = {
     "aw_step_dt": (C.c_int, [_vp, C.c_double, C.POINTER(AwStats)]),
     "aw_advance_to": (C.c_int, [_vp, C.c_double, C.POINTER(AwStats)]),
     "aw_advance_graph": (C.c_int, [_vp, C.c_double, C.c_int32, C.POINTER(AwStats)]),
+    "aw_get_launch_params": (C.c_int, [C.POINTER(AwLaunchParams)]),
+    "aw_set_launch_params": (C.c_int, [C.POINTER(AwLaunchParams)]),
     "aw_compute_dt": (C.c_int, [_vp, _dp]),
     "aw_regrid": (C.c_int, [_vp, C.c_int32]),
     "aw_regrid_with_flags": (C.c_int, [_vp, _i8p, C.c_int64, C.c_int32]),

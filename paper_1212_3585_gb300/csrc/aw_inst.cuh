@@ -26,7 +26,7 @@ struct Launch {
   // threads per 64 cells, against 2 per 16 with 4x4 tiles, whose x pass fills 160 of 256 lanes),
   // 4x4 on levels below 20,000 cells so that their tiles still spread over the SMs; 4x4x4 in 3D
   // (shared memory)
-  static int weno_tile(long long n) { return (D == 2 && n >= 20000) ? 8 : 4; }
+  static int weno_tile(long long n) { return (D == 2 && n >= launch_params().tile8_min_cells) ? 8 : 4; }
   using CP = PredCfg<D, M, PDE>;
   using CF = FluxCfg<D, M, PDE>;
   // a quarter of the cells (face items) per CTA when the full-size CTAs would give fewer than two
@@ -50,7 +50,7 @@ struct Launch {
   static int flux_ctas(const HotArgs& a) { return flux_ctas_of<CF>(a); }
   static int update_ctas(const HotArgs& a) { return a.na > 0 ? (a.na + 127) / 128 : 0; }
   static int project_ctas(int nv) { return nv > 0 ? (int)(((long long)nv * V + 127) / 128) : 0; }
-  static bool small(int ctas) { return ctas < 2 * sm_count(); }
+  static bool small(int ctas) { return ctas < launch_params().small_ctas_per_sm * sm_count(); }
 
   // the dynamic shared memory attribute, once per kernel (request-loop workers launch concurrently)
   template <class K>

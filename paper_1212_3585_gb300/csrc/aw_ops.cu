@@ -1,4 +1,7 @@
-// aw_ops.cu -- selects the compiled hot-kernel instantiation for a configuration.
+// aw_ops.cu -- selects the compiled hot-kernel instantiation for a configuration; holds the
+// process-wide launch-shape rules.
+#include <atomic>
+
 #include "aw_ops.h"
 
 namespace aw {
@@ -12,6 +15,23 @@ HotOps ops_2_3_1();
 HotOps ops_2_2_2();
 HotOps ops_2_3_2();
 HotOps ops_3_2_2();
+
+static std::atomic<long long> g_pass_min_cells{4096}, g_tile8_min_cells{20000};
+static std::atomic<int> g_small_ctas_per_sm{2};
+
+LaunchParams launch_params() {
+  LaunchParams p;
+  p.pass_min_cells = g_pass_min_cells.load();
+  p.tile8_min_cells = g_tile8_min_cells.load();
+  p.small_ctas_per_sm = g_small_ctas_per_sm.load();
+  return p;
+}
+
+void set_launch_params(const LaunchParams& p) {
+  g_pass_min_cells.store(p.pass_min_cells);
+  g_tile8_min_cells.store(p.tile8_min_cells);
+  g_small_ctas_per_sm.store(p.small_ctas_per_sm);
+}
 
 bool get_ops(int D, int M, int PDE, HotOps* out) {
   int key = D * 100 + M * 10 + PDE;

@@ -31,4 +31,15 @@ struct HotOps {
 
 // returns false when the configuration is not compiled in
 bool get_ops(int D, int M, int PDE, HotOps* out);
+
+// launch-shape rules (aw_set_launch_params): WENO by passes from pass_min_cells cells per level,
+// 2D WENO tiles of 8x8 from tile8_min_cells, quarter-size predictor/flux CTAs when the full-size
+// ones give fewer than small_ctas_per_sm CTAs per SM.  Process-wide; the results never depend on
+// them, only the speed.
+struct LaunchParams {
+  long long pass_min_cells, tile8_min_cells;
+  int small_ctas_per_sm;
+};
+LaunchParams launch_params();
+void set_launch_params(const LaunchParams& p);
 }  // namespace aw

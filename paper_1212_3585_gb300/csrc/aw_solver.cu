@@ -1506,8 +1506,9 @@ int aw_create(const aw_config* cfg, uintptr_t stream, aw_solver** out) {
     alloc((void**)&L.clist, L.n * sizeof(int32_t));
     alloc((void**)&L.tflag, L.ntd);
     alloc((void**)&L.tiles, L.ntd * sizeof(int32_t));
-    // WENO by passes from 4096 cells (on tinier levels the tiles' single launch is quicker)
-    if (weno_by_passes(s) && L.n >= 4096) {
+    // WENO by passes from 4096 cells by default (on tinier levels the tiles' single launch is
+    // quicker)
+    if (weno_by_passes(s) && L.n >= launch_params().pass_min_cells) {
       alloc((void**)&L.xmark, L.n);
       alloc((void**)&L.xslot, L.n * sizeof(int32_t));
       if (s->D == 3) {
@@ -2128,6 +2129,28 @@ int aw_totals(aw_solver* s, double* tot) {
       tot[v] += vol * acc;
     }
   }
+  return AW_OK;
+}
+
+int aw_get_launch_params(aw_launch_params* out) {
+  if (!out) AW_FAIL(AW_EINVAL, "null argument");
+  LaunchParams p = launch_params();
+  memset(out, 0, sizeof *out);
+  out->pass_min_cells = p.pass_min_cells;
+  out->tile8_min_cells = p.tile8_min_cells;
+  out->small_ctas_per_sm = p.small_ctas_per_sm;
+  return AW_OK;
+}
+
+int aw_set_launch_params(const aw_launch_params* in) {
+  if (!in) AW_FAIL(AW_EINVAL, "null argument");
+  if (in->pass_min_cells < 0 || in->tile8_min_cells < 0 || in->small_ctas_per_sm < 0 || in->small_ctas_per_sm > 64)
+    AW_FAIL(AW_EINVAL, "launch parameters out of range");
+  LaunchParams p;
+  p.pass_min_cells = in->pass_min_cells;
+  p.tile8_min_cells = in->tile8_min_cells;
+  p.small_ctas_per_sm = in->small_ctas_per_sm;
+  set_launch_params(p);
   return AW_OK;
 }
 

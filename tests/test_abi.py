@@ -48,7 +48,8 @@ def test_struct_layouts_match_header(tmp_path):
     """sizes and field offsets of the ctypes structures equal those the C compiler gives the
     header's structures"""
     structs = {"aw_config": pg.AwConfig, "aw_stats": pg.AwStats, "aw_cell": pg.AwCell,
-               "aw_srv_info": pg.AwSrvInfo, "aw_srv_summary": pg.AwSrvSummary}
+               "aw_srv_info": pg.AwSrvInfo, "aw_srv_summary": pg.AwSrvSummary,
+               "aw_launch_params": _lib.AwLaunchParams}
     lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "aderweno.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
@@ -66,3 +67,15 @@ def test_struct_layouts_match_header(tmp_path):
         assert c_layout[(cname, "size")] == ctypes.sizeof(py), cname
         for fname, _ in py._fields_:
             assert c_layout[(cname, fname)] == getattr(py, fname).offset, (cname, fname)
+
+
+def test_launch_params_roundtrip_without_gpu():
+    """the launch-shape rules are host state: read, changed, rejected when out of range, restored"""
+    before = pg.get_launch_params()
+    assert before == {"pass_min_cells": 4096, "tile8_min_cells": 20000, "small_ctas_per_sm": 2}
+    pg.set_launch_params(small_ctas_per_sm=0, pass_min_cells=0)
+    assert pg.get_launch_params() == {"pass_min_cells": 0, "tile8_min_cells": 20000, "small_ctas_per_sm": 0}
+    with pytest.raises(pg.AwError):
+        pg.set_launch_params(small_ctas_per_sm=65)
+    pg.set_launch_params(**before)
+    assert pg.get_launch_params() == before
