@@ -92,8 +92,8 @@ __device__ __forceinline__ void warp0_compact(int ncand, Pred pred, int16_t* lis
 // staged in shared memory through the boundary map; x sweeps run on every box line that feeds
 // an active cell of the tile, then y (and z) sweeps on the active cells only (compacted work
 // lists, Eqs. eqn.weno, eqn.weno.y, eqn.weno.z).  Output: WENO dofs per active cell.  Used for
-// levels below 4096 cells and for batched launches; larger levels of a single solve run the same
-// reconstructions by passes (k_weno_x/y, k_weno3_x/y/z below), without the halo recomputation.
+// levels below 4096 cells (by default); larger levels run the same reconstructions by passes
+// (k_weno_x/y, k_weno3_x/y/z below, and their batched forms), without the halo recomputation.
 // ------------------------------------------------------------------------------------------
 template <int D, int M, int PDE, int TS>
 struct WenoCfg {
@@ -267,9 +267,9 @@ __global__ void __launch_bounds__(256) k_weno(const __grid_constant__ HotArgs a)
 // inflow state.
 // ------------------------------------------------------------------------------------------
 template <int M, int PDE>
-__global__ void __launch_bounds__(128) k_weno_x(const __grid_constant__ HotArgs a) {
+__device__ __forceinline__ void weno_x_body(const HotArgs& a, const int bid) {
   constexpr int D = 2, N = M + 1, V = nvars(D, PDE), W = 2 * M + 1;
-  const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long it = (long long)bid * blockDim.x + threadIdx.x;
   if (it >= (long long)a.nxs * V) return;
   const int slot = (int)(it / V), v = (int)(it % V);
   const LevelView& L = a.lv;
@@ -296,12 +296,17 @@ __global__ void __launch_bounds__(128) k_weno_x(const __grid_constant__ HotArgs 
   for (int p = 0; p < N; p++) dst[p] = o[p];
 }
 
+template <int M, int PDE>
+__global__ void __launch_bounds__(128) k_weno_x(const __grid_constant__ HotArgs a) {
+  weno_x_body<M, PDE>(a, blockIdx.x);
+}
+
 // 3D: the same by three passes -- x sweeps of the rows feeding the y sweeps, y sweeps of the
 // cells feeding the z sweeps, z sweeps of the active cells -- with the same exact ghost mapping
 template <int M, int PDE>
-__global__ void __launch_bounds__(128) k_weno3_x(const __grid_constant__ HotArgs a) {
+__device__ __forceinline__ void weno3_x_body(const HotArgs& a, const int bid) {
   constexpr int D = 3, N = M + 1, V = nvars(D, PDE), W = 2 * M + 1;
-  const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long it = (long long)bid * blockDim.x + threadIdx.x;
   if (it >= (long long)a.nxs * V) return;
   const int slot = (int)(it / V), v = (int)(it % V);
   const LevelView& L = a.lv;
@@ -329,9 +334,14 @@ __global__ void __launch_bounds__(128) k_weno3_x(const __grid_constant__ HotArgs
 }
 
 template <int M, int PDE>
-__global__ void __launch_bounds__(128) k_weno3_y(const __grid_constant__ HotArgs a) {
+__global__ void __launch_bounds__(128) k_weno3_x(const __grid_constant__ HotArgs a) {
+  weno3_x_body<M, PDE>(a, blockIdx.x);
+}
+
+template <int M, int PDE>
+__device__ __forceinline__ void weno3_y_body(const HotArgs& a, const int bid) {
   constexpr int D = 3, N = M + 1, V = nvars(D, PDE), W = 2 * M + 1;
-  const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long it = (long long)bid * blockDim.x + threadIdx.x;
   if (it >= (long long)a.nys * N * V) return;
   const int ysl = (int)(it / (N * V)), rem = (int)(it % (N * V)), p = rem / V, v = rem % V;
   const LevelView& L = a.lv;
@@ -364,9 +374,14 @@ __global__ void __launch_bounds__(128) k_weno3_y(const __grid_constant__ HotArgs
 }
 
 template <int M, int PDE>
-__global__ void __launch_bounds__(128) k_weno3_z(const __grid_constant__ HotArgs a) {
+__global__ void __launch_bounds__(128) k_weno3_y(const __grid_constant__ HotArgs a) {
+  weno3_y_body<M, PDE>(a, blockIdx.x);
+}
+
+template <int M, int PDE>
+__device__ __forceinline__ void weno3_z_body(const HotArgs& a, const int bid) {
   constexpr int D = 3, N = M + 1, V = nvars(D, PDE), W = 2 * M + 1, NSP = N * N * N;
-  const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long it = (long long)bid * blockDim.x + threadIdx.x;
   if (it >= (long long)a.na * N * N * V) return;
   const int k = (int)(it / (N * N * V)), rem = (int)(it % (N * N * V)), pq = rem / V, v = rem % V;
   const int p = pq % N, q = pq / N;
@@ -400,9 +415,14 @@ __global__ void __launch_bounds__(128) k_weno3_z(const __grid_constant__ HotArgs
 }
 
 template <int M, int PDE>
-__global__ void __launch_bounds__(128) k_weno_y(const __grid_constant__ HotArgs a) {
+__global__ void __launch_bounds__(128) k_weno3_z(const __grid_constant__ HotArgs a) {
+  weno3_z_body<M, PDE>(a, blockIdx.x);
+}
+
+template <int M, int PDE>
+__device__ __forceinline__ void weno_y_body(const HotArgs& a, const int bid) {
   constexpr int D = 2, N = M + 1, V = nvars(D, PDE), W = 2 * M + 1, NSP = N * N;
-  const long long it = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long it = (long long)bid * blockDim.x + threadIdx.x;
   if (it >= (long long)a.na * N * V) return;
   const int k = (int)(it / (N * V)), rem = (int)(it % (N * V)), p = rem / V, v = rem % V;
   const LevelView& L = a.lv;
@@ -432,6 +452,11 @@ __global__ void __launch_bounds__(128) k_weno_y(const __grid_constant__ HotArgs 
   double* dst = a.wh + ((long long)k * V + v) * NSP;
 #pragma unroll
   for (int q = 0; q < N; q++) dst[p + N * q] = o[q];
+}
+
+template <int M, int PDE>
+__global__ void __launch_bounds__(128) k_weno_y(const __grid_constant__ HotArgs a) {
+  weno_y_body<M, PDE>(a, blockIdx.x);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -952,6 +977,20 @@ __global__ void k_update_batch(const __grid_constant__ HotBatch b) {
   const int m = batch_member(b, blockIdx.x);
   update_body<D, M, PDE>(b.a[m], blockIdx.x - b.start[m]);
 }
+
+// WENO by passes over the members whose level has them (the same bodies)
+#define AW_BATCHED_PASS(kname, bname)                                              \
+  template <int M, int PDE>                                                        \
+  __global__ void __launch_bounds__(128) kname(const __grid_constant__ HotBatch b) { \
+    const int m = batch_member(b, blockIdx.x);                                     \
+    bname<M, PDE>(b.a[m], blockIdx.x - b.start[m]);                                \
+  }
+AW_BATCHED_PASS(k_weno_x_batch, weno_x_body)
+AW_BATCHED_PASS(k_weno_y_batch, weno_y_body)
+AW_BATCHED_PASS(k_weno3_x_batch, weno3_x_body)
+AW_BATCHED_PASS(k_weno3_y_batch, weno3_y_body)
+AW_BATCHED_PASS(k_weno3_z_batch, weno3_z_body)
+#undef AW_BATCHED_PASS
 
 // virtual children of every member from their mothers' predictor at tau = sub / r
 template <int D, int M, int PDE>

@@ -21,8 +21,8 @@ inline int sm_count() {
 
 template <int D, int M, int PDE>
 struct Launch {
-  // WENO tiles, for levels below 4096 cells and batched launches (larger levels of a single solve
-  // run the WENO by passes, k_weno_x/y and k_weno3_x/y/z): 8x8 cells in 2D (6 sweep passes of 256
+  // WENO tiles, for levels below the passes threshold (4096 cells by default; larger levels run the
+  // WENO by passes, k_weno_x/y and k_weno3_x/y/z, batched or not): 8x8 cells in 2D (6 sweep passes of 256
   // threads per 64 cells, against 2 per 16 with 4x4 tiles, whose x pass fills 160 of 256 lanes),
   // 4x4 on levels below 20,000 cells so that their tiles still spread over the SMs; 4x4x4 in 3D
   // (shared memory)
@@ -157,7 +157,42 @@ struct Launch {
     return 1;
   }
   // members whose level has 8x8 tiles and members with 4x4 tiles run as two launches
+  // WENO by passes for the members whose level has them (one launch per pass over those members)
+  template <class K>
+  static int pass_b(HotBatch& b, K kernel, long long (*items)(const HotArgs&), cudaStream_t st) {
+    const int blocks = fill_starts(b, [&](const HotArgs& a) { return (int)((items(a) + 127) / 128); });
+    if (!blocks) return 0;
+    kernel<<<blocks, 128, 0, st>>>(b);
+    return 1;
+  }
+  static int weno_passes_b(HotBatch& b, cudaStream_t st) {
+    constexpr int N = M + 1;
+    if constexpr (D == 2) {
+      int n = pass_b(b, k_weno_x_batch<M, PDE>, [](const HotArgs& a) { return (long long)a.nxs * V; }, st);
+      return n + pass_b(b, k_weno_y_batch<M, PDE>, [](const HotArgs& a) { return (long long)a.na * N * V; }, st);
+    } else {
+      int n = pass_b(b, k_weno3_x_batch<M, PDE>, [](const HotArgs& a) { return (long long)a.nxs * V; }, st);
+      n += pass_b(b, k_weno3_y_batch<M, PDE>, [](const HotArgs& a) { return (long long)a.nys * N * V; }, st);
+      return n + pass_b(b, k_weno3_z_batch<M, PDE>, [](const HotArgs& a) { return (long long)a.na * N * N * V; }, st);
+    }
+  }
+  static bool has_passes(const HotArgs& a) { return a.xs && (D == 2 || a.ys); }
   static int weno_b(HotBatch& b, cudaStream_t st) {
+    int np = 0;
+    for (int m = 0; m < b.n; m++) np += has_passes(b.a[m]);
+    if (np == b.n) return weno_passes_b(b, st);
+    if (np > 0) {
+      HotBatch p, t;
+      p.n = t.n = 0;
+      for (int m = 0; m < b.n; m++) {
+        if (has_passes(b.a[m])) p.a[p.n++] = b.a[m];
+        else t.a[t.n++] = b.a[m];
+      }
+      return weno_passes_b(p, st) + weno_tiles_b(t, st);
+    }
+    return weno_tiles_b(b, st);
+  }
+  static int weno_tiles_b(HotBatch& b, cudaStream_t st) {
     if constexpr (D == 2) {
       bool mixed = false;
       for (int m = 1; m < b.n; m++) mixed |= b.a[m].ts != b.a[0].ts;
