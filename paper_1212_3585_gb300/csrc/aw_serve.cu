@@ -66,16 +66,18 @@ struct aw_server {
   bool any_submitted = false;
 };
 
-// Device bytes one solve of `c` needs: the dense per-level grids (exact) plus per-active arrays
-// for a quarter of the finest level's cells (the AMR meshes of these workloads stay below that)
-// and a fixed allowance for the CUDA context's share and staging buffers.
+// Device bytes one solve of `c` needs: the dense per-level grids (exact, with the row marks and
+// slot maps of the WENO by passes) plus per-active arrays for a quarter of the finest level's
+// cells (the AMR meshes of these workloads stay below that; the WENO sweep buffers counted at two
+// rows per active cell) and a fixed allowance for the CUDA context's share and staging buffers.
 static int64_t footprint_bytes(const aw_config& c) {
   int V = aw::nvars(c.dim, c.pde), N = c.M + 1;
   int64_t nsp = 1;
   for (int a = 0; a < c.dim; a++) nsp *= N;
   int64_t nst = nsp * N;
-  int64_t dense_per_cell = 8 * V + 4 + 8 + 4 * 5;
-  int64_t active_per_cell = 8 * (V * nsp + V * nst + 4 * c.dim * V);
+  int64_t dense_per_cell = 8 * V + 4 + 8 + 4 * 5 + 5 * (c.dim == 3 ? 2 : 1);
+  int64_t sweeps = 2 * 8 * V * N * (c.dim == 3 ? 1 + N : 1);
+  int64_t active_per_cell = 8 * (V * nsp + V * nst + 4 * c.dim * V) + sweeps;
   int64_t total = 0, finest = 0, rr = 1;
   int r = c.lmax > 0 ? c.refine_factor : 1;
   for (int l = 0; l <= c.lmax; l++) {
