@@ -73,6 +73,27 @@ def test_free_stream_uniform_and_amr():
         assert np.allclose(u1[act], cons, rtol=1e-13, atol=1e-13)
 
 
+def test_lts_level0_step_not_limited_by_refinement():
+    """level l takes r^l steps per level-0 step, so refining cells of a constant state (cells
+    r^l times smaller) leaves the level-0 time step unchanged (Eq. eqn.update.criterion)"""
+    q = [1.1, 0.4, -0.3, 0.9]
+    for lmax in (1, 2):
+        cfg = oracle.make_cfg(dim=2, M=2, n=(9, 9, 1), lo=(0, 0, 0), hi=(1, 1.5, 1), lmax=lmax, r=3,
+                              auto_regrid=0)
+        o = oracle.Oracle(cfg)
+        o.set_initial(oracle.IC_CONST, q, nrefine=0)
+        dt_uniform = o.compute_dt()
+        for lv in range(lmax):
+            meta, _ = o.cells()
+            act = np.flatnonzero((meta[:, 0] == lv) & (meta[:, 1] == 0))
+            flags = np.zeros(len(meta), dtype=np.int8)
+            flags[act[len(act) // 2:len(act) // 2 + 3]] = 1
+            o.regrid_with_flags(flags, init_mode=1)
+        _, _, act = o.counts()
+        assert all(a > 0 for a in act)
+        assert o.compute_dt() == pytest.approx(dt_uniform, rel=1e-14)
+
+
 @pytest.mark.parametrize("M,lmax", [(2, 1), (3, 2)])
 def test_conservation_amr_lts_periodic(M, lmax):
     cfg = oracle.make_cfg(dim=2, M=M, n=(12, 12, 1), lo=(0, 0, 0), hi=(10, 10, 1), lmax=lmax, r=3,
