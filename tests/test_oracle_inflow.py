@@ -8,6 +8,9 @@ interior trace).
 * A supersonic channel: a contact discontinuity enters with the inflow state and leaves the
   channel filled with it (a transmissive boundary would keep the initial state).
 * An inflow state equal to the adjacent constant state gives the transmissive solution.
+* The reconstruction next to an inflow (transmissive) face is the 1D WENO of the stencil line
+  extended by the inflow state (the nearest cell).  The tests above cannot see which ghost
+  state a cell's stencil holds: WENO puts all weight on the stencil inside the constant state.
 """
 import numpy as np
 import pytest
@@ -69,3 +72,32 @@ def test_inflow_of_the_boundary_state_equals_transmissive():
         runs.append(o.cells())
     assert np.array_equal(runs[0][0], runs[1][0])
     assert np.max(np.abs(runs[0][1] - runs[1][1])) < 1e-14
+
+
+@pytest.mark.parametrize("M", [2, 3])
+@pytest.mark.parametrize("axis", [0, 1])
+def test_boundary_reconstruction_sees_the_ghost_states(M, axis):
+    """the WENO polynomial of a cell within M of a boundary is the 1D WENO of its stencil line
+    with the ghost states of the reading: the inflow state beyond an inflow face, the nearest
+    cell (clamp) beyond a transmissive one.  The data vary only along `axis`, so the sweep along
+    the other axis returns its constant line exactly."""
+    n, nt, c_in = 9, 3, 2.5
+    I, T, P = oracle.BC_INFLOW, oracle.BC_TRANSMISSIVE, oracle.BC_PERIODIC
+    bc = [I, T, P, P, P, P] if axis == 0 else [P, P, I, T, P, P]
+    ext = (n, nt, 1) if axis == 0 else (nt, n, 1)
+    cfg = oracle.make_cfg(dim=2, pde=oracle.PDE_LINADV, M=M, n=ext, lo=(0, 0, 0), hi=(ext[0], ext[1], 1), bc=bc,
+                          adv=(1.0, 1.0, 0.0), inflow=(c_in,))
+    o = oracle.Oracle(cfg)
+    o.set_initial(oracle.IC_CONST, [0.0], nrefine=0)
+    prof = np.random.default_rng(20 + M).uniform(0.5, 1.5, n)
+    u = np.tile(prof, (nt, 1)) if axis == 0 else np.tile(prof[:, None], (1, nt))
+    o.set_cell_averages(u.reshape(-1, 1))
+    o.weno_level(0)
+    N = M + 1
+    wh = o.internal(0, 0).reshape(ext[1], ext[0], N, N)      # [j][i][q][p], nodal
+    line = np.concatenate([np.full(M, c_in), prof, np.full(M, prof[-1])])
+    for c in list(range(M)) + list(range(n - M, n)):
+        expect = oracle.weno1d(M, line[c:c + 2 * M + 1])
+        for t in range(nt):
+            w = wh[t, c] if axis == 0 else wh[c, t].T        # rows: the other axis' nodes
+            assert np.array_equal(w, np.tile(expect, (N, 1))), (c, t)
