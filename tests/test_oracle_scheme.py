@@ -274,6 +274,49 @@ def test_coarse_fine_patch_design_order(M, lo_order, ly):
         assert min(orders) > lo_order, (norm, e, orders)
 
 
+def _patch3_errors(n, t_end):
+    """3D counterpart of _patch_errors: sin 2 pi (x + y + z) advected by (1, 1/2, 1/4) on a
+    periodic n^3 base grid whose middle cube [1/4, 3/4)^3 is refined once (r = 3, M = 2, local
+    time stepping).  Returns the L2 and max-norm errors over the active cells and the change of
+    the total."""
+    a = (1.0, 0.5, 0.25)
+    cfg = oracle.make_cfg(dim=3, pde=oracle.PDE_LINADV, M=2, n=(n, n, n), lo=(0, 0, 0), hi=(1, 1, 1), adv=a,
+                          lmax=1, r=3, auto_regrid=0, cfl=0.9)
+    o = oracle.Oracle(cfg, threads=8)
+    o.set_initial(oracle.IC_FOURIER, [0.0, 1, 0, 1, 1, 1, 1.0, 0.0], nrefine=0)
+    meta, _ = o.cells()
+    mid = lambda c: (c >= n // 4) & (c < 3 * n // 4)
+    o.regrid_with_flags((mid(meta[:, 2]) & mid(meta[:, 3]) & mid(meta[:, 4])).astype(np.int8), init_mode=1)
+    tot0 = o.totals()[0]
+    while o.t < t_end:
+        rc, _ = o.step(t_end)
+        assert rc == 0
+    meta, u = o.cells()
+    act = meta[:, 1] == 0
+    assert np.count_nonzero(meta[act, 0] == 1) == (3 * n // 2) ** 3
+    h = (1.0 / n) / 3.0 ** meta[act, 0]
+    x, w = gl01(6)
+    # the box average of sin 2 pi (x + y + z) is the imaginary part of the product over the axes
+    # of the averages of exp(2 pi i x_a)
+    ex = np.ones(np.count_nonzero(act), dtype=complex)
+    for b in range(3):
+        xa = (meta[act, 2 + b] * h)[:, None] + x[None, :] * h[:, None] - a[b] * t_end
+        ex *= np.sum(w[None, :] * np.exp(2j * np.pi * xa), axis=1)
+    err = u[act, 0] - ex.imag
+    return math.sqrt(np.sum(err ** 2 * h ** 3)), np.max(np.abs(err)), o.totals()[0] - tot0
+
+
+def test_coarse_fine_patch_3d():
+    """coarse/fine faces with two transverse directions, 3D memory variables, projection and
+    averaging over r^3 children: the total is conserved and both norms keep the design order 3
+    (measured from 8^3 to 16^3: 3.03 in L2, 3.24 in the max norm)"""
+    e = [_patch3_errors(n, 0.25) for n in (8, 16)]
+    for norm in (0, 1):
+        order = math.log(e[0][norm] / e[1][norm], 2)
+        assert order > 2.7, (norm, e, order)
+    assert max(abs(e[0][2]), abs(e[1][2])) < 1e-13
+
+
 def _linadv_err(M, n, t_end):
     cfg = oracle.make_cfg(dim=2, pde=oracle.PDE_LINADV, M=M, n=(n, n, 1), lo=(0, 0, 0), hi=(1, 1, 1),
                           adv=(1.0, 1.0, 0.0))
