@@ -4,8 +4,8 @@ result itself against the exact solution:
   * Sod's shock tube as a planar strip along x and along y, with one AMR level and local time
     stepping, Rusanov and Osher fluxes (exact Riemann solution);
   * the linear GLM cleaning wave of MHD-GLM (d'Alembert's solution for B_x and psi);
-  * linear advection across a fixed refined patch of cells twice as high as wide (the exact
-    translated wave, max norm).
+  * linear advection across a fixed refined patch of cells twice as high as wide, and across a
+    refined cube in 3D (the exact translated wave, max norm).
 
 Each step is compared with the oracle within the normwise tolerance, on identical meshes.
 """
@@ -81,3 +81,26 @@ def test_anisotropic_coarse_fine_patch():
     ex = np.sum(w[None, :, None] * w[None, None, :] * np.sin(2 * np.pi * (X + 2 * Y / ly)), axis=(1, 2))
     # the oracle's max-norm error here is 2.02e-3 (24 cells, M=3)
     assert np.max(np.abs(u[act, 0] - ex)) < 2.2e-3
+
+
+def test_coarse_fine_patch_3d():
+    n, a, t_end = 12, (1.0, 0.5, 0.25), 0.25
+    p = Pair(dim=3, pde="linadv", M=2, n=(n, n, n), r=3, lmax=1, cfl=0.9, adv=a)
+    p.init("fourier", [0.0, 1, 0, 1, 1, 1, 1.0, 0.0], passes=0)
+    meta, _ = p.o.cells()
+    mid = lambda c: (c >= n // 4) & (c < 3 * n // 4)
+    flags = (mid(meta[:, 2]) & mid(meta[:, 3]) & mid(meta[:, 4])).astype(np.int8)
+    p.o.regrid_with_flags(flags, init_mode=1)
+    p.g.regrid_with_flags(flags, init_mode=1)
+    p.check_cells(tol=1e-12)
+    advance(p, t_end, regrid=False)
+    meta, u = p.g.cells()
+    act = meta[:, 1] == 0
+    h = (1.0 / n) / 3.0 ** meta[act, 0]
+    x, w = gl01(6)
+    ex = np.ones(np.count_nonzero(act), dtype=complex)
+    for b in range(3):
+        xa = (meta[act, 2 + b] * h)[:, None] + x[None, :] * h[:, None] - a[b] * t_end
+        ex *= np.sum(w[None, :] * np.exp(2j * np.pi * xa), axis=1)
+    # the oracle's max-norm error here is 1.91e-2 (12^3, M=2)
+    assert np.max(np.abs(u[act, 0] - ex.imag)) < 2.1e-2
