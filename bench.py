@@ -306,18 +306,46 @@ def run_efficiency(args):
     return 0
 
 
+def oracle_sample(ocfg, ic, params, steps, sample):
+    """The FP64 CPU oracle as it stands on all host cores: cell updates per second over `steps`
+    level-0 steps after the initial condition and its refinement passes"""
+    import oracle
+    threads = os.cpu_count() or 1
+    o = oracle.Oracle(ocfg, threads=threads)
+    o.set_initial(ic, params)
+    n0 = o.updates()[0]
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        rc, _ = o.step()
+        if rc != 0:
+            raise RuntimeError(f"oracle step failed ({rc})")
+    el = time.perf_counter() - t0
+    n = o.updates()[0] - n0
+    return {"value": n / el, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+            "cell_updates": int(n), "seconds": el}
+
+
 def run_configs(args):
     """Throughput of the other configurations (one JSON line each, device time with CUDA events on
     the solver's stream, after a warm-up solve): the vortex at 32^2 (20 steps) and its labelled
     scaled variants at 1024^2 and 2048^2, the 3D explosion (64^3 base, l_max = 2) on a time-boxed
-    sample of level-0 steps after the initial refinement, and the MHD Orszag-Tang run to t = 0.5."""
+    sample of level-0 steps after the initial refinement, and the MHD Orszag-Tang run to t = 0.5.
+    Unless --no-cpu-baseline, each line is followed by the oracle's rate on a bounded sample of the
+    same configuration (host cores, stated in the line)."""
     import numpy as np
     import torch
     import aw_inputs
+    import oracle
     import paper_1212_3585_gb300 as pg
     torch.cuda.set_device(0)
     stream = torch.cuda.current_stream()
     names = ["weno", "predictor", "face_flux", "update", "projection"]
+
+    def cpu(name, ocfg, ic, params, steps, sample):
+        if args.no_cpu_baseline:
+            return
+        print(json.dumps({"config": name, "cpu_baseline": oracle_sample(ocfg, ic, params, steps, sample)}),
+              flush=True)
 
     def measure(name, cfg, ic, params, steps=None, t_end=None, flops=None):
         s = pg.Solver(cfg, stream.cuda_stream)
@@ -362,8 +390,13 @@ def run_configs(args):
     for n, label in ((32, "vortex 32^2 (configuration)"), (1024, "vortex 1024^2 (scaled variant)"),
                      (2048, "vortex 2048^2 (scaled variant)")):
         cfg = pg.make_config(dim=2, M=2, n=(n, n, 1), lo=(0, 0, 0), hi=(10, 10, 1), bc=P, cfl=0.9)
-        measure(f"{label}: 2D Euler M=2 periodic [0,10]^2, CFL 0.9, 20 steps", cfg, pg.AW_IC_VORTEX, vortex,
-                steps=20, flops=f2)
+        name = f"{label}: 2D Euler M=2 periodic [0,10]^2, CFL 0.9, 20 steps"
+        measure(name, cfg, pg.AW_IC_VORTEX, vortex, steps=20, flops=f2)
+        m = min(n, 1024)
+        cpu(name, oracle.make_cfg(dim=2, M=2, n=(m, m, 1), lo=(0, 0, 0), hi=(10, 10, 1), cfl=0.9), oracle.IC_VORTEX,
+            vortex, 20 if n == 32 else 1,
+            "all 20 steps" if n == 32 else f"one level-0 step of the same vortex on {m}^2 (a uniform grid costs "
+                                          "the same per cell update at any size)")
     # configuration 1 again through the latency path (device-side dt, CUDA graph of 20 steps):
     # the end time is the host path's time after 20 steps, so exactly the same 20 steps are taken
     cfg = pg.make_config(dim=2, M=2, n=(32, 32, 1), lo=(0, 0, 0), hi=(10, 10, 1), bc=P, cfl=0.9)
@@ -394,14 +427,24 @@ def run_configs(args):
     cfg = pg.make_config(dim=2, pde=pg.AW_PDE_MHD_GLM, M=3, n=(128, 128, 1), lo=(0, 0, 0),
                          hi=(2 * np.pi, 2 * np.pi, 1), bc=P, r=3, lmax=1, gamma=5.0 / 3.0, c_h=2.0, cfl=0.6,
                          auto_regrid=1)
-    measure("MHD-GLM Orszag-Tang type: M=3, base 128^2 on [0,2pi]^2, r=3, l_max=1, CFL 0.6, t_end=0.5", cfg,
-            pg.AW_IC_OT, [], t_end=0.5, flops=predictor_flops_per_cell(2, 3, 9, 4, MHD_FLUX_FLOPS_2D))
+    name = "MHD-GLM Orszag-Tang type: M=3, base 128^2 on [0,2pi]^2, r=3, l_max=1, CFL 0.6, t_end=0.5"
+    measure(name, cfg, pg.AW_IC_OT, [], t_end=0.5, flops=predictor_flops_per_cell(2, 3, 9, 4, MHD_FLUX_FLOPS_2D))
+    cpu(name, oracle.make_cfg(dim=2, pde=oracle.PDE_MHD, M=3, n=(128, 128, 1), lo=(0, 0, 0),
+                              hi=(2 * np.pi, 2 * np.pi, 1), r=3, lmax=1, gamma=5.0 / 3.0, c_h=2.0, cfl=0.6),
+        oracle.IC_OT, [], 2, "the first 2 level-0 steps")
     cfg = pg.make_config(dim=3, M=2, n=(64, 64, 64), lo=(-1, -1, -1), hi=(1, 1, 1), bc=T, r=3, lmax=2, cfl=0.6,
                          auto_regrid=1)
     f3 = predictor_flops_per_cell(3, 2, 5, 3, EULER_FLUX_FLOPS[3])
-    measure(f"3D explosion: Euler M=2, base 64^3 on [-1,1]^3, r=3, l_max=2, CFL 0.6; sample: the first "
-            f"{args.cfg3_steps} level-0 steps after the initial refinement", cfg, pg.AW_IC_EXPLOSION,
-            aw_inputs.EXPLOSION, steps=args.cfg3_steps, flops=f3)
+    name = (f"3D explosion: Euler M=2, base 64^3 on [-1,1]^3, r=3, l_max=2, CFL 0.6; sample: the first "
+            f"{args.cfg3_steps} level-0 steps after the initial refinement")
+    measure(name, cfg, pg.AW_IC_EXPLOSION, aw_inputs.EXPLOSION, steps=args.cfg3_steps, flops=f3)
+    # the oracle cannot hold the 576^3 finest level on the host: the same depth, r, M and CFL on a
+    # 4^3 base (per cell update the oracle's cost does not depend on the base)
+    cpu(name, oracle.make_cfg(dim=3, M=2, n=(4, 4, 4), lo=(-1, -1, -1), hi=(1, 1, 1), bc=oracle.BC_TRANSMISSIVE,
+                              r=3, lmax=2, cfl=0.6),
+        oracle.IC_EXPLOSION, aw_inputs.EXPLOSION, 1,
+        "the first level-0 step after the initial refinement of the same explosion on a 4^3 base (same r, l_max, "
+        "M, CFL)")
     return 0
 
 
