@@ -13,7 +13,9 @@
   * Design order of accuracy on the isentropic vortex of Sec. 4.1 with its exact solution
     (advection by (1,1)): observed L2 order of rho close to M+1.
   * Design order in the max norm of linear advection across a fixed refined patch, where the
-    errors of coarse/fine faces (Sec. 3.1.3) concentrate.
+    errors of coarse/fine faces (Sec. 3.1.3) concentrate: in 2D on square and on anisotropic
+    cells, and in 3D with conservation of the total.
+  * Local time stepping leaves the level-0 step of a refined constant state unchanged.
   * The errors the paper prints for the vortex on its coarse uniform grids (Table tab.conv2,
     tests/golden/tab_conv2_uniform.txt).
 """
