@@ -1,0 +1,118 @@
+"""The C ABI's argument checks, on the CPU: every call below is rejected with AW_EINVAL and a
+message naming the problem before it touches the device (no GPU is needed)."""
+import ctypes as C
+
+import pytest
+
+import paper_1212_3585_gb300 as pg
+from paper_1212_3585_gb300 import _lib
+
+P, T, R, I = pg.AW_BC_PERIODIC, pg.AW_BC_TRANSMISSIVE, pg.AW_BC_REFLECTIVE, pg.AW_BC_INFLOW
+
+
+def create_error(cfg):
+    L = _lib.load()
+    h = C.c_void_p()
+    rc = L.aw_create(C.byref(cfg), 0, C.byref(h))
+    return rc, L.aw_last_error().decode(), h.value
+
+
+BAD_CONFIGS = [
+    (dict(dim=1), "dim"),
+    (dict(dim=4), "dim"),
+    (dict(M=0), "M must"),
+    (dict(M=4), "M must"),
+    (dict(pde=3), "unknown pde"),
+    (dict(pde=-1), "unknown pde"),
+    (dict(lmax=-1), "lmax"),
+    (dict(lmax=99), "lmax"),
+    (dict(lmax=1, r=1), "refine_factor"),
+    (dict(lmax=1, M=3, r=2), "refine_factor"),        # r >= M (the child box holds a stencil)
+    (dict(lmax=1, r=99), "refine_factor"),
+    (dict(n=(0, 8, 1)), "grid size"),
+    (dict(n=(8, -1, 1)), "grid size"),
+    (dict(dim=3, n=(8, 8, 0)), "grid size"),
+    (dict(lo=(0, 1, 0), hi=(1, 1, 1)), "empty domain on axis 1"),
+    (dict(lo=(2, 0, 0), hi=(1, 1, 1)), "empty domain on axis 0"),
+    (dict(bc=[P, T, P, P, P, P]), "pair up on axis 0"),
+    (dict(bc=[T, T, T, P, T, T]), "pair up on axis 1"),
+    (dict(bc=[T, T, T, T, 7, T], dim=3, n=(8, 8, 8)), "unknown boundary condition 7"),
+    (dict(bc=[R, T, P, P, P, P], pde=pg.AW_PDE_MHD_GLM), "reflective"),
+    (dict(cfl=0.0), "cfl"),
+    (dict(cfl=float("nan")), "cfl"),
+    (dict(flux=5), "unknown numerical flux"),
+    (dict(flux=pg.AW_FLUX_OSHER, pde=pg.AW_PDE_MHD_GLM), "Osher"),
+    (dict(dim=3, M=3, n=(8, 8, 8)), "not compiled in"),
+    (dict(dim=3, pde=pg.AW_PDE_MHD_GLM, n=(8, 8, 8)), "not compiled in"),
+    (dict(dim=3, M=1, n=(8, 8, 8)), "not compiled in"),
+]
+
+
+@pytest.mark.parametrize("kw,msg", BAD_CONFIGS, ids=[m + str(i) for i, (_, m) in enumerate(BAD_CONFIGS)])
+def test_create_rejects(kw, msg):
+    rc, err, h = create_error(pg.make_config(**kw))
+    assert rc == _lib.AW_EINVAL and msg in err, (rc, err)
+    assert not h                                          # no solver is handed out
+
+
+def test_create_rejects_null_arguments():
+    L = _lib.load()
+    h = C.c_void_p()
+    assert L.aw_create(None, 0, C.byref(h)) == _lib.AW_EINVAL
+    cfg = pg.make_config()
+    assert L.aw_create(C.byref(cfg), 0, None) == _lib.AW_EINVAL
+    assert "null argument" in L.aw_last_error().decode()
+
+
+def test_calls_on_a_null_solver():
+    L = _lib.load()
+    st = pg.AwStats()
+    d = C.c_double(0.0)
+    checks = [
+        L.aw_step(None, 1.0, C.byref(st)),
+        L.aw_step_dt(None, 0.1, C.byref(st)),
+        L.aw_advance_to(None, 1.0, C.byref(st)),
+        L.aw_advance_graph(None, 1.0, 4, C.byref(st)),
+        L.aw_compute_dt(None, C.byref(d)),
+        L.aw_set_initial(None, pg.AW_IC_CONST, None, 0, 0),
+        L.aw_set_cell_averages(None, None, 0),
+    ]
+    assert all(rc == _lib.AW_EINVAL for rc in checks), checks
+
+
+def test_batch_rejects_bad_member_lists():
+    L = _lib.load()
+    st = (pg.AwStats * 1)()
+    rc = (C.c_int32 * 1)()
+    none = (C.c_void_p * 1)(None)
+    assert L.aw_advance_batch(none, 0, 1.0, 0, st, rc) == _lib.AW_EINVAL
+    assert L.aw_advance_batch(none, pg.AW_BATCH_MAX + 1, 1.0, 0, st, rc) == _lib.AW_EINVAL
+    assert L.aw_advance_batch(none, 1, 1.0, 0, st, rc) == _lib.AW_EINVAL
+    assert "null solver 0" in L.aw_last_error().decode()
+
+
+def test_server_rejects_bad_arguments():
+    L = _lib.load()
+    h = C.c_void_p()
+    for budget, workers in ((0, 1), (-5, 1), (1 << 30, 0), (1 << 30, 257)):
+        assert L.aw_srv_create(budget, workers, C.byref(h)) == _lib.AW_EINVAL
+    assert L.aw_srv_create(1 << 30, 1, None) == _lib.AW_EINVAL
+    assert "bad server arguments" in L.aw_srv_last_error().decode()
+    assert L.aw_srv_set_batching(None, 2) == _lib.AW_EINVAL
+    assert "max_batch" in L.aw_srv_last_error().decode()
+
+
+def test_noalloc_step_rejects_before_the_device():
+    L = _lib.load()
+    buf = (C.c_double * 4)()
+    cfg = pg.make_config(n=(16, 16, 1))
+    # cell count that does not match the grid
+    assert L.aw_cfl_dt_noalloc(C.byref(cfg), buf, 100, buf, 0) == _lib.AW_EINVAL
+    assert "does not match" in L.aw_last_error().decode()
+    # a grid beyond the static scratch (8192 blocks of 256 cells)
+    big = pg.make_config(n=(2048, 1025, 1))
+    assert L.aw_cfl_dt_noalloc(C.byref(big), buf, 2048 * 1025, buf, 0) == _lib.AW_EINVAL
+    assert "at most 2097152 cells" in L.aw_last_error().decode()
+    assert L.aw_cfl_dt_noalloc(C.byref(cfg), None, 256, buf, 0) == _lib.AW_EINVAL
+    bad = pg.make_config(n=(16, 16, 1), cfl=-1.0)
+    assert L.aw_cfl_dt_noalloc(C.byref(bad), buf, 256, buf, 0) == _lib.AW_EINVAL
