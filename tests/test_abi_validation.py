@@ -7,7 +7,7 @@ import pytest
 import paper_1212_3585_gb300 as pg
 from paper_1212_3585_gb300 import _lib
 
-P, T, R, I = pg.AW_BC_PERIODIC, pg.AW_BC_TRANSMISSIVE, pg.AW_BC_REFLECTIVE, pg.AW_BC_INFLOW
+P, T, R = pg.AW_BC_PERIODIC, pg.AW_BC_TRANSMISSIVE, pg.AW_BC_REFLECTIVE
 
 
 def create_error(cfg):
