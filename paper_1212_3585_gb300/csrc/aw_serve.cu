@@ -89,11 +89,21 @@ static int64_t footprint_bytes(const aw_config& c) {
   return total + finest / 4 * active_per_cell + ((int64_t)64 << 20);
 }
 
+// the request's own stream; on failure the CUDA error goes into the request's message
+static int create_stream(cudaStream_t* st, std::string* err) {
+  cudaError_t e = cudaStreamCreateWithFlags(st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) return AW_OK;
+  *st = nullptr;
+  *err = std::string("stream creation failed: ") + cudaGetErrorString(e);
+  return AW_ECUDA;
+}
+
 static void run_request(aw_server* S, Request& R) {
   cudaSetDevice(S->device);
   cudaStream_t st = nullptr;
   aw_solver* sol = nullptr;
-  int rc = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess ? AW_OK : AW_ECUDA;
+  std::string err0;
+  int rc = create_stream(&st, &err0);
   if (rc == AW_OK) rc = aw_create(&R.cfg, (uintptr_t)st, &sol);
   if (rc == AW_OK)
     rc = aw_set_initial(sol, R.ic, R.params.empty() ? nullptr : R.params.data(), (int32_t)R.params.size(), -1);
@@ -107,7 +117,7 @@ static void run_request(aw_server* S, Request& R) {
     R.u.resize((size_t)n * aw::nvars(R.cfg.dim, R.cfg.pde));
     rc = aw_read_cells(sol, R.meta.data(), R.u.data(), n, &n);
   }
-  if (rc != AW_OK) R.err = aw_last_error();
+  if (rc != AW_OK) R.err = err0.empty() ? aw_last_error() : err0;
   R.cell_updates = stats.cell_updates;
   R.level0_steps = stats.level0_steps;
   aw_destroy(sol);
@@ -121,7 +131,8 @@ static void run_batch(aw_server* S, std::vector<Request*>& G) {
   cudaSetDevice(S->device);
   const int n = (int)G.size();
   cudaStream_t st = nullptr;
-  int rc0 = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess ? AW_OK : AW_ECUDA;
+  std::string err0;
+  int rc0 = create_stream(&st, &err0);
   std::vector<aw_solver*> sol(n, nullptr);
   std::vector<aw_solver*> run;
   std::vector<int> idx;
@@ -132,7 +143,7 @@ static void run_batch(aw_server* S, std::vector<Request*>& G) {
     if (rc == AW_OK)
       rc = aw_set_initial(sol[i], R.ic, R.params.empty() ? nullptr : R.params.data(), (int32_t)R.params.size(), -1);
     R.rc = rc;
-    if (rc != AW_OK) R.err = rc0 == AW_OK ? aw_last_error() : "stream creation failed";
+    if (rc != AW_OK) R.err = rc0 == AW_OK ? aw_last_error() : err0;
     else { run.push_back(sol[i]); idx.push_back(i); }
   }
   if (!run.empty()) {

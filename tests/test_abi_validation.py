@@ -116,3 +116,33 @@ def test_noalloc_step_rejects_before_the_device():
     assert L.aw_cfl_dt_noalloc(C.byref(cfg), None, 256, buf, 0) == _lib.AW_EINVAL
     bad = pg.make_config(n=(16, 16, 1), cfl=-1.0)
     assert L.aw_cfl_dt_noalloc(C.byref(bad), buf, 256, buf, 0) == _lib.AW_EINVAL
+
+
+def test_request_loop_reports_failures_without_a_device():
+    """host logic of the request loop on a machine without a usable GPU: an oversized request is
+    refused at submission, admitted requests fail alone with AW_ECUDA and a message naming the
+    CUDA error, the statistics count them, unknown ids are refused and the loop shuts down"""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present: the requests would run")
+    except ImportError:
+        pass
+    import aw_inputs
+    srv = pg.Server(hbm_budget_bytes=1 << 20, max_concurrent=2)
+    with pytest.raises(pg.AwError) as ei:
+        srv.submit(pg.make_config(M=3, n=(64, 64, 1), lmax=2, bc=T), pg.AW_IC_RP4, aw_inputs.rp4_params(1), 0.01)
+    assert ei.value.code == _lib.AW_EINVAL and "budget" in str(ei.value)
+    srv.close()
+    srv = pg.Server(hbm_budget_bytes=1 << 30, max_concurrent=2)
+    ids = [srv.submit(pg.make_config(n=(8, 8, 1)), pg.AW_IC_CONST, [1.0, 0.1, 0.2, 1.0], 0.01) for _ in range(3)]
+    srv.wait_all()
+    assert [srv.poll(i) for i in ids] == [3] * 3                # AW_REQ_FAILED
+    with pytest.raises(pg.AwError) as ei:
+        srv.result(ids[0], 4)
+    assert ei.value.code == _lib.AW_ECUDA and "stream creation failed" in str(ei.value)
+    s = srv.stats()
+    assert (s.done, s.failed, s.queued, s.running) == (0, 3, 0, 0)
+    with pytest.raises(pg.AwError):
+        srv.poll(10 ** 6)
+    srv.close()
