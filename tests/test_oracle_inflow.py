@@ -101,3 +101,26 @@ def test_boundary_reconstruction_sees_the_ghost_states(M, axis):
         for t in range(nt):
             w = wh[t, c] if axis == 0 else wh[c, t].T        # rows: the other axis' nodes
             assert np.array_equal(w, np.tile(expect, (N, 1))), (c, t)
+
+
+@pytest.mark.parametrize("M", [2])
+def test_boundary_reconstruction_sees_the_ghost_states_3d(M):
+    """the same along z in 3D: data varying only with z, an inflow face at z = 0 and a
+    transmissive one at the top; the x and y sweeps return their constant lines exactly"""
+    n, nt, c_in = 9, 3, 2.5
+    I, T, P = oracle.BC_INFLOW, oracle.BC_TRANSMISSIVE, oracle.BC_PERIODIC
+    cfg = oracle.make_cfg(dim=3, pde=oracle.PDE_LINADV, M=M, n=(nt, nt, n), lo=(0, 0, 0), hi=(nt, nt, n),
+                          bc=[P, P, P, P, I, T], adv=(0.0, 0.0, 1.0), inflow=(c_in,))
+    o = oracle.Oracle(cfg)
+    o.set_initial(oracle.IC_CONST, [0.0], nrefine=0)
+    prof = np.random.default_rng(30 + M).uniform(0.5, 1.5, n)
+    o.set_cell_averages(np.repeat(prof, nt * nt).reshape(-1, 1))     # canonical order (k, j, i)
+    o.weno_level(0)
+    N = M + 1
+    wh = o.internal(0, 0).reshape(n, nt, nt, N, N, N)                 # [k][j][i][r][q][p], nodal
+    line = np.concatenate([np.full(M, c_in), prof, np.full(M, prof[-1])])
+    for c in list(range(M)) + list(range(n - M, n)):
+        expect = oracle.weno1d(M, line[c:c + 2 * M + 1])
+        for j in range(nt):
+            for i in range(nt):
+                assert np.array_equal(wh[c, j, i], np.broadcast_to(expect[:, None, None], (N, N, N))), (c, j, i)
