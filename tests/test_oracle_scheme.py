@@ -96,7 +96,7 @@ def test_lts_level0_step_not_limited_by_refinement():
         assert o.compute_dt() == pytest.approx(dt_uniform, rel=1e-14)
 
 
-@pytest.mark.parametrize("M,lmax", [(2, 1), (3, 2)])
+@pytest.mark.parametrize("M,lmax", [(1, 1), (2, 1), (3, 2)])
 def test_conservation_amr_lts_periodic(M, lmax):
     cfg = oracle.make_cfg(dim=2, M=M, n=(12, 12, 1), lo=(0, 0, 0), hi=(10, 10, 1), lmax=lmax, r=3,
                           chi_ref=0.1, chi_rec=0.01, auto_regrid=1)
@@ -110,6 +110,46 @@ def test_conservation_amr_lts_periodic(M, lmax):
         assert rc == 0
     tot1 = o.totals()
     assert np.allclose(tot1, tot0, rtol=1e-13, atol=1e-13 * np.abs(tot0).max())
+
+
+def test_conservation_amr_lts_mhd():
+    """all nine totals of MHD-GLM (psi included) on a periodic AMR mesh with local time stepping:
+    the Orszag-Tang data (constant density, so the density indicator refines nothing) with a
+    refined block of cells kept fixed"""
+    cfg = oracle.make_cfg(dim=2, pde=oracle.PDE_MHD, M=3, n=(12, 12, 1), lo=(0, 0, 0), hi=(2 * math.pi, 2 * math.pi, 1),
+                          lmax=1, r=3, gamma=5.0 / 3.0, c_h=2.0, cfl=0.6, auto_regrid=0)
+    o = oracle.Oracle(cfg, threads=8)
+    o.set_initial(oracle.IC_OT, [], nrefine=0)
+    meta, _ = o.cells()
+    o.regrid_with_flags(((meta[:, 2] >= 2) & (meta[:, 2] < 7) & (meta[:, 3] >= 4) & (meta[:, 3] < 9)).astype(np.int8),
+                        init_mode=1)
+    _, _, act = o.counts()
+    assert act[1] == 25 * 9
+    tot0 = o.totals()
+    for _ in range(2):
+        rc, _ = o.step()
+        assert rc == 0
+    assert np.allclose(o.totals(), tot0, rtol=0, atol=1e-13 * np.abs(tot0).max())
+
+
+def test_conservation_amr_lts_3d():
+    """all five totals of the 3D explosion in a periodic box with one AMR level: a refined block
+    of 3^3 base cells, kept fixed, cuts through the jump, so coarse/fine faces of every
+    orientation carry the flow (the indicator would refine the whole of this coarse grid)"""
+    cfg = oracle.make_cfg(dim=3, M=2, n=(6, 6, 6), lo=(-1, -1, -1), hi=(1, 1, 1), bc=oracle.BC_PERIODIC, lmax=1,
+                          r=3, cfl=0.6, auto_regrid=0)
+    o = oracle.Oracle(cfg, threads=8)
+    o.set_initial(oracle.IC_EXPLOSION, [0.5, 1.0, 1.0, 0.125, 0.1], nrefine=0)
+    meta, _ = o.cells()
+    blk = lambda c: (c >= 1) & (c < 4)
+    o.regrid_with_flags((blk(meta[:, 2]) & blk(meta[:, 3]) & blk(meta[:, 4])).astype(np.int8), init_mode=1)
+    _, _, act = o.counts()
+    assert act == [216 - 27, 27 * 27]
+    tot0 = o.totals()
+    for _ in range(2):
+        rc, _ = o.step()
+        assert rc == 0
+    assert np.allclose(o.totals(), tot0, rtol=0, atol=1e-13 * np.abs(tot0).max())
 
 
 @pytest.mark.parametrize("M", [2, 3])
