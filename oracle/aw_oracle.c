@@ -1534,9 +1534,17 @@ void *orc_create(const orc_cfg *c) {
   S->d = c->dim;
   S->N = c->M + 1;
   S->P.pde = c->pde; S->P.d = c->dim; S->P.gamma = c->gamma; S->P.c_h = c->c_h; S->P.flux = c->flux;
-  if (c->flux == 1 && c->pde == PDE_MHD) { seterr("the Osher flux is available for Euler and linear advection"); return NULL; }
+  if (c->flux == 1 && c->pde == PDE_MHD) {
+    seterr("the Osher flux is available for Euler and linear advection");
+    free(S);
+    return NULL;
+  }
   for (int i = 0; i < 6; i++)
-    if (c->bc[i] == BC_REFLECTIVE && c->pde == PDE_MHD) { seterr("reflective walls are available for Euler and linear advection"); return NULL; }
+    if (c->bc[i] == BC_REFLECTIVE && c->pde == PDE_MHD) {
+      seterr("reflective walls are available for Euler and linear advection");
+      free(S);
+      return NULL;
+    }
   for (int a = 0; a < 3; a++) S->P.adv[a] = c->adv[a];
   S->V = c->pde == PDE_LINADV ? 1 : (c->pde == PDE_EULER ? c->dim + 2 : 9);
   S->P.V = S->V;
