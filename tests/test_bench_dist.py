@@ -1,4 +1,5 @@
-"""The N>1 path of bench.py: independent replicas, job time = slowest rank (gloo, CPU, 2 ranks)."""
+"""bench.py on the CPU: the N>1 path (independent replicas, job time = slowest rank; gloo, 2 ranks),
+the reference arm's JSON line and the oracle leg of --configs."""
 import os
 
 import pytest
@@ -67,3 +68,14 @@ def test_reference_arm_line(monkeypatch, capsys):
         assert key in line, key
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_oracle_sample_of_a_configuration():
+    """the oracle leg of `bench.py --configs`: cell updates per second over a bounded number of
+    level-0 steps, on all host cores"""
+    import bench
+    import oracle
+    out = bench.oracle_sample(oracle.make_cfg(dim=2, M=2, n=(8, 8, 1), lo=(0, 0, 0), hi=(10, 10, 1), cfl=0.9),
+                              oracle.IC_VORTEX, [5.0, 5.0, 5.0, 1.0, 1.0, 1.0, 1.0], 3, "three steps")
+    assert out["kind"] == "oracle" and out["sample"] == "three steps" and out["cores"] >= 1
+    assert out["cell_updates"] == 3 * 64 and out["value"] > 0
