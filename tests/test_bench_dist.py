@@ -73,7 +73,6 @@ def test_reference_arm_line(monkeypatch, capsys):
 def test_oracle_sample_of_a_configuration():
     """the oracle leg of `bench.py --configs`: cell updates per second over a bounded number of
     level-0 steps, on all host cores"""
-    import bench
     import oracle
     out = bench.oracle_sample(oracle.make_cfg(dim=2, M=2, n=(8, 8, 1), lo=(0, 0, 0), hi=(10, 10, 1), cfl=0.9),
                               oracle.IC_VORTEX, [5.0, 5.0, 5.0, 1.0, 1.0, 1.0, 1.0], 3, "three steps")
