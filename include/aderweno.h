@@ -331,6 +331,29 @@ int aw_selftest_reciprocal(const double* x_dev, int64_t n, double* out_dev, uint
  * Nothing is allocated or freed. */
 int aw_cfl_dt_noalloc(const aw_config* cfg, const double* u_dev, int64_t n_cells, double* dt_dev, uintptr_t stream);
 
+/* Reference-element tables the kernels use for order M (1..3) and refinement factor r (2..4),
+ * computed on the host in long double and rounded to double; no device work, no solver needed.
+ * They are the Gauss-Legendre rule on [0,1] and the nodal Lagrange basis through it (Sec. 2.2);
+ * the WENO stencils of Eq. eqn.stencildef with their reconstruction matrices (the inverse of
+ * the integral-conservation system of Eq. eqn.rec.x) and the oscillation-indicator matrix of
+ * Eq. eqn.sigmas; the time block of the predictor matrix K1 of Sec. 2.3 in its factorised
+ * form; and the child-box averages and fine-point values of the basis used by the projection
+ * of Sec. 3.1.3.  With N = M + 1, out[] receives, in this order:
+ *   N, Ns (number of stencils), r;
+ *   x[N], w[N]                 nodes and weights;
+ *   SL[4], lam[4]              left extent and linear weight of stencil s (unused entries 0);
+ *   Ainv[4][N][N]              Ainv[s][p][e]: nodal value p of the polynomial of stencil s from
+ *                              the averages of its cells e = 0..N-1 (leftmost first);
+ *   Sig[N][N]                  sigma = c^T Sig c for nodal coefficients c;
+ *   Dm[N][N]                   Dm[i][l] = psi_l'(x_i);
+ *   G[N][N]                    K_t^{-1} diag(w), K_t[a][b] = psi_a(1) psi_b(1) - w_b Dm[b][a];
+ *   psi0[N], psi1[N]           psi_l(0), psi_l(1);
+ *   Wc[r][N]                   Wc[c][l]: average of psi_l over [c/r, (c+1)/r];
+ *   Pf[r][N][N]                Pf[c][i][l] = psi_l((c + x_i)/r);
+ * 11 + 4N + 7N^2 + rN + rN^2 doubles, written to *n.  AW_EINVAL for M or r out of range, a null
+ * n, or cap < *n (out untouched). */
+int aw_tables_host(int32_t M, int32_t r, double* out, int64_t cap, int64_t* n);
+
 #ifdef __cplusplus
 }
 #endif

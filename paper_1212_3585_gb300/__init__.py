@@ -184,6 +184,26 @@ def set_launch_params(pass_min_cells=None, tile8_min_cells=None, small_ctas_per_
     _lib.check(_lib.load().aw_set_launch_params(C.byref(p)))
 
 
+def tables_host(M: int, r: int) -> dict:
+    """aw_tables_host: the reference-element tables the kernels use, unpacked into arrays."""
+    L = _lib.load()
+    n = C.c_int64(0)
+    L.aw_tables_host(M, r, None, 0, C.byref(n))
+    buf = np.zeros(n.value)
+    _lib.check(L.aw_tables_host(M, r, buf.ctypes.data_as(C.POINTER(C.c_double)), n.value, C.byref(n)))
+    N, ns = int(buf[0]), int(buf[1])
+    sizes = [("x", (N,)), ("w", (N,)), ("SL", (4,)), ("lam", (4,)), ("Ainv", (4, N, N)), ("Sig", (N, N)),
+             ("Dm", (N, N)), ("G", (N, N)), ("psi0", (N,)), ("psi1", (N,)), ("Wc", (r, N)), ("Pf", (r, N, N))]
+    out, k = {"N": N, "Ns": ns, "r": int(buf[2])}, 3
+    for name, shape in sizes:
+        m = int(np.prod(shape))
+        out[name] = buf[k:k + m].reshape(shape)
+        k += m
+    out["SL"] = out["SL"][:ns].astype(int)
+    out["lam"], out["Ainv"] = out["lam"][:ns], out["Ainv"][:ns]
+    return out
+
+
 def advance_batch(solvers, t_end, stream: int = 0):
     """aw_advance_batch: advance independent solvers of one kernel configuration to t_end with
     their hot kernels batched per level and sub-step.  Returns (stats, rc) per solver; raises

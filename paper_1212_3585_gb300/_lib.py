@@ -100,6 +100,7 @@ SIGNATURES = {
     "aw_srv_destroy": (None, [_vp]),
     "aw_selftest_reciprocal": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_size_t]),
     "aw_cfl_dt_noalloc": (C.c_int, [C.POINTER(AwConfig), C.c_void_p, C.c_int64, C.c_void_p, C.c_size_t]),
+    "aw_tables_host": (C.c_int, [C.c_int32, C.c_int32, _dp, C.c_int64, C.POINTER(C.c_int64)]),
     "aw_kernel_launches": (C.c_int64, [_vp]),
     "aw_advance_batch": (C.c_int, [C.POINTER(_vp), C.c_int32, C.c_double, C.c_size_t, C.POINTER(AwStats),
                                    C.POINTER(C.c_int32)]),

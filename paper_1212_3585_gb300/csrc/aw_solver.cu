@@ -2154,6 +2154,43 @@ int aw_set_launch_params(const aw_launch_params* in) {
   return AW_OK;
 }
 
+int aw_tables_host(int32_t M, int32_t r, double* out, int64_t cap, int64_t* n) {
+  if (!n) AW_FAIL(AW_EINVAL, "null argument");
+  if (M < 1 || M > 3) AW_FAIL(AW_EINVAL, "M must be 1, 2 or 3");
+  if (r < 2 || r > MAXR) AW_FAIL(AW_EINVAL, "r must be in 2..%d", MAXR);
+  const int N = M + 1;
+  const int64_t need = 11 + 4 * N + 7 * N * N + r * N + r * N * N;
+  *n = need;
+  if (!out || cap < need) AW_FAIL(AW_EINVAL, "need room for %lld doubles", (long long)need);
+  Tables T;
+  if (!build_tables(M, r, &T)) AW_FAIL(AW_EINVAL, "table construction failed");
+  int64_t k = 0;
+  out[k++] = N;
+  out[k++] = T.Ns;
+  out[k++] = r;
+  for (int i = 0; i < N; i++) out[k++] = T.x[i];
+  for (int i = 0; i < N; i++) out[k++] = T.w[i];
+  for (int s = 0; s < 4; s++) out[k++] = s < T.Ns ? T.SL[s] : 0.0;
+  for (int s = 0; s < 4; s++) out[k++] = s < T.Ns ? T.lam[s] : 0.0;
+  for (int s = 0; s < 4; s++)
+    for (int p = 0; p < N; p++)
+      for (int e = 0; e < N; e++) out[k++] = s < T.Ns ? T.Ainv[s][p][e] : 0.0;
+  for (int p = 0; p < N; p++)
+    for (int m = 0; m < N; m++) out[k++] = T.Sig[p][m];
+  for (int i = 0; i < N; i++)
+    for (int l = 0; l < N; l++) out[k++] = T.Dm[i][l];
+  for (int a = 0; a < N; a++)
+    for (int b = 0; b < N; b++) out[k++] = T.G[a][b];
+  for (int l = 0; l < N; l++) out[k++] = T.psi0[l];
+  for (int l = 0; l < N; l++) out[k++] = T.psi1[l];
+  for (int c = 0; c < r; c++)
+    for (int l = 0; l < N; l++) out[k++] = T.Wc[c][l];
+  for (int c = 0; c < r; c++)
+    for (int i = 0; i < N; i++)
+      for (int l = 0; l < N; l++) out[k++] = T.Pf[c][i][l];
+  return k == need ? AW_OK : AW_EINVAL;
+}
+
 int aw_cfl_dt_noalloc(const aw_config* cfg, const double* u_dev, int64_t n_cells, double* dt_dev, uintptr_t stream) {
   if (!cfg || !u_dev || !dt_dev) AW_FAIL(AW_EINVAL, "null argument");
   const aw_config& c = *cfg;
