@@ -350,8 +350,14 @@ int aw_cfl_dt_noalloc(const aw_config* cfg, const double* u_dev, int64_t n_cells
  *   psi0[N], psi1[N]           psi_l(0), psi_l(1);
  *   Wc[r][N]                   Wc[c][l]: average of psi_l over [c/r, (c+1)/r];
  *   Pf[r][N][N]                Pf[c][i][l] = psi_l((c + x_i)/r);
- * 11 + 4N + 7N^2 + rN + rN^2 doubles, written to *n.  AW_EINVAL for M or r out of range, a null
- * n, or cap < *n (out untouched). */
+ *   Pt[r][N]                   Pt[k][l] = psi_l(k/r);
+ *   gsum[N]                    row sums of G;
+ *   Bq[4][N-1][N-1]            sigma of stencil s as a quadratic form of the differences d of its
+ *                              other cells' averages to the centre cell's: sigma = sum_{i<=j}
+ *                              Bq[s][i][j] d_i d_j (the upper triangle of Ainv^T Sig Ainv, with
+ *                              the centre cell's row and column removed, off-diagonal doubled);
+ * 11 + 5N + 7N^2 + 2rN + rN^2 + 4(N-1)^2 doubles, written to *n.  AW_EINVAL for M or r out of
+ * range, a null n, or cap < *n (out untouched). */
 int aw_tables_host(int32_t M, int32_t r, double* out, int64_t cap, int64_t* n);
 
 #ifdef __cplusplus

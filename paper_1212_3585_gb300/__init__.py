@@ -193,14 +193,15 @@ def tables_host(M: int, r: int) -> dict:
     _lib.check(L.aw_tables_host(M, r, buf.ctypes.data_as(C.POINTER(C.c_double)), n.value, C.byref(n)))
     N, ns = int(buf[0]), int(buf[1])
     sizes = [("x", (N,)), ("w", (N,)), ("SL", (4,)), ("lam", (4,)), ("Ainv", (4, N, N)), ("Sig", (N, N)),
-             ("Dm", (N, N)), ("G", (N, N)), ("psi0", (N,)), ("psi1", (N,)), ("Wc", (r, N)), ("Pf", (r, N, N))]
+             ("Dm", (N, N)), ("G", (N, N)), ("psi0", (N,)), ("psi1", (N,)), ("Wc", (r, N)), ("Pf", (r, N, N)),
+             ("Pt", (r, N)), ("gsum", (N,)), ("Bq", (4, N - 1, N - 1))]
     out, k = {"N": N, "Ns": ns, "r": int(buf[2])}, 3
     for name, shape in sizes:
         m = int(np.prod(shape))
         out[name] = buf[k:k + m].reshape(shape)
         k += m
     out["SL"] = out["SL"][:ns].astype(int)
-    out["lam"], out["Ainv"] = out["lam"][:ns], out["Ainv"][:ns]
+    out["lam"], out["Ainv"], out["Bq"] = out["lam"][:ns], out["Ainv"][:ns], out["Bq"][:ns]
     return out
 
 

@@ -2159,7 +2159,7 @@ int aw_tables_host(int32_t M, int32_t r, double* out, int64_t cap, int64_t* n) {
   if (M < 1 || M > 3) AW_FAIL(AW_EINVAL, "M must be 1, 2 or 3");
   if (r < 2 || r > MAXR) AW_FAIL(AW_EINVAL, "r must be in 2..%d", MAXR);
   const int N = M + 1;
-  const int64_t need = 11 + 4 * N + 7 * N * N + r * N + r * N * N;
+  const int64_t need = 11 + 5 * N + 7 * N * N + 2 * r * N + r * N * N + 4 * (N - 1) * (N - 1);
   *n = need;
   if (!out || cap < need) AW_FAIL(AW_EINVAL, "need room for %lld doubles", (long long)need);
   Tables T;
@@ -2188,6 +2188,12 @@ int aw_tables_host(int32_t M, int32_t r, double* out, int64_t cap, int64_t* n) {
   for (int c = 0; c < r; c++)
     for (int i = 0; i < N; i++)
       for (int l = 0; l < N; l++) out[k++] = T.Pf[c][i][l];
+  for (int c = 0; c < r; c++)
+    for (int l = 0; l < N; l++) out[k++] = T.Pt[c][l];
+  for (int a = 0; a < N; a++) out[k++] = T.gsum[a];
+  for (int s = 0; s < 4; s++)
+    for (int i = 0; i < N - 1; i++)
+      for (int j = 0; j < N - 1; j++) out[k++] = s < T.Ns ? T.Bq[s][i][j] : 0.0;
   return k == need ? AW_OK : AW_EINVAL;
 }
 

@@ -50,11 +50,26 @@ def test_tables_match_the_oracle(M, r):
     assert close(g["Wc"], [[r * ipoly(psi[l], c / r, (c + 1) / r) for l in range(N)] for c in range(r)], 1e-13)
     assert close(g["Pf"], [[[poly(psi[l], (c + x[i]) / r) for l in range(N)] for i in range(N)] for c in range(r)],
                  1e-13)
+    assert close(g["Pt"], [[poly(psi[l], c / r) for l in range(N)] for c in range(r)], 1e-13)
     k1inv, _, _ = oracle.st_matrices(M, 2)
     nsp = N * N
     w = o["w"]
     G = np.array([[k1inv[nsp * a, nsp * b] * w[0] * w[0] * w[b] for b in range(N)] for a in range(N)])
     assert close(g["G"], G, 1e-12)
+    assert close(g["gsum"], G.sum(axis=1), 1e-12)
+    # sigma of each stencil as a quadratic form of the differences to the centre cell's average
+    for s, sl in enumerate(o["SL"]):
+        B = o["ainv"][s].T @ o["sig"] @ o["ainv"][s]
+        keep = [e for e in range(N) if e != sl]
+        Bq = np.array([[0.0 if j < i else (1.0 if i == j else 2.0) * B[keep[i], keep[j]] for j in range(N - 1)]
+                       for i in range(N - 1)])
+        assert close(g["Bq"][s], Bq, 1e-10)
+        # and it gives the oracle's sigma: stencil values v, differences d = v - v_centre
+        v = np.random.default_rng(s).uniform(-1, 1, N)
+        v[sl] = 0.3
+        c = o["ainv"][s] @ v
+        d = np.array([v[e] - v[sl] for e in keep])
+        assert abs(d @ g["Bq"][s] @ d - c @ o["sig"] @ c) <= 1e-11 * max(1.0, abs(c @ o["sig"] @ c))
 
 
 def test_tables_host_rejects_bad_arguments():
@@ -64,4 +79,6 @@ def test_tables_host_rejects_bad_arguments():
     for M, r in ((0, 3), (4, 3), (2, 1), (2, 5)):
         assert L.aw_tables_host(M, r, None, 0, C.byref(n)) == pg._lib.AW_EINVAL
     assert L.aw_tables_host(2, 3, None, 0, None) == pg._lib.AW_EINVAL
-    assert L.aw_tables_host(2, 3, None, 0, C.byref(n)) == pg._lib.AW_EINVAL and n.value == 11 + 12 + 63 + 9 + 27
+    N, r = 3, 3
+    need = 11 + 5 * N + 7 * N * N + 2 * r * N + r * N * N + 4 * (N - 1) ** 2
+    assert L.aw_tables_host(2, 3, None, 0, C.byref(n)) == pg._lib.AW_EINVAL and n.value == need
