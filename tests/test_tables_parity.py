@@ -82,3 +82,12 @@ def test_tables_host_rejects_bad_arguments():
     N, r = 3, 3
     need = 11 + 5 * N + 7 * N * N + 2 * r * N + r * N * N + 4 * (N - 1) ** 2
     assert L.aw_tables_host(2, 3, None, 0, C.byref(n)) == pg._lib.AW_EINVAL and n.value == need
+
+
+@pytest.mark.parametrize("M", [1, 2, 3])
+def test_predictor_time_block_carries_the_initial_data(M):
+    """the factorised predictor adds the reconstruction w_h(node) itself in place of the
+    K1^-1 F0 w term: that needs K_t^-1 psi(0) = 1, i.e. G (psi(0) / w) = 1 for G = K_t^-1 diag(w)
+    (a function constant in time solves the time block with unit data at tau = 0)"""
+    g = pg.tables_host(M, 3)
+    assert np.allclose(g["G"] @ (g["psi0"] / g["w"]), 1.0, rtol=0, atol=1e-13)
