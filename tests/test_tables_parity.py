@@ -1,6 +1,7 @@
 """Parity of the reference-element tables of the CUDA path (computed on the host by the library,
-aw_tables_host, in long double) with the oracle's own tables (built independently in double):
-no GPU is needed.  The oracle's basis is given by its coefficients in powers of (xi - 1/2), so the
+aw_tables_host, in long double) with the oracle's own tables (built independently in double),
+and of the factorised predictor form the kernels implement with the oracle's full Picard
+iteration: no GPU is needed.  The oracle's basis is given by its coefficients in powers of (xi - 1/2), so the
 derivative matrix, end values, child averages and fine-point values are evaluated here from those
 polynomials; the predictor's time block G is read off the oracle's full space-time matrix K1^-1,
 which in the nodal tensor basis is diag(1 / (w x w)) (x) K_t^-1 (Sec. 2.3)."""
@@ -91,3 +92,43 @@ def test_predictor_time_block_carries_the_initial_data(M):
     (a function constant in time solves the time block with unit data at tau = 0)"""
     g = pg.tables_host(M, 3)
     assert np.allclose(g["G"] @ (g["psi0"] / g["w"]), 1.0, rtol=0, atol=1e-13)
+
+
+def factorised_predictor(o, g, wh, dt, dx, d, P):
+    """the predictor in the factorised nodal form the kernels use, written with numpy and the
+    library's tables: with the nodal tensor basis,
+      q(node, s) = w_h(node) - sum_s' G[s][s'] sum_a (dt / dx_a) sum_k Dm[i_a][k] f_a(q(node_{i_a -> k}, s'))
+    iterated P times from q = w_h (constant in time)"""
+    N, V = g["N"], o.V
+    shape = (V,) + (N,) * d                   # [v][i_z][i_y][i_x] in C order of the oracle's p + N q + N^2 r
+    w = wh.reshape(shape)
+    q = np.repeat(w[..., None], N, axis=-1)   # [..., s]
+    for _ in range(P):
+        flat = q.reshape(V, -1)
+        F = np.stack([np.array([o.flux(flat[:, m], a) for m in range(flat.shape[1])]).T.reshape(q.shape) * dt / dx[a]
+                      for a in range(d)])     # [a][v][...nodes][s]
+        rhs = np.zeros_like(q)
+        for a in range(d):
+            axis = 1 + (d - 1 - a)              # the array axis of coordinate a
+            rhs += np.moveaxis(np.tensordot(g["Dm"], np.moveaxis(F[a], axis, 0), axes=(1, 0)), 0, axis)
+        q = w[..., None] - np.einsum("st,...t->...s", g["G"], rhs)
+    # back to the oracle's layout [v][node + nsp * s]
+    return np.moveaxis(q, -1, 1).reshape(V, -1)
+
+
+@pytest.mark.parametrize("d,pde,M", [(2, oracle.PDE_EULER, 3), (2, oracle.PDE_EULER, 2), (3, oracle.PDE_EULER, 2),
+                                     (2, oracle.PDE_MHD, 3), (2, oracle.PDE_LINADV, 1)])
+def test_factorised_predictor_equals_the_full_picard_iteration(d, pde, M):
+    """the kernels' factorised form computes exactly the Picard iteration of Eq. eqn.stdg.final
+    with the full space-time matrices (the oracle), up to rounding"""
+    cfg = oracle.make_cfg(dim=d, pde=pde, M=M, n=(4, 4, 4), adv=(1.0, -0.5, 0.25))
+    o = oracle.Oracle(cfg)
+    g = pg.tables_host(M, 3)
+    rng = np.random.default_rng(40 + 10 * d + M)
+    base = {oracle.PDE_EULER: [1.0, 0.3, -0.2, 0.1, 2.5][:d + 2], oracle.PDE_LINADV: [1.0],
+            oracle.PDE_MHD: [1.0, 0.3, -0.2, 0.1, 2.5, 0.4, 0.3, -0.2, 0.05]}[pde]
+    wh = (np.array(base)[:, None] * (1.0 + 0.05 * rng.standard_normal((o.V, o.nsp)))).ravel()
+    dt, dx = 0.02, (0.1, 0.08, 0.12)[:d]
+    ref = o.predictor(wh, dt, dx).reshape(o.V, o.nst)
+    got = factorised_predictor(o, g, wh, dt, dx, d, M + 1)
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
