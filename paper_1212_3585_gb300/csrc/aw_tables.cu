@@ -1,5 +1,5 @@
-// aw_tables.cpp -- reference-element tables of the ADER-WENO scheme, computed on the host in
-// long double:
+// aw_tables.cu -- reference-element tables of the ADER-WENO scheme, computed on the host in
+// long double (aw_tables_host exports them):
 //   * Gauss-Legendre nodes/weights on [0,1] (bracketing of the sign changes of P_N, then Newton),
 //   * nodal Lagrange basis psi_l through those nodes (Sec. 2.2) in product form, its derivative
 //     matrix Dm[i][l] = psi_l'(x_i) from the barycentric weights,
