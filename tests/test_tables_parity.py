@@ -132,3 +132,15 @@ def test_factorised_predictor_equals_the_full_picard_iteration(d, pde, M):
     ref = o.predictor(wh, dt, dx).reshape(o.V, o.nst)
     got = factorised_predictor(o, g, wh, dt, dx, d, M + 1)
     assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("M", [1, 2, 3])
+def test_difference_form_identities(M):
+    """the kernels reconstruct from the differences to the cell's own average and drop the centre
+    cell's column (reading R4b): exact because every stencil reproduces constants (each row of
+    Ainv sums to 1) and Sigma annihilates them (a constant has equal nodal values)"""
+    g = pg.tables_host(M, 3)
+    N = g["N"]
+    assert np.allclose(g["Ainv"].sum(axis=2), 1.0, rtol=0, atol=1e-13)
+    assert np.allclose(g["Sig"] @ np.ones(N), 0.0, rtol=0, atol=1e-12 * np.abs(g["Sig"]).max())
+    assert np.allclose(g["Dm"] @ np.ones(N), 0.0, rtol=0, atol=1e-12 * np.abs(g["Dm"]).max())
