@@ -144,3 +144,40 @@ def test_difference_form_identities(M):
     assert np.allclose(g["Ainv"].sum(axis=2), 1.0, rtol=0, atol=1e-13)
     assert np.allclose(g["Sig"] @ np.ones(N), 0.0, rtol=0, atol=1e-12 * np.abs(g["Sig"]).max())
     assert np.allclose(g["Dm"] @ np.ones(N), 0.0, rtol=0, atol=1e-12 * np.abs(g["Dm"]).max())
+
+
+def weno1d_difference_form(g, v):
+    """one-dimensional WENO as the kernels form it: the N-1 differences to the centre average,
+    stencil polynomials from the other columns of Ainv, sigma from the quadratic form Bq, weights
+    lambda / (sigma + 1e-14)^8"""
+    N = g["N"]
+    M = N - 1
+    c = v[M]
+    out, om = np.zeros(N), []
+    polys = []
+    for s in range(g["Ns"]):
+        sl = g["SL"][s]
+        keep = [e for e in range(N) if e != sl]
+        d = np.array([v[M - sl + e] - c for e in keep])
+        polys.append(g["Ainv"][s][:, keep] @ d)
+        sigma = d @ g["Bq"][s] @ d
+        om.append(g["lam"][s] / (sigma + 1e-14) ** 8)
+    om = np.array(om) / sum(om)
+    for s in range(g["Ns"]):
+        out += om[s] * polys[s]
+    return out + c
+
+
+@pytest.mark.parametrize("M", [1, 2, 3])
+def test_weno_difference_form_equals_the_oracle(M):
+    g = pg.tables_host(M, 3)
+    rng = np.random.default_rng(50 + M)
+    x = np.arange(2 * M + 1) - M
+    cases = [rng.uniform(0.5, 1.5, 2 * M + 1) for _ in range(20)]
+    cases += [1.0 + 0.1 * np.sin(0.7 * x + p) for p in rng.uniform(0, 6, 10)]          # smooth
+    cases += [np.where(x >= k, 2.0, 1.0) for k in range(-M, M + 1)]                    # jumps
+    cases += [1e5 + 1e-3 * rng.standard_normal(2 * M + 1)]                              # large constant part
+    for v in cases:
+        ref = oracle.weno1d(M, v)
+        got = weno1d_difference_form(g, v)
+        assert np.max(np.abs(got - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref))), (v, got, ref)
