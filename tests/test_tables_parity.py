@@ -181,3 +181,28 @@ def test_weno_difference_form_equals_the_oracle(M):
         ref = oracle.weno1d(M, v)
         got = weno1d_difference_form(g, v)
         assert np.max(np.abs(got - ref)) <= 1e-12 * max(1.0, np.max(np.abs(ref))), (v, got, ref)
+
+
+@pytest.mark.parametrize("d,M,r", [(2, 3, 3), (2, 2, 2), (3, 2, 3), (2, 1, 4)])
+def test_projection_with_the_tables_equals_the_oracle(d, M, r):
+    """virtual children as the kernels form them (Sec. 3.1.3): the average over child box c of the
+    mother's q_h at tau = k/r is sum over nodes of prod_a Wc[c_a][i_a] times Pt[k][s] times the
+    node's value; likewise for w_h without the time factor.  The oracle integrates by quadrature."""
+    o = oracle.Oracle(oracle.make_cfg(dim=d, pde=oracle.PDE_EULER, M=M, n=(4, 4, 4), r=r, lmax=1))
+    g = pg.tables_host(M, r)
+    N, V = M + 1, o.V
+    rng = np.random.default_rng(60 + 10 * d + M)
+    qh = rng.standard_normal(V * o.nst)
+    wh = rng.standard_normal(V * o.nsp)
+    q = qh.reshape((V, N) + (N,) * d)          # [v][s][i_z][i_y][i_x]
+    w = wh.reshape((V,) + (N,) * d)
+    for c in [tuple(int(v) for v in rng.integers(0, r, d)) for _ in range(4)]:
+        u = w
+        for a in range(d):                      # axes (v, [z], y, x): x is last, then y, then z
+            u = np.tensordot(u, g["Wc"][c[a]], axes=([u.ndim - 1], [0]))
+        assert np.allclose(u, o.project_sp(wh, c), rtol=0, atol=1e-13 * np.abs(wh).max())
+        for k in range(r):
+            t = np.tensordot(q, g["Pt"][k], axes=([1], [0]))     # the time axis
+            for a in range(d):
+                t = np.tensordot(t, g["Wc"][c[a]], axes=([t.ndim - 1], [0]))
+            assert np.allclose(t, o.project_st(qh, c, k / r), rtol=0, atol=1e-13 * np.abs(qh).max())
