@@ -206,3 +206,33 @@ def test_projection_with_the_tables_equals_the_oracle(d, M, r):
             for a in range(d):
                 t = np.tensordot(t, g["Wc"][c[a]], axes=([t.ndim - 1], [0]))
             assert np.allclose(t, o.project_st(qh, c, k / r), rtol=0, atol=1e-13 * np.abs(qh).max())
+
+
+@pytest.mark.parametrize("d,M,r", [(2, 3, 3), (3, 2, 3), (2, 2, 4)])
+def test_coarse_trace_at_fine_points_with_the_tables(d, M, r):
+    """the fine side of a coarse/fine face (Eq. eqn.memory.sum, reading R18): the coarse q_h at
+    the fine face's Gauss point jt (transverse offset c_b = fine index - r * coarse index) and time
+    node s of sub-step k, as the kernels form it from psi0/psi1 along the normal and Pf in the
+    transverse directions and in time, equals the oracle's direct evaluation at
+    ((c_b + x_jt) / r, (k + x_s) / r)"""
+    o = oracle.Oracle(oracle.make_cfg(dim=d, pde=oracle.PDE_LINADV, M=M, n=(4, 4, 4), r=r, lmax=1))
+    g = pg.tables_host(M, r)
+    N = M + 1
+    rng = np.random.default_rng(70 + 10 * d + M)
+    qh = rng.standard_normal(o.nst)
+    q = qh.reshape((N,) + (N,) * d)            # [s][i_z][i_y][i_x]
+    x = g["x"]
+    for _ in range(6):
+        a = int(rng.integers(0, d))            # normal axis
+        side = int(rng.integers(0, 2))         # the coarse cell's face: low (0) or high (1)
+        c = [int(v) for v in rng.integers(0, r, d)]
+        jt = [int(v) for v in rng.integers(0, N, d)]
+        k, s = int(rng.integers(0, r)), int(rng.integers(0, N))
+        t = np.tensordot(q, g["Pf"][k][s], axes=([0], [0]))
+        xi = []
+        for b in range(d):
+            basis = (g["psi1"] if side else g["psi0"]) if b == a else g["Pf"][c[b]][jt[b]]
+            t = np.tensordot(t, basis, axes=([t.ndim - 1], [0]))
+            xi.append(float(side) if b == a else (c[b] + x[jt[b]]) / r)
+        ref = o.eval_st(qh, xi, (k + x[s]) / r)[0]
+        assert abs(float(t) - ref) <= 1e-13 * np.abs(qh).max(), (a, side, c, jt, k, s)
