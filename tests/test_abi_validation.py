@@ -146,3 +146,36 @@ def test_request_loop_reports_failures_without_a_device():
     with pytest.raises(pg.AwError):
         srv.poll(10 ** 6)
     srv.close()
+
+
+def test_request_loop_under_concurrent_submission_without_a_device():
+    """the loop's locking, on the CPU: four threads submit 50 requests each while four workers
+    take them (each fails at its stream for want of a device); ids are unique, every request ends
+    FAILED, the statistics add up and the loop shuts down"""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present: the requests would run")
+    except ImportError:
+        pass
+    import threading
+    srv = pg.Server(hbm_budget_bytes=1 << 30, max_concurrent=4)
+    ids, lock = [], threading.Lock()
+
+    def submit():
+        mine = [srv.submit(pg.make_config(n=(8, 8, 1)), pg.AW_IC_CONST, [1.0, 0.1, 0.2, 1.0], 0.01)
+                for _ in range(50)]
+        with lock:
+            ids.extend(mine)
+
+    threads = [threading.Thread(target=submit) for _ in range(4)]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    srv.wait_all()
+    assert len(ids) == 200 and len(set(ids)) == 200
+    assert all(srv.poll(i) == 3 for i in ids)                      # AW_REQ_FAILED
+    s = srv.stats()
+    assert (s.done, s.failed, s.queued, s.running) == (0, 200, 0, 0)
+    srv.close()
