@@ -179,3 +179,25 @@ def test_request_loop_under_concurrent_submission_without_a_device():
     s = srv.stats()
     assert (s.done, s.failed, s.queued, s.running) == (0, 200, 0, 0)
     srv.close()
+
+
+def test_batched_request_loop_reports_failures_without_a_device():
+    """with batching on, queued requests of one configuration are taken together: without a
+    device every member fails with the stream's CUDA error, and all are accounted for"""
+    try:
+        import torch
+        if torch.cuda.is_available():
+            pytest.skip("a GPU is present: the requests would run")
+    except ImportError:
+        pass
+    srv = pg.Server(hbm_budget_bytes=1 << 30, max_concurrent=2, max_batch=4)
+    ids = [srv.submit(pg.make_config(n=(8, 8, 1)), pg.AW_IC_CONST, [1.0, 0.1, 0.2, 1.0], 0.01) for _ in range(9)]
+    srv.wait_all()
+    assert all(srv.poll(i) == 3 for i in ids)                      # AW_REQ_FAILED
+    for i in ids:
+        with pytest.raises(pg.AwError) as ei:
+            srv.result(i, 4)
+        assert ei.value.code == _lib.AW_ECUDA and "stream creation failed" in str(ei.value)
+    s = srv.stats()
+    assert (s.done, s.failed) == (0, 9)
+    srv.close()
