@@ -1,5 +1,7 @@
 """The C ABI library loads without a GPU and exports every symbol include/aderweno.h declares;
-the Python binding declares a signature for each (no compute calls here)."""
+the Python binding declares a signature for each, whose argument and return types match the
+header's prototypes in width and pointee; the ctypes structures have the header's layouts (no
+compute calls here)."""
 import ctypes
 import os
 import re
@@ -79,3 +81,62 @@ def test_launch_params_roundtrip_without_gpu():
         pg.set_launch_params(small_ctas_per_sm=65)
     pg.set_launch_params(**before)
     assert pg.get_launch_params() == before
+
+
+def prototypes():
+    """(return type, name, [parameter types]) of every function the header declares"""
+    src = open(os.path.join(ROOT, "include", "aderweno.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"#[^\n]*", "", src)
+    out = []
+    for m in re.finditer(r"([A-Za-z_][\w \*]*?)\b(aw_\w+)\s*\(([^;{]*)\)\s*;", src):
+        ret, name, params = m.group(1).strip(), m.group(2), m.group(3)
+        types = []
+        for p in [p.strip() for p in params.split(",") if p.strip() and p.strip() != "void"]:
+            t = re.sub(r"\b\w+$", "", p).strip()          # drop the parameter name
+            types.append(re.sub(r"\s+", " ", t.replace("*", " * ")).strip())
+        out.append((re.sub(r"\s+", " ", ret.replace("*", " * ")).strip(), name, types))
+    return out
+
+
+SCALARS = {"int": ctypes.c_int, "int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "double": ctypes.c_double,
+           "uintptr_t": ctypes.c_size_t}
+STRUCTS = {"aw_config": pg.AwConfig, "aw_stats": pg.AwStats, "aw_cell": pg.AwCell, "aw_srv_info": pg.AwSrvInfo,
+           "aw_srv_summary": pg.AwSrvSummary, "aw_launch_params": _lib.AwLaunchParams,
+           "int8_t": ctypes.c_int8, "int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "double": ctypes.c_double}
+OPAQUE = {"aw_solver", "aw_server"}
+
+
+def compatible(ctype, ct):
+    """does the ctypes type ct pass the C type ctype (spelled with spaces around '*')?"""
+    words = [w for w in ctype.split() if w != "const"]
+    stars = words.count("*")
+    base = words[0]
+    if stars == 0:
+        return SCALARS.get(base) is ct and ct is not None
+    if ct is ctypes.c_void_p:                       # any pointer may travel as void*
+        return base in OPAQUE and stars == 1 or base not in OPAQUE
+    if stars == 1 and base == "char":
+        return ct is ctypes.c_char_p
+    if not hasattr(ct, "_type_"):
+        return False
+    inner = ct._type_
+    if stars == 2 and base in OPAQUE:               # aw_solver** / aw_solver* const*
+        return inner is ctypes.c_void_p
+    return stars == 1 and STRUCTS.get(base) is inner
+
+
+def test_binding_signatures_match_the_header():
+    protos = prototypes()
+    assert {p[1] for p in protos} == set(declared())
+    for ret, name, params in protos:
+        restype, argtypes = _lib.SIGNATURES[name]
+        assert len(argtypes) == len(params), (name, params)
+        for ctype, ct in zip(params, argtypes):
+            assert compatible(ctype, ct), (name, ctype, ct)
+        if ret == "void":
+            assert restype is None, name
+        elif ret == "const char *":
+            assert restype is ctypes.c_char_p, name
+        else:
+            assert restype is SCALARS[ret], (name, ret, restype)
