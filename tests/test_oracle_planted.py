@@ -41,6 +41,14 @@ PLANTED = [
     ("energy flux v (E + 0.9 p)",
      "f[d + 1] = vn * (E + p);", "f[d + 1] = vn * (E + 0.9 * p);",
      "tests/test_oracle_riemann.py::test_sod_converges_to_exact_solution[2]"),
+    ("time step from the largest axis term instead of the sum over axes",
+     "for (int a = 0; a < S->d; a++) den += max_speed(&S->P, u, a) / dx[a];",
+     "for (int a = 0; a < S->d; a++) { double t_ = max_speed(&S->P, u, a) / dx[a]; if (t_ > den) den = t_; }",
+     "tests/test_oracle_dt.py::test_dt_euler_2d_constant_state"),
+    ("time step from the smallest spacing over the sum of speeds",
+     "for (int a = 0; a < S->d; a++) den += max_speed(&S->P, u, a) / dx[a];",
+     "for (int a = 0; a < S->d; a++) den += max_speed(&S->P, u, a) / (dx[0] < dx[1] ? dx[0] : dx[1]);",
+     "tests/test_oracle_dt.py::test_dt_euler_3d_constant_state"),
     ("indicator without its cross terms",
      "    for (int l = 0; l < d; l++) {\n      double D2, G, A;", "    for (int l = k; l <= k; l++) {\n      double D2, G, A;",
      "tests/test_oracle_indicator.py::test_mixed_derivative_counts"),
