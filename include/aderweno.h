@@ -324,6 +324,12 @@ int aw_selftest_reciprocal(const double* x_dev, int64_t n, double* out_dev, uint
  *            canonical order (k, j, i); read only.
  *   n_cells: must equal the grid's cell count and be at most 8192 * 256 = 2,097,152
  *            (AW_EINVAL otherwise, before any device work).
+ * Result values that aw_compute_dt rejects: the result is only known on the device, so where
+ * aw_compute_dt returns AW_ENONPHYSICAL this call still returns AW_OK and writes the rejected
+ * value to dt_dev: 0 when some cell's step is NaN or not positive (NaN averages, for example),
+ * and a value of at least 1e300 (1e300 or +inf) when no wave speed limits the step (every speed
+ * zero).  Like aw_compute_dt it does not test rho > 0 or p > 0: a cell with c^2 < 0 gets the
+ * modulus of its complex wave speeds.  The caller checks the value before stepping with it.
  * Scratch: a fixed 64 KiB array in the library's device memory, which every GPU that loads the
  * library holds until the process exits.  The first call on a device looks up its address
  * (make that call before any stream capture).  The array is shared: calls whose device work

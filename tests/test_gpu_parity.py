@@ -1,9 +1,13 @@
 """Parity of the CUDA path with the FP64 oracle, element by element on the same seeded inputs.
 
-Tolerance: 1e-10 relative per step for cell averages and kernel outputs (normalised by the
-largest magnitude of each variable); the mesh (levels, statuses, indices) must be identical
-given identical refinement flags.  Sizes span several WENO tiles (8x8 in 2D, 4x4x4 in 3D) and
-a ragged tail.
+Tolerance: 1e-10 relative per step for cell averages and kernel outputs, per variable (each
+variable's largest difference over the largest magnitude of that variable, floored at 1e-2 of
+the largest magnitude of the state for variables that hold rounding noise only; see
+``tests/pairs.py``); the mesh (levels, statuses, indices) must be identical given identical
+refinement flags.  Sizes span
+several WENO tiles (8x8 in 2D, 4x4x4 in 3D) and a ragged tail.  The product path's own regrid
+(device indicator, flags and regrid inside ``aw_step`` / ``aw_advance_to``) is held to the
+oracle's own regrid over whole solves, with identical trees at every level-0 step.
 """
 import numpy as np
 import pytest
@@ -11,7 +15,9 @@ import pytest
 import aw_inputs
 import oracle
 import paper_1212_3585_gb300 as pg
-from tests.pairs import RTOL, Pair, rel_err
+from tests.pairs import IC_MAP, RTOL, Pair, rel_err
+
+IC_MAP_G = {k: v[1] for k, v in IC_MAP.items()}
 
 pytestmark = pytest.mark.gpu
 
@@ -132,12 +138,115 @@ def test_indicator_matches_oracle():
     p.step(regrid=False)
     fo = p.o.compute_flags(0)
     fg = p.g.compute_flags(0)
+    chi_o = {}
     for lv in range(2):
         co = p.o.internal(2, lv)
         cg = p.g.internal(2, lv)
         assert rel_err(cg, co) <= 1e-9
-    # flags may only differ where the indicator sits on a threshold
-    assert np.mean(fo == fg) > 0.999
+        chi_o[lv] = co
+    # flags may only differ where the indicator sits on a threshold: every mismatched cell's
+    # neighbourhood maximum of chi (reading R14) is within 1e-9 of chi_ref or chi_rec
+    meta, _ = p.o.cells()
+    bad = np.nonzero(fo != fg)[0]
+    if bad.size:
+        hat = chi_hat(meta, chi_o, (14, 14, 1), 3, periodic=False)
+        for c in bad:
+            h = hat[c]
+            assert min(abs(h - 0.2) / 0.2, abs(h - 0.1) / 0.1) <= 1e-9, (c, meta[c], h, fo[c], fg[c])
+
+
+def chi_hat(meta, chi, n, r, periodic):
+    """the neighbourhood maximum of the indicator (reading R14) per existing cell in canonical
+    order: over the cell and its same-level Voronoi neighbours of status 0 or -1 (out-of-domain
+    neighbours skipped unless periodic), for cells of status 0 or -1; NaN elsewhere"""
+    out = np.full(len(meta), np.nan)
+    dim = 3 if n[2] > 1 else 2
+    for lv, cl in chi.items():
+        sel = np.nonzero(meta[:, 0] == lv)[0]
+        L = [n[a] * r ** lv for a in range(3)] if dim == 3 else [n[0] * r ** lv, n[1] * r ** lv, 1]
+        st = np.full((L[2], L[1], L[0]), -9, dtype=np.int64)
+        cv = np.full((L[2], L[1], L[0]), -np.inf)
+        m = meta[sel]
+        st[m[:, 4], m[:, 3], m[:, 2]] = m[:, 1]
+        cv[m[:, 4], m[:, 3], m[:, 2]] = cl
+        offs = [(di, dj, dk) for dk in ((-1, 0, 1) if dim == 3 else (0,)) for dj in (-1, 0, 1) for di in (-1, 0, 1)]
+        for idx, (lv_, s_, i, j, k) in zip(sel, m):
+            if s_ not in (0, -1):
+                continue
+            h = cv[k, j, i]
+            for di, dj, dk in offs:
+                ii, jj, kk = i + di, j + dj, k + dk
+                if periodic:
+                    ii, jj, kk = ii % L[0], jj % L[1], kk % L[2]
+                elif not (0 <= ii < L[0] and 0 <= jj < L[1] and 0 <= kk < L[2]):
+                    continue
+                if st[kk, jj, ii] in (0, -1):
+                    h = max(h, cv[kk, jj, ii])
+            out[idx] = h
+    return out
+
+
+def _own_refinement(p, ic, params):
+    """each side's own initial refinement (its indicator, l_max passes at t = 0); trees must agree"""
+    oi, gi = IC_MAP[ic]
+    p.o.set_initial(oi, params, nrefine=p.lmax)
+    p.g.set_initial(gi, params, nrefine=-1)
+    return p.check_cells(tol=1e-12)
+
+
+@pytest.mark.parametrize("case", ["vortex", "explosion"])
+def test_product_path_own_regrid_whole_solve(case):
+    """The path the bench and the request loop run: every level-0 step is the CFL step of aw_step
+    followed by the device's own indicator, flags, closure and regrid (auto_regrid = 1), against
+    the oracle's own orc_step with its own regrid. Trees identical and averages within the
+    per-variable tolerance after every level-0 step, the last step clipped at t_end; then the
+    same solve through the one call aw_advance_to on a fresh solver gives the same tree and
+    averages. Vortex: the smooth AMR vortex of the oracle's AMR convergence pin (Sec. 4.1) with
+    refinement around its core; explosion: the 2D AMR explosion at a small base (two levels)."""
+    if case == "vortex":
+        kw = dict(dim=2, M=3, n=(16, 16, 1), lo=(0, 0, 0), hi=(10, 10, 1), bc="periodic", r=3, lmax=1,
+                  chi_ref=0.02, chi_rec=0.01, cfl=0.9)
+        ic, params, t_end = "vortex", VORTEX, 0.6
+    else:
+        kw = dict(dim=2, M=3, n=(14, 14, 1), lo=(-1, -1, 0), hi=(1, 1, 1), bc="transmissive", r=3, lmax=2,
+                  cfl=0.6)
+        ic, params, t_end = "explosion", EXPL, 0.12
+    p = Pair(auto_regrid=1, **kw)
+    _own_refinement(p, ic, params)
+    assert p.g.counts()[3][1] > 0
+    steps, trees_changed, prev = 0, 0, p.o.cells()[0]
+    while p.o.t < t_end:
+        p.solve_step(t_end)
+        steps += 1
+        cur = p.o.cells()[0]
+        trees_changed += int(cur.shape != prev.shape or not np.array_equal(cur, prev))
+        prev = cur
+    assert steps >= 5 and p.g.t == t_end
+    assert trees_changed >= 1          # the regrid did change the tree along the way
+    mo, uo = p.o.cells()
+    q = Pair(auto_regrid=1, **kw)
+    q.o = None
+    g2 = q.g
+    g2.set_initial(IC_MAP_G[ic], params, nrefine=-1)
+    st = g2.advance_to(t_end)
+    assert st.level0_steps == steps
+    mg, ug = g2.cells()
+    assert np.array_equal(mg, mo), "aw_advance_to's tree differs from the oracle's"
+    assert rel_err(ug[mo[:, 1] <= 0], uo[mo[:, 1] <= 0]) <= RTOL
+
+
+def test_3d_explosion_r3_two_levels():
+    """The 3D explosion configuration's hierarchy on a small base: r = 3, l_max = 2 (nine fine
+    sub-steps per level-0 step, two coarse/fine interface levels), M = 2, transmissive, CFL 0.6;
+    trees identical and averages within the per-variable tolerance after every level-0 step and
+    every regrid."""
+    p = Pair(dim=3, M=2, n=(5, 5, 5), lo=(-1, -1, -1), hi=(1, 1, 1), bc="transmissive", r=3, lmax=2, cfl=0.6,
+             threads=16)
+    p.init("explosion", EXPL)
+    n, na, cpl, apl = p.g.counts()
+    assert apl[1] > 0 and apl[2] > 0
+    for _ in range(2):
+        p.step()
 
 
 def test_random_flags_tree_parity():
