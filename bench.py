@@ -1,19 +1,28 @@
 #!/usr/bin/env python
-"""Benchmark: ADER-WENO cell-updates/s on the 2D AMR explosion workload.
+"""Benchmark: ADER-WENO cell-updates/s on the 3D AMR explosion (the headline) or the 2D one.
 
-Workload (one "step" = one complete solve): 2D Euler, gamma 1.4, FP64, ADER-WENO M=3 (fourth
-order), base grid 100x100 on [-1,1]^2, refinement factor 3, l_max = 2, local time stepping,
-Loehner density indicator, cylindrical explosion (rho=1, p=1 inside r=0.5; rho=0.125, p=0.1
-outside), transmissive boundaries, Rusanov flux, CFL 0.6, from t=0 to t=0.25.  Each solve
-re-initialises the mesh on the device (aw_reset + initial condition + l_max refinement passes)
-and advances to t_end with a regrid after every level-0 step.
+Headline workload (--workload explosion3d, the default): 3D Euler, gamma 1.4, FP64, ADER-WENO M=2
+(third order), base grid 64^3 on [-1,1]^3, refinement factor 3, l_max = 2 (576^3 effective),
+local time stepping, Loehner density indicator, spherical explosion (rho=1, p=1 inside r=0.5;
+rho=0.125, p=0.1 outside), transmissive boundaries, Rusanov flux, CFL 0.6, to t=0.25.  A whole
+solve is a hundred level-0 steps of several seconds each, so one "step" is one level-0 step of
+the solve as the library runs it (aw_step: CFL time step, the nine level-2 sub-steps with their
+coarse levels, the regrid after it), taken after the initial condition, its refinement passes and
+the W warm-up level-0 steps: the timed steps are level-0 steps W+1 .. W+K of the solve.
+Secondary workload (--workload explosion2d): the 2D explosion (M=3, base 100^2, r=3, l_max=2,
+t=0.25), one step = one complete solve from aw_reset.
 
-value   = cell updates (active cell advanced by its level's dt) per second, device-resident
-e2e     = the same through the C ABI with host buffers: level-0 averages uploaded from pinned
-          host memory, data-driven refinement, solve, all cell averages read back
+Three passes run the same steps from the same start (every pass computes the same bits):
+value   = cell updates (active cell advanced by its level's dt) per second, device time of the timed
+          steps with CUDA events on the solver's stream, no per-kernel events; L2 flushed (256 MB
+          write) between steps
+kernels = a second pass with the library's per-kernel CUDA events on (aw_set_profiling): each
+          kernel's share and the dominant kernel's average launch duration, for the roofline
+e2e     = a third pass through the C ABI with host buffers: every step uploads the state from
+          pinned host memory (aw_set_cell_averages), steps, and reads every cell back into pinned
+          host memory (aw_read_cells); wall time with the copies
 roofline= the dominant kernel's algorithmic FP64 FLOP rate against the FP64 peak
-cpu_baseline = the FP64 CPU oracle on all host cores, on the first four level-0 steps of the same
-          solve (and on one core, on the first level-0 step)
+cpu_baseline = the FP64 CPU oracle on all host cores, on a bounded sample of the same workload
 
 Multi-GPU: one independent replica per rank (the path has no exchange step), weak scaling.
 
@@ -43,6 +52,21 @@ WORKLOAD = ("2D Euler FP64, ADER-WENO M=3, base 100x100 on [-1,1]^2, r=3, l_max=
 CFG = dict(dim=2, M=3, n=(100, 100, 1), lo=(-1.0, -1.0, 0.0), hi=(1.0, 1.0, 1.0), r=3, lmax=2, gamma=1.4,
            chi_ref=0.2, chi_rec=0.1, cfl=0.6)
 T_END = 0.25
+WORKLOADS = {
+    "explosion3d": {
+        "desc": ("3D Euler FP64, ADER-WENO M=2, base 64x64x64 on [-1,1]^3, r=3, l_max=2, local time stepping, "
+                 "spherical explosion (R=0.5; rho,p = 1,1 inside; 0.125,0.1 outside), transmissive, Rusanov, "
+                 "CFL 0.6, t_end=0.25"),
+        "cfg": dict(dim=3, M=2, n=(64, 64, 64), lo=(-1.0, -1.0, -1.0), hi=(1.0, 1.0, 1.0), r=3, lmax=2, gamma=1.4,
+                    chi_ref=0.2, chi_rec=0.1, cfl=0.6),
+        "t_end": 0.25, "step": "level0",
+        # the host cannot hold the oracle's 576^3 finest level: its samples run the same r, l_max,
+        # M and CFL on a small base (the oracle's cost per cell update does not depend on the base)
+        "oracle_base": 5, "reference_base": 3,
+    },
+    "explosion2d": {"desc": WORKLOAD, "cfg": CFG, "t_end": T_END, "step": "solve", "oracle_base": None,
+                    "reference_base": None},
+}
 SM_COUNT = 152
 FP64_FMA_PER_CLK_PER_SM = 2      # sm_103a: measured 0.598 T DFMA/s at ~1.97 GHz on 152 SMs
 SM_MAX_MHZ = 2070.0
@@ -52,6 +76,8 @@ HBM_GBS = 6792.1                 # measured copy bandwidth of this GB300 pool
 # 141.52 MB); scaled by the cells of an average launch.  Must be re-captured whenever k_predict
 # changes.
 PREDICTOR_DRAM_BYTES_PER_CELL = (51356416 + 141521408) / (6264 * 16)
+# the same for the 3D workload's kernels (none captured on their current build yet)
+PREDICTOR_DRAM_BYTES_PER_CELL_3D = {}
 
 
 def _measured_hbm():
@@ -513,79 +539,140 @@ def dist_setup():
     return ws, rank, local
 
 
-def run_reference(args):
-    """The FP64 CPU oracle as it stands, timed on the host cores; each step = the first level-0
-    step of the workload (setup untimed)."""
+def _oracle_cfg(wl, base=None):
+    """the oracle's configuration of workload wl (optionally on a smaller base grid)"""
+    import oracle
+    c = dict(wl["cfg"])
+    if base is not None:
+        c["n"] = (base, base, base) if c["dim"] == 3 else (base, base, 1)
+    return oracle.make_cfg(dim=c["dim"], M=c["M"], n=c["n"], lo=c["lo"], hi=c["hi"], bc=oracle.BC_TRANSMISSIVE,
+                           r=c["r"], lmax=c["lmax"], gamma=c["gamma"], chi_ref=c["chi_ref"], chi_rec=c["chi_rec"],
+                           cfl=c["cfl"], auto_regrid=1)
+
+
+def _oracle_first_step(wl, base, threads):
+    """the oracle as it stands: initial condition and refinement passes (untimed), then the first
+    level-0 step of the workload (timed); returns (cell updates, seconds)"""
     import oracle
     import aw_inputs
+    o = oracle.Oracle(_oracle_cfg(wl, base), threads=threads)
+    o.set_initial(oracle.IC_EXPLOSION, aw_inputs.EXPLOSION)
+    u0 = o.updates()[0]
+    t0 = time.perf_counter()
+    rc, _ = o.step(wl["t_end"])
+    el = time.perf_counter() - t0
+    if rc != 0:
+        raise RuntimeError(f"oracle step failed ({rc})")
+    return o.updates()[0] - u0, el
+
+
+def run_reference(args, wl):
+    """The FP64 CPU oracle as it stands, timed on the host cores; each step = the first level-0
+    step of the workload (setup untimed): on the workload's own grid for the 2D explosion, on a
+    3^3 base with the same r, l_max, M and CFL for the 3D one (the 576^3 finest level does not fit
+    the host, and the oracle's cost per cell update does not depend on the base)."""
     threads = os.cpu_count() or 1
     times, updates = [], []
     for i in range(args.warmup + args.steps):
-        o = oracle.Oracle(oracle.make_cfg(dim=2, M=3, n=CFG["n"], lo=CFG["lo"], hi=CFG["hi"],
-                                          bc=oracle.BC_TRANSMISSIVE, r=3, lmax=2, cfl=0.6, auto_regrid=1),
-                          threads=threads)
-        o.set_initial(oracle.IC_EXPLOSION, aw_inputs.EXPLOSION)
-        u0 = o.updates()[0]
-        t0 = time.perf_counter()
-        o.step(T_END)
-        el = time.perf_counter() - t0
+        n, el = _oracle_first_step(wl, wl["reference_base"], threads)
         if i >= args.warmup:
             times.append(el)
-            updates.append(o.updates()[0] - u0)
-        del o
+            updates.append(n)
     value = sum(updates) / sum(times)
-    sample = "first level-0 step (all 3 levels, LTS, regrid) of the workload, per step"
+    if wl["reference_base"]:
+        b = wl["reference_base"]
+        sample = (f"first level-0 step (all 3 levels, LTS, regrid) of the same explosion on a {b}^3 base "
+                  f"(same r, l_max, M, CFL; {updates[0]} cell updates), per step")
+    else:
+        sample = "first level-0 step (all 3 levels, LTS, regrid) of the workload, per step"
     return {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "l2": "n/a (CPU)", "parallelism": "none"},
+        "config": {"workload": wl["desc"], "l2": "n/a (CPU)", "parallelism": "none"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
 
 
-def cpu_baseline_sample(level0_steps=4):
-    """The oracle as it stands on all host cores (OpenMP over cells), timed on the first
-    level-0 steps of the workload (about 10 s of CPU work); setup untimed."""
+def cpu_baseline_sample(wl, level0_steps=4):
+    """The oracle as it stands on all host cores (OpenMP over cells), about 10-30 s of CPU work,
+    setup untimed: the 2D explosion's first level-0 steps on its own grid (and its first step on
+    one core); the 3D explosion's first level-0 step on a 5^3 base with the same r, l_max, M and
+    CFL (the 576^3 finest level does not fit the host)."""
     import oracle
     import aw_inputs
     threads = os.cpu_count() or 1
-    o = oracle.Oracle(oracle.make_cfg(dim=2, M=3, n=CFG["n"], lo=CFG["lo"], hi=CFG["hi"],
-                                      bc=oracle.BC_TRANSMISSIVE, r=3, lmax=2, cfl=0.6, auto_regrid=1),
-                      threads=threads)
+    if wl["oracle_base"]:
+        b = wl["oracle_base"]
+        n, el = _oracle_first_step(wl, b, threads)
+        return {"value": n / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+                "sample": (f"first level-0 step after the initial refinement of the same explosion on a {b}^3 base "
+                           f"(same r, l_max, M, CFL; {n} cell updates, {el:.1f} s)")}
+    o = oracle.Oracle(_oracle_cfg(wl), threads=threads)
     o.set_initial(oracle.IC_EXPLOSION, aw_inputs.EXPLOSION)
     u0 = o.updates()[0]
     t0 = time.perf_counter()
     for _ in range(level0_steps):
-        o.step(T_END)
+        o.step(wl["t_end"])
     el = time.perf_counter() - t0
     n = o.updates()[0] - u0
     out = {"value": n / el, "unit": UNIT, "cores": threads, "kind": "oracle",
            "sample": f"first {level0_steps} level-0 steps of the workload ({n} cell updates, {el:.1f} s)"}
-    # the same oracle on one core, on the first level-0 step
-    o1 = oracle.Oracle(oracle.make_cfg(dim=2, M=3, n=CFG["n"], lo=CFG["lo"], hi=CFG["hi"],
-                                       bc=oracle.BC_TRANSMISSIVE, r=3, lmax=2, cfl=0.6, auto_regrid=1), threads=1)
-    o1.set_initial(oracle.IC_EXPLOSION, aw_inputs.EXPLOSION)
-    u1 = o1.updates()[0]
-    t1 = time.perf_counter()
-    o1.step(T_END)
-    el1 = time.perf_counter() - t1
-    n1 = o1.updates()[0] - u1
+    n1, el1 = _oracle_first_step(wl, None, 1)
     out["single_core"] = {"value": n1 / el1, "unit": UNIT, "cores": 1,
                           "sample": f"first level-0 step of the workload ({n1} cell updates, {el1:.1f} s)"}
     return out
 
 
+def kernel_flops(D, M, V):
+    """algorithmic FP64 FLOP per cell update of the three hot kernels (Euler)"""
+    P = M + 1
+    return {"weno": weno_flops_per_cell(D, M, V), "predictor": predictor_flops_per_cell(D, M, V, P, EULER_FLUX_FLOPS[D]),
+            "face_flux": flux_flops_per_cell(D, M, V)}
+
+
+KERNEL_NAMES = ["weno", "predictor", "face_flux", "update", "projection"]
+KERNEL_SYMBOLS = {"weno": "k_weno*", "predictor": "k_predict", "face_flux": "k_flux", "update": "k_update",
+                  "projection": "k_project"}
+
+
+def roofline_entry(kms, kn, upd, flops, D, M, traffic_per_cell):
+    """the dominant kernel of a profiled pass: algorithmic FP64 FLOP per launch over its average
+    launch duration, against the FP64 peak"""
+    import numpy as np
+    dom = int(np.argmax(kms))
+    name = KERNEL_NAMES[dom]
+    if name not in flops or kn[dom] <= 0:
+        return {"bound": "alu", "kernel": name, "achieved": None, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": None, "traffic": None}
+    cells_per_launch = upd / kn[dom] if name == "predictor" else None
+    ach = flops[name] * upd / (kms[dom] * 1e-3) / 1e12
+    tr = traffic_per_cell.get(name)
+    return {"bound": "alu", "kernel": f"{KERNEL_SYMBOLS[name]}<{D},{M},Euler>", "achieved": ach,
+            "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+            "traffic": (tr * upd / kn[dom]) if tr is not None else None,
+            "traffic_note": ("DRAM read+write bytes per launch: ncu bytes per cell of a captured launch x cells per "
+                             "average launch" if tr is not None else "no ncu capture of this kernel's current build"),
+            "flops_per_cell_update": flops[name], "launches": int(kn[dom]), "cell_updates": int(upd),
+            "avg_launch_ms": float(kms[dom] / kn[dom]), "cells_per_launch": cells_per_launch,
+            "peak_note": "FP64 FMA pipe: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (derived; 1.195 measured)"}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="explosion3d", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--base", type=int, default=100, help="level-0 cells per direction (workload: 100)")
+    ap.add_argument("--profile-steps", type=int, default=3,
+                    help="steps of the profiled pass: the first timed steps again (0: all of them)")
+    ap.add_argument("--e2e-steps", type=int, default=5,
+                    help="steps of the end-to-end pass: the first timed steps again (0: all of them)")
+    ap.add_argument("--base", type=int, default=0, help="level-0 cells per direction (workload: 64 in 3D, 100 in 2D)")
     ap.add_argument("--serve", action="store_true", help="request-stream benchmark of the serving loop")
     ap.add_argument("--requests", type=int, default=48)
     ap.add_argument("--serve-base-max", type=int, default=96)
@@ -595,7 +682,7 @@ def main():
     ap.add_argument("--concurrency", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=float, default=160.0)
     ap.add_argument("--serve-batch", type=int, default=8, help="batch size of the batched request loop")
-    ap.add_argument("--t-end", type=float, default=T_END, help="end time (workload: 0.25)")
+    ap.add_argument("--t-end", type=float, default=0.0, help="end time (workloads: 0.25)")
     ap.add_argument("--efficiency", action="store_true",
                     help="cost per cell update of orders 2-4, uniform vs AMR (r=4, l_max=2)")
     ap.add_argument("--eff-base", type=int, default=25)
@@ -604,11 +691,20 @@ def main():
     ap.add_argument("--cfg3-steps", type=int, default=2)
     ap.add_argument("--eff-t-end", type=float, default=0.1)
     args = ap.parse_args()
-    if args.base != 100 or args.t_end != T_END:
-        CFG["n"] = (args.base, args.base, 1)
-        globals()["T_END"] = args.t_end
-        globals()["WORKLOAD"] = WORKLOAD.replace("base 100x100", f"base {args.base}x{args.base}").replace(
-            "t_end=0.25", f"t_end={args.t_end}")
+    wl = dict(WORKLOADS[args.workload])
+    wl["cfg"] = dict(wl["cfg"])
+    D = wl["cfg"]["dim"]
+    if args.base:
+        b0 = wl["cfg"]["n"][0]
+        wl["cfg"]["n"] = (args.base, args.base, args.base if D == 3 else 1)
+        dims = "x".join([str(b0)] * D)
+        wl["desc"] = wl["desc"].replace(f"base {dims}", "base " + "x".join([str(args.base)] * D))
+    if args.t_end:
+        wl["desc"] = wl["desc"].replace(f"t_end={wl['t_end']}", f"t_end={args.t_end}")
+        wl["t_end"] = args.t_end
+    if args.workload == "explosion2d":       # --configs/--tune use the 2D workload's globals
+        CFG["n"] = wl["cfg"]["n"]
+        globals()["T_END"] = wl["t_end"]
     ws, rank, local = dist_setup()
     if args.serve:
         return run_serve(args) if rank == 0 else 0
@@ -621,7 +717,7 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return 0
-        print(json.dumps(run_reference(args)))
+        print(json.dumps(run_reference(args, wl)))
         return 0
 
     import numpy as np
@@ -639,42 +735,6 @@ def main():
         if pgroup:
             pgroup.barrier()
 
-    stream = torch.cuda.current_stream()
-    cfg = pg.make_config(bc=pg.AW_BC_TRANSMISSIVE, auto_regrid=1, **CFG)
-    s = pg.Solver(cfg, stream.cuda_stream)
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > 129 MB of L2
-
-    def solve():
-        s.reset()
-        s.set_initial(pg.AW_IC_EXPLOSION, aw_inputs.EXPLOSION, -1)
-        st = s.advance_to(T_END)
-        return st.cell_updates, st.level0_steps
-
-    for _ in range(args.warmup):
-        solve()
-        flush.fill_(1)
-    torch.cuda.synchronize()
-    s.set_profiling(True)
-    s.kernel_times()
-    launches0 = s.kernel_launches()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    upd, l0 = 0, 0
-    barrier()
-    torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for i in range(args.steps):
-            evs[i][0].record(stream)
-            u, n0 = solve()
-            evs[i][1].record(stream)
-            upd += u
-            l0 += n0
-            flush.fill_(1)
-        torch.cuda.synchronize()
-    barrier()
-    ms = sum(a.elapsed_time(b) for a, b in evs)
-    launches = s.kernel_launches() - launches0
-    kms, kn = s.kernel_times()
-    s.set_profiling(False)
     def max_reduce(x):
         if not pgroup:
             return x
@@ -682,93 +742,191 @@ def main():
         pgroup.all_reduce(t, op=pgroup.ReduceOp.MAX)
         return float(t.item())
 
+    t_end = wl["t_end"]
+    per_solve = wl["step"] == "solve"
+    M, V = wl["cfg"]["M"], D + 2
+    stream = torch.cuda.current_stream()
+    cfg = pg.make_config(bc=pg.AW_BC_TRANSMISSIVE, auto_regrid=1, **wl["cfg"])
+    s = pg.Solver(cfg, stream.cuda_stream)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")   # > 129 MB of L2
+
+    def start():
+        """initial condition and its l_max refinement passes on the device"""
+        s.reset()
+        s.set_initial(pg.AW_IC_EXPLOSION, aw_inputs.EXPLOSION, -1)
+
+    def one_step():
+        """one benchmark step: a whole solve, or the next level-0 step of the running solve"""
+        if per_solve:
+            start()
+            st = s.advance_to(t_end)
+        else:
+            if not s.t < t_end:
+                raise RuntimeError(f"the solve reached t_end = {t_end} before the last timed step")
+            st = s.step(t_end)
+        return st.cell_updates, st.level0_steps
+
+    def warm():
+        if not per_solve:
+            start()
+        for _ in range(args.warmup):
+            one_step()
+            flush.fill_(1)
+        torch.cuda.synchronize()
+
+    # ---- pass 1: the value (device time, no per-kernel events) ----
+    warm()
+    t_first = s.t
+    launches0 = s.kernel_launches()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    upd, l0, step_updates, max_cells = 0, 0, [], 0
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        for i in range(args.steps):
+            evs[i][0].record(stream)
+            u, n0 = one_step()
+            evs[i][1].record(stream)
+            upd += u
+            l0 += n0
+            step_updates.append(int(u))
+            flush.fill_(1)
+            max_cells = max(max_cells, s.counts()[0])
+        torch.cuda.synchronize()
+    barrier()
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms = sum(step_ms)
+    launches = s.kernel_launches() - launches0
+    t_last = s.t
+    counts_last = s.counts()
     value, ms = combine_replicas(upd, ms, ws, max_reduce)
 
-    # dominant kernel and its algorithmic FP64 rate
-    names = ["weno", "predictor", "face_flux", "update", "projection"]
-    dom = int(np.argmax(kms))
-    upd_per_step = upd / args.steps
-    V = 4
-    pf = predictor_flops_per_cell(2, 3, V, 4, EULER_FLUX_FLOPS[2])
-    roofline = None
-    if names[dom] == "predictor" and kn[dom] > 0:
-        ach = pf * upd / (kms[dom] * 1e-3) / 1e12
-        cells_per_launch = upd / kn[dom]
-        roofline = {"bound": "alu", "kernel": "k_predict<2,3,Euler>", "achieved": ach, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                    "traffic": PREDICTOR_DRAM_BYTES_PER_CELL * cells_per_launch,
-                    "traffic_note": "bytes per average launch: ncu dram read+write of a full-size launch per cell x cells per launch",
-                    "cells_per_launch": cells_per_launch,
-                    "flops_per_cell_update": pf, "launches": int(kn[dom]),
-                    "avg_launch_ms": float(kms[dom] / kn[dom]),
-                    "peak_note": "FP64 FMA pipe: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (derived; 1.195 measured)"}
-    else:
-        roofline = {"bound": "alu", "kernel": names[dom], "achieved": None, "peak": FP64_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": None, "traffic": None}
-    kernel_share = {n: float(kms[i] / max(kms.sum(), 1e-9)) for i, n in enumerate(names)}
-    flops = {"weno": weno_flops_per_cell(2, 3, V), "predictor": pf, "face_flux": flux_flops_per_cell(2, 3, V)}
+    # ---- pass 2: the same steps with the library's per-kernel events (shares, roofline) ----
+    kprof = min(args.profile_steps or args.steps, args.steps)
+    ke2e = min(args.e2e_steps or args.steps, args.steps)
+    warm()
+    s.set_profiling(True)
+    s.kernel_times()
+    upd_p = 0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(kprof):
+        u, _ = one_step()
+        upd_p += u
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms_p = e0.elapsed_time(e1)
+    kms, kn = s.kernel_times()
+    s.set_profiling(False)
+    if upd_p != sum(step_updates[:kprof]):
+        raise RuntimeError("the profiled pass did not repeat the timed steps")
+
+    flops = kernel_flops(D, M, V)
+    traffic = PREDICTOR_DRAM_BYTES_PER_CELL_3D if D == 3 else {"predictor": PREDICTOR_DRAM_BYTES_PER_CELL}
+    roofline = roofline_entry(kms, kn, upd_p, flops, D, M, traffic)
+    kernel_share = {n: float(kms[i] / max(kms.sum(), 1e-9)) for i, n in enumerate(KERNEL_NAMES)}
     hbm = _measured_hbm()
-    bpc = bytes_per_cell(2, 3, V)
+    bpc = bytes_per_cell(D, M, V)
     kernels = {}
-    for i, n in enumerate(names[:3]):
+    for i, n in enumerate(KERNEL_NAMES[:3]):
         if kms[i] <= 0:
             continue
         t = kms[i] * 1e-3
         kernels[n] = {"ms_total": float(kms[i]), "launches": int(kn[i]), "share": kernel_share[n],
-                      "fp64_tflops": flops[n] * upd / t / 1e12,
-                      "fp64_frac": flops[n] * upd / t / 1e12 / FP64_PEAK_TFLOPS,
-                      "hbm_gbs_algorithmic": bpc[n] * upd / t / 1e9,
-                      "hbm_frac": bpc[n] * upd / t / 1e9 / hbm,
+                      "fp64_tflops": flops[n] * upd_p / t / 1e12,
+                      "fp64_frac": flops[n] * upd_p / t / 1e12 / FP64_PEAK_TFLOPS,
+                      "hbm_gbs_algorithmic": bpc[n] * upd_p / t / 1e9,
+                      "hbm_frac": bpc[n] * upd_p / t / 1e9 / hbm,
                       "flops_per_cell_update": flops[n], "bytes_per_cell_update": bpc[n]}
-
     # the whole step: algorithmic FP64 work of WENO, predictor and face flux per cell update over
-    # the timed device time of the solve (bookkeeping, projection and host gaps included)
-    step_flops = sum(flops.values()) * upd / args.steps
-    step_tf = step_flops / (ms / args.steps * 1e-3) / 1e12
+    # the timed device time (bookkeeping, projection and host gaps included)
+    step_tf = sum(flops.values()) * upd / (ms * 1e-3) / 1e12
+    unit_desc = ("one complete solve from aw_reset (initial condition, refinement passes, solve to t_end)"
+                 if per_solve else
+                 f"one level-0 step (aw_step: CFL dt, r^l_max sub-steps, regrid); timed: level-0 steps "
+                 f"{args.warmup + 1}..{args.warmup + args.steps} of the solve, t = {t_first:.5f} .. {t_last:.5f}")
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "cell_updates_per_solve": upd_per_step, "level0_steps_per_solve": l0 / args.steps,
-                   "l2": "flushed between timed solves (256 MB write)", "parallelism": f"replicas x{ws}"},
+        "config": {"workload": wl["desc"], "step": unit_desc, "cell_updates_per_step": upd / args.steps,
+                   "level0_steps_per_step": l0 / args.steps, "cell_updates_by_step": step_updates,
+                   "ms_by_step": step_ms,
+                   "cells_after_last_step": int(counts_last[0]), "active_per_level_after_last_step":
+                       [int(a) for a in counts_last[3]],
+                   "l2": "flushed between timed steps (256 MB write)", "parallelism": f"replicas x{ws}"},
         "roofline": roofline,
-        "step_fp64": {"achieved": step_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": step_tf / FP64_PEAK_TFLOPS,
-                      "flops_per_cell_update": sum(flops.values())},
-        "kernel_time_share": kernel_share, "kernels": kernels, "gpu_launches": int(launches),
+        "step_fp64": {"achieved": step_tf, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                      "frac": step_tf / FP64_PEAK_TFLOPS, "flops_per_cell_update": sum(flops.values())},
+        "kernel_time_share": kernel_share, "kernels": kernels,
+        "profiled_pass": {"steps": kprof, "ms": ms_p, "ms_unprofiled_same_steps": float(sum(step_ms[:kprof])),
+                          "hot_kernels_share_of_step": float(kms.sum() / ms_p),
+                          "note": "the same steps again with a CUDA event pair around every hot launch; "
+                                  "the rest of the step is regrid, compaction, dt, averaging and host gaps"},
+        "gpu_launches": int(launches),
         "clocks": clk.summary(),
     }
 
     if not args.no_e2e:
-        # end to end through the C ABI with host buffers
-        s.reset()
-        s.set_initial(pg.AW_IC_EXPLOSION, aw_inputs.EXPLOSION, 0)
-        _, u0 = s.cells()
-        h_u0 = torch.from_numpy(u0).pin_memory()
-        n_out = 0
-        t_e2e, upd_e2e = 0.0, 0
-        ncell_out = 0
-        for i in range(args.warmup + args.steps):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
+        # ---- pass 3: end to end through the C ABI with pinned host buffers ----
+        if per_solve:
             s.reset()
-            s.set_cell_averages(h_u0.numpy())
-            for _ in range(cfg.lmax):
-                s.regrid(0)
-            st = s.advance_to(T_END)
-            meta, u = s.cells()
-            el = time.perf_counter() - t0
-            if i >= args.warmup:
-                t_e2e += el
-                upd_e2e += st.cell_updates
-                ncell_out = len(u)
-        e2e_val = ws * upd_e2e / t_e2e
-        out["e2e"] = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(u0.nbytes),
-                      "d2h_bytes_per_step": int(ncell_out * (V * 8 + 20)),
-                      "note": "level-0 averages uploaded from pinned host memory, data-driven refinement "
-                              "(projection mode), solve, every cell read back"}
+            s.set_initial(pg.AW_IC_EXPLOSION, aw_inputs.EXPLOSION, 0)
+            _, u0 = s.cells()                       # the level-0 initial averages: the solve's input
+            h_u = torch.empty((max_cells, V), dtype=torch.float64).pin_memory().numpy()
+            h_m = torch.empty((max_cells, 5), dtype=torch.int32).pin_memory().numpy()
+            h_u0 = torch.from_numpy(u0).pin_memory().numpy()
+            t_e2e, upd_e2e, h2d, d2h = 0.0, 0, 0, 0
+            for i in range(args.warmup + ke2e):
+                flush.fill_(1)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                s.reset()
+                s.set_cell_averages(h_u0)          # H2D: the initial level-0 averages
+                for _ in range(cfg.lmax):
+                    s.regrid(1)                     # the initial refinement passes of set_initial
+                st = s.advance_to(t_end)
+                n = s.cells_into(h_m, h_u)          # D2H: every cell of the result
+                el = time.perf_counter() - t0
+                if i >= args.warmup:
+                    t_e2e += el
+                    upd_e2e += st.cell_updates
+                    h2d += h_u0.nbytes
+                    d2h += n * (V * 8 + 20)
+            note = ("every step: level-0 initial averages uploaded from pinned host memory, the initial "
+                    "refinement passes, the solve, every cell read back into pinned host memory")
+        else:
+            warm()
+            cap = int(max_cells * 1.05) + 64
+            h_u = torch.empty((cap, V), dtype=torch.float64).pin_memory().numpy()
+            h_m = torch.empty((cap, 5), dtype=torch.int32).pin_memory().numpy()
+            n = s.cells_into(h_m, h_u)              # the state the first timed step starts from
+            t_e2e, upd_e2e, h2d, d2h = 0.0, 0, 0, 0
+            for i in range(ke2e):
+                flush.fill_(1)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                s.set_cell_averages(h_u[:n])        # H2D: the step's input state
+                h2d += n * V * 8
+                u, _ = one_step()
+                n = s.cells_into(h_m, h_u)          # D2H: the step's result, every cell
+                d2h += n * (V * 8 + 20)
+                t_e2e += time.perf_counter() - t0
+                upd_e2e += u
+            note = ("every step: the whole state uploaded from pinned host memory (aw_set_cell_averages), "
+                    "the level-0 step, every cell read back into pinned host memory (aw_read_cells)")
+        if upd_e2e != sum(step_updates[:ke2e]):
+            raise RuntimeError("the end-to-end pass did not repeat the timed steps")
+        t_job = max_reduce(t_e2e)
+        same = combine_replicas(sum(step_updates[:ke2e]), sum(step_ms[:ke2e]), ws, max_reduce)[0]
+        out["e2e"] = {"value": ws * upd_e2e / t_job, "unit": UNIT, "h2d_bytes_per_step": int(h2d // ke2e),
+                      "d2h_bytes_per_step": int(d2h // ke2e), "ms_per_step": 1e3 * t_job / ke2e, "steps": ke2e,
+                      "value_same_steps": same,
+                      "note": note + f"; the first {ke2e} timed steps again (value_same_steps: the device-timed "
+                                     "value over those steps); L2 flushed between steps, host wall time"}
     if rank == 0:
         if not args.no_cpu_baseline and ws == 1:
-            out["cpu_baseline"] = cpu_baseline_sample()
+            out["cpu_baseline"] = cpu_baseline_sample(wl)
         print(json.dumps(out))
     s.close()
     if pgroup:

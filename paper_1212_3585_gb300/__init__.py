@@ -126,6 +126,18 @@ class Solver:
         m = np.frombuffer(meta, dtype=np.int32).reshape(-1, 5)[:n].copy()
         return m, u[:n]
 
+    def cells_into(self, meta, u):
+        """aw_read_cells into caller-owned buffers (for example pinned host memory): meta is a
+        C-contiguous int32 array of shape (cap, 5) (level, status, i, j, k), u a C-contiguous
+        float64 array of shape (cap, V); returns the number of cells written"""
+        assert meta.dtype == np.int32 and meta.flags.c_contiguous and meta.shape[1:] == (5,)
+        assert u.dtype == np.float64 and u.flags.c_contiguous and u.shape[1:] == (self.V,)
+        assert meta.shape[0] == u.shape[0]
+        got = C.c_int64()
+        _lib.check(self.L.aw_read_cells(self.h, meta.ctypes.data_as(C.POINTER(AwCell)), _dp(u), meta.shape[0],
+                                        C.byref(got)))
+        return got.value
+
     def internal(self, what, level=0):
         got = C.c_int64()
         rc = self.L.aw_read_internal(self.h, what, level, None, 0, C.byref(got))

@@ -49,14 +49,17 @@ def test_reference_arm_other_ranks_exit_without_work(monkeypatch):
     assert bench.main() == 0
 
 
-def test_reference_arm_line(monkeypatch, capsys):
-    """rank 0 of the reference arm prints one JSON line with the contract's keys (the oracle on a
-    reduced base grid, one step, to keep the CPU suite short)"""
+@pytest.mark.parametrize("workload", ["explosion2d", "explosion3d"])
+def test_reference_arm_line(monkeypatch, capsys, workload):
+    """rank 0 of the reference arm prints one JSON line with the contract's keys (the 2D oracle on
+    a reduced base grid, the 3D one on its 3^3 sample, one step each, to keep the CPU suite short)"""
     import json
     monkeypatch.setenv("RANK", "0")
     monkeypatch.setenv("WORLD_SIZE", "1")
-    monkeypatch.setattr("sys.argv", ["bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
-                                     "--base", "24", "--t-end", "0.01"])
+    argv = ["bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0", "--workload", workload]
+    if workload == "explosion2d":
+        argv += ["--base", "24", "--t-end", "0.01"]
+    monkeypatch.setattr("sys.argv", argv)
     # main() rewrites these for a custom base grid and end time: restored after the test
     monkeypatch.setitem(bench.CFG, "n", bench.CFG["n"])
     monkeypatch.setattr(bench, "T_END", bench.T_END)
@@ -68,6 +71,9 @@ def test_reference_arm_line(monkeypatch, capsys):
         assert key in line, key
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["config"]["workload"].startswith("3D" if workload == "explosion3d" else "2D")
+    if workload == "explosion2d":
+        assert "base 24x24" in line["config"]["workload"]
 
 
 def test_oracle_sample_of_a_configuration():
