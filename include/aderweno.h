@@ -188,14 +188,18 @@ int aw_advance_graph(aw_solver* s, double t_end, int32_t chunk, aw_stats* stats)
  * pass_min_cells cells (default 4096; tiles below), 2D WENO tiles of 8x8 cells on levels of at
  * least tile8_min_cells cells (default 20000; 4x4 below), and quarter-size predictor and flux
  * CTAs when the full-size ones would give fewer than small_ctas_per_sm CTAs per SM (default 2;
- * 0 never).  Process-wide.  The first two are fixed per level when a solver is created, the
- * third applies to every launch.  AW_EINVAL for negative values or small_ctas_per_sm > 64.
+ * 0 never), and fuse_flux_update: 1 (default) runs the face fluxes and the update of Eq.
+ * eq:finite_vol as one kernel (the face CTA that delivers the last face flux a chunk of cells
+ * needs updates that chunk; nothing waits), 0 as two kernels; the averages are bitwise the
+ * same.  Process-wide.  The first
+ * two are fixed per level when a solver is created, the others apply to every launch.
+ * AW_EINVAL for negative values, small_ctas_per_sm > 64 or fuse_flux_update not 0 or 1.
  * bench.py --tune times the workload over these parameters. */
 typedef struct aw_launch_params {
   int64_t pass_min_cells;
   int64_t tile8_min_cells;
   int32_t small_ctas_per_sm;
-  int32_t reserved;
+  int32_t fuse_flux_update;
 } aw_launch_params;
 int aw_get_launch_params(aw_launch_params* out);
 int aw_set_launch_params(const aw_launch_params* in);
@@ -308,10 +312,19 @@ const char* aw_srv_last_error(void);
 void aw_srv_destroy(aw_server* s);
 
 /* Self-test of the Newton-Raphson reciprocal the kernels use in place of IEEE division
- * (y <- y + y(1 - x y) twice from a single-precision seed): out_dev[k] = that reciprocal of
- * x_dev[k], out_dev[n + k] = 1.0 / x_dev[k] by IEEE division, for k < n (device buffers owned
- * by the caller; out_dev holds 2n doubles).  Asynchronous on `stream`. */
+ * (y <- y + y(1 - x y) twice from the hardware's approximate reciprocal): out_dev[k] = that
+ * reciprocal of x_dev[k], out_dev[n + k] = 1.0 / x_dev[k] by IEEE division, for k < n (device
+ * buffers owned by the caller; out_dev holds 2n doubles).  Asynchronous on `stream`.
+ * AW_EINVAL for null pointers or n < 0. */
 int aw_selftest_reciprocal(const double* x_dev, int64_t n, double* out_dev, uintptr_t stream);
+
+/* Self-test of the one-step reciprocal and square root of the face fluxes (no counterpart in
+ * the paper; both are Newton steps from the hardware's approximations, relative error below
+ * 2^-38): out_dev[k] = the one-step reciprocal of x_dev[k], out_dev[n + k] = 1.0 / x_dev[k],
+ * out_dev[2n + k] = the one-step square root, out_dev[3n + k] = sqrt(x_dev[k]) (CUDA), for
+ * k < n (device buffers owned by the caller; out_dev holds 4n doubles; the square roots want
+ * x >= 0).  Asynchronous on `stream`.  AW_EINVAL for null pointers or n < 0. */
+int aw_selftest_flux_math(const double* x_dev, int64_t n, double* out_dev, uintptr_t stream);
 
 /* Allocation-free CFL time step of a uniform grid (the paper has no counterpart; this is a
  * convenience for callers that cannot allocate device memory when they need it, such as code

@@ -183,16 +183,17 @@ def get_launch_params() -> dict:
     p = _lib.AwLaunchParams()
     _lib.check(_lib.load().aw_get_launch_params(C.byref(p)))
     return {"pass_min_cells": p.pass_min_cells, "tile8_min_cells": p.tile8_min_cells,
-            "small_ctas_per_sm": p.small_ctas_per_sm}
+            "small_ctas_per_sm": p.small_ctas_per_sm, "fuse_flux_update": p.fuse_flux_update}
 
 
-def set_launch_params(pass_min_cells=None, tile8_min_cells=None, small_ctas_per_sm=None):
+def set_launch_params(pass_min_cells=None, tile8_min_cells=None, small_ctas_per_sm=None, fuse_flux_update=None):
     """aw_set_launch_params: change some of the launch-shape rules (speed only, never results)."""
     cur = get_launch_params()
     p = _lib.AwLaunchParams()
     p.pass_min_cells = cur["pass_min_cells"] if pass_min_cells is None else int(pass_min_cells)
     p.tile8_min_cells = cur["tile8_min_cells"] if tile8_min_cells is None else int(tile8_min_cells)
     p.small_ctas_per_sm = cur["small_ctas_per_sm"] if small_ctas_per_sm is None else int(small_ctas_per_sm)
+    p.fuse_flux_update = cur["fuse_flux_update"] if fuse_flux_update is None else int(fuse_flux_update)
     _lib.check(_lib.load().aw_set_launch_params(C.byref(p)))
 
 

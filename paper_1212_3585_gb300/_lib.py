@@ -51,7 +51,7 @@ class AwSrvSummary(C.Structure):
 
 class AwLaunchParams(C.Structure):
     _fields_ = [("pass_min_cells", C.c_int64), ("tile8_min_cells", C.c_int64), ("small_ctas_per_sm", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("fuse_flux_update", C.c_int32)]
 
 
 class AwCell(C.Structure):
@@ -99,6 +99,7 @@ SIGNATURES = {
     "aw_srv_last_error": (C.c_char_p, []),
     "aw_srv_destroy": (None, [_vp]),
     "aw_selftest_reciprocal": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_size_t]),
+    "aw_selftest_flux_math": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p, C.c_size_t]),
     "aw_cfl_dt_noalloc": (C.c_int, [C.POINTER(AwConfig), C.c_void_p, C.c_int64, C.c_void_p, C.c_size_t]),
     "aw_tables_host": (C.c_int, [C.c_int32, C.c_int32, _dp, C.c_int64, C.POINTER(C.c_int64)]),
     "aw_kernel_launches": (C.c_int64, [_vp]),

@@ -121,6 +121,30 @@ __device__ __forceinline__ double rcp_nr(double x) {
   return fma(y, e, y);
 }
 
+// The same with one Newton-Raphson step: the seed's relative error (about 2^-20) squared, below
+// 2^-38 (tested against IEEE division), for 2 FP64 FMAs less.  Used for 1/rho in the Euler
+// fluxes of the predictor and of the face fluxes, and in the WENO weights; an error of 2^-38
+// there changes a cell average by about 1e-12 of its size per step, far below the 1e-10 the
+// solver is held to.
+__device__ __forceinline__ double rcp_nr1(double x) {
+  const double y = rcp_approx(x);
+  return fma(y, fma(-x, y, 1.0), y);
+}
+
+// Square root of x >= 0 from the hardware's approximate reciprocal square root z ~ x^(-1/2)
+// (PTX rsqrt.approx.ftz.f64, relative error about 2^-20) and one Newton step for the root of
+// s^2 = x written with z: s = x z, s <- s + (x - s^2) z / 2.  Relative error below 2^-38 (tested
+// against CUDA's sqrt), for about half the FP64 operations of a correctly rounded root.  Used
+// for the sound speed in the face fluxes' spectral radius.  Arguments below 1e-300 (zero and
+// subnormals, which the approximation flushes to zero) are taken as 1e-300.
+__device__ __forceinline__ double sqrt_nr1(double x) {
+  x = fmax(x, 1e-300);
+  double z;
+  asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(z) : "d"(x));
+  const double s = x * z;
+  return fma(fma(-s, s, x), 0.5 * z, s);
+}
+
 // ------------------------------------------------------------------------------------------
 // PDE systems.  Euler (Eq. eq:Euler-system), ideal MHD with hyperbolic GLM cleaning (Sec. 4.2,
 // rationalised units) and linear advection.  All in FP64.
@@ -133,7 +157,7 @@ struct Pde<PDE_EULER, D> {
   static constexpr int V = D + 2;
   // fluxes in every direction at one state, sharing the primitive variables
   __device__ __forceinline__ static void fluxes(const double* q, double (*F)[V], const Phys& P) {
-    double ir = rcp_nr(q[0]);
+    double ir = rcp_nr1(q[0]);
     double v[D];
 #pragma unroll
     for (int a = 0; a < D; a++) v[a] = q[1 + a] * ir;
@@ -263,10 +287,11 @@ struct Pde<PDE_LINADV, D> {
   __device__ __forceinline__ static bool physical(const double* q, const Phys&) { return q[0] == q[0]; }
 };
 
-// Euler flux in direction n and the spectral radius of its Jacobian at one state, sharing 1/rho.
+// Euler flux in direction n and the spectral radius of its Jacobian at one state, sharing 1/rho
+// (face fluxes: one-step reciprocal and square root).
 template <int D>
 __device__ __forceinline__ double euler_flux_speed(const double* q, int n, double* f, const Phys& P) {
-  const double ir = rcp_nr(q[0]);
+  const double ir = rcp_nr1(q[0]);
   const double vn = q[1 + n] * ir;
   double ke = q[1] * q[1];
 #pragma unroll
@@ -277,7 +302,7 @@ __device__ __forceinline__ double euler_flux_speed(const double* q, int n, doubl
   for (int a = 0; a < D; a++) f[1 + a] = (a == n) ? fma(q[1 + a], vn, p) : q[1 + a] * vn;
   f[D + 1] = vn * (q[D + 1] + p);
   const double c2 = P.gamma * p * ir;
-  return c2 >= 0.0 ? fabs(vn) + sqrt(c2) : sqrt(fma(vn, vn, -c2));
+  return c2 >= 0.0 ? fabs(vn) + sqrt_nr1(c2) : sqrt(fma(vn, vn, -c2));
 }
 
 // |A(q)| dq for the Euler flux in direction n, from the characteristic decomposition: wave
@@ -416,6 +441,9 @@ struct HotArgs {
   const int32_t* yslot;
   double* ys;
   int nys;
+  // fused face flux and update (k_flux_update): face arrivals per chunk of active cells, zeroed
+  // before each launch
+  int* fsync;
 };
 
 // Several independent solves of the same kernel configuration in one launch: member m owns CTAs

@@ -59,7 +59,7 @@ __device__ __forceinline__ void weno1d(const Tables& T, const double* v, int str
       sig = fma(t, d[i], sig);
     }
     // lambda_s / (sigma + eps)^8 from the reciprocal of sigma + eps (>= 1e-14)
-    double y = rcp_nr(sig + 1e-14), y2 = y * y, y4 = y2 * y2, y8 = y4 * y4;
+    double y = rcp_nr1(sig + 1e-14), y2 = y * y, y4 = y2 * y2, y8 = y4 * y4;
     double om = (s < (M % 2 == 0 ? 1 : 2)) ? 1e5 * y8 : y8;
     sum += om;
 #pragma unroll
@@ -67,7 +67,7 @@ __device__ __forceinline__ void weno1d(const Tables& T, const double* v, int str
   }
   // sum >= lambda_s / (sigma_s + eps)^8 of the smoothest stencil: a normal double unless every
   // sigma exceeds ~1e38 (IEEE division there)
-  double is = sum >= 1e-300 ? rcp_nr(sum) : 1.0 / sum;
+  double is = sum >= 1e-300 ? rcp_nr1(sum) : 1.0 / sum;
 #pragma unroll
   for (int p = 0; p < N; p++) out[p] = fma(acc[p], is, c);
 }
@@ -589,26 +589,120 @@ __global__ void __launch_bounds__(PredCfg<D, M, PDE, DIV>::THREADS) k_predict(co
   predict_body<D, M, PDE, DIV>(a, blockIdx.x);
 }
 
-// Face flux configuration: IPB face items of N^d quadrature points per CTA.
+// Face flux configuration: CPB face items per CTA (a chunk of CPB active cells for the low faces),
+// one thread per (face item, spatial quadrature point of the face), each thread looping over the
+// N time nodes; CPB is a multiple of 32, so every warp is full.
 template <int D, int M, int PDE, int DIV = 1>
 struct FluxCfg {
-  static constexpr int N = M + 1, NPT = ipow(N, D), V = nvars(D, PDE);
-  static constexpr int CPB = 256 / NPT / DIV > 0 ? 256 / NPT / DIV : 1;   // face items per CTA
-  static constexpr int THREADS = CPB * NPT;
-  static constexpr int SMEM = THREADS * V * 8;
-  static_assert(CPB * V <= THREADS, "flux_finish needs one thread per (face item, variable)");
+  static constexpr int N = M + 1, NF = ipow(N, D - 1), V = nvars(D, PDE);
+  static constexpr int TARGET = PDE == PDE_MHD ? 128 : 256;   // threads of a full-size CTA, about
+  static constexpr int FULL = 32 * (TARGET / (32 * NF) > 0 ? TARGET / (32 * NF) : 1);
+  static constexpr int CPB = FULL / DIV > 0 ? FULL / DIV : 1;   // face items per CTA
+  static constexpr int THREADS = CPB * NF;
+  // CTAs per SM the register allocation must allow (at least 16 warps per SM)
+  static constexpr int MINB = THREADS <= 256 / DIV ? 3 : 2;
+  // shared memory per thread: the coarse mother's polynomial contracted along the normal (V*N per
+  // thread, V*N*NF per item; fine sides of coarse/fine faces), later this thread's share of the
+  // face integral (V), and the mother's values at its face point and the N time nodes (V*N)
+  static constexpr int SMEM = THREADS * V * 2 * N * 8;
 };
 
 enum { FK_SAME = 0, FK_FINE = 1, FK_COARSE = 2, FK_BOUNDARY = 3, FK_SKIP = 4 };
 
-// one face (axis d, side) of an active cell: the point contribution of this thread
-template <int D, int M, int PDE, int d>
-__device__ __forceinline__ int flux_point(const HotArgs& a, bool ok, const int* ijk, const double* qA, int g, int side,
-                                          double* contrib, int* nbo) {
-  constexpr int N = M + 1, V = nvars(D, PDE), NSP = ipow(N, D), NST = NSP * N;
-  constexpr int dstr = ipow(N, d);
+// per-item data of a flux CTA, shared by its threads
+template <int CPB>
+struct FluxShm {
+  int kind[CPB];
+  int item[3 * CPB];   // cell, axis, side
+  int nb[3 * CPB];     // the neighbour across the face (through the boundary conditions)
+  int nbaid[CPB];      // its active id when it is an active cell of this level (FK_SAME), else -1
+};
+
+// N-term trace of a nodal polynomial along the normal: sum_k p[k] q[k * STR]
+template <int N, int STR>
+__device__ __forceinline__ double trace_n(const double* p, const double* q) {
+  double t = p[0] * q[0];
+#pragma unroll
+  for (int k = 1; k < N; k++) t = fma(p[k], q[k * STR], t);
+  return t;
+}
+
+// Euler Rusanov flux times two (Eq. eqn.rusanov without its factor 1/2, which the caller folds
+// into the quadrature weight): F(q-) + F(q+) - s_max (q+ - q-)
+template <int D>
+__device__ __forceinline__ void rusanov_euler_x2(const double* qm, const double* qp, int n, double* out,
+                                                 const Phys& P) {
+  constexpr int V = D + 2;
+  double fm[V], fp[V];
+  const double sm = euler_flux_speed<D>(qm, n, fm, P), sp = euler_flux_speed<D>(qp, n, fp, P);
+  const double s = sm > sp ? sm : sp;
+#pragma unroll
+  for (int v = 0; v < V; v++) out[v] = fma(-s, qp[v] - qm[v], fm[v] + fp[v]);
+}
+
+// The kind of a face (axis d, side) of an active cell, the neighbour across it (through the
+// boundary conditions), that neighbour's active id when it is an active cell of this level, and,
+// on the fine side of a coarse/fine face, the active id of the virtual neighbour's coarse mother.
+template <int D>
+__device__ __forceinline__ int face_kind(const HotArgs& a, bool ok, const int* ijk, int d, int side, int* nb,
+                                         int* aidb, int* maid) {
   const LevelView& L = a.lv;
-  int jt[3] = {0, 0, 0}, s;
+  nb[0] = ijk[0]; nb[1] = ijk[1]; nb[2] = ijk[2];
+  *aidb = -1;
+  *maid = -1;
+  if (!ok) return FK_SKIP;
+  int o;
+  const int c = (d == 0 ? ijk[0] : (d == 1 ? ijk[1] : ijk[2])) + (side ? 1 : -1);
+  const bool inside = bcmap(L.L, a.bc, d, c, &o);
+  if (d == 0) nb[0] = o;
+  else if (d == 1) nb[1] = o;
+  else nb[2] = o;
+  if (!inside) return FK_BOUNDARY;
+  const long long nbd = didx(L, nb[0], nb[1], nb[2]);
+  const int8_t sn = L.st[nbd];
+  if (sn == 0) {
+    if (side) return FK_SKIP;
+    *aidb = L.aid[nbd];
+    return FK_SAME;
+  }
+  if (sn != 1) return FK_COARSE;
+  const LevelView& Lm = a.lvm;
+  const int r = a.T.r;
+  *maid = Lm.aid[didx(Lm, nb[0] / r, nb[1] / r, D == 3 ? nb[2] / r : 0)];
+  return FK_FINE;
+}
+
+// Fine side of a coarse/fine face, first stage: the coarse mother's space-time polynomial
+// contracted along the normal at its face toward this cell.  Thread g of the item takes the
+// transverse basis index g: R[(v*N + lt)*NF + g] for every variable v and time basis lt.
+template <int D, int M, int PDE, int d>
+__device__ __forceinline__ void fine_normal(const HotArgs& a, int side, const double* qC, int g, double* R) {
+  constexpr int N = M + 1, V = nvars(D, PDE), NSP = ipow(N, D), NST = NSP * N, NF = ipow(N, D - 1);
+  const double* pm = side ? a.T.psi0 : a.T.psi1;
+  int off = 0;
+  {
+    int t = g;
+#pragma unroll
+    for (int b = 0; b < D; b++) {
+      if (b == d) continue;
+      off += (t % N) * ipow(N, b);
+      t /= N;
+    }
+  }
+#pragma unroll 1
+  for (int v = 0; v < V; v++)
+#pragma unroll
+    for (int lt = 0; lt < N; lt++) R[(v * N + lt) * NF + g] = trace_n<N, ipow(N, d)>(pm, qC + v * NST + off + lt * NSP);
+}
+
+// second stage: at this thread's face point (transverse nodes of face point g of the fine cell,
+// mapped into the mother by the child offsets) and every time node of the sub-step,
+// qf[v*N + s], from the item's normal contractions R.
+template <int D, int M, int PDE, int d>
+__device__ __forceinline__ void fine_transverse(const HotArgs& a, const int* ijk, int g, const double* R, double* qf) {
+  constexpr int N = M + 1, V = nvars(D, PDE), NF = ipow(N, D - 1);
+  const int r = a.T.r;
+  int jt[3] = {0, 0, 0}, ch[3] = {0, 0, 0};
   {
     int t = g;
 #pragma unroll
@@ -616,207 +710,204 @@ __device__ __forceinline__ int flux_point(const HotArgs& a, bool ok, const int* 
       if (b == d) continue;
       jt[b] = t % N;
       t /= N;
-    }
-    s = t;
-  }
-  int nbase = NSP * s;
-  double wgt = a.T.w[s];
-#pragma unroll
-  for (int b = 0; b < D; b++)
-    if (b != d) { nbase += jt[b] * ipow(N, b); wgt *= a.T.w[jt[b]]; }
-  int kind = FK_SKIP;
-  int nb[3] = {ijk[0], ijk[1], ijk[2]};
-  long long nbd = 0;
-  if (ok) {
-    bool inside = bcmap(L.L, a.bc, d, ijk[d] + (side ? 1 : -1), &nb[d]);
-    if (!inside) kind = FK_BOUNDARY;
-    else {
-      nbd = didx(L, nb[0], nb[1], nb[2]);
-      int8_t sn = L.st[nbd];
-      kind = sn == 0 ? (side ? FK_SKIP : FK_SAME) : (sn == 1 ? FK_FINE : FK_COARSE);
+      ch[b] = ijk[b] % r;   // transverse axes: the fine cell and its virtual neighbour share the mother's slab
     }
   }
-  nbo[0] = nb[0]; nbo[1] = nb[1]; nbo[2] = nb[2];
+  double qsp[V][N];
 #pragma unroll
-  for (int v = 0; v < V; v++) contrib[v] = 0.0;
-  if (kind == FK_SAME || kind == FK_FINE || kind == FK_BOUNDARY) {
-    const double* pa = side ? a.T.psi1 : a.T.psi0;
-    double qa[V], qb[V], f[V];
+  for (int v = 0; v < V; v++)
 #pragma unroll
-    for (int v = 0; v < V; v++) {
-      double t = pa[0] * qA[v * NST + nbase];
+    for (int lt = 0; lt < N; lt++) qsp[v][lt] = 0.0;
 #pragma unroll
-      for (int k = 1; k < N; k++) t = fma(pa[k], qA[v * NST + nbase + k * dstr], t);
-      qa[v] = t;
-    }
-    if (kind == FK_BOUNDARY && a.bc[2 * d + side] == BC_INFLOW) {
-      // inflow face: the outer state is the prescribed inflow state
-      const double* ql = side ? qa : a.P.inflow;
-      const double* qr = side ? a.P.inflow : qa;
-      if constexpr (PDE == PDE_EULER) {
-        if (a.flux == 1) osher_euler<D>(ql, qr, d, f, a.P);
-        else rusanov<PDE, D>(ql, qr, d, f, a.P);
-      } else {
-        rusanov<PDE, D>(ql, qr, d, f, a.P);
-      }
-    } else if (kind == FK_BOUNDARY && a.bc[2 * d + side] == BC_REFLECTIVE) {
-      // reflecting wall: the outer state is the mirror image of the trace
-      double qm[V];
+  for (int tg = 0; tg < NF; tg++) {
+    int t = tg;
+    double th = 1.0;
 #pragma unroll
-      for (int v = 0; v < V; v++) qm[v] = qa[v];
-      if constexpr (PDE == PDE_EULER) qm[1 + d] = -qm[1 + d];
-      const double* ql = side ? qa : qm;
-      const double* qr = side ? qm : qa;
-      if constexpr (PDE == PDE_EULER) {
-        if (a.flux == 1) osher_euler<D>(ql, qr, d, f, a.P);
-        else rusanov<PDE, D>(ql, qr, d, f, a.P);
-      } else {
-        rusanov<PDE, D>(ql, qr, d, f, a.P);
-      }
-    } else if (kind == FK_BOUNDARY) {
-      Pde<PDE, D>::flux(qa, d, f, a.P);
-    } else {
-      if (kind == FK_SAME) {
-        const double* qB = a.qh + (long long)L.aid[nbd] * V * NST;
-        const double* pb = side ? a.T.psi0 : a.T.psi1;
-#pragma unroll
-        for (int v = 0; v < V; v++) {
-          double t = pb[0] * qB[v * NST + nbase];
-#pragma unroll
-          for (int k = 1; k < N; k++) t = fma(pb[k], qB[v * NST + nbase + k * dstr], t);
-          qb[v] = t;
-        }
-      } else {
-        // coarse mother of the virtual neighbour, evaluated at this cell's face point and sub-step
-        const LevelView& Lm = a.lvm;
-        const int r = a.T.r;
-        int cm[3] = {nb[0] / r, nb[1] / r, D == 3 ? nb[2] / r : 0};
-        const double* qC = a.qhm + (long long)Lm.aid[didx(Lm, cm[0], cm[1], cm[2])] * V * NST;
-        double bas[D][N], bt[N];
-#pragma unroll
-        for (int b = 0; b < D; b++)
-#pragma unroll
-          for (int l = 0; l < N; l++)
-            bas[b][l] = (b == d) ? (side ? a.T.psi0[l] : a.T.psi1[l]) : a.T.Pf[ijk[b] - r * cm[b]][jt[b]][l];
-#pragma unroll
-        for (int l = 0; l < N; l++) bt[l] = a.T.Pf[a.sub][s][l];
-#pragma unroll
-        for (int v = 0; v < V; v++) qb[v] = 0.0;
-        for (int nn = 0; nn < NST; nn++) {
-          int t = nn;
-          double th = 1.0;
-#pragma unroll
-          for (int b = 0; b < D; b++) { th *= bas[b][t % N]; t /= N; }
-          th *= bt[t];
-#pragma unroll
-          for (int v = 0; v < V; v++) qb[v] = fma(th, qC[v * NST + nn], qb[v]);
-        }
-      }
-      const double* ql = side ? qa : qb;
-      const double* qr = side ? qb : qa;
-      if constexpr (PDE == PDE_EULER) {
-        if (a.flux == 1) osher_euler<D>(ql, qr, d, f, a.P);
-        else rusanov<PDE, D>(ql, qr, d, f, a.P);
-      } else {
-        rusanov<PDE, D>(ql, qr, d, f, a.P);
-      }
+    for (int b = 0; b < D; b++) {
+      if (b == d) continue;
+      th *= a.T.Pf[ch[b]][jt[b]][t % N];
+      t /= N;
     }
 #pragma unroll
-    for (int v = 0; v < V; v++) contrib[v] = wgt * f[v];
+    for (int v = 0; v < V; v++)
+#pragma unroll
+      for (int lt = 0; lt < N; lt++) qsp[v][lt] = fma(th, R[(v * N + lt) * NF + tg], qsp[v][lt]);
   }
-  return kind;
+#pragma unroll
+  for (int v = 0; v < V; v++)
+#pragma unroll
+    for (int s = 0; s < N; s++) {
+      const double* bt = a.T.Pf[a.sub][s];
+      double t = bt[0] * qsp[v][0];
+#pragma unroll
+      for (int lt = 1; lt < N; lt++) t = fma(bt[lt], qsp[v][lt], t);
+      qf[v * N + s] = t;
+    }
 }
 
-// reduce the point contributions of every (face item, variable) of the CTA and finish the face
-template <int D, int M, int PDE, int DIV>
-__device__ __forceinline__ void flux_finish(const HotArgs& a, const double* sh, const int* sitem, const int* skind,
-                                            const int* snb) {
-  constexpr int N = M + 1, NPT = ipow(N, D), V = nvars(D, PDE);
-  constexpr int IPB = FluxCfg<D, M, PDE, DIV>::CPB;
-  const int t = threadIdx.x;
-  if (t >= IPB * V) return;
-  const int li = t / V, v = t % V;
-  const int kind = skind[li];
-  if (kind == FK_SKIP) return;
-  const int cell = sitem[3 * li], d = sitem[3 * li + 1], side = sitem[3 * li + 2];
-  const LevelView& L = a.lv;
-  const double dt = a.dtl[a.level];
-  double area = 1.0;
+// One face (axis d, side) of an active cell at spatial face point g: this thread's share of the
+// face integral, summed over the N time nodes into acc (quadrature weights included).  qf holds
+// the virtual neighbour's values on the fine side of a coarse/fine face.  FL: the numerical flux
+// (0 Rusanov, 1 Osher-Solomon; Euler), a template parameter so that the Rusanov kernels do not
+// carry the Osher flux's registers.
+template <int D, int M, int PDE, int d, int FL>
+__device__ __forceinline__ void flux_face(const HotArgs& a, int kind, const double* qA, const double* qB,
+                                          const double* qf, int g, int side, double* acc) {
+  constexpr int N = M + 1, V = nvars(D, PDE), NSP = ipow(N, D), NST = NSP * N;
+  constexpr int dstr = ipow(N, d);
+  int sbase = 0;
+  double ws = 1.0;
+  {
+    int t = g;
 #pragma unroll
-  for (int b = 0; b < D; b++)
-    if (b != d) area *= L.dx[b];
-  double F;
-  if (kind == FK_COARSE) {
-    // fine cells of the refined neighbour that touch this face; their memory slot faces this cell
-    const LevelView& Lc = a.lvc;
-    const int r = a.T.r;
-    long long di = a.alist[cell];
-    int ijk[3] = {(int)(di % L.L[0]), (int)((di / L.L[0]) % L.L[1]), (int)(di / ((long long)L.L[0] * L.L[1]))};
-    const int* nb = snb + 3 * li;
-    const int t0 = d == 0 ? 1 : 0;
-    const int t1 = d == 2 ? 1 : 2;
-    double acc = 0.0;
-    const int nr2 = (D == 3) ? r : 1;
-    for (int c1 = 0; c1 < nr2; c1++)
-      for (int c0 = 0; c0 < r; c0++) {
-        int fc[3] = {0, 0, 0};
-        fc[d] = side ? r * nb[d] : r * nb[d] + r - 1;
-        fc[t0] = r * ijk[t0] + c0;
-        if (D == 3) fc[t1] = r * ijk[t1] + c1;
-        int fa = Lc.aid[didx(Lc, fc[0], fc[1], fc[2])];
-        if (fa < 0) { atomicOr(a.err, 2); continue; }
-        double* m = a.memc + ((long long)fa * 2 * D + 2 * d + (1 - side)) * V + v;
-        acc += *m;
-        *m = 0.0;
-      }
-    F = acc / (dt * area);
-  } else {
-    double acc = 0.0;
-    const double* src = sh + (li * NPT) * V + v;
-#pragma unroll
-    for (int g = 0; g < NPT; g++) acc += src[g * V];
-    F = acc;
+    for (int b = 0; b < D; b++) {
+      if (b == d) continue;
+      const int j = t % N;
+      t /= N;
+      sbase += j * ipow(N, b);
+      ws *= a.T.w[j];
+    }
   }
-  a.fl[((long long)cell * 2 * D + 2 * d + side) * V + v] = F;
-  if (kind == FK_FINE) a.mem[((long long)cell * 2 * D + 2 * d + side) * V + v] += F * dt * area;
+#pragma unroll
+  for (int v = 0; v < V; v++) acc[v] = 0.0;
+  if (kind != FK_SAME && kind != FK_FINE && kind != FK_BOUNDARY) return;
+  const double* pa = side ? a.T.psi1 : a.T.psi0;
+  const double* pb = side ? a.T.psi0 : a.T.psi1;
+  const int bck = kind == FK_BOUNDARY ? a.bc[2 * d + side] : -1;
+  // a transmissive boundary face takes the flux of the trace itself
+  const bool plain = kind == FK_BOUNDARY && bck != BC_INFLOW && bck != BC_REFLECTIVE;
+  const bool x2 = PDE == PDE_EULER && FL == 0 && !plain;   // rusanov_euler_x2
+  const double wsp = x2 ? 0.5 * ws : ws;
+#pragma unroll 1
+  for (int s = 0; s < N; s++) {
+    const int nbase = sbase + NSP * s;
+    double qa[V], ql[V], qr[V], f[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) qa[v] = trace_n<N, dstr>(pa, qA + v * NST + nbase);
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+      double qo;   // the state across the face
+      if (kind == FK_SAME) qo = trace_n<N, dstr>(pb, qB + v * NST + nbase);
+      else if (kind == FK_FINE) qo = qf[v * N + s];
+      else if (bck == BC_INFLOW) qo = a.P.inflow[v];
+      else if (bck == BC_REFLECTIVE && PDE == PDE_EULER && v == 1 + d) qo = -qa[v];
+      else qo = qa[v];
+      ql[v] = side ? qa[v] : qo;
+      qr[v] = side ? qo : qa[v];
+    }
+    if (plain) {
+      Pde<PDE, D>::flux(qa, d, f, a.P);
+    } else if constexpr (PDE == PDE_EULER && FL == 1) {
+      osher_euler<D>(ql, qr, d, f, a.P);
+    } else if constexpr (PDE == PDE_EULER) {
+      rusanov_euler_x2<D>(ql, qr, d, f, a.P);
+    } else {
+      rusanov<PDE, D>(ql, qr, d, f, a.P);
+    }
+    const double wgt = wsp * a.T.w[s];
+#pragma unroll
+    for (int v = 0; v < V; v++) acc[v] = fma(wgt, f[v], acc[v]);
+  }
+}
+
+// reduce the face points' shares of every (face item, variable) of the CTA and finish the face
+template <int D, int M, int PDE, int DIV>
+__device__ __forceinline__ void flux_finish(const HotArgs& a, const double* sh,
+                                            const FluxShm<FluxCfg<D, M, PDE, DIV>::CPB>& fs) {
+  using C = FluxCfg<D, M, PDE, DIV>;
+  constexpr int NF = C::NF, V = C::V, CPB = C::CPB;
+  const LevelView& L = a.lv;
+  for (int t = threadIdx.x; t < CPB * V; t += C::THREADS) {
+    const int li = t / V, v = t - (t / V) * V;
+    const int kind = fs.kind[li];
+    if (kind == FK_SKIP) continue;
+    const int cell = fs.item[3 * li], d = fs.item[3 * li + 1], side = fs.item[3 * li + 2];
+    const double dt = a.dtl[a.level];
+    double area = 1.0;
+#pragma unroll
+    for (int b = 0; b < D; b++)
+      if (b != d) area *= L.dx[b];
+    double F;
+    if (kind == FK_COARSE) {
+      // fine cells of the refined neighbour that touch this face; their memory slot faces this cell
+      const LevelView& Lc = a.lvc;
+      const int r = a.T.r;
+      int ci[3];
+      cell_ijk(L, a.alist[cell], ci);
+      const int* nb = fs.nb + 3 * li;
+      const int t0 = d == 0 ? 1 : 0;
+      const int t1 = d == 2 ? 1 : 2;
+      double acc = 0.0;
+      const int nr2 = (D == 3) ? r : 1;
+      for (int c1 = 0; c1 < nr2; c1++)
+        for (int c0 = 0; c0 < r; c0++) {
+          // fine cell (axis by axis, so that nothing is indexed at run time): across the face on
+          // axis d, offsets c0, c1 on the transverse axes t0, t1
+          int fc[3];
+#pragma unroll
+          for (int b = 0; b < 3; b++)
+            fc[b] = b == d ? (side ? r * nb[b] : r * nb[b] + r - 1)
+                           : (b == t0 ? r * ci[b] + c0 : ((D == 3 && b == t1) ? r * ci[b] + c1 : 0));
+          const int fa = Lc.aid[didx(Lc, fc[0], fc[1], fc[2])];
+          if (fa < 0) { atomicOr(a.err, 2); continue; }
+          double* m = a.memc + ((long long)fa * 2 * D + 2 * d + (1 - side)) * V + v;
+          acc += *m;
+          *m = 0.0;
+        }
+      F = acc / (dt * area);
+    } else {
+      double acc = 0.0;
+      const double* src = sh + (li * NF) * V + v;
+#pragma unroll
+      for (int g = 0; g < NF; g++) acc += src[g * V];
+      F = acc;
+    }
+    a.fl[((long long)cell * 2 * D + 2 * d + side) * V + v] = F;
+    // a low face between two active cells of this level is also the -d neighbour's high face: a
+    // copy in its high slot, so that the update reads only its own cell's 2*D slots
+    if (kind == FK_SAME) a.fl[((long long)fs.nbaid[li] * 2 * D + 2 * d + 1) * V + v] = F;
+    if (kind == FK_FINE) a.mem[((long long)cell * 2 * D + 2 * d + side) * V + v] += F * dt * area;
+  }
 }
 
 // ------------------------------------------------------------------------------------------
 // Face flux kernel (Eqs. flux:F..flux:H, eqn.rusanov, eqn.osher, eqn.memory.sum).  Work items are
-// faces: the low face of every active cell on every axis (by chunks of cells, the axes of a chunk
-// in turn), then the listed high faces whose neighbour is not an active cell of this level
-// (boundary, coarse or fine neighbour).  One thread per (face, quadrature point); the
-// N^(d-1) x N space-time Gauss points of a face coincide with the nodal points, so a trace is
-// one N-term contraction along the normal.  Faces toward a virtual child are fine sides of a
-// coarse/fine face: the coarse predictor is evaluated at this cell's points and sub-step, and
-// the face integral is added to this cell's memory variable.  Faces toward a virtual mother are
-// coarse sides: the flux is the sum of the fine cells' memory variables over the r sub-steps,
-// normalised by dt * area of this level.
+// faces: the listed high faces whose neighbour is not an active cell of this level (boundary,
+// coarse or fine neighbour), then the low face of every active cell on every axis (by chunks of
+// CPB cells, the axes of a chunk in turn).  One thread per (face, spatial quadrature point), looping
+// over the N time nodes; the N^(d-1) x N space-time Gauss points of a face coincide with the
+// nodal points, so a trace is one N-term contraction along the normal.  Faces toward a virtual
+// child are fine sides of a coarse/fine face: the coarse predictor is evaluated at this cell's
+// points and sub-step (contracted along the normal by the item's threads together, then across
+// the face by each thread for its point), and the face integral is added to this cell's memory
+// variable.  Faces toward a virtual mother are coarse sides: the flux is the sum of the fine
+// cells' memory variables over the r sub-steps, normalised by dt * area of this level.
 // ------------------------------------------------------------------------------------------
-template <int D, int M, int PDE, int DIV = 1>
-__device__ __forceinline__ void flux_body(const HotArgs& a, const int bid) {
+template <int D, int M, int PDE, int DIV, int FL>
+__device__ __forceinline__ void flux_body(const HotArgs& a, const int bid,
+                                          FluxShm<FluxCfg<D, M, PDE, DIV>::CPB>& fs) {
   using C = FluxCfg<D, M, PDE, DIV>;
-  constexpr int N = M + 1, NPT = C::NPT, V = C::V;
+  constexpr int N = M + 1, NF = C::NF, V = C::V, CPB = C::CPB;
   constexpr int NST = ipow(N, D + 1);
   extern __shared__ double sh[];
-  __shared__ int skind[C::CPB];
-  __shared__ int snb[3 * C::CPB];
-  __shared__ int sitem[3 * C::CPB];
-  const int li = threadIdx.x / NPT, g = threadIdx.x % NPT;
-  // CTAs 0..D*nchunk-1 take the low faces: chunk c of CPB active cells, axis d = CTA mod D, so
-  // the D passes over a chunk run back to back and share its predictor data in L2.  The rest
-  // take the listed high faces (item e = d * na + cell).
-  const long long nlob = (long long)D * ((a.na + C::CPB - 1) / C::CPB);
+  const int li = threadIdx.x / NF, g = threadIdx.x - (threadIdx.x / NF) * NF;
+  // The first CTAs take the listed high faces (item e = d * na + cell), the others the low faces:
+  // chunk c of CPB active cells, the chunks from the last to the first, axis d = CTA mod D, so the
+  // D passes over a chunk run back to back and share its predictor data in L2 (and, in the fused
+  // kernel, the faces a chunk needs from later chunks are mostly done when its own are).
+  const long long nchunk = (a.na + CPB - 1) / CPB;
+  const long long nhb = (a.nh + CPB - 1) / CPB;
   bool ok;
   int cell = 0, d = 0, side = 0;
-  if (bid < nlob) {
-    const long long chunk = bid / D;
-    d = (int)(bid - chunk * D);
-    const long long c = chunk * C::CPB + li;
+  if (bid >= nhb) {
+    const long long q = bid - nhb;
+    const long long chunk = nchunk - 1 - q / D;
+    d = (int)(q - (q / D) * D);
+    const long long c = chunk * CPB + li;
     ok = c < a.na;
     cell = ok ? (int)c : 0;
   } else {
-    const long long h = (bid - nlob) * C::CPB + li;
+    const long long h = bid * CPB + li;
     ok = h < a.nh;
     if (ok) {
       const long long e = a.hflist[h];
@@ -827,67 +918,152 @@ __device__ __forceinline__ void flux_body(const HotArgs& a, const int bid) {
   }
   const LevelView& L = a.lv;
   int ijk[3] = {0, 0, 0};
-  if (ok) {
-    long long di = a.alist[cell];
-    ijk[0] = (int)(di % L.L[0]);
-    ijk[1] = (int)((di / L.L[0]) % L.L[1]);
-    ijk[2] = (int)(di / ((long long)L.L[0] * L.L[1]));
+  if (ok) cell_ijk(L, a.alist[cell], ijk);
+  int nb[3], aidb, maid;
+  const int kind = face_kind<D>(a, ok, ijk, d, side, nb, &aidb, &maid);
+  double* R = sh + li * NF * V * N;
+  double* qf = sh + C::THREADS * V * N + threadIdx.x * V * N;
+  if (__syncthreads_or(kind == FK_FINE)) {
+    // fine sides of coarse/fine faces: the virtual neighbour's values from its coarse mother
+    const double* qC = a.qhm + (long long)(maid < 0 ? 0 : maid) * V * NST;
+    if (kind == FK_FINE) {
+      if (d == 0) fine_normal<D, M, PDE, 0>(a, side, qC, g, R);
+      else if (D == 2 || d == 1) fine_normal<D, M, PDE, 1>(a, side, qC, g, R);
+      else fine_normal<D, M, PDE, (D == 3 ? 2 : 1)>(a, side, qC, g, R);
+    }
+    __syncthreads();
+    if (kind == FK_FINE) {
+      if (d == 0) fine_transverse<D, M, PDE, 0>(a, ijk, g, R, qf);
+      else if (D == 2 || d == 1) fine_transverse<D, M, PDE, 1>(a, ijk, g, R, qf);
+      else fine_transverse<D, M, PDE, (D == 3 ? 2 : 1)>(a, ijk, g, R, qf);
+    }
+    __syncthreads();   // R is read no more: its space takes the face points' shares below
   }
   const double* qA = a.qh + (long long)cell * V * NST;
-  double contrib[V];
-  int nb[3];
-  int kind;
-  if (d == 0) kind = flux_point<D, M, PDE, 0>(a, ok, ijk, qA, g, side, contrib, nb);
-  else if (D == 2 || d == 1) kind = flux_point<D, M, PDE, 1>(a, ok, ijk, qA, g, side, contrib, nb);
-  else kind = flux_point<D, M, PDE, (D == 3 ? 2 : 1)>(a, ok, ijk, qA, g, side, contrib, nb);
+  const double* qB = a.qh + (long long)(aidb < 0 ? 0 : aidb) * V * NST;
+  double acc[V];
+  if (d == 0) flux_face<D, M, PDE, 0, FL>(a, kind, qA, qB, qf, g, side, acc);
+  else if (D == 2 || d == 1) flux_face<D, M, PDE, 1, FL>(a, kind, qA, qB, qf, g, side, acc);
+  else flux_face<D, M, PDE, (D == 3 ? 2 : 1), FL>(a, kind, qA, qB, qf, g, side, acc);
 #pragma unroll
-  for (int v = 0; v < V; v++) sh[threadIdx.x * V + v] = contrib[v];
+  for (int v = 0; v < V; v++) sh[threadIdx.x * V + v] = acc[v];
   if (g == 0) {
-    skind[li] = ok ? kind : FK_SKIP;
-    snb[3 * li] = nb[0]; snb[3 * li + 1] = nb[1]; snb[3 * li + 2] = nb[2];
-    sitem[3 * li] = cell; sitem[3 * li + 1] = d; sitem[3 * li + 2] = side;
+    fs.kind[li] = kind;
+    fs.nb[3 * li] = nb[0]; fs.nb[3 * li + 1] = nb[1]; fs.nb[3 * li + 2] = nb[2];
+    fs.item[3 * li] = cell; fs.item[3 * li + 1] = d; fs.item[3 * li + 2] = side;
+    fs.nbaid[li] = aidb;
   }
   __syncthreads();
-  flux_finish<D, M, PDE, DIV>(a, sh, sitem, skind, snb);
+  flux_finish<D, M, PDE, DIV>(a, sh, fs);
 }
 
-template <int D, int M, int PDE, int DIV>
-__global__ void __launch_bounds__(FluxCfg<D, M, PDE, DIV>::THREADS) k_flux(const __grid_constant__ HotArgs a) {
-  flux_body<D, M, PDE, DIV>(a, blockIdx.x);
+template <int D, int M, int PDE, int DIV, int FL>
+__global__ void __launch_bounds__(FluxCfg<D, M, PDE, DIV>::THREADS, FluxCfg<D, M, PDE, DIV>::MINB) k_flux(const __grid_constant__ HotArgs a) {
+  __shared__ FluxShm<FluxCfg<D, M, PDE, DIV>::CPB> fs;
+  flux_body<D, M, PDE, DIV, FL>(a, blockIdx.x, fs);
 }
 
-// ------------------------------------------------------------------------------------------
-// Update kernel, Eq. eq:finite_vol (source zero): one thread per active cell.  The high face of
-// axis d is the low face of the +d neighbour when that neighbour is active on this level.
-// ------------------------------------------------------------------------------------------
-template <int D, int M, int PDE>
-__device__ __forceinline__ void update_body(const HotArgs& a, const int bid) {
+// Eq. eq:finite_vol (source zero) for active cell `cell`: u -= dt/dx_d (F_high - F_low) per axis.
+// The high face of every axis is in the cell's own high slot (the flux kernel copies a +d
+// neighbour's low face there), so the cell reads only its 2*D contiguous slots.  L2: read the
+// fluxes through L2 only (other CTAs of the same kernel wrote them).
+template <int D, int M, int PDE, bool L2>
+__device__ __forceinline__ void update_cell(const HotArgs& a, int cell, double dt) {
   constexpr int V = nvars(D, PDE);
-  const int cell = bid * blockDim.x + threadIdx.x;
-  if (cell >= a.na) return;
   const LevelView& L = a.lv;
-  long long di = a.alist[cell];
-  int ijk[3] = {(int)(di % L.L[0]), (int)((di / L.L[0]) % L.L[1]), (int)(di / ((long long)L.L[0] * L.L[1]))};
-  const double dt = a.dtl[a.level];
-  if (dt == 0.0) return;   // a step of length zero leaves the averages as they are
+  const long long di = a.alist[cell];
+  const double* fc = a.fl + (long long)cell * 2 * D * V;
   double u[V];
 #pragma unroll
   for (int v = 0; v < V; v++) u[v] = L.u[v * L.n + di];
+#pragma unroll
   for (int d = 0; d < D; d++) {
-    const double* flo = a.fl + ((long long)cell * 2 * D + 2 * d) * V;
-    const double* fhi = a.fl + ((long long)cell * 2 * D + 2 * d + 1) * V;
-    int nb[3] = {ijk[0], ijk[1], ijk[2]};
-    if (bcmap(L.L, a.bc, d, ijk[d] + 1, &nb[d])) {
-      long long nd = didx(L, nb[0], nb[1], nb[2]);
-      if (L.st[nd] == 0) fhi = a.fl + ((long long)L.aid[nd] * 2 * D + 2 * d) * V;
-    }
     const double c = dt / L.dx[d];
 #pragma unroll
-    for (int v = 0; v < V; v++) u[v] -= c * (fhi[v] - flo[v]);
+    for (int v = 0; v < V; v++) {
+      const double* lo = fc + 2 * d * V + v;
+      const double fhi = L2 ? __ldcg(lo + V) : lo[V], flo = L2 ? __ldcg(lo) : lo[0];
+      u[v] -= c * (fhi - flo);
+    }
   }
 #pragma unroll
   for (int v = 0; v < V; v++) L.u[v * L.n + di] = u[v];
   if (!Pde<PDE, D>::physical(u, a.P)) atomicOr(a.err, 1);
+}
+
+// ------------------------------------------------------------------------------------------
+// Fused face flux and update (Eq. eq:finite_vol with Eqs. eqn.rusanov / eqn.osher /
+// eqn.memory.sum), without any wait.  The CTAs of k_flux; chunk c holds the active cells
+// c*CPB .. c*CPB+CPB-1.  Each of a chunk's cells needs 2*D face fluxes (a low and a high face per
+// axis), and every face item a CTA finishes is an arrival at the chunks that read it: a low face
+// at its own cell's chunk, and, when the -d neighbour is an active cell of this level, at that
+// neighbour's chunk too (it is the neighbour's high face); a listed high face at its cell's
+// chunk.  So every cell receives exactly 2*D arrivals.  A CTA publishes its fluxes, then adds its
+// arrivals to the per-chunk counters; the CTA whose addition brings a chunk's counter to 2*D times
+// its cells applies the one-step update to that chunk.  The update does the arithmetic of
+// k_update in the same order, so the averages are bitwise those of the two-kernel path.
+// ------------------------------------------------------------------------------------------
+template <int D, int M, int PDE, int DIV, int FL>
+__device__ __forceinline__ void flux_update_body(const HotArgs& a, const int bid,
+                                                 FluxShm<FluxCfg<D, M, PDE, DIV>::CPB>& fs) {
+  using C = FluxCfg<D, M, PDE, DIV>;
+  constexpr int V = C::V, CPB = C::CPB;
+  flux_body<D, M, PDE, DIV, FL>(a, bid, fs);
+  __shared__ int s_nfull;
+  __shared__ int s_full[CPB + 1];   // chunks this CTA completed
+  const int t = threadIdx.x;
+  if (t == 0) s_nfull = 0;
+  // publish this CTA's fluxes before any arrival is counted
+  if (t < CPB * V) __threadfence();
+  __syncthreads();
+  const long long nhb = (a.nh + CPB - 1) / CPB;
+  auto arrive = [&](int chunk, int n) {
+    const int cells = min(CPB, a.na - chunk * CPB);
+    if (atomicAdd(a.fsync + chunk, n) + n == 2 * D * cells) {
+      __threadfence();
+      s_full[atomicAdd(&s_nfull, 1)] = chunk;
+    }
+  };
+  if (t < CPB) {
+    if (bid >= nhb) {
+      // low faces: the chunk's own cells, and the -d neighbours that are active cells of this level
+      const int chunk = (int)((a.na + CPB - 1) / CPB - 1 - (bid - nhb) / D);
+      if (t == 0) arrive(chunk, min(CPB, a.na - chunk * CPB));
+      if (chunk * CPB + t < a.na && fs.nbaid[t] >= 0) arrive(fs.nbaid[t] / CPB, 1);
+    } else {
+      const long long h = bid * CPB + t;
+      if (h < a.nh) arrive(fs.item[3 * t] / CPB, 1);
+    }
+  }
+  __syncthreads();
+  const int nfull = s_nfull;
+  if (nfull == 0) return;
+  const double dt = a.dtl[a.level];
+  if (dt == 0.0) return;   // a step of length zero leaves the averages as they are
+  // Eq. eq:finite_vol for the cells of the completed chunks, one thread per cell (the fluxes come
+  // from L2: other CTAs wrote them)
+  for (int k = t; k < nfull * CPB; k += C::THREADS) {
+    const int cell = s_full[k / CPB] * CPB + (k - (k / CPB) * CPB);
+    if (cell < a.na) update_cell<D, M, PDE, true>(a, cell, dt);
+  }
+}
+
+template <int D, int M, int PDE, int DIV, int FL>
+__global__ void __launch_bounds__(FluxCfg<D, M, PDE, DIV>::THREADS, FluxCfg<D, M, PDE, DIV>::MINB) k_flux_update(const __grid_constant__ HotArgs a) {
+  __shared__ FluxShm<FluxCfg<D, M, PDE, DIV>::CPB> fs;
+  flux_update_body<D, M, PDE, DIV, FL>(a, blockIdx.x, fs);
+}
+
+// ------------------------------------------------------------------------------------------
+// Update kernel, Eq. eq:finite_vol (source zero): one thread per active cell (update_cell).
+// ------------------------------------------------------------------------------------------
+template <int D, int M, int PDE>
+__device__ __forceinline__ void update_body(const HotArgs& a, const int bid) {
+  const int cell = bid * blockDim.x + threadIdx.x;
+  if (cell >= a.na) return;
+  const double dt = a.dtl[a.level];
+  if (dt == 0.0) return;   // a step of length zero leaves the averages as they are
+  update_cell<D, M, PDE, false>(a, cell, dt);
 }
 
 template <int D, int M, int PDE>
@@ -966,10 +1142,19 @@ __global__ void __launch_bounds__(PredCfg<D, M, PDE>::THREADS) k_predict_batch(c
   predict_body<D, M, PDE>(b.a[m], blockIdx.x - b.start[m]);
 }
 
-template <int D, int M, int PDE>
-__global__ void __launch_bounds__(FluxCfg<D, M, PDE>::THREADS) k_flux_batch(const __grid_constant__ HotBatch b) {
+template <int D, int M, int PDE, int FL>
+__global__ void __launch_bounds__(FluxCfg<D, M, PDE>::THREADS, FluxCfg<D, M, PDE>::MINB) k_flux_batch(const __grid_constant__ HotBatch b) {
   const int m = batch_member(b, blockIdx.x);
-  flux_body<D, M, PDE>(b.a[m], blockIdx.x - b.start[m]);
+  __shared__ FluxShm<FluxCfg<D, M, PDE>::CPB> fs;
+  flux_body<D, M, PDE, 1, FL>(b.a[m], blockIdx.x - b.start[m], fs);
+}
+
+// fused face flux and update of every member (each member counts the arrivals of its own chunks)
+template <int D, int M, int PDE, int FL>
+__global__ void __launch_bounds__(FluxCfg<D, M, PDE>::THREADS, FluxCfg<D, M, PDE>::MINB) k_flux_update_batch(const __grid_constant__ HotBatch b) {
+  const int m = batch_member(b, blockIdx.x);
+  __shared__ FluxShm<FluxCfg<D, M, PDE>::CPB> fs;
+  flux_update_body<D, M, PDE, 1, FL>(b.a[m], blockIdx.x - b.start[m], fs);
 }
 
 template <int D, int M, int PDE>

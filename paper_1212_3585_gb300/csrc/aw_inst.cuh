@@ -107,19 +107,56 @@ struct Launch {
     }
     return 1;
   }
-  static int flux(const HotArgs& a, cudaStream_t st) {
+  // the face flux kernels of one numerical flux (FL: 0 Rusanov, 1 Osher-Solomon, Euler only)
+  template <int FL>
+  static int flux_fl(const HotArgs& a, cudaStream_t st) {
     int blocks = flux_ctas_of<CF>(a);
     if (!blocks) return 0;
     if (small(blocks)) {
       static std::once_flag init;
-      smem_attr(k_flux<D, M, PDE, SMALL>, CFs::SMEM, init);
-      k_flux<D, M, PDE, SMALL><<<flux_ctas_of<CFs>(a), CFs::THREADS, CFs::SMEM, st>>>(a);
+      smem_attr(k_flux<D, M, PDE, SMALL, FL>, CFs::SMEM, init);
+      k_flux<D, M, PDE, SMALL, FL><<<flux_ctas_of<CFs>(a), CFs::THREADS, CFs::SMEM, st>>>(a);
     } else {
       static std::once_flag init;
-      smem_attr(k_flux<D, M, PDE, 1>, CF::SMEM, init);
-      k_flux<D, M, PDE, 1><<<blocks, CF::THREADS, CF::SMEM, st>>>(a);
+      smem_attr(k_flux<D, M, PDE, 1, FL>, CF::SMEM, init);
+      k_flux<D, M, PDE, 1, FL><<<blocks, CF::THREADS, CF::SMEM, st>>>(a);
     }
     return 1;
+  }
+  static int flux(const HotArgs& a, cudaStream_t st) {
+    if constexpr (PDE == PDE_EULER) {
+      if (a.flux == 1) return flux_fl<1>(a, st);
+    }
+    return flux_fl<0>(a, st);
+  }
+  // fused face flux and update: the per-chunk arrival counters zeroed on the stream, then one launch
+  template <class C>
+  static cudaError_t clear_fsync(const HotArgs& a, cudaStream_t st) {
+    const size_t n = (size_t)((a.na + C::CPB - 1) / C::CPB);
+    return cudaMemsetAsync(a.fsync, 0, n * sizeof(int), st);
+  }
+  template <int FL>
+  static int flux_update_fl(const HotArgs& a, cudaStream_t st) {
+    int blocks = flux_ctas_of<CF>(a);
+    if (!blocks) return 0;
+    if (small(blocks)) {
+      static std::once_flag init;
+      smem_attr(k_flux_update<D, M, PDE, SMALL, FL>, CFs::SMEM, init);
+      clear_fsync<CFs>(a, st);
+      k_flux_update<D, M, PDE, SMALL, FL><<<flux_ctas_of<CFs>(a), CFs::THREADS, CFs::SMEM, st>>>(a);
+    } else {
+      static std::once_flag init;
+      smem_attr(k_flux_update<D, M, PDE, 1, FL>, CF::SMEM, init);
+      clear_fsync<CF>(a, st);
+      k_flux_update<D, M, PDE, 1, FL><<<blocks, CF::THREADS, CF::SMEM, st>>>(a);
+    }
+    return 1;
+  }
+  static int flux_update(const HotArgs& a, cudaStream_t st) {
+    if constexpr (PDE == PDE_EULER) {
+      if (a.flux == 1) return flux_update_fl<1>(a, st);
+    }
+    return flux_update_fl<0>(a, st);
   }
   static int update(const HotArgs& a, cudaStream_t st) {
     const int blocks = update_ctas(a);
@@ -218,13 +255,37 @@ struct Launch {
     k_predict_batch<D, M, PDE><<<blocks, CP::THREADS, CP::SMEM, st>>>(b);
     return 1;
   }
-  static int flux_b(HotBatch& b, cudaStream_t st) {
+  template <int FL>
+  static int flux_b_fl(HotBatch& b, cudaStream_t st) {
     const int blocks = fill_starts(b, flux_ctas);
     if (!blocks) return 0;
     static std::once_flag init;
-    smem_attr(k_flux_batch<D, M, PDE>, CF::SMEM, init);
-    k_flux_batch<D, M, PDE><<<blocks, CF::THREADS, CF::SMEM, st>>>(b);
+    smem_attr(k_flux_batch<D, M, PDE, FL>, CF::SMEM, init);
+    k_flux_batch<D, M, PDE, FL><<<blocks, CF::THREADS, CF::SMEM, st>>>(b);
     return 1;
+  }
+  // every member of a batch has the same numerical flux
+  static int flux_b(HotBatch& b, cudaStream_t st) {
+    if constexpr (PDE == PDE_EULER) {
+      if (b.n > 0 && b.a[0].flux == 1) return flux_b_fl<1>(b, st);
+    }
+    return flux_b_fl<0>(b, st);
+  }
+  template <int FL>
+  static int flux_update_b_fl(HotBatch& b, cudaStream_t st) {
+    const int blocks = fill_starts(b, flux_ctas);
+    if (!blocks) return 0;
+    static std::once_flag init;
+    smem_attr(k_flux_update_batch<D, M, PDE, FL>, CF::SMEM, init);
+    for (int m = 0; m < b.n; m++) clear_fsync<CF>(b.a[m], st);
+    k_flux_update_batch<D, M, PDE, FL><<<blocks, CF::THREADS, CF::SMEM, st>>>(b);
+    return 1;
+  }
+  static int flux_update_b(HotBatch& b, cudaStream_t st) {
+    if constexpr (PDE == PDE_EULER) {
+      if (b.n > 0 && b.a[0].flux == 1) return flux_update_b_fl<1>(b, st);
+    }
+    return flux_update_b_fl<0>(b, st);
   }
   static int update_b(HotBatch& b, cudaStream_t st) {
     const int blocks = fill_starts(b, update_ctas);
@@ -244,7 +305,9 @@ struct Launch {
     o.D = D; o.M = M; o.PDE = PDE; o.V = V;
     o.weno_tile = &weno_tile;
     o.weno = &weno; o.predict = &predict; o.flux = &flux; o.update = &update; o.project = &project;
+    o.flux_update = &flux_update;
     o.weno_b = &weno_b; o.predict_b = &predict_b; o.flux_b = &flux_b; o.update_b = &update_b;
+    o.flux_update_b = &flux_update_b;
     o.project_b = &project_b;
     return o;
   }

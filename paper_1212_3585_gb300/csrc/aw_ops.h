@@ -16,6 +16,8 @@ struct HotOps {
   int (*predict)(const HotArgs&, cudaStream_t);
   int (*flux)(const HotArgs&, cudaStream_t);
   int (*update)(const HotArgs&, cudaStream_t);
+  // the face flux and the update in one launch (k_flux_update), bitwise what flux + update give
+  int (*flux_update)(const HotArgs&, cudaStream_t);
   // project virtual cells (vlist, nv) from mother dofs `src` (space-time if spacetime != 0,
   // else spatial WENO dofs), into the dense averages (dense != 0) or into out[k*V + v]
   int (*project)(const HotArgs&, const int32_t* vlist, int nv, const double* src, int spacetime,
@@ -26,6 +28,7 @@ struct HotOps {
   int (*predict_b)(HotBatch&, cudaStream_t);
   int (*flux_b)(HotBatch&, cudaStream_t);
   int (*update_b)(HotBatch&, cudaStream_t);
+  int (*flux_update_b)(HotBatch&, cudaStream_t);
   int (*project_b)(HotBatch&, cudaStream_t);
 };
 
@@ -34,11 +37,13 @@ bool get_ops(int D, int M, int PDE, HotOps* out);
 
 // launch-shape rules (aw_set_launch_params): WENO by passes from pass_min_cells cells per level,
 // 2D WENO tiles of 8x8 from tile8_min_cells, quarter-size predictor/flux CTAs when the full-size
-// ones give fewer than small_ctas_per_sm CTAs per SM.  Process-wide; the results never depend on
-// them, only the speed.
+// ones give fewer than small_ctas_per_sm CTAs per SM, the face flux and the update fused into one
+// launch (fuse_flux_update != 0) or two.  Process-wide; the results never depend on them, only
+// the speed.
 struct LaunchParams {
   long long pass_min_cells, tile8_min_cells;
   int small_ctas_per_sm;
+  int fuse_flux_update;
 };
 LaunchParams launch_params();
 void set_launch_params(const LaunchParams& p);

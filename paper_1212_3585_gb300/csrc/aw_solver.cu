@@ -126,6 +126,7 @@ struct Level {
   int8_t* hflag = nullptr;     // per (axis, active id): the high face needs computing
   int32_t* hflist = nullptr;   // compacted high faces, axis * na + active id
   int nh = 0;
+  int32_t* fsync = nullptr;    // arrival counters of the fused face flux and update, per chunk
   long long cap = 0;
 };
 
@@ -155,6 +156,7 @@ struct aw_solver {
   cudaGraphExec_t gexec = nullptr;  // its instantiated graph, reused while the arguments match
   HotArgs gargs;
   int gchunk = 0;
+  bool gfused = false;
   int* d_err = nullptr;
   int* d_cnt = nullptr;
   int* h_cnt = nullptr;
@@ -383,7 +385,7 @@ __global__ void k_dt(LevelView L, const int32_t* alist, int na, RtPhys R, double
 // ---- device-side time step of a uniform mesh (aw_advance_graph): the host logic of step_cfl on
 // one thread -- dt0 from the CFL reduction, clipped at t_end, the time advanced, the level time
 // steps dt0 / r^l written -- so that level-0 steps need no host synchronisation.  A step after
-// t_end, after a non-physical update or without a stable time step gets dt = 0 (k_update leaves
+// t_end, after a non-physical update or without a stable time step gets dt = 0 (the update leaves
 // the averages unchanged) ----
 __global__ void k_dt_commit(unsigned long long* dtmin, GState* g, double* dtl, int r, int* err) {
   const double h = __longlong_as_double((long long)*dtmin);
@@ -936,11 +938,13 @@ static int ensure_active_cap(aw_solver* s, int l, long long need) {
   Level& L = s->lev[l];
   if (need <= L.cap) return AW_OK;
   long long cap = std::max(need + need / 2, (long long)64);
-  for (void* p : {(void*)L.wh, (void*)L.qh, (void*)L.fl, (void*)L.mem, (void*)L.hflag, (void*)L.hflist})
+  for (void* p : {(void*)L.wh, (void*)L.qh, (void*)L.fl, (void*)L.mem, (void*)L.hflag, (void*)L.hflist,
+                  (void*)L.fsync})
     dfree(s->stream, p);
   L.wh = L.qh = L.fl = L.mem = nullptr;
   L.hflag = nullptr;
   L.hflist = nullptr;
+  L.fsync = nullptr;
   L.cap = 0;
   size_t V = s->V;
   cudaStream_t st = s->stream;
@@ -949,7 +953,8 @@ static int ensure_active_cap(aw_solver* s, int l, long long need) {
       dalloc(st, (void**)&L.wh, cap * V * s->NSP * sizeof(double)) != cudaSuccess ||
       dalloc(st, (void**)&L.qh, cap * V * s->NST * sizeof(double)) != cudaSuccess ||
       dalloc(st, (void**)&L.fl, cap * 2 * s->D * V * sizeof(double)) != cudaSuccess ||
-      dalloc(st, (void**)&L.mem, cap * 2 * s->D * V * sizeof(double)) != cudaSuccess)
+      dalloc(st, (void**)&L.mem, cap * 2 * s->D * V * sizeof(double)) != cudaSuccess ||
+      dalloc(st, (void**)&L.fsync, cap * sizeof(int32_t)) != cudaSuccess)
     AW_FAIL(AW_ENOMEM, "per-active arrays of level %d (%lld cells)", l, cap);
   L.cap = cap;
   return AW_OK;
@@ -1085,6 +1090,7 @@ static HotArgs make_args(const aw_solver* s, int l, int sub) {
     a.ys = L.ys;
     a.nys = L.ny;
   }
+  a.fsync = L.fsync;
   return a;
 }
 
@@ -1116,8 +1122,12 @@ static int advance(aw_solver* s, int l, int sub) {
   CK(cudaGetLastError());
   if (l < s->lmax)
     for (int k = 0; k < s->r; k++) TRY(advance(s, l + 1, k));
-  s->launches += timed(s, KIND_FLUX, [&] { return s->ops.flux(a, st); });
-  s->launches += timed(s, KIND_UPDATE, [&] { return s->ops.update(a, st); });
+  if (launch_params().fuse_flux_update) {
+    s->launches += timed(s, KIND_FLUX, [&] { return s->ops.flux_update(a, st); });
+  } else {
+    s->launches += timed(s, KIND_FLUX, [&] { return s->ops.flux(a, st); });
+    s->launches += timed(s, KIND_UPDATE, [&] { return s->ops.update(a, st); });
+  }
   CK(cudaGetLastError());
   if (l >= 1 && sub == s->r - 1) TRY(average_into(s, l - 1));
   return AW_OK;
@@ -1322,7 +1332,7 @@ static void free_solver(aw_solver* s) {
                     (void*)L.alist, (void*)L.vlist, (void*)L.mlist, (void*)L.clist, (void*)L.tflag, (void*)L.tiles,
                     (void*)L.wh, (void*)L.qh, (void*)L.fl, (void*)L.mem, (void*)L.hflag, (void*)L.hflist,
                     (void*)L.xmark, (void*)L.xslot, (void*)L.xlist, (void*)L.xs, (void*)L.ymark, (void*)L.yslot,
-                    (void*)L.ylist, (void*)L.ys})
+                    (void*)L.ylist, (void*)L.ys, (void*)L.fsync})
       dfree(st, p);
   }
   for (void* p : {(void*)s->d_dtl, (void*)s->d_dtmin, (void*)s->d_err, (void*)s->d_cnt, (void*)s->d_bcnt,
@@ -1399,6 +1409,15 @@ __global__ void k_selftest_rcp(const double* x, long long n, double* out) {
   if (k >= n) return;
   out[k] = rcp_nr(x[k]);
   out[n + k] = 1.0 / x[k];
+}
+
+__global__ void k_selftest_flux_math(const double* x, long long n, double* out) {
+  long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  out[k] = rcp_nr1(x[k]);
+  out[n + k] = 1.0 / x[k];
+  out[2 * n + k] = sqrt_nr1(x[k]);
+  out[3 * n + k] = sqrt(x[k]);
 }
 
 // ------------------------------------------------------------------------------------------
@@ -1724,8 +1743,12 @@ static int advance_batch(aw_solver* const* S, int n, const bool* live, int l, in
   CK(cudaGetLastError());
   if (deeper)
     for (int k = 0; k < r; k++) TRY(advance_batch(S, n, live, l + 1, k, st, launches));
-  *launches += ops.flux_b(b, st);
-  *launches += ops.update_b(b, st);
+  if (launch_params().fuse_flux_update) {
+    *launches += ops.flux_update_b(b, st);
+  } else {
+    *launches += ops.flux_b(b, st);
+    *launches += ops.update_b(b, st);
+  }
   CK(cudaGetLastError());
   if (l >= 1 && sub == r - 1)
     for (int k = 0; k < b.n; k++) TRY(average_into(S[idx[k]], l - 1));
@@ -1911,9 +1934,10 @@ int aw_advance_graph(aw_solver* s, double t_end, int32_t chunk, aw_stats* st) {
   // kept while the launch arguments (every pointer and size of the level) stay the same
   const Level& L = s->lev[0];
   HotArgs a = make_args(s, 0, 0);
-  const int per_step = 2 + (L.ntiles > 0 ? (a.xs ? s->D : 1) : 0) + 3;
+  const bool fused = launch_params().fuse_flux_update != 0;
+  const int per_step = 2 + (L.ntiles > 0 ? (a.xs ? s->D : 1) : 0) + (fused ? 2 : 3);
   cudaError_t ce = cudaSuccess;
-  if (!s->gexec || s->gchunk != chunk || memcmp(&s->gargs, &a, sizeof a) != 0) {
+  if (!s->gexec || s->gchunk != chunk || s->gfused != fused || memcmp(&s->gargs, &a, sizeof a) != 0) {
     if (s->gexec) cudaGraphExecDestroy(s->gexec);
     s->gexec = nullptr;
     cudaGraph_t graph = nullptr;
@@ -1924,8 +1948,12 @@ int aw_advance_graph(aw_solver* s, double t_end, int32_t chunk, aw_stats* st) {
         k_dt_commit<<<1, 1, 0, gs>>>(s->d_dtmin, s->d_gs, s->d_dtl, s->r, s->d_err);
         s->ops.weno(a, gs);
         s->ops.predict(a, gs);
-        s->ops.flux(a, gs);
-        s->ops.update(a, gs);
+        if (fused) {
+          s->ops.flux_update(a, gs);
+        } else {
+          s->ops.flux(a, gs);
+          s->ops.update(a, gs);
+        }
       }
       ce = cudaStreamEndCapture(gs, &graph);
     }
@@ -1938,6 +1966,7 @@ int aw_advance_graph(aw_solver* s, double t_end, int32_t chunk, aw_stats* st) {
     }
     memcpy(&s->gargs, &a, sizeof a);   // every byte, padding included, for the memcmp above
     s->gchunk = chunk;
+    s->gfused = fused;
   }
   cudaGraphExec_t exec = s->gexec;
   // replay until the device time reaches t_end, one host synchronisation per chunk
@@ -2139,17 +2168,20 @@ int aw_get_launch_params(aw_launch_params* out) {
   out->pass_min_cells = p.pass_min_cells;
   out->tile8_min_cells = p.tile8_min_cells;
   out->small_ctas_per_sm = p.small_ctas_per_sm;
+  out->fuse_flux_update = p.fuse_flux_update;
   return AW_OK;
 }
 
 int aw_set_launch_params(const aw_launch_params* in) {
   if (!in) AW_FAIL(AW_EINVAL, "null argument");
-  if (in->pass_min_cells < 0 || in->tile8_min_cells < 0 || in->small_ctas_per_sm < 0 || in->small_ctas_per_sm > 64)
+  if (in->pass_min_cells < 0 || in->tile8_min_cells < 0 || in->small_ctas_per_sm < 0 || in->small_ctas_per_sm > 64 ||
+      (in->fuse_flux_update != 0 && in->fuse_flux_update != 1))
     AW_FAIL(AW_EINVAL, "launch parameters out of range");
   LaunchParams p;
   p.pass_min_cells = in->pass_min_cells;
   p.tile8_min_cells = in->tile8_min_cells;
   p.small_ctas_per_sm = in->small_ctas_per_sm;
+  p.fuse_flux_update = in->fuse_flux_update;
   set_launch_params(p);
   return AW_OK;
 }
@@ -2245,6 +2277,14 @@ int aw_selftest_reciprocal(const double* x_dev, int64_t n, double* out_dev, uint
   if (!x_dev || !out_dev || n < 0) AW_FAIL(AW_EINVAL, "bad argument");
   if (n == 0) return AW_OK;
   k_selftest_rcp<<<nblk(n, 256), 256, 0, (cudaStream_t)stream>>>(x_dev, n, out_dev);
+  CK(cudaGetLastError());
+  return AW_OK;
+}
+
+int aw_selftest_flux_math(const double* x_dev, int64_t n, double* out_dev, uintptr_t stream) {
+  if (!x_dev || !out_dev || n < 0) AW_FAIL(AW_EINVAL, "bad argument");
+  if (n == 0) return AW_OK;
+  k_selftest_flux_math<<<nblk(n, 256), 256, 0, (cudaStream_t)stream>>>(x_dev, n, out_dev);
   CK(cudaGetLastError());
   return AW_OK;
 }

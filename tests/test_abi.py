@@ -74,11 +74,15 @@ def test_struct_layouts_match_header(tmp_path):
 def test_launch_params_roundtrip_without_gpu():
     """the launch-shape rules are host state: read, changed, rejected when out of range, restored"""
     before = pg.get_launch_params()
-    assert before == {"pass_min_cells": 4096, "tile8_min_cells": 20000, "small_ctas_per_sm": 2}
-    pg.set_launch_params(small_ctas_per_sm=0, pass_min_cells=0)
-    assert pg.get_launch_params() == {"pass_min_cells": 0, "tile8_min_cells": 20000, "small_ctas_per_sm": 0}
+    assert before == {"pass_min_cells": 4096, "tile8_min_cells": 20000, "small_ctas_per_sm": 2,
+                      "fuse_flux_update": 1}
+    pg.set_launch_params(small_ctas_per_sm=0, pass_min_cells=0, fuse_flux_update=0)
+    assert pg.get_launch_params() == {"pass_min_cells": 0, "tile8_min_cells": 20000, "small_ctas_per_sm": 0,
+                                      "fuse_flux_update": 0}
     with pytest.raises(pg.AwError):
         pg.set_launch_params(small_ctas_per_sm=65)
+    with pytest.raises(pg.AwError):
+        pg.set_launch_params(fuse_flux_update=2)
     pg.set_launch_params(**before)
     assert pg.get_launch_params() == before
 
