@@ -71,13 +71,14 @@ SM_COUNT = 152
 FP64_FMA_PER_CLK_PER_SM = 2      # sm_103a: measured 0.598 T DFMA/s at ~1.97 GHz on 152 SMs
 SM_MAX_MHZ = 2070.0
 HBM_GBS = 6792.1                 # measured copy bandwidth of this GB300 pool
-# DRAM bytes per cell of k_predict<2,3,Euler> from one ncu capture of a full-size level-2 launch
-# of this workload (6264 CTAs x 16 cells: dram__bytes_read.sum 51.36 MB + dram__bytes_write.sum
-# 141.52 MB); scaled by the cells of an average launch.  Must be re-captured whenever k_predict
-# changes.
-PREDICTOR_DRAM_BYTES_PER_CELL = (51356416 + 141521408) / (6264 * 16)
-# the same for the 3D workload's kernels (none captured on their current build yet)
-PREDICTOR_DRAM_BYTES_PER_CELL_3D = {}
+# DRAM bytes per cell of the predictor from one ncu capture of a launch of the kernel's current
+# build, scaled by the cells of an average launch of the timed steps.  3D (k_predict<3,2,Euler>):
+# a level-2 launch of the same explosion on a 20^3 base (63693 CTAs x 8 cells, 2.2 GB of
+# predictor data, far above the 129 MB L2): dram__bytes_read.sum 551.31 MB +
+# dram__bytes_write.sum 1589.96 MB.  The 2D workload's kernel changed after its capture (None:
+# no traffic figure).  Must be re-captured whenever k_predict changes.
+PREDICTOR_DRAM_BYTES_PER_CELL = None
+PREDICTOR_DRAM_BYTES_PER_CELL_3D = {"predictor": (551310848 + 1589964000) / (63693 * 8)}
 
 
 def _measured_hbm():
@@ -822,7 +823,8 @@ def main():
         raise RuntimeError("the profiled pass did not repeat the timed steps")
 
     flops = kernel_flops(D, M, V)
-    traffic = PREDICTOR_DRAM_BYTES_PER_CELL_3D if D == 3 else {"predictor": PREDICTOR_DRAM_BYTES_PER_CELL}
+    traffic = PREDICTOR_DRAM_BYTES_PER_CELL_3D if D == 3 else (
+        {"predictor": PREDICTOR_DRAM_BYTES_PER_CELL} if PREDICTOR_DRAM_BYTES_PER_CELL else {})
     roofline = roofline_entry(kms, kn, upd_p, flops, D, M, traffic)
     kernel_share = {n: float(kms[i] / max(kms.sum(), 1e-9)) for i, n in enumerate(KERNEL_NAMES)}
     hbm = _measured_hbm()
