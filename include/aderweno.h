@@ -46,6 +46,7 @@ extern "C" {
 #define AW_ENONPHYSICAL (-4) /* rho <= 0, p <= 0 or NaN appeared in an updated cell average */
 #define AW_ETIMEOUT (-5)     /* a bounded device-side wait gave up */
 #define AW_ESTATE (-6)       /* call not valid in the solver's current state */
+#define AW_ELIMIT (-7)       /* the solver's own device-memory limit (aw_set_memory_limit) refused an allocation */
 
 #define AW_PDE_EULER 0
 #define AW_PDE_MHD_GLM 1
@@ -243,6 +244,19 @@ int aw_num_vars(const aw_solver* s);
  * (re-uses the solver's device memory for a new problem). */
 int aw_reset(aw_solver* s);
 
+/* Device-memory limit of one solver (no counterpart in the paper; the request loop admits
+ * requests by their device bytes with it): an allocation that would take the solver's live
+ * device bytes above `bytes` is refused, and the call that needed it returns AW_ELIMIT.  0 (the
+ * default) removes the limit.  A call that failed with AW_ELIMIT leaves the solve part way
+ * through a step or a regrid: restart it (aw_reset and a new initial condition) or destroy the
+ * solver.  aw_reset also clears the record of the refusal.  AW_EINVAL for bytes < 0. */
+int aw_set_memory_limit(aw_solver* s, int64_t bytes);
+
+/* Device bytes the solver holds (its own allocations, not the CUDA context): live now, peak
+ * since creation, and refused: the live total that the largest refused allocation would have
+ * reached (0 if none).  NULL outputs are skipped. */
+int aw_get_memory(const aw_solver* s, int64_t* live, int64_t* peak, int64_t* refused);
+
 /* Per-kernel timing: when on, every launch of the hot kernels is bracketed by CUDA events on the
  * solver's stream.  aw_kernel_times() synchronises, returns the accumulated device time (ms) and
  * launch count per kind since the previous call, and restarts the accumulation.
@@ -274,17 +288,34 @@ typedef struct aw_server aw_server;
 #define AW_REQ_FAILED 3
 
 typedef struct aw_srv_info {
-  int64_t cell_updates, level0_steps, footprint_bytes;
-  double queue_ms, run_ms, total_ms;   /* submit -> start, start -> done, submit -> done */
+  int64_t cell_updates, level0_steps;
+  int64_t footprint_bytes;             /* the device bytes reserved for the run that finished it */
+  double queue_ms, run_ms, total_ms;   /* submit -> start of the last run, its start -> done, submit -> done */
+  int64_t requeues;                    /* runs restarted because the solve outgrew its reservation */
+  int64_t peak_bytes;                  /* the solver's own peak device bytes in the last run */
 } aw_srv_info;
 
 typedef struct aw_srv_summary {
   int64_t done, failed, queued, running;
   double p50_ms, p99_ms;               /* time to solution (submit -> done) of finished requests */
   double solves_per_s, cell_updates_per_s;   /* over first submit -> last completion */
+  int64_t requeues;                    /* restarts of outgrown runs, all requests */
+  int64_t budget_bytes;                /* the loop's device-memory budget */
+  int64_t peak_reserved_bytes;         /* the most bytes the admitted runs ever held reserved together */
 } aw_srv_summary;
 
-/* Start `max_concurrent` worker threads on the current device with a device-memory budget. */
+/* Start `max_concurrent` worker threads on the current device with a device-memory budget.
+ * Admission by bytes: a request is admitted (oldest first) when its reservation fits what the
+ * running requests leave of the budget; its solver runs under that reservation as its memory
+ * limit (aw_set_memory_limit, less 64 MiB for the CUDA context and staging).  The first
+ * reservation is an estimate: the dense per-level grids exactly, per-active arrays for a quarter
+ * of the finest level.  A solve that outgrows its reservation (AW_ELIMIT: a mesh that refines
+ * more than that) gives its memory back and goes back to the head of the queue with a larger
+ * reservation (at least the bytes it was refused, at least twice the old one, at most what every
+ * cell of every level active would take), and waits there until the budget has room for it; it
+ * then runs again from its initial condition.  So the reservations of running requests never
+ * exceed the budget, and a request fails for memory only if it needs more than the whole
+ * budget. */
 int aw_srv_create(int64_t hbm_budget_bytes, int32_t max_concurrent, aw_server** out);
 
 /* Cross-request batching in the loop: a worker that admits the oldest queued request also admits

@@ -174,6 +174,16 @@ class Solver:
     def sync(self):
         _lib.check(self.L.aw_sync(self.h))
 
+    def set_memory_limit(self, nbytes):
+        """aw_set_memory_limit: refuse allocations above nbytes of live device memory (0: none)"""
+        _lib.check(self.L.aw_set_memory_limit(self.h, int(nbytes)))
+
+    def memory(self):
+        """aw_get_memory: (live, peak, refused) device bytes of this solver"""
+        v = [C.c_int64(), C.c_int64(), C.c_int64()]
+        _lib.check(self.L.aw_get_memory(self.h, C.byref(v[0]), C.byref(v[1]), C.byref(v[2])))
+        return tuple(x.value for x in v)
+
     def kernel_launches(self):
         return self.L.aw_kernel_launches(self.h)
 

@@ -8,6 +8,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "lib", "libaderweno.so")
 
 AW_OK, AW_EINVAL, AW_ENOMEM, AW_ECUDA, AW_ENONPHYSICAL, AW_ETIMEOUT, AW_ESTATE = 0, -1, -2, -3, -4, -5, -6
+AW_ELIMIT = -7
 AW_PDE_EULER, AW_PDE_MHD_GLM, AW_PDE_LINADV = 0, 1, 2
 AW_BC_PERIODIC, AW_BC_TRANSMISSIVE, AW_BC_REFLECTIVE, AW_BC_INFLOW = 0, 1, 2, 3
 AW_FLUX_RUSANOV, AW_FLUX_OSHER = 0, 1
@@ -40,13 +41,15 @@ class AwStats(C.Structure):
 
 class AwSrvInfo(C.Structure):
     _fields_ = [("cell_updates", C.c_int64), ("level0_steps", C.c_int64), ("footprint_bytes", C.c_int64),
-                ("queue_ms", C.c_double), ("run_ms", C.c_double), ("total_ms", C.c_double)]
+                ("queue_ms", C.c_double), ("run_ms", C.c_double), ("total_ms", C.c_double),
+                ("requeues", C.c_int64), ("peak_bytes", C.c_int64)]
 
 
 class AwSrvSummary(C.Structure):
     _fields_ = [("done", C.c_int64), ("failed", C.c_int64), ("queued", C.c_int64), ("running", C.c_int64),
                 ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("solves_per_s", C.c_double),
-                ("cell_updates_per_s", C.c_double)]
+                ("cell_updates_per_s", C.c_double), ("requeues", C.c_int64), ("budget_bytes", C.c_int64),
+                ("peak_reserved_bytes", C.c_int64)]
 
 
 class AwLaunchParams(C.Structure):
@@ -87,6 +90,8 @@ SIGNATURES = {
     "aw_num_vars": (C.c_int, [_vp]),
     "aw_sync": (C.c_int, [_vp]),
     "aw_reset": (C.c_int, [_vp]),
+    "aw_set_memory_limit": (C.c_int, [_vp, C.c_int64]),
+    "aw_get_memory": (C.c_int, [_vp, _i64p, _i64p, _i64p]),
     "aw_set_profiling": (C.c_int, [_vp, C.c_int32]),
     "aw_kernel_times": (C.c_int, [_vp, _dp, _i64p]),
     "aw_srv_create": (C.c_int, [C.c_int64, C.c_int32, C.POINTER(_vp)]),

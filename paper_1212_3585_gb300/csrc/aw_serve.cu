@@ -1,12 +1,15 @@
 // aw_serve.cu -- request loop for independent AMR solves (continuous admission).
 //
 // Requests (a configuration, an initial condition and an end time) are queued by aw_srv_submit.
-// Worker threads admit them in arrival order as soon as their device-memory footprint fits the
+// Worker threads admit them in arrival order as soon as their device-memory reservation fits the
 // remaining budget and a worker is free; each admitted request gets its own CUDA stream and
-// solver, so the kernels of concurrent requests overlap on the GPU.  A finished request's cell
-// averages are copied to host memory and its device memory is released at once, which admits
-// the next request.  Every request runs exactly the same kernels as a solve on its own, so its
-// result does not depend on what else is running.
+// solver, so the kernels of concurrent requests overlap on the GPU.  The solver runs with its
+// reservation as its memory limit: a solve whose mesh outgrows the reservation is refused the
+// allocation (AW_ELIMIT), gives its memory back and is queued again at the head with a larger
+// reservation, to run again from its initial condition once the budget has room.  A finished
+// request's cell averages are copied to host memory and its device memory is released at once,
+// which admits the next request.  Every request runs exactly the same kernels as a solve on its
+// own, so its result does not depend on what else is running.
 //
 // With batching on (aw_srv_set_batching), a worker that admits the oldest request also admits
 // queued requests of the same kernel configuration and end time (up to the batch size, in arrival
@@ -43,6 +46,7 @@ struct Request {
   std::string err;
   clk::time_point t_submit, t_start, t_done;
   int64_t cell_updates = 0, level0_steps = 0;
+  int64_t requeues = 0, peak_bytes = 0, refused_bytes = 0;
   std::vector<aw_cell> meta;
   std::vector<double> u;
 };
@@ -51,7 +55,7 @@ struct Request {
 
 struct aw_server {
   int device = 0;
-  int64_t budget = 0, in_use = 0;
+  int64_t budget = 0, in_use = 0, peak_in_use = 0, requeues = 0;
   int nworkers = 1;
   int max_batch = 1;
   std::mutex mu;
@@ -66,11 +70,15 @@ struct aw_server {
   bool any_submitted = false;
 };
 
-// Device bytes one solve of `c` needs: the dense per-level grids (exact, with the row marks and
-// slot maps of the WENO by passes) plus per-active arrays for a quarter of the finest level's
-// cells (the AMR meshes of these workloads stay below that; the WENO sweep buffers counted at two
-// rows per active cell) and a fixed allowance for the CUDA context's share and staging buffers.
-static int64_t footprint_bytes(const aw_config& c) {
+// the part of a reservation that is not the solver's own allocations: the CUDA context's share
+// and staging buffers
+static const int64_t kAllowance = (int64_t)64 << 20;
+
+// Device bytes one solve of `c` is first reserved: the dense per-level grids (exact, with the row
+// marks and slot maps of the WENO by passes) plus per-active arrays for `active_frac` of the finest
+// level's cells (a quarter for the first reservation: the AMR meshes of these workloads mostly stay
+// below that; the WENO sweep buffers counted at two rows per active cell) and the allowance.
+static int64_t footprint_bytes(const aw_config& c, double active_frac = 0.25) {
   int V = aw::nvars(c.dim, c.pde), N = c.M + 1;
   int64_t nsp = 1;
   for (int a = 0; a < c.dim; a++) nsp *= N;
@@ -78,15 +86,32 @@ static int64_t footprint_bytes(const aw_config& c) {
   int64_t dense_per_cell = 8 * V + 4 + 8 + 4 * 5 + 5 * (c.dim == 3 ? 2 : 1);
   int64_t sweeps = 2 * 8 * V * N * (c.dim == 3 ? 1 + N : 1);
   int64_t active_per_cell = 8 * (V * nsp + V * nst + 4 * c.dim * V) + sweeps;
-  int64_t total = 0, finest = 0, rr = 1;
+  int64_t total = 0, finest = 0, all = 0, rr = 1;
   int r = c.lmax > 0 ? c.refine_factor : 1;
   for (int l = 0; l <= c.lmax; l++) {
     int64_t n = (int64_t)c.nx * rr * c.ny * rr * (c.dim == 3 ? c.nz * rr : 1);
     total += n * dense_per_cell;
     finest = n;
+    all += n;
     rr *= r;
   }
-  return total + finest / 4 * active_per_cell + ((int64_t)64 << 20);
+  if (active_frac > 1.0)   // every cell of every level active, with the arrays' growth headroom
+    return total + (int64_t)(1.5 * (double)all * (double)active_per_cell) + kAllowance;
+  return total + (int64_t)(active_frac * (double)finest) * active_per_cell + kAllowance;
+}
+
+// the bound on any reservation of `c`: every cell of every level active
+static int64_t footprint_max(const aw_config& c) { return footprint_bytes(c, 2.0); }
+
+// After a run that the solver's memory limit stopped (AW_ELIMIT): the next reservation, at least
+// the bytes it was refused with half again as headroom and at least twice the old one, at most
+// footprint_max and the budget; 0 if even the refused bytes exceed the budget.
+static int64_t next_reservation(const aw_server* S, const Request& R) {
+  const int64_t refused = R.refused_bytes + kAllowance;
+  int64_t want = std::max(2 * R.footprint, refused + refused / 2);
+  want = std::min(want, std::max(footprint_max(R.cfg), refused));
+  if (want > S->budget) want = refused <= S->budget ? S->budget : 0;
+  return want;
 }
 
 // the request's own stream; on failure the CUDA error goes into the request's message
@@ -105,6 +130,7 @@ static void run_request(aw_server* S, Request& R) {
   std::string err0;
   int rc = create_stream(&st, &err0);
   if (rc == AW_OK) rc = aw_create(&R.cfg, (uintptr_t)st, &sol);
+  if (rc == AW_OK) rc = aw_set_memory_limit(sol, std::max<int64_t>(R.footprint - kAllowance, 1));
   if (rc == AW_OK)
     rc = aw_set_initial(sol, R.ic, R.params.empty() ? nullptr : R.params.data(), (int32_t)R.params.size(), -1);
   aw_stats stats;
@@ -120,6 +146,7 @@ static void run_request(aw_server* S, Request& R) {
   if (rc != AW_OK) R.err = err0.empty() ? aw_last_error() : err0;
   R.cell_updates = stats.cell_updates;
   R.level0_steps = stats.level0_steps;
+  if (sol) aw_get_memory(sol, nullptr, &R.peak_bytes, &R.refused_bytes);
   aw_destroy(sol);
   if (st) cudaStreamDestroy(st);
   R.rc = rc;
@@ -140,6 +167,7 @@ static void run_batch(aw_server* S, std::vector<Request*>& G) {
     Request& R = *G[i];
     int rc = rc0;
     if (rc == AW_OK) rc = aw_create(&R.cfg, (uintptr_t)st, &sol[i]);
+    if (rc == AW_OK) rc = aw_set_memory_limit(sol[i], std::max<int64_t>(R.footprint - kAllowance, 1));
     if (rc == AW_OK)
       rc = aw_set_initial(sol[i], R.ic, R.params.empty() ? nullptr : R.params.data(), (int32_t)R.params.size(), -1);
     R.rc = rc;
@@ -169,7 +197,10 @@ static void run_batch(aw_server* S, std::vector<Request*>& G) {
       R.rc = r;
     }
   }
-  for (int i = 0; i < n; i++) aw_destroy(sol[i]);
+  for (int i = 0; i < n; i++) {
+    if (sol[i]) aw_get_memory(sol[i], nullptr, &G[i]->peak_bytes, &G[i]->refused_bytes);
+    aw_destroy(sol[i]);
+  }
   if (st) cudaStreamDestroy(st);
 }
 
@@ -209,6 +240,7 @@ static void worker_main(aw_server* S) {
       }
     }
     S->in_use += need;
+    S->peak_in_use = std::max(S->peak_in_use, S->in_use);
     S->running += (int)G.size();
     const clk::time_point t0 = clk::now();
     for (Request* R : G) {
@@ -220,10 +252,28 @@ static void worker_main(aw_server* S) {
     else run_batch(S, G);
     lk.lock();
     const clk::time_point t1 = clk::now();
+    std::vector<int64_t> again;   // outgrown runs, back to the head of the queue in arrival order
     for (Request* R : G) {
       R->t_done = t1;
+      if (R->rc == AW_ELIMIT) {
+        const int64_t next = next_reservation(S, *R);
+        if (next > 0) {
+          R->footprint = next;
+          R->requeues++;
+          S->requeues++;
+          R->state = AW_REQ_QUEUED;
+          R->rc = AW_OK;
+          R->err.clear();
+          R->refused_bytes = 0;
+          again.push_back(R->id);
+          continue;
+        }
+        R->rc = AW_ENOMEM;
+        R->err = "the solve needs more device memory than the whole budget of the loop";
+      }
       R->state = R->rc == AW_OK ? AW_REQ_DONE : AW_REQ_FAILED;
     }
+    for (auto it = again.rbegin(); it != again.rend(); ++it) S->queue.push_front(*it);
     S->in_use -= need;
     S->running -= (int)G.size();
     S->cv_done.notify_all();
@@ -320,6 +370,8 @@ int aw_srv_result(aw_server* S, int64_t id, aw_cell* meta, double* u, int64_t ca
     info->run_ms = std::chrono::duration<double, std::milli>(R.t_done - R.t_start).count();
     info->total_ms = std::chrono::duration<double, std::milli>(R.t_done - R.t_submit).count();
     info->footprint_bytes = R.footprint;
+    info->requeues = R.requeues;
+    info->peak_bytes = R.peak_bytes;
   }
   if (cap < *n) SRV_FAIL(AW_EINVAL, "capacity too small");
   if (meta) memcpy(meta, R.meta.data(), sizeof(aw_cell) * R.meta.size());
@@ -360,6 +412,9 @@ int aw_srv_stats(aw_server* S, aw_srv_summary* out) {
     out->solves_per_s = span > 0 ? tts.size() / span : 0.0;
     out->cell_updates_per_s = span > 0 ? upd / span : 0.0;
   }
+  out->requeues = S->requeues;
+  out->budget_bytes = S->budget;
+  out->peak_reserved_bytes = S->peak_in_use;
   return AW_OK;
 }
 

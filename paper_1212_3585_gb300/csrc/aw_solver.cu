@@ -19,6 +19,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <unordered_map>
 #include <string>
 #include <vector>
 
@@ -57,10 +58,6 @@ static const int CHUNK = 4096;
 static const int NSLOT = 8;
 
 // stream-ordered device allocation on the solver's stream
-static cudaError_t dalloc(cudaStream_t st, void** p, size_t bytes) { return cudaMallocAsync(p, bytes ? bytes : 1, st); }
-static void dfree(cudaStream_t st, void* p) {
-  if (p) cudaFreeAsync(p, st);
-}
 
 // the default pool of a device keeps freed memory for reuse instead of returning it at every
 // synchronisation (set once per device)
@@ -172,7 +169,43 @@ struct aw_solver {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_used;
   double kind_ms[8] = {0};
   int64_t kind_n[8] = {0};
+  // device memory of the solver: bytes of every live allocation, their sum and its maximum, an
+  // optional limit (aw_set_memory_limit; 0: none) and the largest total a refused allocation
+  // would have reached
+  std::unordered_map<void*, size_t> alloc_bytes;
+  int64_t mem_live = 0, mem_peak = 0, mem_limit = 0, mem_refused = 0;
 };
+
+// Stream-ordered device allocation on the solver's stream, counted against the solver's memory
+// limit: an allocation that would take the live total above the limit is refused (the caller
+// then fails with AW_ELIMIT, see oom_code).
+static cudaError_t dalloc(aw_solver* s, void** p, size_t bytes) {
+  if (!bytes) bytes = 1;
+  if (s->mem_limit > 0 && s->mem_live + (int64_t)bytes > s->mem_limit) {
+    s->mem_refused = std::max(s->mem_refused, s->mem_live + (int64_t)bytes);
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  cudaError_t e = cudaMallocAsync(p, bytes, s->stream);
+  if (e != cudaSuccess) return e;
+  s->alloc_bytes[*p] = bytes;
+  s->mem_live += (int64_t)bytes;
+  s->mem_peak = std::max(s->mem_peak, s->mem_live);
+  return cudaSuccess;
+}
+
+static void dfree(aw_solver* s, void* p) {
+  if (!p) return;
+  auto it = s->alloc_bytes.find(p);
+  if (it != s->alloc_bytes.end()) {
+    s->mem_live -= (int64_t)it->second;
+    s->alloc_bytes.erase(it);
+  }
+  cudaFreeAsync(p, s->stream);
+}
+
+// the status of a failed device allocation: AW_ELIMIT once the solver's own limit refused one
+static int oom_code(const aw_solver* s) { return s->mem_refused ? AW_ELIMIT : AW_ENOMEM; }
 
 enum { KIND_WENO = 0, KIND_PREDICT = 1, KIND_FLUX = 2, KIND_UPDATE = 3, KIND_PROJECT = 4 };
 
@@ -865,11 +898,11 @@ static RtPhys rtphys(const aw_solver* s) {
 
 static int ensure_buf(aw_solver* s, long long ndouble) {
   if (ndouble <= s->buf_cap) return AW_OK;
-  dfree(s->stream, s->d_buf);
+  dfree(s, s->d_buf);
   s->d_buf = nullptr;
   long long cap = std::max(ndouble, (long long)1024);
-  if (dalloc(s->stream, (void**)&s->d_buf, cap * sizeof(double)) != cudaSuccess)
-    AW_FAIL(AW_ENOMEM, "staging buffer of %lld doubles", cap);
+  if (dalloc(s, (void**)&s->d_buf, cap * sizeof(double)) != cudaSuccess)
+    AW_FAIL(oom_code(s), "staging buffer of %lld doubles", cap);
   s->buf_cap = cap;
   return AW_OK;
 }
@@ -879,9 +912,9 @@ static int compact(aw_solver* s, const int8_t* a, long long n, int mode, int val
                    int slot) {
   long long nb = (n + CHUNK - 1) / CHUNK;
   if (nb > s->bcnt_cap) {
-    dfree(s->stream, s->d_bcnt);
+    dfree(s, s->d_bcnt);
     s->d_bcnt = nullptr;
-    if (dalloc(s->stream, (void**)&s->d_bcnt, nb * sizeof(int)) != cudaSuccess) AW_FAIL(AW_ENOMEM, "scan scratch");
+    if (dalloc(s, (void**)&s->d_bcnt, nb * sizeof(int)) != cudaSuccess) AW_FAIL(oom_code(s), "scan scratch");
     s->bcnt_cap = nb;
   }
   k_ccount<<<(unsigned)nb, 256, 0, s->stream>>>(a, n, mode, val, s->d_bcnt);
@@ -899,11 +932,11 @@ static int ensure_list(aw_solver* s, int32_t** list, long long* cap, long long n
   if (need <= *cap) return AW_OK;
   long long c = std::max(need + need / 2, (long long)64);
   c = std::min(c, s->lev[l].n);
-  dfree(s->stream, *list);
+  dfree(s, *list);
   *list = nullptr;
   *cap = 0;
-  if (dalloc(s->stream, (void**)list, c * sizeof(int32_t)) != cudaSuccess)
-    AW_FAIL(AW_ENOMEM, "sweep list of level %d (%lld entries)", l, c);
+  if (dalloc(s, (void**)list, c * sizeof(int32_t)) != cudaSuccess)
+    AW_FAIL(oom_code(s), "sweep list of level %d (%lld entries)", l, c);
   *cap = c;
   return AW_OK;
 }
@@ -911,11 +944,11 @@ static int ensure_list(aw_solver* s, int32_t** list, long long* cap, long long n
 static int ensure_sweeps(aw_solver* s, double** buf, long long* cap, long long count, long long per, int l) {
   if (count <= *cap) return AW_OK;
   long long c = std::max(count + count / 4, (long long)64);
-  dfree(s->stream, *buf);
+  dfree(s, *buf);
   *buf = nullptr;
   *cap = 0;
-  if (dalloc(s->stream, (void**)buf, c * per * sizeof(double)) != cudaSuccess)
-    AW_FAIL(AW_ENOMEM, "sweep buffer of level %d (%lld entries)", l, c);
+  if (dalloc(s, (void**)buf, c * per * sizeof(double)) != cudaSuccess)
+    AW_FAIL(oom_code(s), "sweep buffer of level %d (%lld entries)", l, c);
   *cap = c;
   return AW_OK;
 }
@@ -940,22 +973,21 @@ static int ensure_active_cap(aw_solver* s, int l, long long need) {
   long long cap = std::max(need + need / 2, (long long)64);
   for (void* p : {(void*)L.wh, (void*)L.qh, (void*)L.fl, (void*)L.mem, (void*)L.hflag, (void*)L.hflist,
                   (void*)L.fsync})
-    dfree(s->stream, p);
+    dfree(s, p);
   L.wh = L.qh = L.fl = L.mem = nullptr;
   L.hflag = nullptr;
   L.hflist = nullptr;
   L.fsync = nullptr;
   L.cap = 0;
   size_t V = s->V;
-  cudaStream_t st = s->stream;
-  if (dalloc(st, (void**)&L.hflag, cap * s->D) != cudaSuccess ||
-      dalloc(st, (void**)&L.hflist, cap * s->D * sizeof(int32_t)) != cudaSuccess ||
-      dalloc(st, (void**)&L.wh, cap * V * s->NSP * sizeof(double)) != cudaSuccess ||
-      dalloc(st, (void**)&L.qh, cap * V * s->NST * sizeof(double)) != cudaSuccess ||
-      dalloc(st, (void**)&L.fl, cap * 2 * s->D * V * sizeof(double)) != cudaSuccess ||
-      dalloc(st, (void**)&L.mem, cap * 2 * s->D * V * sizeof(double)) != cudaSuccess ||
-      dalloc(st, (void**)&L.fsync, cap * sizeof(int32_t)) != cudaSuccess)
-    AW_FAIL(AW_ENOMEM, "per-active arrays of level %d (%lld cells)", l, cap);
+  if (dalloc(s, (void**)&L.hflag, cap * s->D) != cudaSuccess ||
+      dalloc(s, (void**)&L.hflist, cap * s->D * sizeof(int32_t)) != cudaSuccess ||
+      dalloc(s, (void**)&L.wh, cap * V * s->NSP * sizeof(double)) != cudaSuccess ||
+      dalloc(s, (void**)&L.qh, cap * V * s->NST * sizeof(double)) != cudaSuccess ||
+      dalloc(s, (void**)&L.fl, cap * 2 * s->D * V * sizeof(double)) != cudaSuccess ||
+      dalloc(s, (void**)&L.mem, cap * 2 * s->D * V * sizeof(double)) != cudaSuccess ||
+      dalloc(s, (void**)&L.fsync, cap * sizeof(int32_t)) != cudaSuccess)
+    AW_FAIL(oom_code(s), "per-active arrays of level %d (%lld cells)", l, cap);
   L.cap = cap;
   return AW_OK;
 }
@@ -1333,11 +1365,11 @@ static void free_solver(aw_solver* s) {
                     (void*)L.wh, (void*)L.qh, (void*)L.fl, (void*)L.mem, (void*)L.hflag, (void*)L.hflist,
                     (void*)L.xmark, (void*)L.xslot, (void*)L.xlist, (void*)L.xs, (void*)L.ymark, (void*)L.yslot,
                     (void*)L.ylist, (void*)L.ys, (void*)L.fsync})
-      dfree(st, p);
+      dfree(s, p);
   }
   for (void* p : {(void*)s->d_dtl, (void*)s->d_dtmin, (void*)s->d_err, (void*)s->d_cnt, (void*)s->d_bcnt,
                   (void*)s->d_buf, (void*)s->d_gs})
-    dfree(st, p);
+    dfree(s, p);
   // the host blocks may still be the target of copies in flight
   cudaStreamSynchronize(st);
   if (s->gstream) {
@@ -1489,7 +1521,7 @@ int aw_create(const aw_config* cfg, uintptr_t stream, aw_solver** out) {
   keep_pool(dev);
   auto alloc = [&](void** p, size_t bytes) {
     if (rc != AW_OK) return;
-    if (dalloc(s->stream, p, bytes) != cudaSuccess) {
+    if (dalloc(s, p, bytes) != cudaSuccess) {
       rc = AW_ENOMEM;
       char b[200];
       snprintf(b, sizeof b, "device allocation of %zu bytes failed", bytes);
@@ -1583,6 +1615,7 @@ void aw_destroy(aw_solver* s) {
 
 int aw_reset(aw_solver* s) {
   if (!s) AW_FAIL(AW_EINVAL, "null solver");
+  s->mem_refused = 0;
   for (int l = 0; l <= s->lmax; l++) {
     Level& L = s->lev[l];
     CK(cudaMemsetAsync(L.st, l == 0 ? 0 : ST_NONE, L.n, s->stream));
@@ -1590,6 +1623,22 @@ int aw_reset(aw_solver* s) {
   }
   TRY(rebuild_lists(s));
   s->t = 0.0;
+  return AW_OK;
+}
+
+int aw_set_memory_limit(aw_solver* s, int64_t bytes) {
+  if (!s) AW_FAIL(AW_EINVAL, "null solver");
+  if (bytes < 0) AW_FAIL(AW_EINVAL, "the memory limit must be >= 0 (0: none)");
+  s->mem_limit = bytes;
+  s->mem_refused = 0;
+  return AW_OK;
+}
+
+int aw_get_memory(const aw_solver* s, int64_t* live, int64_t* peak, int64_t* refused) {
+  if (!s) AW_FAIL(AW_EINVAL, "null solver");
+  if (live) *live = s->mem_live;
+  if (peak) *peak = s->mem_peak;
+  if (refused) *refused = s->mem_refused;
   return AW_OK;
 }
 
@@ -1788,7 +1837,8 @@ static int batch_run(aw_solver* const* S, int n, double t_end, cudaStream_t st, 
       if (rc != AW_OK) { fail(m, rc); continue; }
       clip[m] = S[m]->t + dt[m] >= t_end;
       if (clip[m]) dt[m] = t_end - S[m]->t;
-      TRY(step_begin(S[m], dt[m]));
+      rc = step_begin(S[m], dt[m]);
+      if (rc != AW_OK) fail(m, rc);
     }
     // the step of every member, the hot kernels batched
     int64_t nl = 0;
@@ -1821,11 +1871,17 @@ static int batch_run(aw_solver* const* S, int n, double t_end, cudaStream_t st, 
     for (int m = 0; m < n; m++) {
       rg[m] = live[m] && S[m]->cfg.auto_regrid && S[m]->lmax > 0;
       if (!rg[m]) continue;
+      // a member whose regrid cannot be issued (its memory limit, say) stops alone
+      rc = regrid_prepass(S[m], 0);
+      if (rc == AW_OK) rc = flags_from_chi(S[m]);
+      if (rc == AW_OK) rc = apply_flags_issue(S[m], 0);
+      if (rc == AW_OK) rc = lists_issue(S[m]);
+      if (rc != AW_OK) {
+        fail(m, rc);
+        rg[m] = false;
+        continue;
+      }
       nrg++;
-      TRY(regrid_prepass(S[m], 0));
-      TRY(flags_from_chi(S[m]));
-      TRY(apply_flags_issue(S[m], 0));
-      TRY(lists_issue(S[m]));
     }
     if (nrg) {
       CK(cudaStreamSynchronize(st));
@@ -1905,7 +1961,7 @@ int aw_advance_graph(aw_solver* s, double t_end, int32_t chunk, aw_stats* st) {
     return AW_OK;
   }
   if (!s->d_gs) {
-    if (dalloc(s->stream, (void**)&s->d_gs, sizeof(GState)) != cudaSuccess) AW_FAIL(AW_ENOMEM, "graph state");
+    if (dalloc(s, (void**)&s->d_gs, sizeof(GState)) != cudaSuccess) AW_FAIL(oom_code(s), "graph state");
     s->h_gs = (GState*)pinned_block();
     if (!s->h_gs) AW_FAIL(AW_ENOMEM, "pinned host allocation failed");
     static_assert(sizeof(GState) <= 256, "pinned block");

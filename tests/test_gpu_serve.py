@@ -16,29 +16,131 @@ def rp_config(base, M, lmax):
                           bc=pg.AW_BC_TRANSMISSIVE, r=3, lmax=lmax, cfl=0.5)
 
 
+def ot_config(base, lmax):
+    """MHD-GLM Orszag-Tang type data on the periodic [0, 2 pi]^2 (gamma 5/3, M = 3)"""
+    return pg.make_config(dim=2, pde=pg.AW_PDE_MHD_GLM, M=3, n=(base, base, 1), lo=(0, 0, 0),
+                          hi=(2 * np.pi, 2 * np.pi, 1), bc=pg.AW_BC_PERIODIC, gamma=5.0 / 3.0, r=3, lmax=lmax,
+                          cfl=0.6, c_h=2.0, chi_ref=0.05, chi_rec=0.02)
+
+
+def solo(cfg, ic, p, t_end):
+    s = pg.Solver(cfg)
+    s.set_initial(ic, p, -1)
+    s.advance_to(t_end)
+    out = s.cells()
+    s.close()
+    return out
+
+
 def test_results_identical_alone_and_in_the_mix():
+    """Euler and MHD-GLM requests of different sizes, orders and depths"""
     rng = np.random.default_rng(20121213)
     reqs = []
     for k in range(10):
         base = int(rng.integers(16, 41))
         M = int(rng.choice([2, 3]))
         lmax = int(rng.integers(0, 3))
-        reqs.append((rp_config(base, M, lmax), aw_inputs.rp4_params(1000 + k)))
+        reqs.append((rp_config(base, M, lmax), pg.AW_IC_RP4, aw_inputs.rp4_params(1000 + k)))
+    for base, lmax in ((16, 1), (20, 0), (24, 1)):
+        reqs.append((ot_config(base, lmax), pg.AW_IC_OT, []))
+    order = rng.permutation(len(reqs))
+    reqs = [reqs[i] for i in order]
     srv = pg.Server(hbm_budget_bytes=6 << 30, max_concurrent=4)
-    ids = [srv.submit(cfg, pg.AW_IC_RP4, p, 0.03) for cfg, p in reqs]
+    ids = [srv.submit(cfg, ic, p, 0.03) for cfg, ic, p in reqs]
     srv.wait_all()
     st = srv.stats()
     assert st.done == len(reqs) and st.failed == 0
     assert 0 < st.p50_ms <= st.p99_ms
-    for rid, (cfg, p) in zip(ids[:5], reqs[:5]):
-        m, u, info = srv.result(rid, 4)
-        s = pg.Solver(cfg)
-        s.set_initial(pg.AW_IC_RP4, p, -1)
-        s.advance_to(0.03)
-        m2, u2 = s.cells()
+    assert st.peak_reserved_bytes <= st.budget_bytes == 6 << 30
+    checked_mhd = 0
+    for k, (rid, (cfg, ic, p)) in enumerate(zip(ids, reqs)):
+        if k >= 5 and ic != pg.AW_IC_OT:
+            continue
+        V = 9 if ic == pg.AW_IC_OT else 4
+        m, u, info = srv.result(rid, V)
+        m2, u2 = solo(cfg, ic, p, 0.03)
         assert np.array_equal(m, m2)
         assert np.array_equal(u, u2)
         assert info.cell_updates > 0
+        checked_mhd += ic == pg.AW_IC_OT
+    assert checked_mhd == 3
+    srv.close()
+
+
+VORTEX = [5.0, 5.0, 5.0, 1.0, 1.0, 1.0, 1.0]
+
+
+def full_refinement_config(base=24):
+    """the vortex refined everywhere to l_max = 2 (every indicator value is above chi_ref = -1):
+    its finest level is fully active, four times what a first reservation allows for"""
+    return pg.make_config(dim=2, M=2, n=(base, base, 1), lo=(0, 0, 0), hi=(10, 10, 1), bc=pg.AW_BC_PERIODIC,
+                          r=3, lmax=2, cfl=0.9, chi_ref=-1.0, chi_rec=-2.0)
+
+
+def test_solver_memory_limit():
+    cfg = full_refinement_config()
+    ref = pg.Solver(cfg)
+    ref.set_initial(pg.AW_IC_VORTEX, VORTEX, -1)
+    ref.advance_to(0.1)
+    m0, u0 = ref.cells()
+    live, peak, refused = ref.memory()
+    assert refused == 0 and 0 < live <= peak
+    assert m0[:, 0].max() == 2 and np.all(m0[m0[:, 1] == 0, 0] == 2)   # every active cell on level 2
+    ref.close()
+    s = pg.Solver(cfg)
+    s.set_memory_limit(peak // 2)
+    with pytest.raises(pg.AwError) as ei:
+        s.set_initial(pg.AW_IC_VORTEX, VORTEX, -1)
+        s.advance_to(0.1)
+    assert ei.value.code == pg._lib.AW_ELIMIT
+    live2, peak2, refused2 = s.memory()
+    assert peak2 <= peak // 2 < refused2
+    # the solve restarts from its initial condition once the limit is lifted
+    s.reset()
+    s.set_memory_limit(0)
+    assert s.memory()[2] == 0
+    s.set_initial(pg.AW_IC_VORTEX, VORTEX, -1)
+    s.advance_to(0.1)
+    m, u = s.cells()
+    assert np.array_equal(m, m0) and np.array_equal(u, u0)
+    with pytest.raises(pg.AwError) as ei:
+        s.set_memory_limit(-1)
+    assert ei.value.code == pg._lib.AW_EINVAL
+    s.close()
+
+
+@pytest.mark.parametrize("max_batch", [1, 2])
+def test_request_outgrowing_its_reservation_waits_and_completes(max_batch):
+    """Two requests whose meshes refine everywhere (four times the first reservation) under a
+    budget that holds one grown reservation but not two: each is refused, goes back to the head
+    of the queue with a larger reservation, waits for the other, and completes with the result of
+    its solo solve; the reservations of running requests never exceed the budget"""
+    cfg = full_refinement_config()
+    ref = pg.Solver(cfg)
+    ref.set_initial(pg.AW_IC_VORTEX, VORTEX, -1)
+    ref.advance_to(0.1)
+    m0, u0 = ref.cells()
+    peak = ref.memory()[1]
+    ref.close()
+    small = rp_config(16, 2, 1)
+    ps = aw_inputs.rp4_params(31)
+    m1, u1 = solo(small, pg.AW_IC_RP4, ps, 0.1)
+    budget = int(1.6 * (peak + (64 << 20)))
+    srv = pg.Server(hbm_budget_bytes=budget, max_concurrent=3, max_batch=max_batch)
+    ids = [srv.submit(cfg, pg.AW_IC_VORTEX, VORTEX, 0.1), srv.submit(small, pg.AW_IC_RP4, ps, 0.1),
+           srv.submit(cfg, pg.AW_IC_VORTEX, VORTEX, 0.1)]
+    srv.wait_all()
+    st = srv.stats()
+    assert st.done == 3 and st.failed == 0
+    assert st.requeues >= 2
+    assert st.peak_reserved_bytes <= budget
+    for rid in (ids[0], ids[2]):
+        m, u, info = srv.result(rid, 4)
+        assert np.array_equal(m, m0) and np.array_equal(u, u0)
+        assert info.requeues >= 1
+        assert info.peak_bytes + (64 << 20) <= info.footprint_bytes <= budget
+    m, u, info = srv.result(ids[1], 4)
+    assert np.array_equal(m, m1) and np.array_equal(u, u1)
     srv.close()
 
 
