@@ -189,21 +189,49 @@ int aw_advance_graph(aw_solver* s, double t_end, int32_t chunk, aw_stats* stats)
  * pass_min_cells cells (default 4096; tiles below), 2D WENO tiles of 8x8 cells on levels of at
  * least tile8_min_cells cells (default 20000; 4x4 below), and quarter-size predictor and flux
  * CTAs when the full-size ones would give fewer than small_ctas_per_sm CTAs per SM (default 2;
- * 0 never), and fuse_flux_update: 1 (default) runs the face fluxes and the update of Eq.
+ * 0 never), fuse_flux_update: 1 (default) runs the face fluxes and the update of Eq.
  * eq:finite_vol as one kernel (the face CTA that delivers the last face flux a chunk of cells
- * needs updates that chunk; nothing waits), 0 as two kernels; the averages are bitwise the
- * same.  Process-wide.  The first
+ * needs updates that chunk; nothing waits), 0 as two kernels; and autotune: 1 (default) lets the
+ * library's autotuner pick the CTA size (cells, or faces, per block: full or quarter size) of the
+ * predictor and of the face flux per configuration and level size class, from CUDA-event timings
+ * of the first launches of each (aw_get_tuning), in place of the small_ctas_per_sm rule; 0 the
+ * rule alone.  The averages are bitwise the same for every setting.  Process-wide.  The first
  * two are fixed per level when a solver is created, the others apply to every launch.
- * AW_EINVAL for negative values, small_ctas_per_sm > 64 or fuse_flux_update not 0 or 1.
- * bench.py --tune times the workload over these parameters. */
+ * AW_EINVAL for negative values, small_ctas_per_sm > 64, or fuse_flux_update or autotune not 0
+ * or 1.  bench.py --tune times the workload over these parameters. */
 typedef struct aw_launch_params {
   int64_t pass_min_cells;
   int64_t tile8_min_cells;
   int32_t small_ctas_per_sm;
   int32_t fuse_flux_update;
+  int32_t autotune;
+  int32_t reserved;
 } aw_launch_params;
 int aw_get_launch_params(aw_launch_params* out);
 int aw_set_launch_params(const aw_launch_params* in);
+
+/* The autotuner's state (no counterpart in the paper).  For every configuration (dim, M, pde,
+ * numerical flux), kernel (AW_TUNE_PREDICTOR, AW_TUNE_FLUX) and level size class (floor(log2) of
+ * the level's active cells) that solvers of this process have launched, the first launches try
+ * the full-size (variant 0) and quarter-size (variant 1) CTAs in turn, each timed with a pair of
+ * CUDA events on the solver's stream; once each variant has AW_TUNE_TRIALS timings, the one with
+ * the least device time per active cell (the least over its timings) is used for every later
+ * launch of that class, by every solver.  A new class larger than a class that kept full-size
+ * CTAs, or smaller than one that kept quarter-size CTAs, takes that decision without trials
+ * (inherited = 1).  Single-solver steps only: the batched and graph paths use the rules.  aw_get_tuning copies up to `cap` entries (in key order) into `out` and sets *n to the
+ * number of entries; aw_reset_tuning forgets them all.  AW_EINVAL for a null n or cap < 0. */
+#define AW_TUNE_PREDICTOR 0
+#define AW_TUNE_FLUX 1
+#define AW_TUNE_TRIALS 2
+typedef struct aw_tune_entry {
+  int32_t dim, M, pde, flux, kernel, size_class;
+  int32_t choice;          /* the variant kept, -1 while still trying */
+  int32_t trials[2];       /* timings taken of variants 0 and 1 */
+  int32_t inherited;       /* 1: decided from a neighbouring class, without trials */
+  double ns_per_cell[2];   /* least device time per active cell of variants 0 and 1 */
+} aw_tune_entry;
+int aw_get_tuning(aw_tune_entry* out, int32_t cap, int32_t* n);
+int aw_reset_tuning(void);
 
 /* Stable level-0 time step of the current state (CFL condition over all active cells). */
 int aw_compute_dt(aw_solver* s, double* dt0);

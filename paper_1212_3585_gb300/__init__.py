@@ -193,10 +193,12 @@ def get_launch_params() -> dict:
     p = _lib.AwLaunchParams()
     _lib.check(_lib.load().aw_get_launch_params(C.byref(p)))
     return {"pass_min_cells": p.pass_min_cells, "tile8_min_cells": p.tile8_min_cells,
-            "small_ctas_per_sm": p.small_ctas_per_sm, "fuse_flux_update": p.fuse_flux_update}
+            "small_ctas_per_sm": p.small_ctas_per_sm, "fuse_flux_update": p.fuse_flux_update,
+            "autotune": p.autotune}
 
 
-def set_launch_params(pass_min_cells=None, tile8_min_cells=None, small_ctas_per_sm=None, fuse_flux_update=None):
+def set_launch_params(pass_min_cells=None, tile8_min_cells=None, small_ctas_per_sm=None, fuse_flux_update=None,
+                      autotune=None):
     """aw_set_launch_params: change some of the launch-shape rules (speed only, never results)."""
     cur = get_launch_params()
     p = _lib.AwLaunchParams()
@@ -204,7 +206,26 @@ def set_launch_params(pass_min_cells=None, tile8_min_cells=None, small_ctas_per_
     p.tile8_min_cells = cur["tile8_min_cells"] if tile8_min_cells is None else int(tile8_min_cells)
     p.small_ctas_per_sm = cur["small_ctas_per_sm"] if small_ctas_per_sm is None else int(small_ctas_per_sm)
     p.fuse_flux_update = cur["fuse_flux_update"] if fuse_flux_update is None else int(fuse_flux_update)
+    p.autotune = cur["autotune"] if autotune is None else int(autotune)
     _lib.check(_lib.load().aw_set_launch_params(C.byref(p)))
+
+
+def get_tuning() -> list:
+    """aw_get_tuning: one dict per (configuration, kernel, level size class) the autotuner has seen"""
+    L = _lib.load()
+    n = C.c_int32()
+    _lib.check(L.aw_get_tuning(None, 0, C.byref(n)))
+    buf = (_lib.AwTuneEntry * max(n.value, 1))()
+    _lib.check(L.aw_get_tuning(buf, n.value, C.byref(n)))
+    return [{"dim": e.dim, "M": e.M, "pde": e.pde, "flux": e.flux, "kernel": e.kernel, "size_class": e.size_class,
+             "choice": e.choice, "trials": list(e.trials), "inherited": e.inherited,
+             "ns_per_cell": list(e.ns_per_cell)}
+            for e in buf[: n.value]]
+
+
+def reset_tuning():
+    """aw_reset_tuning: forget every decision of the autotuner"""
+    _lib.check(_lib.load().aw_reset_tuning())
 
 
 def tables_host(M: int, r: int) -> dict:

@@ -9,6 +9,7 @@ LIB_PATH = os.path.join(PKG, "lib", "libaderweno.so")
 
 AW_OK, AW_EINVAL, AW_ENOMEM, AW_ECUDA, AW_ENONPHYSICAL, AW_ETIMEOUT, AW_ESTATE = 0, -1, -2, -3, -4, -5, -6
 AW_ELIMIT = -7
+AW_TUNE_PREDICTOR, AW_TUNE_FLUX, AW_TUNE_TRIALS = 0, 1, 2
 AW_PDE_EULER, AW_PDE_MHD_GLM, AW_PDE_LINADV = 0, 1, 2
 AW_BC_PERIODIC, AW_BC_TRANSMISSIVE, AW_BC_REFLECTIVE, AW_BC_INFLOW = 0, 1, 2, 3
 AW_FLUX_RUSANOV, AW_FLUX_OSHER = 0, 1
@@ -54,7 +55,13 @@ class AwSrvSummary(C.Structure):
 
 class AwLaunchParams(C.Structure):
     _fields_ = [("pass_min_cells", C.c_int64), ("tile8_min_cells", C.c_int64), ("small_ctas_per_sm", C.c_int32),
-                ("fuse_flux_update", C.c_int32)]
+                ("fuse_flux_update", C.c_int32), ("autotune", C.c_int32), ("reserved", C.c_int32)]
+
+
+class AwTuneEntry(C.Structure):
+    _fields_ = [("dim", C.c_int32), ("M", C.c_int32), ("pde", C.c_int32), ("flux", C.c_int32), ("kernel", C.c_int32),
+                ("size_class", C.c_int32), ("choice", C.c_int32), ("trials", C.c_int32 * 2), ("inherited", C.c_int32),
+                ("ns_per_cell", C.c_double * 2)]
 
 
 class AwCell(C.Structure):
@@ -78,6 +85,8 @@ SIGNATURES = {
     "aw_advance_graph": (C.c_int, [_vp, C.c_double, C.c_int32, C.POINTER(AwStats)]),
     "aw_get_launch_params": (C.c_int, [C.POINTER(AwLaunchParams)]),
     "aw_set_launch_params": (C.c_int, [C.POINTER(AwLaunchParams)]),
+    "aw_get_tuning": (C.c_int, [C.POINTER(AwTuneEntry), C.c_int32, C.POINTER(C.c_int32)]),
+    "aw_reset_tuning": (C.c_int, []),
     "aw_compute_dt": (C.c_int, [_vp, _dp]),
     "aw_regrid": (C.c_int, [_vp, C.c_int32]),
     "aw_regrid_with_flags": (C.c_int, [_vp, _i8p, C.c_int64, C.c_int32]),

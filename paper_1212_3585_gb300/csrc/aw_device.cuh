@@ -444,6 +444,9 @@ struct HotArgs {
   // fused face flux and update (k_flux_update): face arrivals per chunk of active cells, zeroed
   // before each launch
   int* fsync;
+  // CTA size of the predictor and face-flux launches: 0 the launch rules, 1 full-size, 4
+  // quarter-size (the autotuner's choice; the results are the same either way)
+  int cta_div;
 };
 
 // Several independent solves of the same kernel configuration in one launch: member m owns CTAs

@@ -51,6 +51,8 @@ struct Launch {
   static int update_ctas(const HotArgs& a) { return a.na > 0 ? (a.na + 127) / 128 : 0; }
   static int project_ctas(int nv) { return nv > 0 ? (int)(((long long)nv * V + 127) / 128) : 0; }
   static bool small(int ctas) { return ctas < launch_params().small_ctas_per_sm * sm_count(); }
+  // quarter-size CTAs: the autotuner's choice for this launch, else the rule above
+  static bool use_small(const HotArgs& a, int ctas) { return a.cta_div == 4 || (a.cta_div != 1 && small(ctas)); }
 
   // the dynamic shared memory attribute, once per kernel (request-loop workers launch concurrently)
   template <class K>
@@ -96,7 +98,7 @@ struct Launch {
   static int predict(const HotArgs& a, cudaStream_t st) {
     int blocks = predict_ctas_of<CP>(a);
     if (!blocks) return 0;
-    if (small(blocks)) {
+    if (use_small(a, blocks)) {
       static std::once_flag init;
       smem_attr(k_predict<D, M, PDE, SMALL>, CPs::SMEM, init);
       k_predict<D, M, PDE, SMALL><<<predict_ctas_of<CPs>(a), CPs::THREADS, CPs::SMEM, st>>>(a);
@@ -112,7 +114,7 @@ struct Launch {
   static int flux_fl(const HotArgs& a, cudaStream_t st) {
     int blocks = flux_ctas_of<CF>(a);
     if (!blocks) return 0;
-    if (small(blocks)) {
+    if (use_small(a, blocks)) {
       static std::once_flag init;
       smem_attr(k_flux<D, M, PDE, SMALL, FL>, CFs::SMEM, init);
       k_flux<D, M, PDE, SMALL, FL><<<flux_ctas_of<CFs>(a), CFs::THREADS, CFs::SMEM, st>>>(a);
@@ -139,7 +141,7 @@ struct Launch {
   static int flux_update_fl(const HotArgs& a, cudaStream_t st) {
     int blocks = flux_ctas_of<CF>(a);
     if (!blocks) return 0;
-    if (small(blocks)) {
+    if (use_small(a, blocks)) {
       static std::once_flag init;
       smem_attr(k_flux_update<D, M, PDE, SMALL, FL>, CFs::SMEM, init);
       clear_fsync<CFs>(a, st);

@@ -19,6 +19,7 @@ HotOps ops_3_2_2();
 static std::atomic<long long> g_pass_min_cells{4096}, g_tile8_min_cells{20000};
 static std::atomic<int> g_small_ctas_per_sm{2};
 static std::atomic<int> g_fuse_flux_update{1};
+static std::atomic<int> g_autotune{1};
 
 LaunchParams launch_params() {
   LaunchParams p;
@@ -26,6 +27,7 @@ LaunchParams launch_params() {
   p.tile8_min_cells = g_tile8_min_cells.load();
   p.small_ctas_per_sm = g_small_ctas_per_sm.load();
   p.fuse_flux_update = g_fuse_flux_update.load();
+  p.autotune = g_autotune.load();
   return p;
 }
 
@@ -34,6 +36,7 @@ void set_launch_params(const LaunchParams& p) {
   g_tile8_min_cells.store(p.tile8_min_cells);
   g_small_ctas_per_sm.store(p.small_ctas_per_sm);
   g_fuse_flux_update.store(p.fuse_flux_update);
+  g_autotune.store(p.autotune);
 }
 
 bool get_ops(int D, int M, int PDE, HotOps* out) {

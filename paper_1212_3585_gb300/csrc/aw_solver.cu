@@ -18,7 +18,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <unordered_map>
 #include <string>
 #include <vector>
@@ -174,6 +176,14 @@ struct aw_solver {
   // would have reached
   std::unordered_map<void*, size_t> alloc_bytes;
   int64_t mem_live = 0, mem_peak = 0, mem_limit = 0, mem_refused = 0;
+  // the autotuner's timed trial launches of this solver, read after the next synchronisation
+  struct TunePending {
+    int key[6];
+    int var;
+    long long na;
+    cudaEvent_t a, b;
+  };
+  std::vector<TunePending> tune_used;
 };
 
 // Stream-ordered device allocation on the solver's stream, counted against the solver's memory
@@ -232,6 +242,120 @@ static int timed(aw_solver* s, int kind, F&& launch) {
   else { s->ev_free.push_back(a); s->ev_free.push_back(b); }
   s->kind_n[kind] += n;
   return n;
+}
+
+// ---- autotuner of the CTA sizes of the predictor and the face flux (aw_get_tuning) ----
+// Both kernels have a full-size and a quarter-size CTA variant that compute bitwise the same
+// results.  Per (dim, M, pde, numerical flux, kernel, level size class) the first launches
+// alternate the two, each timed with an event pair on the solver's stream; once each has
+// AW_TUNE_TRIALS timings, the variant with the least device time per active cell (the least over
+// its timings, which leaves out a first launch's one-off costs) is used for that class by every
+// solver of the process.  A class larger than one that kept full-size CTAs keeps them too, and a
+// class smaller than one that kept quarter-size CTAs keeps those, without trials (more cells give
+// more CTAs, which only favours the larger CTAs): so trials run only between the two.
+struct TuneState {
+  int issued[2] = {0, 0}, trials[2] = {0, 0};
+  double ns_per_cell[2] = {0.0, 0.0};
+  int choice = -1;
+  int inherited = 0;
+};
+static std::mutex g_tune_mu;
+static std::map<std::tuple<int, int, int, int, int, int>, TuneState> g_tune;
+
+static std::tuple<int, int, int, int, int, int> tune_key(const int* k) {
+  return std::make_tuple(k[0], k[1], k[2], k[3], k[4], k[5]);
+}
+
+static int size_class(long long n) {
+  int c = 0;
+  while (n > 1) {
+    n >>= 1;
+    c++;
+  }
+  return c;
+}
+
+// The variant of a launch of `kernel` over `na` active cells: the kept one (0 or 1), or while the
+// class is being tried the one launched fewer times so far, with bit 1 set (a timed trial);
+// -1 when the tuner is off.
+static int tune_pick(const aw_solver* s, int kernel, long long na, int* key) {
+  if (!launch_params().autotune || na <= 0) return -1;
+  key[0] = s->D;
+  key[1] = s->M;
+  key[2] = s->cfg.pde;
+  key[3] = s->cfg.flux;
+  key[4] = kernel;
+  key[5] = size_class(na);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  TuneState& t = g_tune[tune_key(key)];
+  if (t.choice >= 0) return t.choice;
+  if (t.issued[0] + t.issued[1] == 0) {
+    // a new class: decided by a smaller class that kept full-size CTAs or a larger one that kept
+    // quarter-size CTAs
+    for (const auto& kv : g_tune) {
+      const auto& k2 = kv.first;
+      if (std::get<0>(k2) != key[0] || std::get<1>(k2) != key[1] || std::get<2>(k2) != key[2] ||
+          std::get<3>(k2) != key[3] || std::get<4>(k2) != key[4] || kv.second.choice < 0)
+        continue;
+      const int c2 = std::get<5>(k2);
+      if ((c2 < key[5] && kv.second.choice == 0) || (c2 > key[5] && kv.second.choice == 1)) {
+        t.choice = kv.second.choice;
+        t.inherited = 1;
+        return t.choice;
+      }
+    }
+  }
+  const int v = t.issued[1] < t.issued[0] ? 1 : 0;
+  t.issued[v]++;
+  return v | 2;
+}
+
+// the CTA size of a launch for the tuner's variant (0: the launch rules)
+static int tune_div(int v) { return v < 0 ? 0 : ((v & 1) ? 4 : 1); }
+
+// run a launch; time it with an event pair when it is a trial of the tuner
+template <class F>
+static int tuned(aw_solver* s, int v, const int* key, long long na, F&& launch) {
+  if (v < 0 || !(v & 2)) return launch();
+  cudaEvent_t a = take_event(s), b = take_event(s);
+  cudaEventRecord(a, s->stream);
+  const int n = launch();
+  cudaEventRecord(b, s->stream);
+  if (n > 0) {
+    aw_solver::TunePending p;
+    for (int i = 0; i < 6; i++) p.key[i] = key[i];
+    p.var = v & 1;
+    p.na = na;
+    p.a = a;
+    p.b = b;
+    s->tune_used.push_back(p);
+  } else {
+    s->ev_free.push_back(a);
+    s->ev_free.push_back(b);
+  }
+  return n;
+}
+
+// read the solver's finished trials (after a synchronisation of its stream) into the tuner
+static void tune_harvest(aw_solver* s) {
+  if (s->tune_used.empty()) return;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (auto& p : s->tune_used) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      TuneState& t = g_tune[tune_key(p.key)];
+      const double ns = 1e6 * (double)ms / (double)p.na;
+      if (t.choice < 0) {
+        t.ns_per_cell[p.var] = t.trials[p.var] ? std::min(t.ns_per_cell[p.var], ns) : ns;
+        t.trials[p.var]++;
+        if (t.trials[0] >= AW_TUNE_TRIALS && t.trials[1] >= AW_TUNE_TRIALS)
+          t.choice = t.ns_per_cell[1] < t.ns_per_cell[0] ? 1 : 0;
+      }
+    }
+    s->ev_free.push_back(p.a);
+    s->ev_free.push_back(p.b);
+  }
+  s->tune_used.clear();
 }
 
 static void harvest_events(aw_solver* s) {
@@ -1150,14 +1274,19 @@ static int advance(aw_solver* s, int l, int sub) {
   if (l >= 1)
     s->launches += timed(s, KIND_PROJECT, [&] { return s->ops.project(a, L.vlist, L.nv, s->lev[l - 1].qh, 1, nullptr, 1, st); });
   s->launches += timed(s, KIND_WENO, [&] { return s->ops.weno(a, st); });
-  s->launches += timed(s, KIND_PREDICT, [&] { return s->ops.predict(a, st); });
+  int key[6];
+  const int vp = tune_pick(s, AW_TUNE_PREDICTOR, a.na, key);
+  a.cta_div = tune_div(vp);
+  s->launches += tuned(s, vp, key, a.na, [&] { return timed(s, KIND_PREDICT, [&] { return s->ops.predict(a, st); }); });
   CK(cudaGetLastError());
   if (l < s->lmax)
     for (int k = 0; k < s->r; k++) TRY(advance(s, l + 1, k));
+  const int vf = tune_pick(s, AW_TUNE_FLUX, a.na, key);
+  a.cta_div = tune_div(vf);
   if (launch_params().fuse_flux_update) {
-    s->launches += timed(s, KIND_FLUX, [&] { return s->ops.flux_update(a, st); });
+    s->launches += tuned(s, vf, key, a.na, [&] { return timed(s, KIND_FLUX, [&] { return s->ops.flux_update(a, st); }); });
   } else {
-    s->launches += timed(s, KIND_FLUX, [&] { return s->ops.flux(a, st); });
+    s->launches += tuned(s, vf, key, a.na, [&] { return timed(s, KIND_FLUX, [&] { return s->ops.flux(a, st); }); });
     s->launches += timed(s, KIND_UPDATE, [&] { return s->ops.update(a, st); });
   }
   CK(cudaGetLastError());
@@ -1211,6 +1340,7 @@ static int step_begin(aw_solver* s, double dt0) {
 
 // after the stream has reached the copy of the error word to h_cnt[NSLOT * MAXL]: statistics, errors
 static int step_finish(aw_solver* s, double dt0, aw_stats* st) {
+  tune_harvest(s);
   const int err = s->h_cnt[NSLOT * MAXL];
   int64_t rl = 1;
   for (int l = 0; l <= s->lmax; l++) {
@@ -1354,6 +1484,7 @@ static int64_t total_cells(const aw_solver* s) {
 
 static void free_solver(aw_solver* s) {
   harvest_events(s);
+  tune_harvest(s);
   for (auto e : s->ev_free) cudaEventDestroy(e);
   s->ev_free.clear();
   // stream-ordered: after the solver's last work on its stream
@@ -2225,20 +2356,48 @@ int aw_get_launch_params(aw_launch_params* out) {
   out->tile8_min_cells = p.tile8_min_cells;
   out->small_ctas_per_sm = p.small_ctas_per_sm;
   out->fuse_flux_update = p.fuse_flux_update;
+  out->autotune = p.autotune;
   return AW_OK;
 }
 
 int aw_set_launch_params(const aw_launch_params* in) {
   if (!in) AW_FAIL(AW_EINVAL, "null argument");
   if (in->pass_min_cells < 0 || in->tile8_min_cells < 0 || in->small_ctas_per_sm < 0 || in->small_ctas_per_sm > 64 ||
-      (in->fuse_flux_update != 0 && in->fuse_flux_update != 1))
+      (in->fuse_flux_update != 0 && in->fuse_flux_update != 1) || (in->autotune != 0 && in->autotune != 1))
     AW_FAIL(AW_EINVAL, "launch parameters out of range");
   LaunchParams p;
   p.pass_min_cells = in->pass_min_cells;
   p.tile8_min_cells = in->tile8_min_cells;
   p.small_ctas_per_sm = in->small_ctas_per_sm;
   p.fuse_flux_update = in->fuse_flux_update;
+  p.autotune = in->autotune;
   set_launch_params(p);
+  return AW_OK;
+}
+
+int aw_get_tuning(aw_tune_entry* out, int32_t cap, int32_t* n) {
+  if (!n || cap < 0 || (cap > 0 && !out)) AW_FAIL(AW_EINVAL, "null argument or negative capacity");
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  *n = (int32_t)g_tune.size();
+  int32_t i = 0;
+  for (const auto& kv : g_tune) {
+    if (i >= cap) break;
+    aw_tune_entry& e = out[i++];
+    memset(&e, 0, sizeof e);
+    std::tie(e.dim, e.M, e.pde, e.flux, e.kernel, e.size_class) = kv.first;
+    e.choice = kv.second.choice;
+    e.inherited = kv.second.inherited;
+    for (int v = 0; v < 2; v++) {
+      e.trials[v] = kv.second.trials[v];
+      e.ns_per_cell[v] = kv.second.ns_per_cell[v];
+    }
+  }
+  return AW_OK;
+}
+
+int aw_reset_tuning(void) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune.clear();
   return AW_OK;
 }
 

@@ -51,7 +51,7 @@ def test_struct_layouts_match_header(tmp_path):
     header's structures"""
     structs = {"aw_config": pg.AwConfig, "aw_stats": pg.AwStats, "aw_cell": pg.AwCell,
                "aw_srv_info": pg.AwSrvInfo, "aw_srv_summary": pg.AwSrvSummary,
-               "aw_launch_params": _lib.AwLaunchParams}
+               "aw_launch_params": _lib.AwLaunchParams, "aw_tune_entry": _lib.AwTuneEntry}
     lines = ['#include <stddef.h>', '#include <stdio.h>', '#include "aderweno.h"', "int main(void) {"]
     for cname, py in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
@@ -75,14 +75,16 @@ def test_launch_params_roundtrip_without_gpu():
     """the launch-shape rules are host state: read, changed, rejected when out of range, restored"""
     before = pg.get_launch_params()
     assert before == {"pass_min_cells": 4096, "tile8_min_cells": 20000, "small_ctas_per_sm": 2,
-                      "fuse_flux_update": 1}
-    pg.set_launch_params(small_ctas_per_sm=0, pass_min_cells=0, fuse_flux_update=0)
+                      "fuse_flux_update": 1, "autotune": 1}
+    pg.set_launch_params(small_ctas_per_sm=0, pass_min_cells=0, fuse_flux_update=0, autotune=0)
     assert pg.get_launch_params() == {"pass_min_cells": 0, "tile8_min_cells": 20000, "small_ctas_per_sm": 0,
-                                      "fuse_flux_update": 0}
+                                      "fuse_flux_update": 0, "autotune": 0}
     with pytest.raises(pg.AwError):
         pg.set_launch_params(small_ctas_per_sm=65)
     with pytest.raises(pg.AwError):
         pg.set_launch_params(fuse_flux_update=2)
+    with pytest.raises(pg.AwError):
+        pg.set_launch_params(autotune=-1)
     pg.set_launch_params(**before)
     assert pg.get_launch_params() == before
 
@@ -107,7 +109,7 @@ SCALARS = {"int": ctypes.c_int, "int32_t": ctypes.c_int32, "int64_t": ctypes.c_i
            "uintptr_t": ctypes.c_size_t}
 STRUCTS = {"aw_config": pg.AwConfig, "aw_stats": pg.AwStats, "aw_cell": pg.AwCell, "aw_srv_info": pg.AwSrvInfo,
            "aw_srv_summary": pg.AwSrvSummary, "aw_launch_params": _lib.AwLaunchParams,
-           "int8_t": ctypes.c_int8, "int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "double": ctypes.c_double}
+           "aw_tune_entry": _lib.AwTuneEntry, "int8_t": ctypes.c_int8, "int32_t": ctypes.c_int32, "int64_t": ctypes.c_int64, "double": ctypes.c_double}
 OPAQUE = {"aw_solver", "aw_server"}
 
 
@@ -144,3 +146,14 @@ def test_binding_signatures_match_the_header():
             assert restype is ctypes.c_char_p, name
         else:
             assert restype is SCALARS[ret], (name, ret, restype)
+
+
+def test_tuning_state_without_gpu():
+    """the autotuner's table is host state: empty after a reset; a null count is rejected"""
+    pg.reset_tuning()
+    assert pg.get_tuning() == []
+    L = _lib.load()
+    assert L.aw_get_tuning(None, 0, None) == _lib.AW_EINVAL
+    n = ctypes.c_int32(-5)
+    assert L.aw_get_tuning(None, -1, ctypes.byref(n)) == _lib.AW_EINVAL
+    assert L.aw_get_tuning(None, 0, ctypes.byref(n)) == _lib.AW_OK and n.value == 0
