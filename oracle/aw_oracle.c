@@ -414,13 +414,125 @@ static void rusanov(const phys *P, const double *qm, const double *qp, int n, do
   for (int v = 0; v < P->V; v++) out[v] = 0.5 * (fm[v] + fp[v]) - 0.5 * s * (qp[v] - qm[v]);
 }
 
+/* Jacobian A[i][j] = dF_i/dQ_j of the MHD-GLM flux in direction n (the flux above, rationalised
+ * units) with respect to the conserved variables Q = (rho, m_x, m_y, m_z, E, B_x, B_y, B_z, psi),
+ * written out term by term from F with v = m / rho, p = (gamma - 1)(E - rho |v|^2 / 2 - |B|^2 / 2)
+ * and p_t = p + |B|^2 / 2. */
+static void mhd_jacobian(const phys *P, const double *q, int n, double A[9][9]) {
+  const double g1 = P->gamma - 1.0, rho = q[0], E = q[4];
+  double v[3], B[3], v2 = 0.0, B2 = 0.0, vB = 0.0;
+  for (int a = 0; a < 3; a++) {
+    v[a] = q[1 + a] / rho;
+    B[a] = q[5 + a];
+    v2 += v[a] * v[a];
+    B2 += B[a] * B[a];
+    vB += v[a] * B[a];
+  }
+  const double p = g1 * (E - 0.5 * rho * v2 - 0.5 * B2), pt = p + 0.5 * B2;
+  /* dp/dQ and dp_t/dQ */
+  double dp[9] = {0.5 * g1 * v2, -g1 * v[0], -g1 * v[1], -g1 * v[2], g1, -g1 * B[0], -g1 * B[1], -g1 * B[2], 0.0};
+  double dpt[9];
+  for (int j = 0; j < 9; j++) dpt[j] = dp[j];
+  for (int a = 0; a < 3; a++) dpt[5 + a] += B[a];
+  for (int i = 0; i < 9; i++)
+    for (int j = 0; j < 9; j++) A[i][j] = 0.0;
+  /* F_rho = m_n */
+  A[0][1 + n] = 1.0;
+  /* F_m_a = m_a v_n + p_t delta_an - B_a B_n; d(v_n)/d(rho) = -v_n / rho, d(v_n)/d(m_n) = 1 / rho */
+  for (int a = 0; a < 3; a++) {
+    A[1 + a][0] += -v[a] * v[n];
+    A[1 + a][1 + a] += v[n];
+    A[1 + a][1 + n] += v[a];
+    if (a == n)
+      for (int j = 0; j < 9; j++) A[1 + a][j] += dpt[j];
+    A[1 + a][5 + a] -= B[n];
+    A[1 + a][5 + n] -= B[a];
+  }
+  /* F_E = v_n (E + p_t) - B_n (v . B) */
+  A[4][0] += -(E + pt) * v[n] / rho + B[n] * vB / rho;
+  A[4][1 + n] += (E + pt) / rho;
+  A[4][4] += v[n];
+  for (int j = 0; j < 9; j++) A[4][j] += v[n] * dpt[j];
+  A[4][5 + n] -= vB;
+  for (int b = 0; b < 3; b++) {
+    A[4][1 + b] -= B[n] * B[b] / rho;
+    A[4][5 + b] -= B[n] * v[b];
+  }
+  /* F_B_a = v_n B_a - B_n v_a (a != n), F_B_n = psi */
+  for (int a = 0; a < 3; a++) {
+    if (a == n) continue;
+    A[5 + a][0] += (B[n] * v[a] - B[a] * v[n]) / rho;
+    A[5 + a][1 + n] += B[a] / rho;
+    A[5 + a][1 + a] -= B[n] / rho;
+    A[5 + a][5 + a] += v[n];
+    A[5 + a][5 + n] -= v[a];
+  }
+  A[5 + n][8] = 1.0;
+  /* F_psi = c_h^2 B_n */
+  A[8][5 + n] = P->c_h * P->c_h;
+}
+
+/* |A| = A sign(A) for a real V x V matrix with real eigenvalues of modulus at most s (A
+ * diagonalisable: |A| = R |Lambda| R^-1).  sign(A) by the Newton-Schulz iteration for the matrix
+ * sign function, S <- S (3 I - S^2) / 2 from S = A / s: every eigenvalue x of S moves by the
+ * scalar map x (3 - x^2) / 2, which takes x in (0, 1] to 1 and x in [-1, 0) to -1 (quadratically
+ * near +-1, by a factor 1.5 per step while small) and keeps x = 0 at 0, as |A| needs.  80 steps
+ * take every eigenvalue above 1e-14 s to its sign; below that its share of |A| is below 1e-14 s. */
+static void abs_matrix(int V, const double *A, double s, double *out) {
+  double S[MAXV * MAXV], T[MAXV * MAXV], U[MAXV * MAXV];
+  for (int i = 0; i < V * V; i++) S[i] = A[i] / s;
+  for (int it = 0; it < 80; it++) {
+    for (int i = 0; i < V; i++)
+      for (int j = 0; j < V; j++) {
+        double t = 0.0;
+        for (int k = 0; k < V; k++) t += S[i * V + k] * S[k * V + j];
+        T[i * V + j] = (i == j ? 3.0 : 0.0) - t;
+      }
+    for (int i = 0; i < V; i++)
+      for (int j = 0; j < V; j++) {
+        double t = 0.0;
+        for (int k = 0; k < V; k++) t += S[i * V + k] * T[k * V + j];
+        U[i * V + j] = 0.5 * t;
+      }
+    memcpy(S, U, sizeof(double) * V * V);
+  }
+  for (int i = 0; i < V; i++)
+    for (int j = 0; j < V; j++) {
+      double t = 0.0;
+      for (int k = 0; k < V; k++) t += A[i * V + k] * S[k * V + j];
+      out[i * V + j] = t;
+    }
+}
+
 /* |A(q)| applied to dq for the Euler flux in direction n: R |Lambda| L dq with the right and left
  * eigenvectors of the Jacobian written out (eigenvalues u_n - c, u_n (d times), u_n + c).  A state
  * with c^2 <= 0 has complex eigenvalues; there |A| dq is replaced by s dq with s the spectral
- * radius (reading).  Linear advection: |a_n| dq. */
+ * radius (reading).  Linear advection: |a_n| dq.  MHD-GLM: |A| of the Jacobian above by
+ * abs_matrix, with s = max(|v_n| + c_f, c_h) its spectral radius (eigenvalues v_n, v_n +- c_a,
+ * v_n +- c_s, v_n +- c_f and +-c_h); where gamma p / rho <= 0 the fast speed is not real and
+ * |A| dq is replaced by s dq with s = max(|v_n| + sqrt(|B|^2 / rho), c_h) (reading). */
 static void abs_jacobian_apply(const phys *P, const double *q, int n, const double *dq, double *out) {
   int V = P->V, d = P->d;
   if (P->pde == PDE_LINADV) { out[0] = fabs(P->adv[n]) * dq[0]; return; }
+  if (P->pde == PDE_MHD) {
+    const double rho = q[0], a2 = P->gamma * pressure(P, q) / rho;
+    if (!(a2 > 0.0)) {
+      double B2 = q[5] * q[5] + q[6] * q[6] + q[7] * q[7];
+      double s = fabs(q[1 + n] / rho) + sqrt(B2 / rho);
+      if (s < P->c_h) s = P->c_h;
+      for (int v = 0; v < 9; v++) out[v] = s * dq[v];
+      return;
+    }
+    double A[9][9], Aa[81];
+    mhd_jacobian(P, q, n, A);
+    abs_matrix(9, &A[0][0], max_speed(P, q, n), Aa);
+    for (int i = 0; i < 9; i++) {
+      double t = 0.0;
+      for (int j = 0; j < 9; j++) t += Aa[i * 9 + j] * dq[j];
+      out[i] = t;
+    }
+    return;
+  }
   double rho = q[0], vel[3] = {0, 0, 0}, v2 = 0.0;
   for (int a = 0; a < d; a++) { vel[a] = q[1 + a] / rho; v2 += vel[a] * vel[a]; }
   double p = pressure(P, q), c2 = P->gamma * p / rho;
@@ -1534,11 +1646,6 @@ void *orc_create(const orc_cfg *c) {
   S->d = c->dim;
   S->N = c->M + 1;
   S->P.pde = c->pde; S->P.d = c->dim; S->P.gamma = c->gamma; S->P.c_h = c->c_h; S->P.flux = c->flux;
-  if (c->flux == 1 && c->pde == PDE_MHD) {
-    seterr("the Osher flux is available for Euler and linear advection");
-    free(S);
-    return NULL;
-  }
   for (int i = 0; i < 6; i++)
     if (c->bc[i] == BC_REFLECTIVE && c->pde == PDE_MHD) {
       seterr("reflective walls are available for Euler and linear advection");

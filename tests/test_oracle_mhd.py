@@ -32,10 +32,10 @@ def alfven_averages(n, ny, shift):
     return u.reshape(-1, 9)
 
 
-def alfven_error(M, n, t_end):
+def alfven_error(M, n, t_end, flux=0):
     ny = 4
     cfg = oracle.make_cfg(dim=2, pde=oracle.PDE_MHD, M=M, n=(n, ny, 1), lo=(0, 0, 0), hi=(1, ny / n, 1),
-                          gamma=GAMMA, c_h=2.0, cfl=0.9)
+                          gamma=GAMMA, c_h=2.0, cfl=0.9, flux=flux)
     o = oracle.Oracle(cfg, threads=8)
     o.set_initial(oracle.IC_CONST, [1.0, 0.0, 0.0, 0.0, 0.1, 1.0, 0.0, 0.0, 0.0], nrefine=0)
     o.set_cell_averages(alfven_averages(n, ny, 0.0))

@@ -49,6 +49,12 @@ PLANTED = [
      "for (int a = 0; a < S->d; a++) den += max_speed(&S->P, u, a) / dx[a];",
      "for (int a = 0; a < S->d; a++) den += max_speed(&S->P, u, a) / (dx[0] < dx[1] ? dx[0] : dx[1]);",
      "tests/test_oracle_dt.py::test_dt_euler_3d_constant_state"),
+    ("MHD Jacobian: energy flux without the work of the normal field on v.B",
+     "  A[4][5 + n] -= vB;\n", "\n",
+     "tests/test_oracle_osher.py::test_mhd_jacobian_spectrum_and_abs_jacobian_match_numpy"),
+    ("MHD Jacobian: total pressure without the magnetic pressure",
+     "  for (int a = 0; a < 3; a++) dpt[5 + a] += B[a];\n", "\n",
+     "tests/test_oracle_osher.py::test_mhd_jacobian_spectrum_and_abs_jacobian_match_numpy"),
     ("indicator without its cross terms",
      "    for (int l = 0; l < d; l++) {\n      double D2, G, A;", "    for (int l = k; l <= k; l++) {\n      double D2, G, A;",
      "tests/test_oracle_indicator.py::test_mixed_derivative_counts"),
