@@ -75,9 +75,10 @@ HBM_GBS = 6792.1                 # measured copy bandwidth of this GB300 pool
 # build, scaled by the cells of an average launch of the timed steps.  3D (k_predict<3,2,Euler>):
 # a level-2 launch of the same explosion on a 20^3 base (63693 CTAs x 8 cells, 2.2 GB of
 # predictor data, far above the 129 MB L2): dram__bytes_read.sum 551.31 MB +
-# dram__bytes_write.sum 1589.96 MB.  The 2D workload's kernel changed after its capture (None:
-# no traffic figure).  Must be re-captured whenever k_predict changes.
-PREDICTOR_DRAM_BYTES_PER_CELL = None
+# dram__bytes_write.sum 1589.96 MB.  2D (k_predict<2,3,Euler>): a level-2 launch of the 100x100
+# explosion (6264 CTAs x 16 cells): 51.63 MB + 140.97 MB.  Must be re-captured whenever k_predict
+# changes.
+PREDICTOR_DRAM_BYTES_PER_CELL = (51634944 + 140974592) / (6264 * 16)
 PREDICTOR_DRAM_BYTES_PER_CELL_3D = {"predictor": (551310848 + 1589964000) / (63693 * 8)}
 
 
@@ -246,7 +247,8 @@ def run_serve(args):
             else:
                 failed += 1
         return {"solves_per_s": len(tts) / done, "p50_ms": float(np.percentile(tts, 50)),
-                "p99_ms": float(np.percentile(tts, 99)), "cell_updates_per_s": upd / done, "failed": failed}
+                "p99_ms": float(np.percentile(tts, 99)), "cell_updates_per_s": upd / done, "failed": failed,
+                "failure_rate": failed / len(reqs)}
 
     def loop(arrivals, max_batch=1):
         srv = pg.Server(hbm_budget_bytes=int(args.serve_budget_gb * (1 << 30)), max_concurrent=args.concurrency,
@@ -261,7 +263,9 @@ def run_serve(args):
         srv.wait_all()
         st = srv.stats()
         out = {"solves_per_s": st.solves_per_s, "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
-               "cell_updates_per_s": st.cell_updates_per_s, "failed": int(st.failed)}
+               "cell_updates_per_s": st.cell_updates_per_s, "failed": int(st.failed),
+               "failure_rate": int(st.failed) / len(reqs), "requeues": int(st.requeues),
+               "peak_reserved_gb": st.peak_reserved_bytes / 2 ** 30}
         srv.close()
         return out
 
@@ -277,6 +281,9 @@ def run_serve(args):
                       "config": {"workload": f"{len(reqs)} 2D Euler four-quadrant Riemann AMR solves, "
                                              f"base {args.serve_base_min}..{args.serve_base_max}, M in {{2,3}}, "
                                              f"l_max in 0..{args.serve_lmax_max}, r=3, CFL 0.5, t_end={t_end}",
+                                 "sample": (f"the first {len(reqs)} requests of the seeded stream (seed 20121213), "
+                                            f"end time {t_end} instead of the stream's 0.2"
+                                            if t_end != 0.2 else f"the first {len(reqs)} requests of the seeded stream"),
                                  "concurrency": args.concurrency, "budget_gb": args.serve_budget_gb, "batch": args.serve_batch},
                       **res}))
     return 0

@@ -58,7 +58,7 @@ extern "C" {
 #define AW_BC_INFLOW 3       /* ghost cells hold the constant conserved state inflow[]; face flux against it */
 
 #define AW_FLUX_RUSANOV 0  /* Eq. eqn.rusanov */
-#define AW_FLUX_OSHER 1    /* Eq. eqn.osher, 3-point Gauss-Legendre path quadrature (Euler) */
+#define AW_FLUX_OSHER 1    /* Eq. eqn.osher, 3-point Gauss-Legendre path quadrature (Euler, MHD-GLM, linear advection) */
 
 /* initial conditions of Sec. 4; parameter layouts:
  *  AW_IC_CONST:     primitive state (Euler: rho, v_1..v_d, p; MHD: rho, vx, vy, vz, p, Bx, By,
@@ -195,17 +195,23 @@ int aw_advance_graph(aw_solver* s, double t_end, int32_t chunk, aw_stats* stats)
  * library's autotuner pick the CTA size (cells, or faces, per block: full or quarter size) of the
  * predictor and of the face flux per configuration and level size class, from CUDA-event timings
  * of the first launches of each (aw_get_tuning), in place of the small_ctas_per_sm rule; 0 the
- * rule alone.  The averages are bitwise the same for every setting.  Process-wide.  The first
- * two are fixed per level when a solver is created, the others apply to every launch.
- * AW_EINVAL for negative values, small_ctas_per_sm > 64, or fuse_flux_update or autotune not 0
- * or 1.  bench.py --tune times the workload over these parameters. */
+ * rule alone; and persistent: 1 advances every level and sub-step of a batch (aw_advance_batch)
+ * with one persistent cooperative launch for the projection, WENO and predictor of all members,
+ * which also runs the fused face flux and update on a level with no finer level, with grid-wide
+ * barriers between the phases (2D configurations, where the predictor and the face flux share
+ * their CTA shape, with fuse_flux_update = 1); 0 (default: measured faster) the separate
+ * launches.
+ * The averages are bitwise the same for every setting.  Process-wide.  The first two are fixed
+ * per level when a solver is created, the others apply to every launch.  AW_EINVAL for negative
+ * values, small_ctas_per_sm > 64, or fuse_flux_update, autotune or persistent not 0 or 1.
+ * bench.py --tune times the workload over these parameters. */
 typedef struct aw_launch_params {
   int64_t pass_min_cells;
   int64_t tile8_min_cells;
   int32_t small_ctas_per_sm;
   int32_t fuse_flux_update;
   int32_t autotune;
-  int32_t reserved;
+  int32_t persistent;
 } aw_launch_params;
 int aw_get_launch_params(aw_launch_params* out);
 int aw_set_launch_params(const aw_launch_params* in);
@@ -337,7 +343,8 @@ typedef struct aw_srv_summary {
  * running requests leave of the budget; its solver runs under that reservation as its memory
  * limit (aw_set_memory_limit, less 64 MiB for the CUDA context and staging).  The first
  * reservation is an estimate: the dense per-level grids exactly, per-active arrays for a quarter
- * of the finest level.  A solve that outgrows its reservation (AW_ELIMIT: a mesh that refines
+ * of the finest level, or for 1.25 times the largest share of it that finished or refused runs of
+ * the same dim, pde, M, lmax and refine_factor held (the loop learns it from their device bytes).  A solve that outgrows its reservation (AW_ELIMIT: a mesh that refines
  * more than that) gives its memory back and goes back to the head of the queue with a larger
  * reservation (at least the bytes it was refused, at least twice the old one, at most what every
  * cell of every level active would take), and waits there until the budget has room for it; it

@@ -194,11 +194,11 @@ def get_launch_params() -> dict:
     _lib.check(_lib.load().aw_get_launch_params(C.byref(p)))
     return {"pass_min_cells": p.pass_min_cells, "tile8_min_cells": p.tile8_min_cells,
             "small_ctas_per_sm": p.small_ctas_per_sm, "fuse_flux_update": p.fuse_flux_update,
-            "autotune": p.autotune}
+            "autotune": p.autotune, "persistent": p.persistent}
 
 
 def set_launch_params(pass_min_cells=None, tile8_min_cells=None, small_ctas_per_sm=None, fuse_flux_update=None,
-                      autotune=None):
+                      autotune=None, persistent=None):
     """aw_set_launch_params: change some of the launch-shape rules (speed only, never results)."""
     cur = get_launch_params()
     p = _lib.AwLaunchParams()
@@ -207,6 +207,7 @@ def set_launch_params(pass_min_cells=None, tile8_min_cells=None, small_ctas_per_
     p.small_ctas_per_sm = cur["small_ctas_per_sm"] if small_ctas_per_sm is None else int(small_ctas_per_sm)
     p.fuse_flux_update = cur["fuse_flux_update"] if fuse_flux_update is None else int(fuse_flux_update)
     p.autotune = cur["autotune"] if autotune is None else int(autotune)
+    p.persistent = cur["persistent"] if persistent is None else int(persistent)
     _lib.check(_lib.load().aw_set_launch_params(C.byref(p)))
 
 

@@ -55,7 +55,7 @@ class AwSrvSummary(C.Structure):
 
 class AwLaunchParams(C.Structure):
     _fields_ = [("pass_min_cells", C.c_int64), ("tile8_min_cells", C.c_int64), ("small_ctas_per_sm", C.c_int32),
-                ("fuse_flux_update", C.c_int32), ("autotune", C.c_int32), ("reserved", C.c_int32)]
+                ("fuse_flux_update", C.c_int32), ("autotune", C.c_int32), ("persistent", C.c_int32)]
 
 
 class AwTuneEntry(C.Structure):

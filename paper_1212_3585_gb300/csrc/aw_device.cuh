@@ -379,6 +379,153 @@ __device__ __forceinline__ void osher_euler(const double* qm, const double* qp, 
   for (int k = 0; k < V; k++) out[k] = fma(-0.5, acc[k], 0.5 * (fm[k] + fp[k]));
 }
 
+// Jacobian of the MHD-GLM flux in direction n with respect to the conserved variables, by the
+// chain rule through the primitive variables W = (rho, v_x, v_y, v_z, p, B_x, B_y, B_z, psi):
+// A = (dF/dW)(dW/dQ), both factors written out from the flux and the equation of state
+// (rationalised units).  A[i * 9 + j] = dF_i / dQ_j.
+__device__ __forceinline__ void mhd_jacobian(const double* q, int n, double* A, const Phys& P) {
+  const double g = P.gamma, g1 = g - 1.0, rho = q[0], ir = 1.0 / rho;
+  double v[3], B[3];
+#pragma unroll
+  for (int a = 0; a < 3; a++) { v[a] = q[1 + a] * ir; B[a] = q[5 + a]; }
+  const double v2 = v[0] * v[0] + v[1] * v[1] + v[2] * v[2], B2 = B[0] * B[0] + B[1] * B[1] + B[2] * B[2];
+  const double vB = v[0] * B[0] + v[1] * B[1] + v[2] * B[2];
+  const double p = g1 * (q[4] - 0.5 * rho * v2 - 0.5 * B2);
+  const double Ept = g * p / g1 + 0.5 * rho * v2 + B2;   // E + p_t
+  const double vn = v[n], Bn = B[n];
+  // dF/dW, rows F, columns W
+  double FW[81];
+  for (int k = 0; k < 81; k++) FW[k] = 0.0;
+  FW[0 * 9 + 0] = vn;
+  FW[0 * 9 + 1 + n] = rho;
+  for (int a = 0; a < 3; a++) {
+    double* r = FW + (1 + a) * 9;
+    r[0] = v[a] * vn;
+    r[1 + a] += rho * vn;
+    r[1 + n] += rho * v[a];
+    if (a == n) r[4] = 1.0;
+    for (int b = 0; b < 3; b++) r[5 + b] = (a == n ? B[b] : 0.0) - (a == b ? Bn : 0.0) - (b == n ? B[a] : 0.0);
+  }
+  {
+    double* r = FW + 4 * 9;
+    r[0] = 0.5 * vn * v2;
+    for (int b = 0; b < 3; b++) {
+      r[1 + b] = (b == n ? Ept : 0.0) + vn * rho * v[b] - Bn * B[b];
+      r[5 + b] = 2.0 * vn * B[b] - (b == n ? vB : 0.0) - Bn * v[b];
+    }
+    r[4] = vn * g / g1;
+  }
+  for (int a = 0; a < 3; a++) {
+    double* r = FW + (5 + a) * 9;
+    if (a == n) { r[8] = 1.0; continue; }
+    r[1 + n] = B[a];
+    r[1 + a] -= Bn;
+    r[5 + a] = vn;
+    r[5 + n] -= v[a];
+  }
+  FW[8 * 9 + 5 + n] = P.c_h * P.c_h;
+  // dW/dQ
+  double WQ[81];
+  for (int k = 0; k < 81; k++) WQ[k] = 0.0;
+  WQ[0] = 1.0;
+  for (int a = 0; a < 3; a++) {
+    WQ[(1 + a) * 9 + 0] = -v[a] * ir;
+    WQ[(1 + a) * 9 + 1 + a] = ir;
+    WQ[4 * 9 + 1 + a] = -g1 * v[a];
+    WQ[4 * 9 + 5 + a] = -g1 * B[a];
+    WQ[(5 + a) * 9 + 5 + a] = 1.0;
+  }
+  WQ[4 * 9 + 0] = 0.5 * g1 * v2;
+  WQ[4 * 9 + 4] = g1;
+  WQ[8 * 9 + 8] = 1.0;
+  for (int i = 0; i < 9; i++)
+    for (int j = 0; j < 9; j++) {
+      double t = 0.0;
+      for (int k = 0; k < 9; k++) t = fma(FW[i * 9 + k], WQ[k * 9 + j], t);
+      A[i * 9 + j] = t;
+    }
+}
+
+// |A(q)| dq for the MHD-GLM flux in direction n: |A| = A sign(A), the sign by the Newton-Schulz
+// iteration S <- S (3 I - S^2) / 2 from S = A / s, s = max(|v_n| + c_f, c_h) the spectral radius
+// (each eigenvalue x / s in [-1, 1] goes to its sign, 0 stays 0; 80 steps bring every eigenvalue
+// above 1e-14 s to +-1).  Where gamma p / rho <= 0 the fast speed is not real and |A| dq is
+// s dq with s = max(|v_n| + |B| / sqrt(rho), c_h).  The matrices live in local memory.
+template <int D>
+__device__ __noinline__ void mhd_abs_jacobian_apply(const double* q, int n, const double* dq, double* out,
+                                                    const Phys& P) {
+  const double rho = q[0];
+  const double B2 = q[5] * q[5] + q[6] * q[6] + q[7] * q[7];
+  const double m2 = q[1] * q[1] + q[2] * q[2] + q[3] * q[3];
+  const double p = (P.gamma - 1.0) * (q[4] - 0.5 * m2 / rho - 0.5 * B2);
+  if (!(P.gamma * p / rho > 0.0)) {
+    double s = fabs(q[1 + n] / rho) + sqrt(B2 / rho);
+    if (s < P.c_h) s = P.c_h;
+    for (int v = 0; v < 9; v++) out[v] = s * dq[v];
+    return;
+  }
+  double A[81], S[81], T[81];
+  mhd_jacobian(q, n, A, P);
+  const double is = 1.0 / Pde<PDE_MHD, D>::speed(q, n, P);
+  for (int k = 0; k < 81; k++) S[k] = A[k] * is;
+  for (int it = 0; it < 80; it++) {
+    // T = 3 I - S^2
+    for (int i = 0; i < 9; i++)
+      for (int j = 0; j < 9; j++) {
+        double t = 0.0;
+        for (int k = 0; k < 9; k++) t = fma(S[i * 9 + k], S[k * 9 + j], t);
+        T[i * 9 + j] = (i == j ? 3.0 : 0.0) - t;
+      }
+    // S <- S T / 2, a row at a time (row i of the product needs row i of S only)
+    for (int i = 0; i < 9; i++) {
+      double row[9];
+#pragma unroll
+      for (int j = 0; j < 9; j++) {
+        double t = 0.0;
+        for (int k = 0; k < 9; k++) t = fma(S[i * 9 + k], T[k * 9 + j], t);
+        row[j] = 0.5 * t;
+      }
+#pragma unroll
+      for (int j = 0; j < 9; j++) S[i * 9 + j] = row[j];
+    }
+  }
+  double w[9];
+  for (int i = 0; i < 9; i++) {
+    double t = 0.0;
+    for (int k = 0; k < 9; k++) t = fma(S[i * 9 + k], dq[k], t);
+    w[i] = t;
+  }
+  for (int i = 0; i < 9; i++) {
+    double t = 0.0;
+    for (int k = 0; k < 9; k++) t = fma(A[i * 9 + k], w[k], t);
+    out[i] = t;
+  }
+}
+
+// Osher-Solomon flux of Dumbser and Toro for MHD-GLM, Eq. eqn.osher: the straight path between
+// the states, |A| integrated by the 3-point Gauss-Legendre rule on [0,1].
+template <int D>
+__device__ __forceinline__ void osher_mhd(const double* qm, const double* qp, int n, double* out, const Phys& P) {
+  constexpr int V = 9;
+  const double gs[3] = {0.5 - 0.3872983346207417, 0.5, 0.5 + 0.3872983346207417};
+  const double gw[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+  double fm[V], fp[V], dq[V], acc[V];
+  Pde<PDE_MHD, D>::flux(qm, n, fm, P);
+  Pde<PDE_MHD, D>::flux(qp, n, fp, P);
+#pragma unroll
+  for (int k = 0; k < V; k++) { dq[k] = qp[k] - qm[k]; acc[k] = 0.0; }
+  for (int j = 0; j < 3; j++) {
+    double q[V], t[V];
+#pragma unroll
+    for (int k = 0; k < V; k++) q[k] = fma(gs[j], dq[k], qm[k]);
+    mhd_abs_jacobian_apply<D>(q, n, dq, t, P);
+#pragma unroll
+    for (int k = 0; k < V; k++) acc[k] = fma(gw[j], t[k], acc[k]);
+  }
+#pragma unroll
+  for (int k = 0; k < V; k++) out[k] = fma(-0.5, acc[k], 0.5 * (fm[k] + fp[k]));
+}
+
 // Rusanov flux, Eq. eqn.rusanov: s_max is the larger of the two states' largest |eigenvalue|.
 template <int PDE, int D>
 __device__ __forceinline__ void rusanov(const double* qm, const double* qp, int n, double* out, const Phys& P) {

@@ -4,6 +4,8 @@
 // the kernels are laid out to keep every lane of every issued FP64 instruction busy (compacted
 // work lists, one thread per cell x spatial node) rather than for memory traffic.
 #pragma once
+#include <cooperative_groups.h>
+
 #include "aw_device.cuh"
 #include "aw_ops.h"
 
@@ -595,7 +597,11 @@ __global__ void __launch_bounds__(PredCfg<D, M, PDE, DIV>::THREADS) k_predict(co
 template <int D, int M, int PDE, int DIV = 1>
 struct FluxCfg {
   static constexpr int N = M + 1, NF = ipow(N, D - 1), V = nvars(D, PDE);
-  static constexpr int TARGET = PDE == PDE_MHD ? 128 : 256;   // threads of a full-size CTA, about
+  // threads of a full-size CTA: the predictor's CTA size where a whole number of warps of face
+  // items fills it (so that the persistent level kernel k_level_batch runs both bodies in one CTA
+  // shape), else about 256 (128 for the 9 MHD-GLM variables)
+  static constexpr int PT = PredCfg<D, M, PDE, 1>::THREADS;
+  static constexpr int TARGET = PT % (32 * NF) == 0 ? PT : (PDE == PDE_MHD ? 128 : 256);
   static constexpr int FULL = 32 * (TARGET / (32 * NF) > 0 ? TARGET / (32 * NF) : 1);
   static constexpr int CPB = FULL / DIV > 0 ? FULL / DIV : 1;   // face items per CTA
   static constexpr int THREADS = CPB * NF;
@@ -748,8 +754,8 @@ __device__ __forceinline__ void fine_transverse(const HotArgs& a, const int* ijk
 // One face (axis d, side) of an active cell at spatial face point g: this thread's share of the
 // face integral, summed over the N time nodes into acc (quadrature weights included).  qf holds
 // the virtual neighbour's values on the fine side of a coarse/fine face.  FL: the numerical flux
-// (0 Rusanov, 1 Osher-Solomon; Euler), a template parameter so that the Rusanov kernels do not
-// carry the Osher flux's registers.
+// (0 Rusanov, 1 Osher-Solomon; Euler and MHD-GLM), a template parameter so that the Rusanov
+// kernels do not carry the Osher flux's registers.
 template <int D, int M, int PDE, int d, int FL>
 __device__ __forceinline__ void flux_face(const HotArgs& a, int kind, const double* qA, const double* qB,
                                           const double* qf, int g, int side, double* acc) {
@@ -799,6 +805,8 @@ __device__ __forceinline__ void flux_face(const HotArgs& a, int kind, const doub
       Pde<PDE, D>::flux(qa, d, f, a.P);
     } else if constexpr (PDE == PDE_EULER && FL == 1) {
       osher_euler<D>(ql, qr, d, f, a.P);
+    } else if constexpr (PDE == PDE_MHD && FL == 1) {
+      osher_mhd<D>(ql, qr, d, f, a.P);
     } else if constexpr (PDE == PDE_EULER) {
       rusanov_euler_x2<D>(ql, qr, d, f, a.P);
     } else {
@@ -1183,6 +1191,70 @@ __global__ void k_project_batch(const __grid_constant__ HotBatch b) {
   const int m = batch_member(b, blockIdx.x);
   const HotArgs& a = b.a[m];
   project_body<D, M, PDE>(a, a.vlist, a.nv, a.qhm, 1, nullptr, 1, blockIdx.x - b.start[m]);
+}
+
+// ------------------------------------------------------------------------------------------
+// Persistent level kernel of a batch (cross-request batching): one cooperative launch per level
+// and sub-step runs, for every member, the projection of its virtual children, its WENO
+// reconstruction (tiles or passes), its predictor and, when no member has a finer level (whose
+// sub-steps must come in between), its fused face flux and update, one phase after another with
+// a grid-wide barrier between dependent phases.  Every CTA is resident (cooperative launch), so
+// the barriers end.  In each phase the CTAs loop over that phase's work items, the work items of
+// the separate launches with the same bodies, so the results are bitwise those of the separate
+// launches.  The CTA has the predictor's shape, which the face flux shares (FluxCfg), and the
+// WENO and projection bodies take any CTA size.
+// ------------------------------------------------------------------------------------------
+enum { PH_PROJECT = 0, PH_WENO4, PH_WENO8, PH_WENO_X, PH_WENO_Y, PH_WENO_Z, PH_PREDICT, PH_FLUX, NPHASE };
+
+struct LevelBatch {
+  HotBatch b;
+  int start[NPHASE][MAXB + 1];   // work of each phase: member m owns items start[p][m] .. start[p][m+1]-1
+  int with_flux;                 // run the fused face flux and update too
+};
+
+template <int D, int M, int PDE, int FL>
+__global__ void __launch_bounds__(PredCfg<D, M, PDE>::THREADS) k_level_batch(const __grid_constant__ LevelBatch lb) {
+  cooperative_groups::grid_group grid = cooperative_groups::this_grid();
+  __shared__ FluxShm<FluxCfg<D, M, PDE>::CPB> fs;
+  const HotBatch& b = lb.b;
+  auto run = [&](int ph, auto&& body) {
+    const int* st = lb.start[ph];
+    for (int w = blockIdx.x; w < st[b.n]; w += gridDim.x) {
+      int m = 0;
+      while (m + 1 < b.n && w >= st[m + 1]) m++;
+      body(b.a[m], w - st[m]);
+      __syncthreads();   // the next item's body reuses the shared memory
+    }
+  };
+  if (lb.with_flux) {
+    // the fused flux's arrival counters start at zero (several barriers before they are used)
+    const long long g0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, gs = (long long)gridDim.x * blockDim.x;
+    for (int m = 0; m < b.n; m++) {
+      const int nchunk = (b.a[m].na + FluxCfg<D, M, PDE>::CPB - 1) / FluxCfg<D, M, PDE>::CPB;
+      for (long long i = g0; i < nchunk; i += gs) b.a[m].fsync[i] = 0;
+    }
+  }
+  run(PH_PROJECT, [&](const HotArgs& a, int w) { project_body<D, M, PDE>(a, a.vlist, a.nv, a.qhm, 1, nullptr, 1, w); });
+  grid.sync();
+  run(PH_WENO4, [&](const HotArgs& a, int w) { weno_body<D, M, PDE, 4>(a, w); });
+  if constexpr (D == 2) {
+    run(PH_WENO8, [&](const HotArgs& a, int w) { weno_body<D, M, PDE, 8>(a, w); });
+    run(PH_WENO_X, [&](const HotArgs& a, int w) { weno_x_body<M, PDE>(a, w); });
+    grid.sync();
+    run(PH_WENO_Y, [&](const HotArgs& a, int w) { weno_y_body<M, PDE>(a, w); });
+  } else {
+    run(PH_WENO_X, [&](const HotArgs& a, int w) { weno3_x_body<M, PDE>(a, w); });
+    grid.sync();
+    run(PH_WENO_Y, [&](const HotArgs& a, int w) { weno3_y_body<M, PDE>(a, w); });
+    grid.sync();
+    run(PH_WENO_Z, [&](const HotArgs& a, int w) { weno3_z_body<M, PDE>(a, w); });
+  }
+  grid.sync();
+  run(PH_PREDICT, [&](const HotArgs& a, int w) { predict_body<D, M, PDE, 1>(a, w); });
+  if (lb.with_flux) {
+    grid.sync();
+    run(PH_FLUX, [&](const HotArgs& a, int w) { flux_update_body<D, M, PDE, 1, FL>(a, w, fs); });
+  }
 }
 
 template <int D, int M, int PDE>

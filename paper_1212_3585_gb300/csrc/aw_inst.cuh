@@ -109,7 +109,7 @@ struct Launch {
     }
     return 1;
   }
-  // the face flux kernels of one numerical flux (FL: 0 Rusanov, 1 Osher-Solomon, Euler only)
+  // the face flux kernels of one numerical flux (FL: 0 Rusanov, 1 Osher-Solomon; Euler and MHD-GLM)
   template <int FL>
   static int flux_fl(const HotArgs& a, cudaStream_t st) {
     int blocks = flux_ctas_of<CF>(a);
@@ -126,7 +126,7 @@ struct Launch {
     return 1;
   }
   static int flux(const HotArgs& a, cudaStream_t st) {
-    if constexpr (PDE == PDE_EULER) {
+    if constexpr (PDE == PDE_EULER || PDE == PDE_MHD) {
       if (a.flux == 1) return flux_fl<1>(a, st);
     }
     return flux_fl<0>(a, st);
@@ -155,7 +155,7 @@ struct Launch {
     return 1;
   }
   static int flux_update(const HotArgs& a, cudaStream_t st) {
-    if constexpr (PDE == PDE_EULER) {
+    if constexpr (PDE == PDE_EULER || PDE == PDE_MHD) {
       if (a.flux == 1) return flux_update_fl<1>(a, st);
     }
     return flux_update_fl<0>(a, st);
@@ -268,7 +268,7 @@ struct Launch {
   }
   // every member of a batch has the same numerical flux
   static int flux_b(HotBatch& b, cudaStream_t st) {
-    if constexpr (PDE == PDE_EULER) {
+    if constexpr (PDE == PDE_EULER || PDE == PDE_MHD) {
       if (b.n > 0 && b.a[0].flux == 1) return flux_b_fl<1>(b, st);
     }
     return flux_b_fl<0>(b, st);
@@ -284,7 +284,7 @@ struct Launch {
     return 1;
   }
   static int flux_update_b(HotBatch& b, cudaStream_t st) {
-    if constexpr (PDE == PDE_EULER) {
+    if constexpr (PDE == PDE_EULER || PDE == PDE_MHD) {
       if (b.n > 0 && b.a[0].flux == 1) return flux_update_b_fl<1>(b, st);
     }
     return flux_update_b_fl<0>(b, st);
@@ -302,6 +302,75 @@ struct Launch {
     return 1;
   }
 
+  // The persistent level kernel (k_level_batch) of one level and sub-step of a batch: the work of
+  // every phase per member, then one cooperative launch with as many CTAs as the GPU holds at
+  // once (at most the largest phase's work).  Available where the predictor and the face flux
+  // share their CTA shape.
+  static constexpr bool kLevelKernel = PredCfg<D, M, PDE>::THREADS == FluxCfg<D, M, PDE>::THREADS;
+  template <int FL>
+  static int level_b_fl(HotBatch& b, int with_flux, cudaStream_t st) {
+    constexpr int T = PredCfg<D, M, PDE>::THREADS, N = M + 1;
+    constexpr int SMEM0 = PredCfg<D, M, PDE>::SMEM > FluxCfg<D, M, PDE>::SMEM ? PredCfg<D, M, PDE>::SMEM
+                                                                                : FluxCfg<D, M, PDE>::SMEM;
+    constexpr int SMEMW = (D == 2) ? WenoCfg<D, M, PDE, 8>::SMEM : WenoCfg<D, M, PDE, 4>::SMEM;
+    constexpr int SMEM = SMEM0 > SMEMW ? SMEM0 : SMEMW;
+    static LevelBatch lb;   // the 21 KB parameter block, built on the host (one batch at a time per process)
+    static std::mutex mu;
+    std::lock_guard<std::mutex> lk(mu);
+    lb.b = b;
+    lb.with_flux = with_flux;
+    auto cdiv = [](long long x, long long y) { return (int)((x + y - 1) / y); };
+    int most = 0;
+    for (int p = 0; p < NPHASE; p++) {
+      int tot = 0;
+      for (int m = 0; m < b.n; m++) {
+        const HotArgs& a = b.a[m];
+        const bool passes = has_passes(a);
+        int w = 0;
+        switch (p) {
+          case PH_PROJECT: w = a.level >= 1 ? cdiv((long long)a.nv * V, T) : 0; break;
+          case PH_WENO4: w = (!passes && (D == 3 || a.ts != 8)) ? weno_ctas(a) : 0; break;
+          case PH_WENO8: w = (!passes && D == 2 && a.ts == 8) ? weno_ctas(a) : 0; break;
+          case PH_WENO_X: w = passes ? cdiv((long long)a.nxs * V, T) : 0; break;
+          case PH_WENO_Y: w = passes ? cdiv((D == 2 ? (long long)a.na : (long long)a.nys) * N * V, T) : 0; break;
+          case PH_WENO_Z: w = (passes && D == 3) ? cdiv((long long)a.na * N * N * V, T) : 0; break;
+          case PH_PREDICT: w = predict_ctas(a); break;
+          case PH_FLUX: w = with_flux ? flux_ctas(a) : 0; break;
+        }
+        lb.start[p][m] = tot;
+        tot += w;
+      }
+      lb.start[p][b.n] = tot;
+      most = std::max(most, tot);
+    }
+    if (!most) return 0;
+    auto kernel = k_level_batch<D, M, PDE, FL>;
+    static std::once_flag init;
+    static int per_sm = 0;
+    std::call_once(init, [&] {
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, T, SMEM) != cudaSuccess) per_sm = 0;
+    });
+    if (per_sm < 1) return -1;
+    const int grid = std::min(most, per_sm * sm_count());
+    void* args[] = {(void*)&lb};
+    if (cudaLaunchCooperativeKernel((const void*)kernel, dim3(grid), dim3(T), args, SMEM, st) != cudaSuccess) {
+      cudaGetLastError();   // a launch that could not start leaves no sticky error; the caller falls back
+      return -1;
+    }
+    return 1;
+  }
+  static int level_b(HotBatch& b, int with_flux, cudaStream_t st) {
+    if constexpr (!kLevelKernel) {
+      return -1;
+    } else {
+      if constexpr (PDE == PDE_EULER || PDE == PDE_MHD) {
+        if (b.n > 0 && b.a[0].flux == 1) return level_b_fl<1>(b, with_flux, st);
+      }
+      return level_b_fl<0>(b, with_flux, st);
+    }
+  }
+
   static HotOps ops() {
     HotOps o;
     o.D = D; o.M = M; o.PDE = PDE; o.V = V;
@@ -311,6 +380,7 @@ struct Launch {
     o.weno_b = &weno_b; o.predict_b = &predict_b; o.flux_b = &flux_b; o.update_b = &update_b;
     o.flux_update_b = &flux_update_b;
     o.project_b = &project_b;
+    o.level_b = kLevelKernel ? &level_b : nullptr;
     return o;
   }
 };

@@ -20,6 +20,7 @@ static std::atomic<long long> g_pass_min_cells{4096}, g_tile8_min_cells{20000};
 static std::atomic<int> g_small_ctas_per_sm{2};
 static std::atomic<int> g_fuse_flux_update{1};
 static std::atomic<int> g_autotune{1};
+static std::atomic<int> g_persistent{0};
 
 LaunchParams launch_params() {
   LaunchParams p;
@@ -28,6 +29,7 @@ LaunchParams launch_params() {
   p.small_ctas_per_sm = g_small_ctas_per_sm.load();
   p.fuse_flux_update = g_fuse_flux_update.load();
   p.autotune = g_autotune.load();
+  p.persistent = g_persistent.load();
   return p;
 }
 
@@ -37,6 +39,7 @@ void set_launch_params(const LaunchParams& p) {
   g_small_ctas_per_sm.store(p.small_ctas_per_sm);
   g_fuse_flux_update.store(p.fuse_flux_update);
   g_autotune.store(p.autotune);
+  g_persistent.store(p.persistent);
 }
 
 bool get_ops(int D, int M, int PDE, HotOps* out) {

@@ -29,6 +29,11 @@ struct HotOps {
   int (*flux_b)(HotBatch&, cudaStream_t);
   int (*update_b)(HotBatch&, cudaStream_t);
   int (*flux_update_b)(HotBatch&, cudaStream_t);
+  // the persistent level kernel of a batch (k_level_batch): projection, WENO, predictor and (with
+  // with_flux) the fused face flux and update in one cooperative launch; -1 when it cannot be
+  // launched (the separate launches then run), NULL for configurations where the predictor and
+  // the face flux differ in CTA shape
+  int (*level_b)(HotBatch&, int with_flux, cudaStream_t);
   int (*project_b)(HotBatch&, cudaStream_t);
 };
 
@@ -38,14 +43,16 @@ bool get_ops(int D, int M, int PDE, HotOps* out);
 // launch-shape rules (aw_set_launch_params): WENO by passes from pass_min_cells cells per level,
 // 2D WENO tiles of 8x8 from tile8_min_cells, quarter-size predictor/flux CTAs when the full-size
 // ones give fewer than small_ctas_per_sm CTAs per SM, the face flux and the update fused into one
-// launch (fuse_flux_update != 0) or two, and the autotuner of the predictor's and the face flux's
-// CTA sizes (autotune != 0; it replaces the small_ctas_per_sm rule where it has decided).
+// launch (fuse_flux_update != 0) or two, the autotuner of the predictor's and the face flux's CTA
+// sizes (autotune != 0; it replaces the small_ctas_per_sm rule where it has decided), and the
+// persistent level kernel of batches (persistent != 0).
 // Process-wide; the results never depend on them, only the speed.
 struct LaunchParams {
   long long pass_min_cells, tile8_min_cells;
   int small_ctas_per_sm;
   int fuse_flux_update;
   int autotune;
+  int persistent;
 };
 LaunchParams launch_params();
 void set_launch_params(const LaunchParams& p);

@@ -22,6 +22,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <tuple>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -56,6 +57,9 @@ struct Request {
 struct aw_server {
   int device = 0;
   int64_t budget = 0, in_use = 0, peak_in_use = 0, requeues = 0;
+  // per (dim, pde, M, lmax, r): the largest share of its finest level a run of that kind has held
+  // per-active arrays for, learned from the runs' device bytes (first reservations use it)
+  std::map<std::tuple<int, int, int, int, int>, double> active_share;
   int nworkers = 1;
   int max_batch = 1;
   std::mutex mu;
@@ -74,18 +78,18 @@ struct aw_server {
 // and staging buffers
 static const int64_t kAllowance = (int64_t)64 << 20;
 
-// Device bytes one solve of `c` is first reserved: the dense per-level grids (exact, with the row
-// marks and slot maps of the WENO by passes) plus per-active arrays for `active_frac` of the finest
-// level's cells (a quarter for the first reservation: the AMR meshes of these workloads mostly stay
-// below that; the WENO sweep buffers counted at two rows per active cell) and the allowance.
-static int64_t footprint_bytes(const aw_config& c, double active_frac = 0.25) {
+// Device bytes of the dense per-level grids of `c` (exact, with the row marks and slot maps of the
+// WENO by passes), of per-active arrays per active cell (the WENO sweep buffers counted at two rows
+// per active cell), and the finest level's cell count.
+static void footprint_parts(const aw_config& c, int64_t* dense, int64_t* per_active, int64_t* finest_cells,
+                            int64_t* all_cells) {
   int V = aw::nvars(c.dim, c.pde), N = c.M + 1;
   int64_t nsp = 1;
   for (int a = 0; a < c.dim; a++) nsp *= N;
   int64_t nst = nsp * N;
   int64_t dense_per_cell = 8 * V + 4 + 8 + 4 * 5 + 5 * (c.dim == 3 ? 2 : 1);
   int64_t sweeps = 2 * 8 * V * N * (c.dim == 3 ? 1 + N : 1);
-  int64_t active_per_cell = 8 * (V * nsp + V * nst + 4 * c.dim * V) + sweeps;
+  *per_active = 8 * (V * nsp + V * nst + 4 * c.dim * V) + sweeps;
   int64_t total = 0, finest = 0, all = 0, rr = 1;
   int r = c.lmax > 0 ? c.refine_factor : 1;
   for (int l = 0; l <= c.lmax; l++) {
@@ -95,13 +99,50 @@ static int64_t footprint_bytes(const aw_config& c, double active_frac = 0.25) {
     all += n;
     rr *= r;
   }
+  *dense = total;
+  *finest_cells = finest;
+  *all_cells = all;
+}
+
+// Device bytes one solve of `c` is reserved with per-active arrays for `active_frac` of the finest
+// level's cells (a quarter for a first reservation, unless the loop has learned more for this
+// kind of run) plus the dense grids and the allowance.
+static int64_t footprint_bytes(const aw_config& c, double active_frac = 0.25) {
+  int64_t dense, per_active, finest, all;
+  footprint_parts(c, &dense, &per_active, &finest, &all);
   if (active_frac > 1.0)   // every cell of every level active, with the arrays' growth headroom
-    return total + (int64_t)(1.5 * (double)all * (double)active_per_cell) + kAllowance;
-  return total + (int64_t)(active_frac * (double)finest) * active_per_cell + kAllowance;
+    return dense + (int64_t)(1.5 * (double)all * (double)per_active) + kAllowance;
+  return dense + (int64_t)(active_frac * (double)finest) * per_active + kAllowance;
 }
 
 // the bound on any reservation of `c`: every cell of every level active
 static int64_t footprint_max(const aw_config& c) { return footprint_bytes(c, 2.0); }
+
+static std::tuple<int, int, int, int, int> run_kind(const aw_config& c) {
+  return std::make_tuple(c.dim, c.pde, c.M, c.lmax, c.refine_factor);
+}
+
+// A first reservation: per-active arrays for a quarter of the finest level, or for 1.25 times the
+// largest share of it that runs of the same kind held so far, at most footprint_max.
+static int64_t first_reservation(const aw_server* S, const aw_config& c) {
+  double share = 0.25;
+  auto it = S->active_share.find(run_kind(c));
+  if (it != S->active_share.end()) share = std::max(share, 1.25 * it->second);
+  if (share >= 1.0) return footprint_max(c);
+  return std::min(footprint_bytes(c, share), footprint_max(c));
+}
+
+// what a finished or refused run of R tells about its kind: the share of the finest level its
+// per-active arrays (and everything else above the dense grids) came to
+static void learn_share(aw_server* S, const Request& R) {
+  int64_t dense, per_active, finest, all;
+  footprint_parts(R.cfg, &dense, &per_active, &finest, &all);
+  const int64_t held = std::max(R.peak_bytes, R.refused_bytes) - dense;
+  if (held <= 0 || finest <= 0 || per_active <= 0) return;
+  const double share = (double)held / ((double)finest * (double)per_active);
+  double& s = S->active_share[run_kind(R.cfg)];
+  s = std::max(s, share);
+}
 
 // After a run that the solver's memory limit stopped (AW_ELIMIT): the next reservation, at least
 // the bytes it was refused with half again as headroom and at least twice the old one, at most
@@ -220,7 +261,9 @@ static void worker_main(aw_server* S) {
       pick = -1;
       if (!S->queue.empty()) {
         int64_t id = S->queue.front();
-        if (S->in_use + S->req[id].footprint <= S->budget) pick = id;
+        Request& Q = S->req[id];
+        if (Q.requeues == 0) Q.footprint = std::min(first_reservation(S, Q.cfg), S->budget);
+        if (S->in_use + Q.footprint <= S->budget) pick = id;
       }
       return pick >= 0;
     });
@@ -231,6 +274,7 @@ static void worker_main(aw_server* S) {
     // batching: compatible queued requests, in arrival order, while the budget allows
     for (auto it = S->queue.begin(); it != S->queue.end() && (int)G.size() < S->max_batch;) {
       Request& Q = S->req[*it];
+      if (Q.requeues == 0) Q.footprint = std::min(first_reservation(S, Q.cfg), S->budget);
       if (batchable(*G[0], Q) && S->in_use + need + Q.footprint <= S->budget) {
         G.push_back(&Q);
         need += Q.footprint;
@@ -255,6 +299,7 @@ static void worker_main(aw_server* S) {
     std::vector<int64_t> again;   // outgrown runs, back to the head of the queue in arrival order
     for (Request* R : G) {
       R->t_done = t1;
+      learn_share(S, *R);
       if (R->rc == AW_ELIMIT) {
         const int64_t next = next_reservation(S, *R);
         if (next > 0) {

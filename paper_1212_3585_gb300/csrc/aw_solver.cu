@@ -1620,8 +1620,6 @@ int aw_create(const aw_config* cfg, uintptr_t stream, aw_solver** out) {
   }
   if (!(c.cfl > 0.0)) AW_FAIL(AW_EINVAL, "cfl must be positive");
   if (c.flux != AW_FLUX_RUSANOV && c.flux != AW_FLUX_OSHER) AW_FAIL(AW_EINVAL, "unknown numerical flux %d", c.flux);
-  if (c.flux == AW_FLUX_OSHER && c.pde == AW_PDE_MHD_GLM)
-    AW_FAIL(AW_EINVAL, "the Osher flux is available for the Euler equations and linear advection");
   aw_solver* s = new aw_solver();
   s->cfg = c;
   s->D = c.dim;
@@ -1917,13 +1915,23 @@ static int advance_batch(aw_solver* const* S, int n, const bool* live, int l, in
   if (b.n == 0) return AW_OK;
   const HotOps& ops = S[idx[0]]->ops;
   const int r = S[idx[0]]->r;
-  if (l >= 1) *launches += ops.project_b(b, st);
-  *launches += ops.weno_b(b, st);
-  *launches += ops.predict_b(b, st);
+  // the persistent level kernel: projection, WENO and predictor of every member in one launch, and
+  // the fused face flux and update too when no member has a finer level to step in between
+  const LaunchParams lp = launch_params();
+  const int lk = (ops.level_b && lp.persistent && lp.fuse_flux_update) ? ops.level_b(b, deeper ? 0 : 1, st) : -1;
+  if (lk >= 0) {
+    *launches += lk;
+  } else {
+    if (l >= 1) *launches += ops.project_b(b, st);
+    *launches += ops.weno_b(b, st);
+    *launches += ops.predict_b(b, st);
+  }
   CK(cudaGetLastError());
   if (deeper)
     for (int k = 0; k < r; k++) TRY(advance_batch(S, n, live, l + 1, k, st, launches));
-  if (launch_params().fuse_flux_update) {
+  if (lk >= 0 && !deeper) {
+    // done in the persistent kernel
+  } else if (lp.fuse_flux_update) {
     *launches += ops.flux_update_b(b, st);
   } else {
     *launches += ops.flux_b(b, st);
@@ -2357,13 +2365,15 @@ int aw_get_launch_params(aw_launch_params* out) {
   out->small_ctas_per_sm = p.small_ctas_per_sm;
   out->fuse_flux_update = p.fuse_flux_update;
   out->autotune = p.autotune;
+  out->persistent = p.persistent;
   return AW_OK;
 }
 
 int aw_set_launch_params(const aw_launch_params* in) {
   if (!in) AW_FAIL(AW_EINVAL, "null argument");
   if (in->pass_min_cells < 0 || in->tile8_min_cells < 0 || in->small_ctas_per_sm < 0 || in->small_ctas_per_sm > 64 ||
-      (in->fuse_flux_update != 0 && in->fuse_flux_update != 1) || (in->autotune != 0 && in->autotune != 1))
+      (in->fuse_flux_update != 0 && in->fuse_flux_update != 1) || (in->autotune != 0 && in->autotune != 1) ||
+      (in->persistent != 0 && in->persistent != 1))
     AW_FAIL(AW_EINVAL, "launch parameters out of range");
   LaunchParams p;
   p.pass_min_cells = in->pass_min_cells;
@@ -2371,6 +2381,7 @@ int aw_set_launch_params(const aw_launch_params* in) {
   p.small_ctas_per_sm = in->small_ctas_per_sm;
   p.fuse_flux_update = in->fuse_flux_update;
   p.autotune = in->autotune;
+  p.persistent = in->persistent;
   set_launch_params(p);
   return AW_OK;
 }

@@ -41,7 +41,7 @@ BAD_CONFIGS = [
     (dict(cfl=0.0), "cfl"),
     (dict(cfl=float("nan")), "cfl"),
     (dict(flux=5), "unknown numerical flux"),
-    (dict(flux=pg.AW_FLUX_OSHER, pde=pg.AW_PDE_MHD_GLM), "Osher"),
+    (dict(flux=7), "numerical flux"),
     (dict(dim=3, M=3, n=(8, 8, 8)), "not compiled in"),
     (dict(dim=3, pde=pg.AW_PDE_MHD_GLM, n=(8, 8, 8)), "not compiled in"),
     (dict(dim=3, M=1, n=(8, 8, 8)), "not compiled in"),

@@ -167,3 +167,38 @@ def test_batch_other_configurations(kind):
         assert np.array_equal(m, m0) and np.array_equal(u, u0)
         assert st.cell_updates == st0.cell_updates
         s.close()
+
+
+@pytest.mark.parametrize("M", [3, 2])
+def test_persistent_level_kernel_equals_separate_launches(M):
+    """aw_set_launch_params.persistent: one cooperative launch per level and sub-step for the
+    projection, WENO and predictor of every member (with the fused face flux and update on a level
+    where no member has a finer one) gives bitwise the averages of the separate launches, with
+    fewer launches; members of different depths, WENO tiles and passes"""
+    t_end = 0.03
+    specs = member_specs(M)
+    specs.append((pg.make_config(dim=2, M=M, n=(70, 64, 1), lo=(-1, -1, 0), hi=(1, 1, 1), bc=pg.AW_BC_TRANSMISSIVE,
+                                 r=3, lmax=1, cfl=0.6), pg.AW_IC_EXPLOSION, EXPL))   # level 0 by passes
+    out, launches = {}, {}
+    saved = pg.get_launch_params()
+    try:
+        for persistent in (1, 0):
+            pg.set_launch_params(persistent=persistent)
+            sol = []
+            for cfg, ic, p in specs:
+                s = pg.Solver(cfg)
+                s.set_initial(ic, p, -1)
+                sol.append(s)
+            n0 = sum(s.kernel_launches() for s in sol)
+            _, rc = pg.advance_batch(sol, t_end)
+            assert rc == [0] * len(sol)
+            launches[persistent] = sum(s.kernel_launches() for s in sol) - n0
+            out[persistent] = [s.cells() for s in sol]
+            for s in sol:
+                s.close()
+    finally:
+        pg.set_launch_params(**saved)
+    for (m1, u1), (m0, u0) in zip(out[1], out[0]):
+        assert np.array_equal(m1, m0)
+        assert np.array_equal(u1, u0), f"differ by {np.max(np.abs(u1 - u0)):.3e}"
+    assert launches[1] < launches[0], launches

@@ -40,6 +40,10 @@ def cases():
                                                            lo=(0, 0, 0), hi=(2 * np.pi, 2 * np.pi, 1), bc=P,
                                                            gamma=5.0 / 3.0, r=3, lmax=1, cfl=0.6, c_h=2.0),
                                             pg.AW_IC_OT, [], 0.15),
+        "MHD-GLM Orszag-Tang Osher": (pg.make_config(dim=2, pde=pg.AW_PDE_MHD_GLM, M=2, n=(12, 12, 1), lo=(0, 0, 0),
+                                                     hi=(2 * np.pi, 2 * np.pi, 1), bc=P, gamma=5.0 / 3.0, r=3, lmax=1,
+                                                     cfl=0.6, c_h=2.0, flux=pg.AW_FLUX_OSHER),
+                                      pg.AW_IC_OT, [], 0.15),
         "linear advection M=1": (pg.make_config(dim=2, pde=pg.AW_PDE_LINADV, M=1, n=(19, 13, 1), bc=P, cfl=0.9),
                                  pg.AW_IC_FOURIER, aw_inputs.fourier_params(seed=5, dim=2, pde="linadv", nmodes=3),
                                  0.3),

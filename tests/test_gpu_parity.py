@@ -126,6 +126,26 @@ def test_mhd_orszag_tang_amr():
         p.step()
 
 
+@pytest.mark.parametrize("lmax", [0, 1])
+def test_mhd_osher_orszag_tang(lmax):
+    """Osher-Solomon flux for MHD-GLM (Eq. eqn.osher, Sec. 4.2): |A| of the 9 x 9 Jacobian along the
+    path, uniform and with AMR and local time stepping (the Orszag-Tang density is constant at
+    t = 0, so the indicator refines nothing yet: random refinement flags make the coarse/fine
+    faces)"""
+    p = Pair(dim=2, pde="mhd", M=3, n=(12, 12, 1), lo=(0, 0, 0), hi=(2 * np.pi, 2 * np.pi, 1), bc="periodic",
+             r=3, lmax=lmax, gamma=5 / 3, c_h=2.0, flux=1)
+    p.init("ot", [], passes=0)
+    if lmax:
+        meta, _ = p.o.cells()
+        flags = aw_inputs.random_flags(np.random.default_rng(11), meta, p_refine=0.3, p_coarsen=0.0)
+        p.o.regrid_with_flags(flags, init_mode=1)
+        p.g.regrid_with_flags(flags, init_mode=1)
+        p.check_cells(tol=1e-12)
+        assert p.g.counts()[3][1] > 0
+    for _ in range(2):
+        p.step(regrid=False)
+
+
 def test_3d_explosion_amr():
     p = Pair(dim=3, M=2, n=(6, 6, 6), lo=(-1, -1, -1), hi=(1, 1, 1), bc="transmissive", r=3, lmax=1, cfl=0.6)
     p.init("explosion", EXPL)
