@@ -200,10 +200,19 @@ int aw_advance_graph(aw_solver* s, double t_end, int32_t chunk, aw_stats* stats)
  * which also runs the fused face flux and update on a level with no finer level, with grid-wide
  * barriers between the phases (2D configurations, where the predictor and the face flux share
  * their CTA shape, with fuse_flux_update = 1); 0 (default: measured faster) the separate
- * launches.
+ * launches; and graph_steps: 1 captures the launches of every level-0 step of aw_step,
+ * aw_advance_to and aw_advance_batch (all levels and sub-steps) into a CUDA graph on a stream
+ * of the solver's own (of the first member's, for a batch), ordered after the caller's stream,
+ * and launches it: the executable graph of the previous step is updated in place when the new
+ * step has the same launch sequence (the sizes and arguments may differ), else built anew; a
+ * step whose launch arguments are those of the previous graph (the regrid left every level's
+ * lists and sizes as they were) launches that graph again without a capture, unless it holds
+ * timing events (aw_set_profiling, trials of the autotuner) (aw_graph_stats); the persistent
+ * level kernel is not used in a captured step; 0 (default) launches the kernels directly.
  * The averages are bitwise the same for every setting.  Process-wide.  The first two are fixed
  * per level when a solver is created, the others apply to every launch.  AW_EINVAL for negative
- * values, small_ctas_per_sm > 64, or fuse_flux_update, autotune or persistent not 0 or 1.
+ * values, small_ctas_per_sm > 64, or fuse_flux_update, autotune, persistent or graph_steps not
+ * 0 or 1.
  * bench.py --tune times the workload over these parameters. */
 typedef struct aw_launch_params {
   int64_t pass_min_cells;
@@ -212,6 +221,8 @@ typedef struct aw_launch_params {
   int32_t fuse_flux_update;
   int32_t autotune;
   int32_t persistent;
+  int32_t graph_steps;
+  int32_t reserved;        /* set to 0 */
 } aw_launch_params;
 int aw_get_launch_params(aw_launch_params* out);
 int aw_set_launch_params(const aw_launch_params* in);
@@ -224,8 +235,10 @@ int aw_set_launch_params(const aw_launch_params* in);
  * the least device time per active cell (the least over its timings) is used for every later
  * launch of that class, by every solver.  A new class larger than a class that kept full-size
  * CTAs, or smaller than one that kept quarter-size CTAs, takes that decision without trials
- * (inherited = 1).  Single-solver steps only: the batched and graph paths use the rules.  aw_get_tuning copies up to `cap` entries (in key order) into `out` and sets *n to the
- * number of entries; aw_reset_tuning forgets them all.  AW_EINVAL for a null n or cap < 0. */
+ * (inherited = 1).  Single-solver steps only (also when replayed from graphs, graph_steps): the
+ * batched path and aw_advance_graph use the rules.  aw_get_tuning copies up to `cap` entries (in
+ * key order) into `out` and sets *n to the number of entries; aw_reset_tuning forgets them all.
+ * AW_EINVAL for a null n or cap < 0. */
 #define AW_TUNE_PREDICTOR 0
 #define AW_TUNE_FLUX 1
 #define AW_TUNE_TRIALS 2
@@ -290,6 +303,13 @@ int aw_set_memory_limit(aw_solver* s, int64_t bytes);
  * since creation, and refused: the live total that the largest refused allocation would have
  * reached (0 if none).  NULL outputs are skipped. */
 int aw_get_memory(const aw_solver* s, int64_t* live, int64_t* peak, int64_t* refused);
+
+/* Graph replay of level-0 steps (aw_launch_params.graph_steps; no counterpart in the paper): of
+ * the steps of this solver (as a solver, or as the first member of a batch) that ran from a
+ * graph, how many launched the previous graph again unchanged (the same launch arguments at every
+ * level: the mesh did not change in the regrid before), how many were captured and updated the
+ * previous executable graph in place, and how many built one anew.  NULL outputs are skipped. */
+int aw_graph_stats(const aw_solver* s, int64_t* reuses, int64_t* updates, int64_t* instantiations);
 
 /* Per-kernel timing: when on, every launch of the hot kernels is bracketed by CUDA events on the
  * solver's stream.  aw_kernel_times() synchronises, returns the accumulated device time (ms) and

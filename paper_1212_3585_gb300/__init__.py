@@ -184,6 +184,12 @@ class Solver:
         _lib.check(self.L.aw_get_memory(self.h, C.byref(v[0]), C.byref(v[1]), C.byref(v[2])))
         return tuple(x.value for x in v)
 
+    def graph_stats(self):
+        """aw_graph_stats: (reuses, in-place updates, instantiations) of this solver's step graphs"""
+        v = [C.c_int64(), C.c_int64(), C.c_int64()]
+        _lib.check(self.L.aw_graph_stats(self.h, C.byref(v[0]), C.byref(v[1]), C.byref(v[2])))
+        return tuple(x.value for x in v)
+
     def kernel_launches(self):
         return self.L.aw_kernel_launches(self.h)
 
@@ -194,11 +200,11 @@ def get_launch_params() -> dict:
     _lib.check(_lib.load().aw_get_launch_params(C.byref(p)))
     return {"pass_min_cells": p.pass_min_cells, "tile8_min_cells": p.tile8_min_cells,
             "small_ctas_per_sm": p.small_ctas_per_sm, "fuse_flux_update": p.fuse_flux_update,
-            "autotune": p.autotune, "persistent": p.persistent}
+            "autotune": p.autotune, "persistent": p.persistent, "graph_steps": p.graph_steps}
 
 
 def set_launch_params(pass_min_cells=None, tile8_min_cells=None, small_ctas_per_sm=None, fuse_flux_update=None,
-                      autotune=None, persistent=None):
+                      autotune=None, persistent=None, graph_steps=None):
     """aw_set_launch_params: change some of the launch-shape rules (speed only, never results)."""
     cur = get_launch_params()
     p = _lib.AwLaunchParams()
@@ -208,6 +214,7 @@ def set_launch_params(pass_min_cells=None, tile8_min_cells=None, small_ctas_per_
     p.fuse_flux_update = cur["fuse_flux_update"] if fuse_flux_update is None else int(fuse_flux_update)
     p.autotune = cur["autotune"] if autotune is None else int(autotune)
     p.persistent = cur["persistent"] if persistent is None else int(persistent)
+    p.graph_steps = cur["graph_steps"] if graph_steps is None else int(graph_steps)
     _lib.check(_lib.load().aw_set_launch_params(C.byref(p)))
 
 

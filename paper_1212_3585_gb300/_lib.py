@@ -55,7 +55,8 @@ class AwSrvSummary(C.Structure):
 
 class AwLaunchParams(C.Structure):
     _fields_ = [("pass_min_cells", C.c_int64), ("tile8_min_cells", C.c_int64), ("small_ctas_per_sm", C.c_int32),
-                ("fuse_flux_update", C.c_int32), ("autotune", C.c_int32), ("persistent", C.c_int32)]
+                ("fuse_flux_update", C.c_int32), ("autotune", C.c_int32), ("persistent", C.c_int32),
+                ("graph_steps", C.c_int32), ("reserved", C.c_int32)]
 
 
 class AwTuneEntry(C.Structure):
@@ -101,6 +102,7 @@ SIGNATURES = {
     "aw_reset": (C.c_int, [_vp]),
     "aw_set_memory_limit": (C.c_int, [_vp, C.c_int64]),
     "aw_get_memory": (C.c_int, [_vp, _i64p, _i64p, _i64p]),
+    "aw_graph_stats": (C.c_int, [_vp, _i64p, _i64p, _i64p]),
     "aw_set_profiling": (C.c_int, [_vp, C.c_int32]),
     "aw_kernel_times": (C.c_int, [_vp, _dp, _i64p]),
     "aw_srv_create": (C.c_int, [C.c_int64, C.c_int32, C.POINTER(_vp)]),

@@ -21,6 +21,7 @@ static std::atomic<int> g_small_ctas_per_sm{2};
 static std::atomic<int> g_fuse_flux_update{1};
 static std::atomic<int> g_autotune{1};
 static std::atomic<int> g_persistent{0};
+static std::atomic<int> g_graph_steps{0};
 
 LaunchParams launch_params() {
   LaunchParams p;
@@ -30,6 +31,7 @@ LaunchParams launch_params() {
   p.fuse_flux_update = g_fuse_flux_update.load();
   p.autotune = g_autotune.load();
   p.persistent = g_persistent.load();
+  p.graph_steps = g_graph_steps.load();
   return p;
 }
 
@@ -40,6 +42,7 @@ void set_launch_params(const LaunchParams& p) {
   g_fuse_flux_update.store(p.fuse_flux_update);
   g_autotune.store(p.autotune);
   g_persistent.store(p.persistent);
+  g_graph_steps.store(p.graph_steps);
 }
 
 bool get_ops(int D, int M, int PDE, HotOps* out) {

@@ -44,8 +44,9 @@ bool get_ops(int D, int M, int PDE, HotOps* out);
 // 2D WENO tiles of 8x8 from tile8_min_cells, quarter-size predictor/flux CTAs when the full-size
 // ones give fewer than small_ctas_per_sm CTAs per SM, the face flux and the update fused into one
 // launch (fuse_flux_update != 0) or two, the autotuner of the predictor's and the face flux's CTA
-// sizes (autotune != 0; it replaces the small_ctas_per_sm rule where it has decided), and the
-// persistent level kernel of batches (persistent != 0).
+// sizes (autotune != 0; it replaces the small_ctas_per_sm rule where it has decided), the
+// persistent level kernel of batches (persistent != 0), and level-0 steps of AMR solves and of
+// batches replayed from captured CUDA graphs (graph_steps != 0).
 // Process-wide; the results never depend on them, only the speed.
 struct LaunchParams {
   long long pass_min_cells, tile8_min_cells;
@@ -53,6 +54,7 @@ struct LaunchParams {
   int fuse_flux_update;
   int autotune;
   int persistent;
+  int graph_steps;
 };
 LaunchParams launch_params();
 void set_launch_params(const LaunchParams& p);

@@ -15,6 +15,7 @@
 // start and finish.  The two small pinned host buffers of a solver come from a process-wide free
 // list for the same reason.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -136,6 +137,18 @@ struct GState {
   int stop;
 };
 
+// An executable graph of one level-0 step (graph_steps) and what it was captured from: the
+// launch arguments of every level (a step with the same arguments launches the same kernels with
+// the same parameters: the time steps and the mesh live in device memory), whether it can run
+// again as it is (it holds no timing events: no profiling, no trial of the autotuner), and the
+// kernel launches it holds.
+struct StepGraph {
+  cudaGraphExec_t exec = nullptr;
+  std::vector<char> sig;
+  bool reusable = false;
+  int64_t launches = 0;
+};
+
 struct aw_solver {
   aw_config cfg;
   int D, V, N, M, r, lmax, NSP, NST, P;
@@ -156,6 +169,14 @@ struct aw_solver {
   HotArgs gargs;
   int gchunk = 0;
   bool gfused = false;
+  // level-0 steps of AMR solves and batches replayed from CUDA graphs (aw_launch_params.graph_steps):
+  // the graphs of the last single-solver and batched step (captured on gstream), an event that
+  // orders the capture stream after the caller's stream and back, flags set while a step is
+  // being captured and when the capture took timing events, and the counts of aw_graph_stats
+  StepGraph sgraph, bgraph;
+  cudaEvent_t gev = nullptr;
+  bool capturing = false, captured_events = false;
+  int64_t graph_reuses = 0, graph_updates = 0, graph_instantiations = 0;
   int* d_err = nullptr;
   int* d_cnt = nullptr;
   int* h_cnt = nullptr;
@@ -230,14 +251,25 @@ static cudaEvent_t take_event(aw_solver* s) {
   return e;
 }
 
+// record a timing event on the solver's stream; inside a captured step as an event-record node,
+// which records when the graph runs
+static void record(aw_solver* s, cudaEvent_t e) {
+  if (s->capturing) {
+    cudaEventRecordWithFlags(e, s->stream, cudaEventRecordExternal);
+    s->captured_events = true;
+  } else {
+    cudaEventRecord(e, s->stream);
+  }
+}
+
 // run one hot launcher, bracketed by events when profiling
 template <class F>
 static int timed(aw_solver* s, int kind, F&& launch) {
   if (!s->prof) return launch();
   cudaEvent_t a = take_event(s), b = take_event(s);
-  cudaEventRecord(a, s->stream);
+  record(s, a);
   int n = launch();
-  cudaEventRecord(b, s->stream);
+  record(s, b);
   if (n > 0) s->ev_used.push_back({kind, {a, b}});
   else { s->ev_free.push_back(a); s->ev_free.push_back(b); }
   s->kind_n[kind] += n;
@@ -318,9 +350,9 @@ template <class F>
 static int tuned(aw_solver* s, int v, const int* key, long long na, F&& launch) {
   if (v < 0 || !(v & 2)) return launch();
   cudaEvent_t a = take_event(s), b = take_event(s);
-  cudaEventRecord(a, s->stream);
+  record(s, a);
   const int n = launch();
-  cudaEventRecord(b, s->stream);
+  record(s, b);
   if (n > 0) {
     aw_solver::TunePending p;
     for (int i = 0; i < 6; i++) p.key[i] = key[i];
@@ -1354,9 +1386,125 @@ static int step_finish(aw_solver* s, double dt0, aw_stats* st) {
   return AW_OK;
 }
 
+// The launch arguments of a level-0 step of solver s: per level, the hot kernels' arguments and
+// the averaging list (every pointer and size of the mesh; the time steps are read from device
+// memory).  The autotuner's decisions and the launch-shape rules are added by step_signature.
+static void put_solver_signature(const aw_solver* s, std::vector<char>* sig) {
+  auto put = [&](const void* p, size_t n) { sig->insert(sig->end(), (const char*)p, (const char*)p + n); };
+  put(&s, sizeof s);
+  for (int l = 0; l <= s->lmax; l++) {
+    const HotArgs a = make_args(s, l, 0);   // zero-filled, padding included
+    put(&a, sizeof a);
+    put(&s->lev[l].mlist, sizeof s->lev[l].mlist);
+    put(&s->lev[l].nm, sizeof s->lev[l].nm);
+  }
+}
+
+static std::atomic<int64_t> g_tune_epoch{0};   // advanced by aw_reset_tuning
+
+static void step_signature(aw_solver* const* S, int n, const bool* live, std::vector<char>* sig) {
+  sig->clear();
+  const LaunchParams lp = launch_params();
+  const int64_t v[] = {lp.pass_min_cells, lp.tile8_min_cells, lp.small_ctas_per_sm, lp.fuse_flux_update,
+                       lp.autotune, lp.persistent, g_tune_epoch.load()};
+  sig->insert(sig->end(), (const char*)v, (const char*)v + sizeof v);
+  for (int m = 0; m < n; m++) {
+    const char on = live ? (char)live[m] : 1;
+    sig->push_back(on);
+    if (on) put_solver_signature(S[m], sig);
+  }
+}
+
+// Run a level-0 step from a CUDA graph.  issue(stream) issues the step's launches on the given
+// stream, through solvers S[0..n-1], and adds their number to *launches.  The graph runs on S[0]'s
+// own stream gstream (the caller's stream may be one that cannot be captured, the legacy default
+// stream), ordered after the caller's stream `st` and joined back to it.  When the last graph of
+// this slot was captured from the same launch arguments (signature `sig`) and holds no timing
+// events, it is launched again as it is; otherwise the step is captured, with the members'
+// streams pointed at gstream meanwhile, and the executable graph is updated in place when the new
+// capture has its shape (the same kinds of nodes in the same order) or built anew.  Every launch,
+// memset and timing event is captured as it is issued, so the device does exactly what the
+// direct launches do.
+template <class F>
+static int graph_replay(aw_solver* const* S, int n, cudaStream_t st, StepGraph* g, const std::vector<char>& sig,
+                        int64_t* launches, F&& issue) {
+  aw_solver* s = S[0];
+  if (!s->gstream) CK(cudaStreamCreateWithFlags(&s->gstream, cudaStreamNonBlocking));
+  if (!s->gev) CK(cudaEventCreateWithFlags(&s->gev, cudaEventDisableTiming));
+  cudaStream_t gs = s->gstream;
+  CK(cudaEventRecord(s->gev, st));
+  CK(cudaStreamWaitEvent(gs, s->gev, 0));
+  if (g->exec && g->reusable && g->sig == sig) {
+    CK(cudaGraphLaunch(g->exec, gs));
+    *launches += g->launches;
+    s->graph_reuses++;
+  } else {
+    for (int m = 0; m < n; m++) {
+      S[m]->stream = gs;
+      S[m]->capturing = true;
+      S[m]->captured_events = false;
+    }
+    const int64_t before = *launches;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(gs, cudaStreamCaptureModeThreadLocal);
+    int rc = AW_OK;
+    if (e == cudaSuccess) {
+      rc = issue(gs);
+      e = cudaStreamEndCapture(gs, &graph);
+    }
+    bool events = false;
+    for (int m = 0; m < n; m++) {
+      S[m]->stream = st;
+      S[m]->capturing = false;
+      events = events || S[m]->captured_events;
+    }
+    if (rc != AW_OK || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      g->reusable = false;
+      if (rc != AW_OK) return rc;
+      AW_FAIL(AW_ECUDA, "step capture: %s", cudaGetErrorString(e));
+    }
+    if (g->exec) {
+      cudaGraphExecUpdateResultInfo info;
+      if (cudaGraphExecUpdate(g->exec, graph, &info) == cudaSuccess) {
+        s->graph_updates++;
+      } else {
+        cudaGetLastError();   // not a sticky error: the graph is built anew
+        cudaGraphExecDestroy(g->exec);
+        g->exec = nullptr;
+      }
+    }
+    if (!g->exec) {
+      e = cudaGraphInstantiate(&g->exec, graph, 0);
+      if (e != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        g->exec = nullptr;
+        g->reusable = false;
+        AW_FAIL(AW_ECUDA, "step graph instantiation: %s", cudaGetErrorString(e));
+      }
+      s->graph_instantiations++;
+    }
+    cudaGraphDestroy(graph);
+    g->sig = sig;
+    g->reusable = !events;
+    g->launches = *launches - before;
+    CK(cudaGraphLaunch(g->exec, gs));
+  }
+  CK(cudaEventRecord(s->gev, gs));
+  CK(cudaStreamWaitEvent(st, s->gev, 0));
+  return AW_OK;
+}
+
 static int step_dt(aw_solver* s, double dt0, aw_stats* st) {
   TRY(step_begin(s, dt0));
-  TRY(advance(s, 0, 0));
+  if (launch_params().graph_steps) {
+    std::vector<char> sig;
+    step_signature(&s, 1, nullptr, &sig);
+    TRY(graph_replay(&s, 1, s->stream, &s->sgraph, sig, &s->launches,
+                     [&](cudaStream_t) { return advance(s, 0, 0); }));
+  } else
+    TRY(advance(s, 0, 0));
   CK(cudaMemcpyAsync(s->h_cnt + NSLOT * MAXL, s->d_err, sizeof(int), cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
   return step_finish(s, dt0, st);
@@ -1508,6 +1656,9 @@ static void free_solver(aw_solver* s) {
     cudaStreamDestroy(s->gstream);
   }
   if (s->gexec) cudaGraphExecDestroy(s->gexec);
+  if (s->sgraph.exec) cudaGraphExecDestroy(s->sgraph.exec);
+  if (s->bgraph.exec) cudaGraphExecDestroy(s->bgraph.exec);
+  if (s->gev) cudaEventDestroy(s->gev);
   pinned_release(s->h_cnt);
   pinned_release(s->h_dtl);
   pinned_release(s->h_gs);
@@ -1771,6 +1922,14 @@ int aw_get_memory(const aw_solver* s, int64_t* live, int64_t* peak, int64_t* ref
   return AW_OK;
 }
 
+int aw_graph_stats(const aw_solver* s, int64_t* reuses, int64_t* updates, int64_t* instantiations) {
+  if (!s) AW_FAIL(AW_EINVAL, "null solver");
+  if (reuses) *reuses = s->graph_reuses;
+  if (updates) *updates = s->graph_updates;
+  if (instantiations) *instantiations = s->graph_instantiations;
+  return AW_OK;
+}
+
 int aw_set_profiling(aw_solver* s, int32_t on) {
   if (!s) AW_FAIL(AW_EINVAL, "null solver");
   s->prof = on ? 1 : 0;
@@ -1918,7 +2077,10 @@ static int advance_batch(aw_solver* const* S, int n, const bool* live, int l, in
   // the persistent level kernel: projection, WENO and predictor of every member in one launch, and
   // the fused face flux and update too when no member has a finer level to step in between
   const LaunchParams lp = launch_params();
-  const int lk = (ops.level_b && lp.persistent && lp.fuse_flux_update) ? ops.level_b(b, deeper ? 0 : 1, st) : -1;
+  const bool capturing = S[idx[0]]->capturing;
+  const int lk = (ops.level_b && lp.persistent && lp.fuse_flux_update && !capturing)
+                     ? ops.level_b(b, deeper ? 0 : 1, st)
+                     : -1;
   if (lk >= 0) {
     *launches += lk;
   } else {
@@ -1963,6 +2125,7 @@ static int batch_run(aw_solver* const* S, int n, double t_end, cudaStream_t st, 
   }
   double dt[MAXB];
   bool clip[MAXB];
+  std::vector<char> sig;
   for (;;) {
     int nlive = 0;
     for (int m = 0; m < n; m++) nlive += live[m];
@@ -1981,7 +2144,14 @@ static int batch_run(aw_solver* const* S, int n, double t_end, cudaStream_t st, 
     }
     // the step of every member, the hot kernels batched
     int64_t nl = 0;
-    int rc = advance_batch(S, n, live, 0, 0, st, &nl);
+    int rc;
+    if (launch_params().graph_steps) {
+      step_signature(S, n, live, &sig);
+      rc = graph_replay(S, n, st, &S[0]->bgraph, sig, &nl,
+                        [&](cudaStream_t gs) { return advance_batch(S, n, live, 0, 0, gs, &nl); });
+    } else {
+      rc = advance_batch(S, n, live, 0, 0, st, &nl);
+    }
     for (int m = 0; m < n; m++)
       if (live[m]) { S[m]->launches += nl; break; }
     TRY(rc);
@@ -2366,6 +2536,7 @@ int aw_get_launch_params(aw_launch_params* out) {
   out->fuse_flux_update = p.fuse_flux_update;
   out->autotune = p.autotune;
   out->persistent = p.persistent;
+  out->graph_steps = p.graph_steps;
   return AW_OK;
 }
 
@@ -2373,7 +2544,7 @@ int aw_set_launch_params(const aw_launch_params* in) {
   if (!in) AW_FAIL(AW_EINVAL, "null argument");
   if (in->pass_min_cells < 0 || in->tile8_min_cells < 0 || in->small_ctas_per_sm < 0 || in->small_ctas_per_sm > 64 ||
       (in->fuse_flux_update != 0 && in->fuse_flux_update != 1) || (in->autotune != 0 && in->autotune != 1) ||
-      (in->persistent != 0 && in->persistent != 1))
+      (in->persistent != 0 && in->persistent != 1) || (in->graph_steps != 0 && in->graph_steps != 1))
     AW_FAIL(AW_EINVAL, "launch parameters out of range");
   LaunchParams p;
   p.pass_min_cells = in->pass_min_cells;
@@ -2382,6 +2553,7 @@ int aw_set_launch_params(const aw_launch_params* in) {
   p.fuse_flux_update = in->fuse_flux_update;
   p.autotune = in->autotune;
   p.persistent = in->persistent;
+  p.graph_steps = in->graph_steps;
   set_launch_params(p);
   return AW_OK;
 }
@@ -2409,6 +2581,7 @@ int aw_get_tuning(aw_tune_entry* out, int32_t cap, int32_t* n) {
 int aw_reset_tuning(void) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune.clear();
+  g_tune_epoch++;
   return AW_OK;
 }
 

@@ -75,10 +75,11 @@ def test_launch_params_roundtrip_without_gpu():
     """the launch-shape rules are host state: read, changed, rejected when out of range, restored"""
     before = pg.get_launch_params()
     assert before == {"pass_min_cells": 4096, "tile8_min_cells": 20000, "small_ctas_per_sm": 2,
-                      "fuse_flux_update": 1, "autotune": 1, "persistent": 0}
-    pg.set_launch_params(small_ctas_per_sm=0, pass_min_cells=0, fuse_flux_update=0, autotune=0, persistent=0)
+                      "fuse_flux_update": 1, "autotune": 1, "persistent": 0, "graph_steps": 0}
+    pg.set_launch_params(small_ctas_per_sm=0, pass_min_cells=0, fuse_flux_update=0, autotune=0, persistent=1,
+                         graph_steps=1)
     assert pg.get_launch_params() == {"pass_min_cells": 0, "tile8_min_cells": 20000, "small_ctas_per_sm": 0,
-                                      "fuse_flux_update": 0, "autotune": 0, "persistent": 0}
+                                      "fuse_flux_update": 0, "autotune": 0, "persistent": 1, "graph_steps": 1}
     with pytest.raises(pg.AwError):
         pg.set_launch_params(small_ctas_per_sm=65)
     with pytest.raises(pg.AwError):
@@ -87,6 +88,8 @@ def test_launch_params_roundtrip_without_gpu():
         pg.set_launch_params(autotune=-1)
     with pytest.raises(pg.AwError):
         pg.set_launch_params(persistent=3)
+    with pytest.raises(pg.AwError):
+        pg.set_launch_params(graph_steps=2)
     pg.set_launch_params(**before)
     assert pg.get_launch_params() == before
 
