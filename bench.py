@@ -264,7 +264,7 @@ def run_serve(args):
         st = srv.stats()
         out = {"solves_per_s": st.solves_per_s, "p50_ms": st.p50_ms, "p99_ms": st.p99_ms,
                "cell_updates_per_s": st.cell_updates_per_s, "failed": int(st.failed),
-               "failure_rate": int(st.failed) / len(reqs), "requeues": int(st.requeues),
+               "failure_rate": int(st.failed) / len(reqs), "requeues": int(st.requeues), "grows": int(st.grows),
                "peak_reserved_gb": st.peak_reserved_bytes / 2 ** 30}
         srv.close()
         return out

@@ -174,6 +174,18 @@ int aw_advance_to(aw_solver* s, double t_end, aw_stats* stats);
 int aw_advance_batch(aw_solver* const* solvers, int32_t n, double t_end, uintptr_t stream, aw_stats* stats,
                      int32_t* rc);
 
+/* One lockstep level-0 step of a batch (no counterpart in the paper; the request loop's
+ * continuous batching is built on it): every member m with t < t_end[m] takes the one level-0
+ * step that aw_step(solvers[m], t_end[m]) takes (its CFL dt clipped at its own end time, all
+ * levels and sub-steps, its regrid), with the hot kernels batched as in aw_advance_batch; members
+ * already at their end time are left as they are.  So members may have different end times, and
+ * the set of members may change from one call to the next: the step of each member is exactly
+ * its own.  t_end: n end times (AW_EINVAL for NULL or NaN).  stats receive each member's
+ * statistics of this step, rc each member's status; the return value, the members' requirements
+ * and the stream as in aw_advance_batch. */
+int aw_step_batch(aw_solver* const* solvers, int32_t n, const double* t_end, uintptr_t stream, aw_stats* stats,
+                  int32_t* rc);
+
 /* Latency path for a uniform mesh (lmax = 0; no counterpart in the paper): advances to t_end as
  * aw_advance_to does, with the CFL time step reduced, clipped at t_end and turned into the level
  * time steps on the device, so that `chunk` (1..256) level-0 steps run between two host
@@ -347,6 +359,7 @@ typedef struct aw_srv_info {
   double queue_ms, run_ms, total_ms;   /* submit -> start of the last run, its start -> done, submit -> done */
   int64_t requeues;                    /* runs restarted because the solve outgrew its reservation */
   int64_t peak_bytes;                  /* the solver's own peak device bytes in the last run */
+  int64_t grows;                       /* times its reservation grew in place while it ran */
 } aw_srv_info;
 
 typedef struct aw_srv_summary {
@@ -356,6 +369,7 @@ typedef struct aw_srv_summary {
   int64_t requeues;                    /* restarts of outgrown runs, all requests */
   int64_t budget_bytes;                /* the loop's device-memory budget */
   int64_t peak_reserved_bytes;         /* the most bytes the admitted runs ever held reserved together */
+  int64_t grows;                       /* in-place growths of running requests' reservations */
 } aw_srv_summary;
 
 /* Start `max_concurrent` worker threads on the current device with a device-memory budget.
@@ -364,12 +378,15 @@ typedef struct aw_srv_summary {
  * limit (aw_set_memory_limit, less 64 MiB for the CUDA context and staging).  The first
  * reservation is an estimate: the dense per-level grids exactly, per-active arrays for a quarter
  * of the finest level, or for 1.25 times the largest share of it that finished or refused runs of
- * the same dim, pde, M, lmax and refine_factor held (the loop learns it from their device bytes).  A solve that outgrows its reservation (AW_ELIMIT: a mesh that refines
- * more than that) gives its memory back and goes back to the head of the queue with a larger
- * reservation (at least the bytes it was refused, at least twice the old one, at most what every
- * cell of every level active would take), and waits there until the budget has room for it; it
- * then runs again from its initial condition.  So the reservations of running requests never
- * exceed the budget, and a request fails for memory only if it needs more than the whole
+ * the same dim, pde, M, lmax and refine_factor held (the loop learns it from their device
+ * bytes).  A solve whose mesh refines more than its reservation allows has the reservation grown
+ * in place, while it runs, when the budget has room for the growth beside the other running
+ * requests (to the bytes it asked for and half again, or just those bytes; aw_srv_info.grows).
+ * Otherwise (AW_ELIMIT) it gives its memory back and goes back to the head of the queue with a
+ * larger reservation (at least the bytes it was refused, at least twice the old one, at most what
+ * every cell of every level active would take), and waits there until the budget has room for
+ * it; it then runs again from its initial condition.  So the reservations of running requests
+ * never exceed the budget, and a request fails for memory only if it needs more than the whole
  * budget. */
 int aw_srv_create(int64_t hbm_budget_bytes, int32_t max_concurrent, aw_server** out);
 

@@ -271,6 +271,20 @@ def advance_batch(solvers, t_end, stream: int = 0):
     return out
 
 
+def step_batch(solvers, t_ends, stream: int = 0):
+    """aw_step_batch: one lockstep level-0 step of every solver not yet at its own end time, the
+    hot kernels batched.  Returns (stats, rc) per solver; raises AwError with the first failure."""
+    n = len(solvers)
+    arr = (C.c_void_p * n)(*[s.h.value for s in solvers])
+    te = (C.c_double * n)(*[float(t) for t in t_ends])
+    st = (AwStats * n)()
+    rc = (C.c_int32 * n)()
+    code = _lib.load().aw_step_batch(arr, n, te, stream, st, rc)
+    out = list(st), list(rc)
+    _lib.check(code)
+    return out
+
+
 class Server:
     """Request loop of independent solves (aw_srv_*): continuous admission under a device-memory
     budget, concurrent requests on their own streams; with max_batch > 1, compatible queued

@@ -43,14 +43,14 @@ class AwStats(C.Structure):
 class AwSrvInfo(C.Structure):
     _fields_ = [("cell_updates", C.c_int64), ("level0_steps", C.c_int64), ("footprint_bytes", C.c_int64),
                 ("queue_ms", C.c_double), ("run_ms", C.c_double), ("total_ms", C.c_double),
-                ("requeues", C.c_int64), ("peak_bytes", C.c_int64)]
+                ("requeues", C.c_int64), ("peak_bytes", C.c_int64), ("grows", C.c_int64)]
 
 
 class AwSrvSummary(C.Structure):
     _fields_ = [("done", C.c_int64), ("failed", C.c_int64), ("queued", C.c_int64), ("running", C.c_int64),
                 ("p50_ms", C.c_double), ("p99_ms", C.c_double), ("solves_per_s", C.c_double),
                 ("cell_updates_per_s", C.c_double), ("requeues", C.c_int64), ("budget_bytes", C.c_int64),
-                ("peak_reserved_bytes", C.c_int64)]
+                ("peak_reserved_bytes", C.c_int64), ("grows", C.c_int64)]
 
 
 class AwLaunchParams(C.Structure):
@@ -121,6 +121,8 @@ SIGNATURES = {
     "aw_kernel_launches": (C.c_int64, [_vp]),
     "aw_advance_batch": (C.c_int, [C.POINTER(_vp), C.c_int32, C.c_double, C.c_size_t, C.POINTER(AwStats),
                                    C.POINTER(C.c_int32)]),
+    "aw_step_batch": (C.c_int, [C.POINTER(_vp), C.c_int32, _dp, C.c_size_t, C.POINTER(AwStats),
+                                C.POINTER(C.c_int32)]),
 }
 
 _lib = None

@@ -3,6 +3,8 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 
+struct aw_solver;
+
 namespace aw {
 struct HotArgs;
 struct HotBatch;
@@ -58,4 +60,11 @@ struct LaunchParams {
 };
 LaunchParams launch_params();
 void set_launch_params(const LaunchParams& p);
+
+// The request loop's hook on a solver's memory limit: called when an allocation would take the
+// solver's live device bytes to `need`, above its limit; returns the new limit (>= need) when the
+// loop has grown the solve's reservation by that much, or 0 to refuse (the allocation then fails
+// and the call returns AW_ELIMIT).  Called on the thread that advances the solver.
+typedef int64_t (*GrowFn)(void* ctx, int64_t need);
+void set_grow_hook(aw_solver* s, GrowFn fn, void* ctx);
 }  // namespace aw

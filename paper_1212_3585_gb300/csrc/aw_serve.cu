@@ -4,7 +4,8 @@
 // Worker threads admit them in arrival order as soon as their device-memory reservation fits the
 // remaining budget and a worker is free; each admitted request gets its own CUDA stream and
 // solver, so the kernels of concurrent requests overlap on the GPU.  The solver runs with its
-// reservation as its memory limit: a solve whose mesh outgrows the reservation is refused the
+// reservation as its memory limit: a solve whose mesh outgrows the reservation has it grown in
+// place while the budget has room beside the other running requests; otherwise it is refused the
 // allocation (AW_ELIMIT), gives its memory back and is queued again at the head with a larger
 // reservation, to run again from its initial condition once the budget has room.  A finished
 // request's cell averages are copied to host memory and its device memory is released at once,
@@ -22,6 +23,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <memory>
 #include <tuple>
 #include <mutex>
 #include <string>
@@ -30,6 +32,7 @@
 
 #include "aderweno.h"
 #include "aw_device.cuh"
+#include "aw_ops.h"
 
 namespace {
 
@@ -47,7 +50,7 @@ struct Request {
   std::string err;
   clk::time_point t_submit, t_start, t_done;
   int64_t cell_updates = 0, level0_steps = 0;
-  int64_t requeues = 0, peak_bytes = 0, refused_bytes = 0;
+  int64_t requeues = 0, grows = 0, peak_bytes = 0, refused_bytes = 0;
   std::vector<aw_cell> meta;
   std::vector<double> u;
 };
@@ -56,7 +59,7 @@ struct Request {
 
 struct aw_server {
   int device = 0;
-  int64_t budget = 0, in_use = 0, peak_in_use = 0, requeues = 0;
+  int64_t budget = 0, in_use = 0, peak_in_use = 0, requeues = 0, grows = 0;
   // per (dim, pde, M, lmax, r): the largest share of its finest level a run of that kind has held
   // per-active arrays for, learned from the runs' device bytes (first reservations use it)
   std::map<std::tuple<int, int, int, int, int>, double> active_share;
@@ -155,6 +158,40 @@ static int64_t next_reservation(const aw_server* S, const Request& R) {
   return want;
 }
 
+// A running solve that outgrows its reservation asks the loop for more (aw::set_grow_hook): the
+// reservation grows in place, to the bytes asked for and half again (at most what every cell of
+// every level active would take), or to just the bytes asked for, when the budget has room for the
+// growth beside the other running requests' reservations; else the allocation is refused and the
+// solve is queued again (AW_ELIMIT).  The growth is added to the worker's total, which it gives
+// back when the run ends.
+struct GrowCtx {
+  aw_server* S;
+  Request* R;
+  int64_t* held;   // the worker's reserved bytes (all requests of its batch)
+};
+
+static int64_t grow_reservation(void* ctx, int64_t need) {
+  GrowCtx* g = (GrowCtx*)ctx;
+  aw_server* S = g->S;
+  Request& R = *g->R;
+  std::lock_guard<std::mutex> lk(S->mu);
+  const int64_t have = R.footprint - kAllowance;
+  if (need <= have) return have;
+  const int64_t cap = std::max(footprint_max(R.cfg) - kAllowance, need);
+  for (int64_t limit : {std::min(need + need / 2, cap), need}) {
+    const int64_t extra = limit - have;
+    if (S->in_use + extra > S->budget) continue;
+    S->in_use += extra;
+    S->peak_in_use = std::max(S->peak_in_use, S->in_use);
+    *g->held += extra;
+    R.footprint += extra;
+    R.grows++;
+    S->grows++;
+    return limit;
+  }
+  return 0;
+}
+
 // the request's own stream; on failure the CUDA error goes into the request's message
 static int create_stream(cudaStream_t* st, std::string* err) {
   cudaError_t e = cudaStreamCreateWithFlags(st, cudaStreamNonBlocking);
@@ -164,14 +201,16 @@ static int create_stream(cudaStream_t* st, std::string* err) {
   return AW_ECUDA;
 }
 
-static void run_request(aw_server* S, Request& R) {
+static void run_request(aw_server* S, Request& R, int64_t* held) {
   cudaSetDevice(S->device);
   cudaStream_t st = nullptr;
   aw_solver* sol = nullptr;
   std::string err0;
+  GrowCtx gc{S, &R, held};
   int rc = create_stream(&st, &err0);
   if (rc == AW_OK) rc = aw_create(&R.cfg, (uintptr_t)st, &sol);
   if (rc == AW_OK) rc = aw_set_memory_limit(sol, std::max<int64_t>(R.footprint - kAllowance, 1));
+  if (rc == AW_OK) aw::set_grow_hook(sol, grow_reservation, &gc);
   if (rc == AW_OK)
     rc = aw_set_initial(sol, R.ic, R.params.empty() ? nullptr : R.params.data(), (int32_t)R.params.size(), -1);
   aw_stats stats;
@@ -193,62 +232,160 @@ static void run_request(aw_server* S, Request& R) {
   R.rc = rc;
 }
 
-// a batch of requests on one stream: each member created and initialised on its own, then all
-// advanced together
-static void run_batch(aw_server* S, std::vector<Request*>& G) {
-  cudaSetDevice(S->device);
-  const int n = (int)G.size();
-  cudaStream_t st = nullptr;
-  std::string err0;
-  int rc0 = create_stream(&st, &err0);
-  std::vector<aw_solver*> sol(n, nullptr);
-  std::vector<aw_solver*> run;
-  std::vector<int> idx;
-  for (int i = 0; i < n; i++) {
-    Request& R = *G[i];
-    int rc = rc0;
-    if (rc == AW_OK) rc = aw_create(&R.cfg, (uintptr_t)st, &sol[i]);
-    if (rc == AW_OK) rc = aw_set_memory_limit(sol[i], std::max<int64_t>(R.footprint - kAllowance, 1));
-    if (rc == AW_OK)
-      rc = aw_set_initial(sol[i], R.ic, R.params.empty() ? nullptr : R.params.data(), (int32_t)R.params.size(), -1);
-    R.rc = rc;
-    if (rc != AW_OK) R.err = rc0 == AW_OK ? aw_last_error() : err0;
-    else { run.push_back(sol[i]); idx.push_back(i); }
-  }
-  if (!run.empty()) {
-    std::vector<aw_stats> stats(run.size());
-    std::vector<int32_t> rcs(run.size(), AW_OK);
-    int rc = aw_advance_batch(run.data(), (int32_t)run.size(), G[idx[0]]->t_end, (uintptr_t)st, stats.data(), rcs.data());
-    std::string msg = rc != AW_OK ? aw_last_error() : "";
-    for (size_t k = 0; k < run.size(); k++) {
-      Request& R = *G[idx[k]];
-      R.cell_updates = stats[k].cell_updates;
-      R.level0_steps = stats[k].level0_steps;
-      int r = rcs[k];
-      if (r == AW_OK) {
-        int64_t nc = 0;
-        aw_get_counts(run[k], &nc, nullptr, nullptr, nullptr);
-        R.meta.resize(nc);
-        R.u.resize((size_t)nc * aw::nvars(R.cfg.dim, R.cfg.pde));
-        r = aw_read_cells(run[k], R.meta.data(), R.u.data(), nc, &nc);
-        if (r != AW_OK) R.err = aw_last_error();
-      } else {
-        R.err = msg.empty() ? "failed in a batch" : "failed in a batch (first failure of the batch: " + msg + ")";
-      }
-      R.rc = r;
-    }
-  }
-  for (int i = 0; i < n; i++) {
-    if (sol[i]) aw_get_memory(sol[i], nullptr, &G[i]->peak_bytes, &G[i]->refused_bytes);
-    aw_destroy(sol[i]);
-  }
-  if (st) cudaStreamDestroy(st);
-}
-
-// requests that can share batched launches with R
+// requests that can share batched launches with R (end times may differ: continuous batching
+// steps each member to its own)
 static bool batchable(const Request& R, const Request& Q) {
   return R.cfg.dim == Q.cfg.dim && R.cfg.pde == Q.cfg.pde && R.cfg.M == Q.cfg.M && R.cfg.flux == Q.cfg.flux &&
-         R.cfg.refine_factor == Q.cfg.refine_factor && R.t_end == Q.t_end;
+         R.cfg.refine_factor == Q.cfg.refine_factor;
+}
+
+// The end of a run of R, under the lock, after its reservation has been given back: the loop
+// learns from its device bytes; an outgrown run (AW_ELIMIT) goes into `again` with a larger
+// reservation, to be queued at the head; else the request is DONE or FAILED.
+static void finish_locked(aw_server* S, Request* R, std::vector<int64_t>* again) {
+  learn_share(S, *R);
+  if (R->rc == AW_ELIMIT) {
+    const int64_t next = next_reservation(S, *R);
+    if (next > 0) {
+      R->footprint = next;
+      R->requeues++;
+      S->requeues++;
+      R->state = AW_REQ_QUEUED;
+      R->rc = AW_OK;
+      R->err.clear();
+      R->refused_bytes = 0;
+      again->push_back(R->id);
+      return;
+    }
+    R->rc = AW_ENOMEM;
+    R->err = "the solve needs more device memory than the whole budget of the loop";
+  }
+  R->state = R->rc == AW_OK ? AW_REQ_DONE : AW_REQ_FAILED;
+}
+
+// Continuous batching (max_batch > 1): the worker advances its group in lockstep level-0 steps
+// (aw_step_batch), each member to its own end time.  A member that finishes or fails leaves the
+// group at once: its cell averages go to host memory, its solver and reservation are released and
+// waiting callers are woken.  Between steps the worker admits queued requests that can share the
+// group's launches (in arrival order, up to the batch size) when their reservations fit the
+// budget beside the other running requests and the oldest queued request.  The group ends when it
+// has no members left.
+struct Member {
+  Request* R = nullptr;
+  aw_solver* sol = nullptr;
+  GrowCtx gc{};
+};
+
+static void run_continuous(aw_server* S, std::vector<Request*> G, int64_t* held) {
+  cudaSetDevice(S->device);
+  cudaStream_t st = nullptr;
+  std::string err0;
+  const int rc0 = create_stream(&st, &err0);
+  const Request proto = *G[0];   // the kernel configuration of the group
+  std::vector<std::unique_ptr<Member>> mem;
+  // a member's end: results, solver, reservation, state
+  auto leave = [&](Member& m, int rc, const std::string& err) {
+    Request& R = *m.R;
+    if (rc == AW_OK) {
+      int64_t nc = 0;
+      aw_get_counts(m.sol, &nc, nullptr, nullptr, nullptr);
+      R.meta.resize(nc);
+      R.u.resize((size_t)nc * aw::nvars(R.cfg.dim, R.cfg.pde));
+      rc = aw_read_cells(m.sol, R.meta.data(), R.u.data(), nc, &nc);
+      if (rc != AW_OK) R.err = aw_last_error();
+    } else {
+      R.err = err;
+    }
+    R.rc = rc;
+    if (m.sol) aw_get_memory(m.sol, nullptr, &R.peak_bytes, &R.refused_bytes);
+    aw_destroy(m.sol);
+    m.sol = nullptr;
+    std::vector<int64_t> again;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      R.t_done = clk::now();
+      S->in_use -= R.footprint;
+      *held -= R.footprint;
+      S->running--;
+      finish_locked(S, &R, &again);
+      for (auto it = again.rbegin(); it != again.rend(); ++it) S->queue.push_front(*it);
+    }
+    S->cv_done.notify_all();
+    S->cv_work.notify_all();
+  };
+  // a new member: solver, memory limit and growth hook, initial condition
+  auto join = [&](Request* R) {
+    auto m = std::make_unique<Member>();
+    m->R = R;
+    m->gc = GrowCtx{S, R, held};
+    int rc = rc0;
+    if (rc == AW_OK) rc = aw_create(&R->cfg, (uintptr_t)st, &m->sol);
+    if (rc == AW_OK) rc = aw_set_memory_limit(m->sol, std::max<int64_t>(R->footprint - kAllowance, 1));
+    if (rc == AW_OK) aw::set_grow_hook(m->sol, grow_reservation, &m->gc);
+    if (rc == AW_OK)
+      rc = aw_set_initial(m->sol, R->ic, R->params.empty() ? nullptr : R->params.data(), (int32_t)R->params.size(), -1);
+    if (rc != AW_OK) {
+      leave(*m, rc, rc0 == AW_OK ? std::string(aw_last_error()) : err0);
+      return;
+    }
+    mem.push_back(std::move(m));
+  };
+  for (Request* R : G) join(R);
+  std::vector<aw_solver*> sol;
+  std::vector<double> tend;
+  std::vector<aw_stats> stats;
+  std::vector<int32_t> rcs;
+  while (!mem.empty()) {
+    const int n = (int)mem.size();
+    sol.resize(n);
+    tend.resize(n);
+    stats.assign(n, aw_stats{});
+    rcs.assign(n, AW_OK);
+    for (int k = 0; k < n; k++) {
+      sol[k] = mem[k]->sol;
+      tend[k] = mem[k]->R->t_end;
+    }
+    const int rc = aw_step_batch(sol.data(), n, tend.data(), (uintptr_t)st, stats.data(), rcs.data());
+    const std::string msg = rc != AW_OK ? aw_last_error() : "";
+    std::vector<std::unique_ptr<Member>> keep;
+    for (int k = 0; k < n; k++) {
+      Member& m = *mem[k];
+      m.R->cell_updates += stats[k].cell_updates;
+      m.R->level0_steps += stats[k].level0_steps;
+      if (rcs[k] != AW_OK)
+        leave(m, rcs[k], msg.empty() ? "failed in a batch" : "failed in a batch (first failure of the step: " + msg + ")");
+      else if (!(stats[k].t < m.R->t_end))
+        leave(m, AW_OK, "");
+      else
+        keep.push_back(std::move(mem[k]));
+    }
+    mem = std::move(keep);
+    // admit queued requests that can share the launches
+    std::vector<Request*> add;
+    {
+      std::lock_guard<std::mutex> lk(S->mu);
+      for (auto it = S->queue.begin(); it != S->queue.end() && (int)(mem.size() + add.size()) < S->max_batch;) {
+        Request& Q = S->req[*it];
+        if (Q.requeues == 0) Q.footprint = std::min(first_reservation(S, Q.cfg), S->budget);
+        const Request& head = S->req[S->queue.front()];
+        const int64_t keep_free = *it == S->queue.front() ? 0 : head.footprint;
+        if (S->stop || !batchable(proto, Q) || S->in_use + Q.footprint + keep_free > S->budget) {
+          ++it;
+          continue;
+        }
+        S->in_use += Q.footprint;
+        S->peak_in_use = std::max(S->peak_in_use, S->in_use);
+        *held += Q.footprint;
+        S->running++;
+        Q.state = AW_REQ_RUNNING;
+        Q.t_start = clk::now();
+        add.push_back(&Q);
+        it = S->queue.erase(it);
+      }
+    }
+    for (Request* R : add) join(R);
+  }
+  if (st) cudaStreamDestroy(st);
 }
 
 static void worker_main(aw_server* S) {
@@ -292,35 +429,21 @@ static void worker_main(aw_server* S) {
       R->t_start = t0;
     }
     lk.unlock();
-    if (G.size() == 1) run_request(S, *G[0]);
-    else run_batch(S, G);
-    lk.lock();
-    const clk::time_point t1 = clk::now();
-    std::vector<int64_t> again;   // outgrown runs, back to the head of the queue in arrival order
-    for (Request* R : G) {
-      R->t_done = t1;
-      learn_share(S, *R);
-      if (R->rc == AW_ELIMIT) {
-        const int64_t next = next_reservation(S, *R);
-        if (next > 0) {
-          R->footprint = next;
-          R->requeues++;
-          S->requeues++;
-          R->state = AW_REQ_QUEUED;
-          R->rc = AW_OK;
-          R->err.clear();
-          R->refused_bytes = 0;
-          again.push_back(R->id);
-          continue;
-        }
-        R->rc = AW_ENOMEM;
-        R->err = "the solve needs more device memory than the whole budget of the loop";
-      }
-      R->state = R->rc == AW_OK ? AW_REQ_DONE : AW_REQ_FAILED;
+    if (S->max_batch > 1) {
+      // every member releases its own reservation when it leaves the group
+      run_continuous(S, G, &need);
+      lk.lock();
+      continue;
     }
-    for (auto it = again.rbegin(); it != again.rend(); ++it) S->queue.push_front(*it);
+    run_request(S, *G[0], &need);
+    lk.lock();
+    Request* R = G[0];
+    R->t_done = clk::now();
     S->in_use -= need;
-    S->running -= (int)G.size();
+    S->running--;
+    std::vector<int64_t> again;   // an outgrown run, back to the head of the queue
+    finish_locked(S, R, &again);
+    for (auto it = again.rbegin(); it != again.rend(); ++it) S->queue.push_front(*it);
     S->cv_done.notify_all();
     S->cv_work.notify_all();
   }
@@ -417,6 +540,7 @@ int aw_srv_result(aw_server* S, int64_t id, aw_cell* meta, double* u, int64_t ca
     info->footprint_bytes = R.footprint;
     info->requeues = R.requeues;
     info->peak_bytes = R.peak_bytes;
+    info->grows = R.grows;
   }
   if (cap < *n) SRV_FAIL(AW_EINVAL, "capacity too small");
   if (meta) memcpy(meta, R.meta.data(), sizeof(aw_cell) * R.meta.size());
@@ -458,6 +582,7 @@ int aw_srv_stats(aw_server* S, aw_srv_summary* out) {
     out->cell_updates_per_s = span > 0 ? upd / span : 0.0;
   }
   out->requeues = S->requeues;
+  out->grows = S->grows;
   out->budget_bytes = S->budget;
   out->peak_reserved_bytes = S->peak_in_use;
   return AW_OK;

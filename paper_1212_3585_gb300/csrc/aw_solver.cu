@@ -197,6 +197,9 @@ struct aw_solver {
   // would have reached
   std::unordered_map<void*, size_t> alloc_bytes;
   int64_t mem_live = 0, mem_peak = 0, mem_limit = 0, mem_refused = 0;
+  // the request loop's hook that may raise the limit instead of refusing (aw::set_grow_hook)
+  aw::GrowFn grow = nullptr;
+  void* grow_ctx = nullptr;
   // the autotuner's timed trial launches of this solver, read after the next synchronisation
   struct TunePending {
     int key[6];
@@ -213,9 +216,15 @@ struct aw_solver {
 static cudaError_t dalloc(aw_solver* s, void** p, size_t bytes) {
   if (!bytes) bytes = 1;
   if (s->mem_limit > 0 && s->mem_live + (int64_t)bytes > s->mem_limit) {
-    s->mem_refused = std::max(s->mem_refused, s->mem_live + (int64_t)bytes);
-    *p = nullptr;
-    return cudaErrorMemoryAllocation;
+    const int64_t need = s->mem_live + (int64_t)bytes;
+    const int64_t grown = s->grow ? s->grow(s->grow_ctx, need) : 0;
+    if (grown >= need) {
+      s->mem_limit = grown;
+    } else {
+      s->mem_refused = std::max(s->mem_refused, need);
+      *p = nullptr;
+      return cudaErrorMemoryAllocation;
+    }
   }
   cudaError_t e = cudaMallocAsync(p, bytes, s->stream);
   if (e != cudaSuccess) return e;
@@ -1914,6 +1923,15 @@ int aw_set_memory_limit(aw_solver* s, int64_t bytes) {
   return AW_OK;
 }
 
+}  // extern "C"
+
+void aw::set_grow_hook(aw_solver* s, aw::GrowFn fn, void* ctx) {
+  s->grow = fn;
+  s->grow_ctx = ctx;
+}
+
+extern "C" {
+
 int aw_get_memory(const aw_solver* s, int64_t* live, int64_t* peak, int64_t* refused) {
   if (!s) AW_FAIL(AW_EINVAL, "null solver");
   if (live) *live = s->mem_live;
@@ -2108,8 +2126,8 @@ static int advance_batch(aw_solver* const* S, int n, const bool* live, int l, in
 // Returns a failure of the batch as a whole (CUDA errors); a member's own failure (non-physical
 // state, no stable time step) stops that member only and is reported through rcs[m], *first and
 // *first_err.
-static int batch_run(aw_solver* const* S, int n, double t_end, cudaStream_t st, aw_stats* stats, int32_t* rcs,
-                     int* first, std::string* first_err) {
+static int batch_run(aw_solver* const* S, int n, const double* tend, bool one_step, cudaStream_t st,
+                     aw_stats* stats, int32_t* rcs, int* first, std::string* first_err) {
   bool live[MAXB];
   auto fail = [&](int m, int rc) {
     live[m] = false;
@@ -2120,16 +2138,16 @@ static int batch_run(aw_solver* const* S, int n, double t_end, cudaStream_t st, 
     }
   };
   for (int m = 0; m < n; m++) {
-    live[m] = S[m]->t < t_end;
+    live[m] = S[m]->t < tend[m];
     rcs[m] = AW_OK;
   }
   double dt[MAXB];
   bool clip[MAXB];
   std::vector<char> sig;
-  for (;;) {
+  for (int iter = 0;; iter++) {
     int nlive = 0;
     for (int m = 0; m < n; m++) nlive += live[m];
-    if (!nlive) break;
+    if (!nlive || (one_step && iter == 1)) break;
     // the time step of every member, one synchronisation
     for (int m = 0; m < n; m++) if (live[m]) TRY(dt_issue(S[m]));
     CK(cudaStreamSynchronize(st));
@@ -2137,8 +2155,8 @@ static int batch_run(aw_solver* const* S, int n, double t_end, cudaStream_t st, 
       if (!live[m]) continue;
       int rc = dt_finish(S[m], &dt[m]);
       if (rc != AW_OK) { fail(m, rc); continue; }
-      clip[m] = S[m]->t + dt[m] >= t_end;
-      if (clip[m]) dt[m] = t_end - S[m]->t;
+      clip[m] = S[m]->t + dt[m] >= tend[m];
+      if (clip[m]) dt[m] = tend[m] - S[m]->t;
       rc = step_begin(S[m], dt[m]);
       if (rc != AW_OK) fail(m, rc);
     }
@@ -2163,7 +2181,7 @@ static int batch_run(aw_solver* const* S, int n, double t_end, cudaStream_t st, 
       aw_stats one;
       memset(&one, 0, sizeof one);
       rc = step_finish(S[m], dt[m], &one);
-      S[m]->t = clip[m] ? t_end : S[m]->t + dt[m];
+      S[m]->t = clip[m] ? tend[m] : S[m]->t + dt[m];
       if (stats) {
         stats[m].level0_steps += one.level0_steps;
         stats[m].cell_updates += one.cell_updates;
@@ -2208,15 +2226,18 @@ static int batch_run(aw_solver* const* S, int n, double t_end, cudaStream_t st, 
       }
     }
     for (int m = 0; m < n; m++)
-      if (live[m] && !(S[m]->t < t_end)) live[m] = false;
+      if (live[m] && !(S[m]->t < tend[m])) live[m] = false;
   }
   return AW_OK;
 }
 
 extern "C" {
 
-int aw_advance_batch(aw_solver* const* solvers, int32_t n, double t_end, uintptr_t stream, aw_stats* stats,
-                     int32_t* rc_out) {
+}  // extern "C"
+
+// aw_advance_batch (one_step false) and aw_step_batch (one_step true): member m advances to tend[m]
+static int batch_call(aw_solver* const* solvers, int32_t n, const double* tend, bool one_step, uintptr_t stream,
+                      aw_stats* stats, int32_t* rc_out) {
   if (!solvers || n < 1 || n > AW_BATCH_MAX) AW_FAIL(AW_EINVAL, "need 1 <= n <= %d solvers", AW_BATCH_MAX);
   for (int m = 0; m < n; m++) {
     const aw_solver* a = solvers[m];
@@ -2226,6 +2247,7 @@ int aw_advance_batch(aw_solver* const* solvers, int32_t n, double t_end, uintptr
       AW_FAIL(AW_EINVAL, "solver %d differs from solver 0 in dim, pde, M, flux or refine_factor", m);
     for (int k = 0; k < m; k++)
       if (solvers[k] == a) AW_FAIL(AW_EINVAL, "solver %d appears twice", m);
+    if (std::isnan(tend[m])) AW_FAIL(AW_EINVAL, "end time of solver %d is NaN", m);
   }
   cudaStream_t st = (cudaStream_t)stream;
   cudaStream_t own[MAXB];
@@ -2239,7 +2261,7 @@ int aw_advance_batch(aw_solver* const* solvers, int32_t n, double t_end, uintptr
   for (int m = 0; m < n; m++) rcs[m] = AW_OK;
   int first = AW_OK;
   std::string first_err;
-  int fatal = batch_run(solvers, n, t_end, st, stats, rcs, &first, &first_err);
+  int fatal = batch_run(solvers, n, tend, one_step, st, stats, rcs, &first, &first_err);
   std::string fatal_err = g_err;
   cudaError_t e = cudaStreamSynchronize(st);
   if (fatal == AW_OK && e != cudaSuccess) {
@@ -2249,7 +2271,7 @@ int aw_advance_batch(aw_solver* const* solvers, int32_t n, double t_end, uintptr
   for (int m = 0; m < n; m++) {
     solvers[m]->stream = own[m];
     if (stats) stats[m].t = solvers[m]->t;
-    if (fatal != AW_OK && rcs[m] == AW_OK && solvers[m]->t < t_end) rcs[m] = fatal;
+    if (fatal != AW_OK && rcs[m] == AW_OK && solvers[m]->t < tend[m]) rcs[m] = fatal;
     if (rc_out) rc_out[m] = rcs[m];
   }
   if (fatal != AW_OK) {
@@ -2258,6 +2280,21 @@ int aw_advance_batch(aw_solver* const* solvers, int32_t n, double t_end, uintptr
   }
   if (first != AW_OK) g_err = first_err;
   return first;
+}
+
+extern "C" {
+
+int aw_advance_batch(aw_solver* const* solvers, int32_t n, double t_end, uintptr_t stream, aw_stats* stats,
+                     int32_t* rc_out) {
+  double tend[MAXB];
+  for (int m = 0; m < MAXB; m++) tend[m] = t_end;
+  return batch_call(solvers, n, tend, false, stream, stats, rc_out);
+}
+
+int aw_step_batch(aw_solver* const* solvers, int32_t n, const double* t_end, uintptr_t stream, aw_stats* stats,
+                  int32_t* rc_out) {
+  if (!t_end) AW_FAIL(AW_EINVAL, "null end times");
+  return batch_call(solvers, n, t_end, true, stream, stats, rc_out);
 }
 
 int aw_advance_graph(aw_solver* s, double t_end, int32_t chunk, aw_stats* st) {

@@ -151,6 +151,29 @@ def test_request_outgrowing_its_reservation_waits_and_completes(max_batch):
     srv.close()
 
 
+@pytest.mark.parametrize("max_batch", [1, 2])
+def test_request_outgrowing_its_reservation_grows_in_place(max_batch):
+    """Requests whose meshes refine everywhere (four times the first reservation) under a budget
+    with room for their growth: each reservation grows in place while the solve runs, nothing is
+    queued again, the reservations held never exceed the budget, and the results are the solo
+    solve's."""
+    cfg = full_refinement_config()
+    m0, u0 = solo(cfg, pg.AW_IC_VORTEX, VORTEX, 0.1)
+    srv = pg.Server(hbm_budget_bytes=16 << 30, max_concurrent=2, max_batch=max_batch)
+    ids = [srv.submit(cfg, pg.AW_IC_VORTEX, VORTEX, 0.1) for _ in range(2)]
+    srv.wait_all()
+    st = srv.stats()
+    assert st.done == 2 and st.failed == 0
+    assert st.requeues == 0 and st.grows >= 2
+    assert st.peak_reserved_bytes <= st.budget_bytes
+    for rid in ids:
+        m, u, info = srv.result(rid, 4)
+        assert np.array_equal(m, m0) and np.array_equal(u, u0)
+        assert info.requeues == 0 and info.grows >= 1
+        assert info.peak_bytes + (64 << 20) <= info.footprint_bytes
+    srv.close()
+
+
 def test_batched_loop_results_identical_to_solo():
     """with batching on, compatible requests share launches; every result still equals its solo
     solve bit for bit"""
@@ -183,6 +206,74 @@ def test_batched_loop_results_identical_to_solo():
     srv.close()
     with pytest.raises(pg.AwError):
         pg.Server(hbm_budget_bytes=1 << 30, max_concurrent=1, max_batch=pg.AW_BATCH_MAX + 1)
+
+
+def test_continuous_batching_members_leave_and_join():
+    """continuous batching on one worker: requests of one kernel configuration with different end
+    times and grids share a group, each leaves it when it reaches its own end time (so the earlier
+    ones are done before the group ends), a request submitted while the group runs joins it at a
+    step boundary instead of waiting for the group to end, and every result equals its solo solve
+    bit for bit"""
+    import time
+    reqs = [(rp_config(40, 2, 1), aw_inputs.rp4_params(501), 0.03),
+            (rp_config(24, 2, 1), aw_inputs.rp4_params(502), 0.12),
+            (rp_config(32, 2, 1), aw_inputs.rp4_params(503), 0.25)]
+    late = (rp_config(20, 2, 1), aw_inputs.rp4_params(504), 0.05)
+    srv = pg.Server(hbm_budget_bytes=8 << 30, max_concurrent=1, max_batch=4)
+    t0 = time.monotonic()
+    ids = [srv.submit(c, pg.AW_IC_RP4, p, te) for c, p, te in reqs]
+    time.sleep(0.05)
+    t_late = time.monotonic() - t0
+    lid = srv.submit(late[0], pg.AW_IC_RP4, late[1], late[2])
+    srv.wait_all()
+    st = srv.stats()
+    assert st.done == 4 and st.failed == 0
+    infos = []
+    for rid, (c, p, te) in zip(ids + [lid], reqs + [late]):
+        m, u, info = srv.result(rid, 4)
+        m0, u0 = solo(c, pg.AW_IC_RP4, p, te)
+        assert np.array_equal(m, m0) and np.array_equal(u, u0)
+        infos.append(info)
+    done = [i.total_ms for i in infos[:3]]          # the first three were submitted together
+    assert done[0] < done[2] and done[1] < done[2]
+    # the late request started before the group's last member finished: it joined the group
+    assert t_late * 1e3 + infos[3].queue_ms < done[2]
+    assert infos[3].queue_ms < 0.5 * (done[2] - t_late * 1e3)
+    srv.close()
+
+
+def test_step_batch_equals_solo_steps():
+    """aw_step_batch: one lockstep level-0 step of each member not yet at its own end time, each
+    member's step exactly its own aw_step; members at their end time are left as they are"""
+    cfgs = [rp_config(20, 3, 2), rp_config(28, 3, 1), rp_config(16, 3, 0)]
+    ps = [aw_inputs.rp4_params(600 + k) for k in range(3)]
+    ends = [0.02, 0.05, 0.08]
+    sol, ref = [], []
+    for c, p in zip(cfgs, ps):
+        for lst in (sol, ref):
+            s = pg.Solver(c)
+            s.set_initial(pg.AW_IC_RP4, p, -1)
+            lst.append(s)
+    steps = 0
+    while any(s.t < te for s, te in zip(sol, ends)):
+        before = [s.t for s in sol]
+        st, rc = pg.step_batch(sol, ends)
+        assert rc == [0, 0, 0]
+        for k in range(3):
+            if before[k] < ends[k]:
+                one = ref[k].step(ends[k])
+                assert st[k].level0_steps == 1 and st[k].cell_updates == one.cell_updates
+                assert st[k].t == ref[k].t
+            else:
+                assert st[k].level0_steps == 0 and sol[k].t == before[k]
+        steps += 1
+    assert steps >= 3
+    for a, b in zip(sol, ref):
+        ma, ua = a.cells()
+        mb, ub = b.cells()
+        assert np.array_equal(ma, mb) and np.array_equal(ua, ub)
+        a.close()
+        b.close()
 
 
 def test_budget_rejects_oversized_request():
