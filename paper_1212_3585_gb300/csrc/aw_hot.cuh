@@ -1009,7 +1009,9 @@ __device__ __forceinline__ void update_cell(const HotArgs& a, int cell, double d
 // chunk.  So every cell receives exactly 2*D arrivals.  A CTA publishes its fluxes, then adds its
 // arrivals to the per-chunk counters; the CTA whose addition brings a chunk's counter to 2*D times
 // its cells applies the one-step update to that chunk.  The update does the arithmetic of
-// k_update in the same order, so the averages are bitwise those of the two-kernel path.
+// k_update in the same order, so the averages are bitwise those of the two-kernel path.  The CTA
+// that completes a chunk also sets its counter back to zero, so the counters are zero at the start
+// of every launch without a memset (they are zeroed when allocated and at every list rebuild).
 // ------------------------------------------------------------------------------------------
 template <int D, int M, int PDE, int DIV, int FL>
 __device__ __forceinline__ void flux_update_body(const HotArgs& a, const int bid,
@@ -1029,6 +1031,7 @@ __device__ __forceinline__ void flux_update_body(const HotArgs& a, const int bid
     const int cells = min(CPB, a.na - chunk * CPB);
     if (atomicAdd(a.fsync + chunk, n) + n == 2 * D * cells) {
       __threadfence();
+      a.fsync[chunk] = 0;   // complete: no other arrival comes; the counter is ready for the next launch
       s_full[atomicAdd(&s_nfull, 1)] = chunk;
     }
   };
@@ -1048,11 +1051,35 @@ __device__ __forceinline__ void flux_update_body(const HotArgs& a, const int bid
   if (nfull == 0) return;
   const double dt = a.dtl[a.level];
   if (dt == 0.0) return;   // a step of length zero leaves the averages as they are
-  // Eq. eq:finite_vol for the cells of the completed chunks, one thread per cell (the fluxes come
-  // from L2: other CTAs wrote them)
-  for (int k = t; k < nfull * CPB; k += C::THREADS) {
-    const int cell = s_full[k / CPB] * CPB + (k - (k / CPB) * CPB);
-    if (cell < a.na) update_cell<D, M, PDE, true>(a, cell, dt);
+  // Eq. eq:finite_vol for the cells of the completed chunks, one thread per (cell, variable) with
+  // the arithmetic of update_cell (the fluxes come from L2: other CTAs wrote them); then one
+  // thread per cell checks the new state
+  __shared__ double s_u[CPB * V];
+  const LevelView& L = a.lv;
+  for (int j = 0; j < nfull; j++) {
+    const int c0 = s_full[j] * CPB, ncell = min(CPB, a.na - c0);
+    for (int k = t; k < ncell * V; k += C::THREADS) {
+      const int lc = k / V, v = k - lc * V, cell = c0 + lc;
+      const long long di = a.alist[cell];
+      const double* fc = a.fl + (long long)cell * 2 * D * V + v;
+      double u = L.u[v * L.n + di];
+#pragma unroll
+      for (int d = 0; d < D; d++) {
+        const double c = dt / L.dx[d];
+        const double fhi = __ldcg(fc + 2 * d * V + V), flo = __ldcg(fc + 2 * d * V);
+        u -= c * (fhi - flo);
+      }
+      L.u[v * L.n + di] = u;
+      s_u[k] = u;
+    }
+    __syncthreads();
+    if (t < ncell) {
+      double u[V];
+#pragma unroll
+      for (int v = 0; v < V; v++) u[v] = s_u[t * V + v];
+      if (!Pde<PDE, D>::physical(u, a.P)) atomicOr(a.err, 1);
+    }
+    __syncthreads();
   }
 }
 

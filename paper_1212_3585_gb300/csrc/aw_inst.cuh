@@ -131,12 +131,7 @@ struct Launch {
     }
     return flux_fl<0>(a, st);
   }
-  // fused face flux and update: the per-chunk arrival counters zeroed on the stream, then one launch
-  template <class C>
-  static cudaError_t clear_fsync(const HotArgs& a, cudaStream_t st) {
-    const size_t n = (size_t)((a.na + C::CPB - 1) / C::CPB);
-    return cudaMemsetAsync(a.fsync, 0, n * sizeof(int), st);
-  }
+  // fused face flux and update: one launch (the per-chunk arrival counters are zero between launches)
   template <int FL>
   static int flux_update_fl(const HotArgs& a, cudaStream_t st) {
     int blocks = flux_ctas_of<CF>(a);
@@ -144,12 +139,10 @@ struct Launch {
     if (use_small(a, blocks)) {
       static std::once_flag init;
       smem_attr(k_flux_update<D, M, PDE, SMALL, FL>, CFs::SMEM, init);
-      clear_fsync<CFs>(a, st);
       k_flux_update<D, M, PDE, SMALL, FL><<<flux_ctas_of<CFs>(a), CFs::THREADS, CFs::SMEM, st>>>(a);
     } else {
       static std::once_flag init;
       smem_attr(k_flux_update<D, M, PDE, 1, FL>, CF::SMEM, init);
-      clear_fsync<CF>(a, st);
       k_flux_update<D, M, PDE, 1, FL><<<blocks, CF::THREADS, CF::SMEM, st>>>(a);
     }
     return 1;
@@ -279,7 +272,6 @@ struct Launch {
     if (!blocks) return 0;
     static std::once_flag init;
     smem_attr(k_flux_update_batch<D, M, PDE, FL>, CF::SMEM, init);
-    for (int m = 0; m < b.n; m++) clear_fsync<CF>(b.a[m], st);
     k_flux_update_batch<D, M, PDE, FL><<<blocks, CF::THREADS, CF::SMEM, st>>>(b);
     return 1;
   }

@@ -1154,6 +1154,7 @@ static int ensure_active_cap(aw_solver* s, int l, long long need) {
       dalloc(s, (void**)&L.fsync, cap * sizeof(int32_t)) != cudaSuccess)
     AW_FAIL(oom_code(s), "per-active arrays of level %d (%lld cells)", l, cap);
   L.cap = cap;
+  CK(cudaMemsetAsync(L.fsync, 0, cap * sizeof(int32_t), s->stream));
   return AW_OK;
 }
 
@@ -1225,6 +1226,9 @@ static int lists_mid(aw_solver* s) {
 static int lists_finish(aw_solver* s) {
   for (int l = 0; l <= s->lmax; l++) {
     Level& L = s->lev[l];
+    // the fused flux-and-update kernel leaves its arrival counters at zero; zeroed here too, so
+    // that a step that found an inconsistent mesh cannot leave counts behind for the next one
+    if (L.fsync && L.cap > 0) CK(cudaMemsetAsync(L.fsync, 0, L.cap * sizeof(int32_t), s->stream));
     L.ntiles = s->h_cnt[NSLOT * l + 4];
     L.nh = s->h_cnt[NSLOT * l + 5];
     L.nx = s->h_cnt[NSLOT * l + 6];
