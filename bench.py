@@ -874,6 +874,12 @@ def main():
                                   "the rest of the step is regrid, compaction, dt, averaging and host gaps"},
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
+        # the autotuner's CTA sizes for this configuration's level size classes (floor(log2 active
+        # cells)): full- or reduced-size CTAs, with the device ns per cell of each variant's trials
+        "tuning": [{"kernel": ("predictor", "face_flux")[e["kernel"]], "size_class": e["size_class"],
+                    "cta": {-1: "trying", 0: "full", 1: "reduced"}[e["choice"]], "inherited": bool(e["inherited"]),
+                    "ns_per_cell": [round(x, 3) for x in e["ns_per_cell"]]}
+                   for e in pg.get_tuning() if (e["dim"], e["M"], e["pde"]) == (cfg.dim, cfg.M, cfg.pde)],
     }
 
     if not args.no_e2e:

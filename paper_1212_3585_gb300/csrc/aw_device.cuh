@@ -16,6 +16,21 @@ enum { PDE_EULER = 0, PDE_MHD = 1, PDE_LINADV = 2 };
 enum { BC_PERIODIC = 0, BC_TRANSMISSIVE = 1, BC_REFLECTIVE = 2, BC_INFLOW = 3 };
 
 __host__ __device__ constexpr int ipow(int b, int e) { return e == 0 ? 1 : b * ipow(b, e - 1); }
+
+// Units (cells or face items of `per` threads each) of a reduced CTA of about `want` units: `want`
+// itself, or the most units that fit in the whole warps `want` units fill, whichever leaves the
+// smaller share of the last warp's lanes idle (idle lanes waste FP64 issue slots: a warp
+// instruction occupies the pipe whatever its active lanes).
+__host__ __device__ constexpr int warp_fill_units(int want, int per) {
+  return (((want * per) / 32) * 32 / per > 0 &&
+          (long long)(((want * per) / 32) * 32 / per) * per * (((want * per + 31) / 32) * 32) >
+              (long long)want * per * (((((want * per) / 32) * 32 / per) * per + 31) / 32 * 32))
+             ? ((want * per) / 32) * 32 / per
+             : want;
+}
+static_assert(warp_fill_units(8, 9) == 7 && warp_fill_units(24, 3) == 21 && warp_fill_units(2, 27) == 2 &&
+                  warp_fill_units(16, 4) == 16 && warp_fill_units(8, 4) == 8,
+              "reduced CTAs fill their warps");
 __host__ __device__ constexpr int nvars(int D, int PDE) {
   return PDE == PDE_LINADV ? 1 : (PDE == PDE_EULER ? D + 2 : 9);
 }

@@ -480,7 +480,7 @@ struct PredCfg {
   // room for two CTAs per SM; halved where one CTA would fill the shared memory (MHD, 3D)
   static constexpr int CPB1 = (NSP == 4) ? 64 : (NSP == 9) ? 32 : (NSP == 16 ? 16 : (NSP == 27 ? 16 : 4));
   static constexpr int CPB0 = (CPB1 * D * V * NST * 8 > 113 * 1024 && CPB1 > 1) ? CPB1 / 2 : CPB1;
-  static constexpr int CPB = CPB0 / DIV > 0 ? CPB0 / DIV : 1;
+  static constexpr int CPB = DIV == 1 ? CPB0 : warp_fill_units(CPB0 / DIV > 0 ? CPB0 / DIV : 1, NSP);
   static constexpr int THREADS = CPB * NSP;
   static constexpr int SMEM = CPB * D * V * NST * 8;   // fluxes at every space-time node
 };
@@ -593,7 +593,7 @@ __global__ void __launch_bounds__(PredCfg<D, M, PDE, DIV>::THREADS) k_predict(co
 
 // Face flux configuration: CPB face items per CTA (a chunk of CPB active cells for the low faces),
 // one thread per (face item, spatial quadrature point of the face), each thread looping over the
-// N time nodes; CPB is a multiple of 32, so every warp is full.
+// N time nodes; CPB is a multiple of 32, so every warp is full (reduced CTAs: nearly full).
 template <int D, int M, int PDE, int DIV = 1>
 struct FluxCfg {
   static constexpr int N = M + 1, NF = ipow(N, D - 1), V = nvars(D, PDE);
@@ -603,7 +603,8 @@ struct FluxCfg {
   static constexpr int PT = PredCfg<D, M, PDE, 1>::THREADS;
   static constexpr int TARGET = PT % (32 * NF) == 0 ? PT : (PDE == PDE_MHD ? 128 : 256);
   static constexpr int FULL = 32 * (TARGET / (32 * NF) > 0 ? TARGET / (32 * NF) : 1);
-  static constexpr int CPB = FULL / DIV > 0 ? FULL / DIV : 1;   // face items per CTA
+  // face items per CTA (reduced CTAs: about FULL / DIV items, filling their warps)
+  static constexpr int CPB = DIV == 1 ? FULL : warp_fill_units(FULL / DIV > 0 ? FULL / DIV : 1, NF);
   static constexpr int THREADS = CPB * NF;
   // CTAs per SM the register allocation must allow (at least 16 warps per SM)
   static constexpr int MINB = THREADS <= 256 / DIV ? 3 : 2;
