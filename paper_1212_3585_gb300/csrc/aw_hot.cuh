@@ -52,7 +52,8 @@ __device__ __forceinline__ void weno1d(const Tables& T, const double* v, int str
         if (e != Sten<M>::SL(s)) t = fma(T.Ainv[s][p][e], d[k++], t);
       ws[p] = t;
     }
-    double sig = 0.0;
+    // sigma + eps, the quadratic form accumulated onto eps (one addition fewer)
+    double sig = 1e-14;
 #pragma unroll
     for (int i = 0; i < N - 1; i++) {
       double t = T.Bq[s][i][i] * d[i];
@@ -61,9 +62,9 @@ __device__ __forceinline__ void weno1d(const Tables& T, const double* v, int str
       sig = fma(t, d[i], sig);
     }
     // lambda_s / (sigma + eps)^8 from the reciprocal of sigma + eps (>= 1e-14)
-    double y = rcp_nr1(sig + 1e-14), y2 = y * y, y4 = y2 * y2, y8 = y4 * y4;
+    double y = rcp_nr1(sig), y2 = y * y, y4 = y2 * y2, y8 = y4 * y4;
     double om = (s < (M % 2 == 0 ? 1 : 2)) ? 1e5 * y8 : y8;
-    sum += om;
+    sum = s == 0 ? om : sum + om;
 #pragma unroll
     for (int p = 0; p < N; p++) acc[p] = fma(om, ws[p], acc[p]);
   }

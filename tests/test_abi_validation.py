@@ -91,6 +91,21 @@ def test_batch_rejects_bad_member_lists():
     assert "null solver 0" in L.aw_last_error().decode()
 
 
+def test_step_batch_and_graph_stats_reject_bad_arguments():
+    L = _lib.load()
+    st = (pg.AwStats * 1)()
+    rc = (C.c_int32 * 1)()
+    none = (C.c_void_p * 1)(None)
+    te = (C.c_double * 1)(1.0)
+    assert L.aw_step_batch(none, 1, None, 0, st, rc) == _lib.AW_EINVAL
+    assert "null end times" in L.aw_last_error().decode()
+    assert L.aw_step_batch(none, 0, te, 0, st, rc) == _lib.AW_EINVAL
+    assert L.aw_step_batch(none, 1, te, 0, st, rc) == _lib.AW_EINVAL
+    assert "null solver 0" in L.aw_last_error().decode()
+    v = C.c_int64()
+    assert L.aw_graph_stats(None, C.byref(v), None, None) == _lib.AW_EINVAL
+
+
 def test_server_rejects_bad_arguments():
     L = _lib.load()
     h = C.c_void_p()
