@@ -478,8 +478,10 @@ template <int D, int M, int PDE, int DIV = 1>
 struct PredCfg {
   static constexpr int N = M + 1, NSP = ipow(N, D), NST = NSP * N, V = nvars(D, PDE);
   // cells per CTA: 256 threads where the fluxes of all nodes (D V N^(d+1) doubles per cell) leave
-  // room for two CTAs per SM; halved where one CTA would fill the shared memory (MHD, 3D)
-  static constexpr int CPB1 = (NSP == 4) ? 64 : (NSP == 9) ? 32 : (NSP == 16 ? 16 : (NSP == 27 ? 16 : 4));
+  // room for two CTAs per SM; halved where one CTA would fill the shared memory (MHD); 3D Euler
+  // M=2: 7 cells (189 threads, 68 KB), so that three CTAs fit an SM's shared memory (8 cells,
+  // 77.8 KB, fit two)
+  static constexpr int CPB1 = (NSP == 4) ? 64 : (NSP == 9) ? 32 : (NSP == 16 ? 16 : (NSP == 27 ? 14 : 4));
   static constexpr int CPB0 = (CPB1 * D * V * NST * 8 > 113 * 1024 && CPB1 > 1) ? CPB1 / 2 : CPB1;
   static constexpr int CPB = DIV == 1 ? CPB0 : warp_fill_units(CPB0 / DIV > 0 ? CPB0 / DIV : 1, NSP);
   static constexpr int THREADS = CPB * NSP;
@@ -1255,14 +1257,7 @@ __global__ void __launch_bounds__(PredCfg<D, M, PDE>::THREADS) k_level_batch(con
       __syncthreads();   // the next item's body reuses the shared memory
     }
   };
-  if (lb.with_flux) {
-    // the fused flux's arrival counters start at zero (several barriers before they are used)
-    const long long g0 = (long long)blockIdx.x * blockDim.x + threadIdx.x, gs = (long long)gridDim.x * blockDim.x;
-    for (int m = 0; m < b.n; m++) {
-      const int nchunk = (b.a[m].na + FluxCfg<D, M, PDE>::CPB - 1) / FluxCfg<D, M, PDE>::CPB;
-      for (long long i = g0; i < nchunk; i += gs) b.a[m].fsync[i] = 0;
-    }
-  }
+  // (the fused flux's arrival counters are zero between launches: flux_update_body resets them)
   run(PH_PROJECT, [&](const HotArgs& a, int w) { project_body<D, M, PDE>(a, a.vlist, a.nv, a.qhm, 1, nullptr, 1, w); });
   grid.sync();
   run(PH_WENO4, [&](const HotArgs& a, int w) { weno_body<D, M, PDE, 4>(a, w); });
