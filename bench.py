@@ -73,13 +73,13 @@ SM_MAX_MHZ = 2070.0
 HBM_GBS = 6792.1                 # measured copy bandwidth of this GB300 pool
 # DRAM bytes per cell of the predictor from one ncu capture of a launch of the kernel's current
 # build, scaled by the cells of an average launch of the timed steps.  3D (k_predict<3,2,Euler>):
-# a level-2 launch of the same explosion on a 20^3 base (63693 CTAs x 8 cells, 2.2 GB of
-# predictor data, far above the 129 MB L2): dram__bytes_read.sum 551.31 MB +
-# dram__bytes_write.sum 1589.96 MB.  2D (k_predict<2,3,Euler>): a level-2 launch of the 100x100
+# a level-2 launch of the same explosion on a 20^3 base (72792 CTAs x 7 cells, 2.2 GB of
+# predictor data, far above the 129 MB L2): dram__bytes_read.sum 552.00 MB +
+# dram__bytes_write.sum 1590.03 MB.  2D (k_predict<2,3,Euler>): a level-2 launch of the 100x100
 # explosion (6264 CTAs x 16 cells): 51.63 MB + 140.97 MB.  Must be re-captured whenever k_predict
 # changes.
 PREDICTOR_DRAM_BYTES_PER_CELL = (51634944 + 140974592) / (6264 * 16)
-PREDICTOR_DRAM_BYTES_PER_CELL_3D = {"predictor": (551310848 + 1589964000) / (63693 * 8)}
+PREDICTOR_DRAM_BYTES_PER_CELL_3D = {"predictor": (552003328 + 1590025000) / (72792 * 7)}
 
 
 def _measured_hbm():
