@@ -610,7 +610,7 @@ struct FluxCfg {
   static constexpr int CPB = DIV == 1 ? FULL : warp_fill_units(FULL / DIV > 0 ? FULL / DIV : 1, NF);
   static constexpr int THREADS = CPB * NF;
   // CTAs per SM the register allocation must allow (at least 16 warps per SM)
-  static constexpr int MINB = THREADS <= 256 / DIV ? 3 : 2;
+  static constexpr int MINB = (THREADS <= 288 / DIV) ? 3 : 2;
   // shared memory per thread: the coarse mother's polynomial contracted along the normal (V*N per
   // thread, V*N*NF per item; fine sides of coarse/fine faces), later this thread's share of the
   // face integral (V), and the mother's values at its face point and the N time nodes (V*N)
