@@ -341,21 +341,25 @@ __global__ void __launch_bounds__(128) k_weno3_x(const __grid_constant__ HotArgs
   weno3_x_body<M, PDE>(a, blockIdx.x);
 }
 
+// y sweeps: one thread per (cell of the y list, variable), looping over the x dofs p, so that
+// the stencil's slots are looked up once for the N reconstructions
 template <int M, int PDE>
 __device__ __forceinline__ void weno3_y_body(const HotArgs& a, const int bid) {
   constexpr int D = 3, N = M + 1, V = nvars(D, PDE), W = 2 * M + 1;
   const long long it = (long long)bid * blockDim.x + threadIdx.x;
-  if (it >= (long long)a.nys * N * V) return;
-  const int ysl = (int)(it / (N * V)), rem = (int)(it % (N * V)), p = rem / V, v = rem % V;
+  if (it >= (long long)a.nys * V) return;
+  const int ysl = (int)(it / V), v = (int)(it % V);
   const LevelView& L = a.lv;
   int c[3];
   cell_ijk(L, a.ylist[ysl], c);
-  double val[W];
+  long long base[W];   // x sweeps of the stencil's cells (-1: the inflow state)
+  bool neg[W];
 #pragma unroll
   for (int e = 0; e < W; e++) {
     const int jj = c[1] - M + e;
+    neg[e] = false;
     if (beyond_inflow(L.L, a.bc, 1, jj)) {
-      val[e] = a.P.inflow[v];
+      base[e] = -1;
       continue;
     }
     int jm = jj;
@@ -365,15 +369,23 @@ __device__ __forceinline__ void weno3_y_body(const HotArgs& a, const int bid) {
       atomicOr(a.err, 4);
       slot = 0;
     }
-    double x = a.xs[((long long)slot * V + v) * N + p];
-    if (PDE == PDE_EULER && v == 2 && reflected(L.L, a.bc, 1, jj)) x = -x;
-    val[e] = x;
+    base[e] = ((long long)slot * V + v) * N;
+    neg[e] = PDE == PDE_EULER && v == 2 && reflected(L.L, a.bc, 1, jj);
   }
-  double o[N];
-  weno1d<M>(a.T, val, 1, o);
-  double* dst = a.ys + (((long long)ysl * V + v) * N + p) * N;
+#pragma unroll 1
+  for (int p = 0; p < N; p++) {
+    double val[W];
 #pragma unroll
-  for (int q = 0; q < N; q++) dst[q] = o[q];
+    for (int e = 0; e < W; e++) {
+      double x = base[e] < 0 ? a.P.inflow[v] : a.xs[base[e] + p];
+      val[e] = neg[e] ? -x : x;
+    }
+    double o[N];
+    weno1d<M>(a.T, val, 1, o);
+    double* dst = a.ys + (((long long)ysl * V + v) * N + p) * N;
+#pragma unroll
+    for (int q = 0; q < N; q++) dst[q] = o[q];
+  }
 }
 
 template <int M, int PDE>
@@ -381,22 +393,25 @@ __global__ void __launch_bounds__(128) k_weno3_y(const __grid_constant__ HotArgs
   weno3_y_body<M, PDE>(a, blockIdx.x);
 }
 
+// z sweeps: one thread per (active cell, x dof p, variable), looping over the y dofs q, so that
+// the stencil's slots are looked up once for the N reconstructions
 template <int M, int PDE>
 __device__ __forceinline__ void weno3_z_body(const HotArgs& a, const int bid) {
   constexpr int D = 3, N = M + 1, V = nvars(D, PDE), W = 2 * M + 1, NSP = N * N * N;
   const long long it = (long long)bid * blockDim.x + threadIdx.x;
-  if (it >= (long long)a.na * N * N * V) return;
-  const int k = (int)(it / (N * N * V)), rem = (int)(it % (N * N * V)), pq = rem / V, v = rem % V;
-  const int p = pq % N, q = pq / N;
+  if (it >= (long long)a.na * N * V) return;
+  const int k = (int)(it / (N * V)), rem = (int)(it % (N * V)), p = rem / V, v = rem % V;
   const LevelView& L = a.lv;
   int c[3];
   cell_ijk(L, a.alist[k], c);
-  double val[W];
+  long long base[W];   // y sweeps of the stencil's cells (-1: the inflow state)
+  bool neg[W];
 #pragma unroll
   for (int e = 0; e < W; e++) {
     const int kk = c[2] - M + e;
+    neg[e] = false;
     if (beyond_inflow(L.L, a.bc, 2, kk)) {
-      val[e] = a.P.inflow[v];
+      base[e] = -1;
       continue;
     }
     int km = kk;
@@ -406,15 +421,23 @@ __device__ __forceinline__ void weno3_z_body(const HotArgs& a, const int bid) {
       atomicOr(a.err, 4);
       slot = 0;
     }
-    double x = a.ys[(((long long)slot * V + v) * N + p) * N + q];
-    if (PDE == PDE_EULER && v == 3 && reflected(L.L, a.bc, 2, kk)) x = -x;
-    val[e] = x;
+    base[e] = (((long long)slot * V + v) * N + p) * N;
+    neg[e] = PDE == PDE_EULER && v == 3 && reflected(L.L, a.bc, 2, kk);
   }
-  double o[N];
-  weno1d<M>(a.T, val, 1, o);
   double* dst = a.wh + ((long long)k * V + v) * NSP;
+#pragma unroll 1
+  for (int q = 0; q < N; q++) {
+    double val[W];
 #pragma unroll
-  for (int r = 0; r < N; r++) dst[p + N * q + N * N * r] = o[r];
+    for (int e = 0; e < W; e++) {
+      double x = base[e] < 0 ? a.P.inflow[v] : a.ys[base[e] + q];
+      val[e] = neg[e] ? -x : x;
+    }
+    double o[N];
+    weno1d<M>(a.T, val, 1, o);
+#pragma unroll
+    for (int r = 0; r < N; r++) dst[p + N * q + N * N * r] = o[r];
+  }
 }
 
 template <int M, int PDE>

@@ -73,7 +73,7 @@ struct Launch {
     constexpr int N = M + 1;
     if constexpr (D == 3) {
       if (a.xs && a.ys) {   // three passes: x sweeps of the feeding rows, y sweeps, z sweeps
-        const long long nx = (long long)a.nxs * V, ny = (long long)a.nys * N * V, nz = (long long)a.na * N * N * V;
+        const long long nx = (long long)a.nxs * V, ny = (long long)a.nys * V, nz = (long long)a.na * N * V;
         k_weno3_x<M, PDE><<<(unsigned)((nx + 127) / 128), 128, 0, st>>>(a);
         k_weno3_y<M, PDE><<<(unsigned)((ny + 127) / 128), 128, 0, st>>>(a);
         k_weno3_z<M, PDE><<<(unsigned)((nz + 127) / 128), 128, 0, st>>>(a);
@@ -204,8 +204,8 @@ struct Launch {
       return n + pass_b(b, k_weno_y_batch<M, PDE>, [](const HotArgs& a) { return (long long)a.na * N * V; }, st);
     } else {
       int n = pass_b(b, k_weno3_x_batch<M, PDE>, [](const HotArgs& a) { return (long long)a.nxs * V; }, st);
-      n += pass_b(b, k_weno3_y_batch<M, PDE>, [](const HotArgs& a) { return (long long)a.nys * N * V; }, st);
-      return n + pass_b(b, k_weno3_z_batch<M, PDE>, [](const HotArgs& a) { return (long long)a.na * N * N * V; }, st);
+      n += pass_b(b, k_weno3_y_batch<M, PDE>, [](const HotArgs& a) { return (long long)a.nys * V; }, st);
+      return n + pass_b(b, k_weno3_z_batch<M, PDE>, [](const HotArgs& a) { return (long long)a.na * N * V; }, st);
     }
   }
   static bool has_passes(const HotArgs& a) { return a.xs && (D == 2 || a.ys); }
@@ -324,8 +324,8 @@ struct Launch {
           case PH_WENO4: w = (!passes && (D == 3 || a.ts != 8)) ? weno_ctas(a) : 0; break;
           case PH_WENO8: w = (!passes && D == 2 && a.ts == 8) ? weno_ctas(a) : 0; break;
           case PH_WENO_X: w = passes ? cdiv((long long)a.nxs * V, T) : 0; break;
-          case PH_WENO_Y: w = passes ? cdiv((D == 2 ? (long long)a.na : (long long)a.nys) * N * V, T) : 0; break;
-          case PH_WENO_Z: w = (passes && D == 3) ? cdiv((long long)a.na * N * N * V, T) : 0; break;
+          case PH_WENO_Y: w = passes ? cdiv((D == 2 ? (long long)a.na * N : (long long)a.nys) * V, T) : 0; break;
+          case PH_WENO_Z: w = (passes && D == 3) ? cdiv((long long)a.na * N * V, T) : 0; break;
           case PH_PREDICT: w = predict_ctas(a); break;
           case PH_FLUX: w = with_flux ? flux_ctas(a) : 0; break;
         }
