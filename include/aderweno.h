@@ -390,11 +390,17 @@ typedef struct aw_srv_summary {
  * budget. */
 int aw_srv_create(int64_t hbm_budget_bytes, int32_t max_concurrent, aw_server** out);
 
-/* Cross-request batching in the loop: a worker that admits the oldest queued request also admits
- * up to max_batch - 1 further queued requests (in arrival order) that agree with it in dim, pde,
- * M, flux, refine_factor and end time and fit the remaining budget, and advances the group with
- * aw_advance_batch.  1 (the default) turns batching off.  Applies to requests admitted after the
- * call.  AW_EINVAL unless 1 <= max_batch <= AW_BATCH_MAX. */
+/* Continuous cross-request batching in the loop (no counterpart in the paper): a worker that
+ * admits the oldest queued request also admits up to max_batch - 1 further queued requests (in
+ * arrival order) that agree with it in dim, pde, M, flux and refine_factor and fit the remaining
+ * budget (end times, grids and depths may differ), and advances the group one lockstep level-0
+ * step at a time with aw_step_batch.  A member leaves the group as soon as it reaches its end time
+ * or fails: its results are kept and its solver and reservation released.  Between steps the
+ * worker admits further such requests into the running group, up to max_batch members, when
+ * their reservations fit the budget beside the running requests and the oldest queued request.
+ * Every member computes exactly what it computes alone.  1 (the default) turns batching off.
+ * Applies to requests admitted after the call.  AW_EINVAL unless 1 <= max_batch <=
+ * AW_BATCH_MAX. */
 int aw_srv_set_batching(aw_server* srv, int32_t max_batch);
 /* Queue one solve (configuration copied; params copied).  AW_EINVAL if its footprint exceeds
  * the whole budget. */

@@ -275,6 +275,8 @@ def step_batch(solvers, t_ends, stream: int = 0):
     """aw_step_batch: one lockstep level-0 step of every solver not yet at its own end time, the
     hot kernels batched.  Returns (stats, rc) per solver; raises AwError with the first failure."""
     n = len(solvers)
+    if len(t_ends) != n:
+        raise ValueError("one end time per solver")
     arr = (C.c_void_p * n)(*[s.h.value for s in solvers])
     te = (C.c_double * n)(*[float(t) for t in t_ends])
     st = (AwStats * n)()
@@ -287,8 +289,9 @@ def step_batch(solvers, t_ends, stream: int = 0):
 
 class Server:
     """Request loop of independent solves (aw_srv_*): continuous admission under a device-memory
-    budget, concurrent requests on their own streams; with max_batch > 1, compatible queued
-    requests are advanced together with batched launches (aw_srv_set_batching)."""
+    budget, concurrent requests on their own streams, reservations that grow in place; with
+    max_batch > 1, continuous batching: compatible requests share batched launches, leave their
+    group when they finish and join a running group between steps (aw_srv_set_batching)."""
 
     def __init__(self, hbm_budget_bytes: int, max_concurrent: int = 4, max_batch: int = 1):
         self.L = _lib.load()

@@ -13,9 +13,10 @@
 // own, so its result does not depend on what else is running.
 //
 // With batching on (aw_srv_set_batching), a worker that admits the oldest request also admits
-// queued requests of the same kernel configuration and end time (up to the batch size, in arrival
-// order, while the budget allows) and advances them together with aw_advance_batch: one launch
-// per hot kernel, level and sub-step for the whole group.
+// queued requests of the same kernel configuration (up to the batch size, in arrival order, while
+// the budget allows) and advances the group in lockstep level-0 steps with aw_step_batch: one
+// launch per hot kernel, level and sub-step for the whole group.  Members leave the group when
+// they finish and compatible requests join it between steps (run_continuous).
 #include <algorithm>
 #include <chrono>
 #include <cmath>
