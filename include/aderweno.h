@@ -199,12 +199,12 @@ int aw_advance_graph(aw_solver* s, double t_end, int32_t chunk, aw_stats* stats)
 /* Launch shapes (no counterpart in the paper; they change the speed, never a result):
  * WENO by passes (x, then y, then z sweeps over compact lists) on levels of at least
  * pass_min_cells cells (default 4096; tiles below), 2D WENO tiles of 8x8 cells on levels of at
- * least tile8_min_cells cells (default 20000; 4x4 below), and quarter-size predictor and flux
+ * least tile8_min_cells cells (default 20000; 4x4 below), and reduced-size predictor and flux
  * CTAs when the full-size ones would give fewer than small_ctas_per_sm CTAs per SM (default 2;
  * 0 never), fuse_flux_update: 1 (default) runs the face fluxes and the update of Eq.
  * eq:finite_vol as one kernel (the face CTA that delivers the last face flux a chunk of cells
  * needs updates that chunk; nothing waits), 0 as two kernels; and autotune: 1 (default) lets the
- * library's autotuner pick the CTA size (cells, or faces, per block: full or quarter size) of the
+ * library's autotuner pick the CTA size (cells, or faces, per block: full or reduced size) of the
  * predictor and of the face flux per configuration and level size class, from CUDA-event timings
  * of the first launches of each (aw_get_tuning), in place of the small_ctas_per_sm rule; 0 the
  * rule alone; and persistent: 1 advances every level and sub-step of a batch (aw_advance_batch)
@@ -242,11 +242,12 @@ int aw_set_launch_params(const aw_launch_params* in);
 /* The autotuner's state (no counterpart in the paper).  For every configuration (dim, M, pde,
  * numerical flux), kernel (AW_TUNE_PREDICTOR, AW_TUNE_FLUX) and level size class (floor(log2) of
  * the level's active cells) that solvers of this process have launched, the first launches try
- * the full-size (variant 0) and quarter-size (variant 1) CTAs in turn, each timed with a pair of
- * CUDA events on the solver's stream; once each variant has AW_TUNE_TRIALS timings, the one with
+ * the full-size (variant 0) and reduced-size (variant 1: about a quarter, filling whole warps) CTAs
+ * in turn, each timed with a pair of CUDA events on the solver's stream; once each variant has
+ * AW_TUNE_TRIALS timings, the one with
  * the least device time per active cell (the least over its timings) is used for every later
  * launch of that class, by every solver.  A new class larger than a class that kept full-size
- * CTAs, or smaller than one that kept quarter-size CTAs, takes that decision without trials
+ * CTAs, or smaller than one that kept reduced-size CTAs, takes that decision without trials
  * (inherited = 1).  Single-solver steps only (also when replayed from graphs, graph_steps): the
  * batched path and aw_advance_graph use the rules.  aw_get_tuning copies up to `cap` entries (in
  * key order) into `out` and sets *n to the number of entries; aw_reset_tuning forgets them all.

@@ -607,7 +607,7 @@ struct HotArgs {
   // before each launch
   int* fsync;
   // CTA size of the predictor and face-flux launches: 0 the launch rules, 1 full-size, 4
-  // quarter-size (the autotuner's choice; the results are the same either way)
+  // reduced size (the autotuner's choice; the results are the same either way)
   int cta_div;
 };
 

@@ -29,8 +29,8 @@ struct Launch {
   static int weno_tile(long long n) { return (D == 2 && n >= launch_params().tile8_min_cells) ? 8 : 4; }
   using CP = PredCfg<D, M, PDE>;
   using CF = FluxCfg<D, M, PDE>;
-  // a quarter of the cells (face items) per CTA when the full-size CTAs would give fewer than two
-  // CTAs per SM; every cell and face computes exactly the same either way
+  // about a quarter of the cells (face items) per CTA, filling whole warps, when the full-size CTAs
+  // would give fewer than two CTAs per SM; every cell and face computes exactly the same either way
   static constexpr int SMALL = 4;
   using CPs = PredCfg<D, M, PDE, SMALL>;
   using CFs = FluxCfg<D, M, PDE, SMALL>;
@@ -51,7 +51,7 @@ struct Launch {
   static int update_ctas(const HotArgs& a) { return a.na > 0 ? (a.na + 127) / 128 : 0; }
   static int project_ctas(int nv) { return nv > 0 ? (int)(((long long)nv * V + 127) / 128) : 0; }
   static bool small(int ctas) { return ctas < launch_params().small_ctas_per_sm * sm_count(); }
-  // quarter-size CTAs: the autotuner's choice for this launch, else the rule above
+  // reduced-size CTAs: the autotuner's choice for this launch, else the rule above
   static bool use_small(const HotArgs& a, int ctas) { return a.cta_div == 4 || (a.cta_div != 1 && small(ctas)); }
 
   // the dynamic shared memory attribute, once per kernel (request-loop workers launch concurrently)

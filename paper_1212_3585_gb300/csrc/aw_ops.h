@@ -43,7 +43,7 @@ struct HotOps {
 bool get_ops(int D, int M, int PDE, HotOps* out);
 
 // launch-shape rules (aw_set_launch_params): WENO by passes from pass_min_cells cells per level,
-// 2D WENO tiles of 8x8 from tile8_min_cells, quarter-size predictor/flux CTAs when the full-size
+// 2D WENO tiles of 8x8 from tile8_min_cells, reduced-size predictor/flux CTAs when the full-size
 // ones give fewer than small_ctas_per_sm CTAs per SM, the face flux and the update fused into one
 // launch (fuse_flux_update != 0) or two, the autotuner of the predictor's and the face flux's CTA
 // sizes (autotune != 0; it replaces the small_ctas_per_sm rule where it has decided), the

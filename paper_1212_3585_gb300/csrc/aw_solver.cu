@@ -286,13 +286,14 @@ static int timed(aw_solver* s, int kind, F&& launch) {
 }
 
 // ---- autotuner of the CTA sizes of the predictor and the face flux (aw_get_tuning) ----
-// Both kernels have a full-size and a quarter-size CTA variant that compute bitwise the same
-// results.  Per (dim, M, pde, numerical flux, kernel, level size class) the first launches
+// Both kernels have a full-size and a reduced-size CTA variant (about a quarter of the cells or
+// faces, as many as fill whole warps) that compute bitwise the same results.  Per (dim, M, pde,
+// numerical flux, kernel, level size class) the first launches
 // alternate the two, each timed with an event pair on the solver's stream; once each has
 // AW_TUNE_TRIALS timings, the variant with the least device time per active cell (the least over
 // its timings, which leaves out a first launch's one-off costs) is used for that class by every
 // solver of the process.  A class larger than one that kept full-size CTAs keeps them too, and a
-// class smaller than one that kept quarter-size CTAs keeps those, without trials (more cells give
+// class smaller than one that kept reduced-size CTAs keeps those, without trials (more cells give
 // more CTAs, which only favours the larger CTAs): so trials run only between the two.
 struct TuneState {
   int issued[2] = {0, 0}, trials[2] = {0, 0};
@@ -332,7 +333,7 @@ static int tune_pick(const aw_solver* s, int kernel, long long na, int* key) {
   if (t.choice >= 0) return t.choice;
   if (t.issued[0] + t.issued[1] == 0) {
     // a new class: decided by a smaller class that kept full-size CTAs or a larger one that kept
-    // quarter-size CTAs
+    // reduced-size CTAs
     for (const auto& kv : g_tune) {
       const auto& k2 = kv.first;
       if (std::get<0>(k2) != key[0] || std::get<1>(k2) != key[1] || std::get<2>(k2) != key[2] ||
