@@ -90,15 +90,17 @@ def amr_cases():
 @pytest.mark.parametrize("prof", [0, 1])
 def test_amr_steps_replayed_from_graphs(k, prof):
     """graph_steps = 1: every level-0 step of an AMR solve (all levels and sub-steps with local
-    time stepping, the autotuner's timed trials, the per-kernel timing events when profiling, and
-    the regrid between steps) runs from a captured graph.  The solve is bitwise the one launched
-    kernel by kernel, and steps after the first update the executable graph in place."""
+    time stepping, the regrid between steps) runs from a captured graph.  The solve is bitwise the
+    one launched kernel by kernel.  Without timing events (tuner off, no profiling) the steps after
+    the first update the executable graph in place or relaunch it; with profiling and the
+    autotuner's timed trials, their events are captured as event-record nodes that record when
+    the graph runs, and such graphs are never relaunched unchanged."""
     cfg, ic, params, t_end = amr_cases()[k]
     out = {}
     saved = pg.get_launch_params()
     try:
         for g in (1, 0):
-            pg.set_launch_params(graph_steps=g)
+            pg.set_launch_params(graph_steps=g, autotune=prof)
             s = pg.Solver(cfg)
             s.set_profiling(bool(prof))
             s.set_initial(ic, params, -1)
@@ -113,7 +115,9 @@ def test_amr_steps_replayed_from_graphs(k, prof):
     assert np.array_equal(m1, m0), "meshes differ"
     assert np.array_equal(u1, u0), f"averages differ by {np.max(np.abs(u1 - u0)):.3e}"
     assert stats0 == (0, 0, 0)
-    assert reuse + upd + inst == n1 and inst >= 1 and reuse + upd >= 1, (reuse, upd, inst, n1)
+    assert reuse + upd + inst == n1 and inst >= 1, (reuse, upd, inst, n1)
+    if not prof:
+        assert reuse + upd >= 1, (reuse, upd, inst, n1)
     if prof:
         assert reuse == 0                    # a graph with timing events is captured anew each step
         # the timing events of the captured launches record when the graph runs

@@ -219,6 +219,8 @@ def test_continuous_batching_members_leave_and_join():
             (rp_config(24, 2, 1), aw_inputs.rp4_params(502), 0.12),
             (rp_config(32, 2, 1), aw_inputs.rp4_params(503), 0.25)]
     late = (rp_config(20, 2, 1), aw_inputs.rp4_params(504), 0.05)
+    # the solo solves first (they also load every kernel the loop will launch)
+    ref = [solo(c, pg.AW_IC_RP4, p, te) for c, p, te in reqs + [late]]
     srv = pg.Server(hbm_budget_bytes=8 << 30, max_concurrent=1, max_batch=4)
     t0 = time.monotonic()
     ids = [srv.submit(c, pg.AW_IC_RP4, p, te) for c, p, te in reqs]
@@ -229,9 +231,8 @@ def test_continuous_batching_members_leave_and_join():
     st = srv.stats()
     assert st.done == 4 and st.failed == 0
     infos = []
-    for rid, (c, p, te) in zip(ids + [lid], reqs + [late]):
+    for rid, (m0, u0) in zip(ids + [lid], ref):
         m, u, info = srv.result(rid, 4)
-        m0, u0 = solo(c, pg.AW_IC_RP4, p, te)
         assert np.array_equal(m, m0) and np.array_equal(u, u0)
         infos.append(info)
     done = [i.total_ms for i in infos[:3]]          # the first three were submitted together
