@@ -1000,9 +1000,8 @@ __global__ void __launch_bounds__(FluxCfg<D, M, PDE, DIV>::THREADS, FluxCfg<D, M
 
 // Eq. eq:finite_vol (source zero) for active cell `cell`: u -= dt/dx_d (F_high - F_low) per axis.
 // The high face of every axis is in the cell's own high slot (the flux kernel copies a +d
-// neighbour's low face there), so the cell reads only its 2*D contiguous slots.  L2: read the
-// fluxes through L2 only (other CTAs of the same kernel wrote them).
-template <int D, int M, int PDE, bool L2>
+// neighbour's low face there), so the cell reads only its 2*D contiguous slots.
+template <int D, int M, int PDE>
 __device__ __forceinline__ void update_cell(const HotArgs& a, int cell, double dt) {
   constexpr int V = nvars(D, PDE);
   const LevelView& L = a.lv;
@@ -1017,7 +1016,7 @@ __device__ __forceinline__ void update_cell(const HotArgs& a, int cell, double d
 #pragma unroll
     for (int v = 0; v < V; v++) {
       const double* lo = fc + 2 * d * V + v;
-      const double fhi = L2 ? __ldcg(lo + V) : lo[V], flo = L2 ? __ldcg(lo) : lo[0];
+      const double fhi = lo[V], flo = lo[0];
       u[v] -= c * (fhi - flo);
     }
   }
@@ -1125,7 +1124,7 @@ __device__ __forceinline__ void update_body(const HotArgs& a, const int bid) {
   if (cell >= a.na) return;
   const double dt = a.dtl[a.level];
   if (dt == 0.0) return;   // a step of length zero leaves the averages as they are
-  update_cell<D, M, PDE, false>(a, cell, dt);
+  update_cell<D, M, PDE>(a, cell, dt);
 }
 
 template <int D, int M, int PDE>
