@@ -104,6 +104,8 @@ def test_step_batch_and_graph_stats_reject_bad_arguments():
     assert "null solver 0" in L.aw_last_error().decode()
     v = C.c_int64()
     assert L.aw_graph_stats(None, C.byref(v), None, None) == _lib.AW_EINVAL
+    with pytest.raises(ValueError):
+        pg.step_batch([], [1.0])
 
 
 def test_server_rejects_bad_arguments():
